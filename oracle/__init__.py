@@ -1,0 +1,265 @@
+"""FP64 CPU oracle for the Monte-Carlo ELBO step (arXiv 2501.09308).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path (``paper_2501_09308_gb300``) and neither imports the other;
+the only shared module is the seeded input generator
+``paper_2501_09308_gb300.synth``, which holds no inference arithmetic.
+
+``xrdvi_oracle.c`` holds the model, likelihood, priors, Monte-Carlo ELBO,
+analytic gradient, Adam and the fit loop in plain double-precision loops;
+``posterior.py`` holds the posterior over phase combinations.  Every function
+cites the passage of the paper it follows.
+
+Parity pins: see ``tests/test_oracle_*.py``.  Unpinned parts are listed in
+``posterior.py``'s header ("parity unpinned").
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xrdvi_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Prior hyper-parameters (Appendix B.2): mu ~ Norm(0, 0.03), alpha ~ Norm(1, 0.2),
+# r ~ Uni(0, 1), w ~ Gam(3, 100) read with 100 as a rate (mean 0.03 deg).
+PRIOR_MU_SD = 0.03
+PRIOR_ALPHA_MEAN = 1.0
+PRIOR_ALPHA_SD = 0.2
+PRIOR_W_SHAPE = 3.0
+PRIOR_W_RATE = 100.0
+ALPHA_MIN = 1e-3
+
+
+class Prior(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("mu_sd", ctypes.c_double),
+                ("alpha_mean", ctypes.c_double), ("alpha_sd", ctypes.c_double),
+                ("w_shape", ctypes.c_double), ("w_rate", ctypes.c_double),
+                ("alpha_min", ctypes.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (no fast-math, no FMA
+    contraction, so x86 and Arm builds round alike)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P = ctypes.POINTER
+            d, i32, u32, u64 = ctypes.c_double, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+            pd, pi = P(d), P(i32)
+            L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+            L.orc_normals.argtypes = [u64, u32, u32, i32, i32, pd]
+            L.orc_softplus.restype = d
+            L.orc_softplus.argtypes = [d]
+            L.orc_sigmoid.restype = d
+            L.orc_sigmoid.argtypes = [d]
+            L.orc_theta.argtypes = [i32, i32, pd, pd, pd, pd, pd]
+            L.orc_components.argtypes = [d, d, d, pd, pd]
+            L.orc_pvoigt.restype = d
+            L.orc_pvoigt.argtypes = [d, d, d, d]
+            L.orc_profile.argtypes = [i32, pi, pd, pd, i32, pd, pd, i32, pd, d, pd]
+            L.orc_loglik_direct.restype = d
+            L.orc_loglik_direct.argtypes = [i32, pd, pd]
+            L.orc_loglik_deviance.restype = d
+            L.orc_loglik_deviance.argtypes = [i32, pd, pd, pd]
+            L.orc_log_prior.restype = d
+            L.orc_log_prior.argtypes = [P(Prior), pd]
+            L.orc_log_jac.restype = d
+            L.orc_log_jac.argtypes = [pd]
+            L.orc_entropy.restype = d
+            L.orc_entropy.argtypes = [i32, pd]
+            L.orc_elbo_grad.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32,
+                                        pd, pd, pd, pd, pd, pd, pd, pd]
+            L.orc_adam_step.argtypes = [i32, pd, pd, pd, pd, i32, d, d, d, d]
+            L.orc_fit.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, u64, i32, i32,
+                                  d, d, d, d, pd, pd, pd, pd, pd]
+            L.orc_max_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _pi(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Problem:
+    """Double-precision copy of one instance (peak table + pattern + priors)."""
+
+    def __init__(self, offsets, pos, inten, x, y, bg, *, lam=None,
+                 mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
+                 w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN):
+        self.off = np.ascontiguousarray(offsets, dtype=np.int32)
+        self.pos, self.inten = f64(pos), f64(inten)
+        self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
+        self.K, self.N = len(self.off) - 1, len(self.x)
+        if lam is None:
+            # lambda = 1 / eta with eta = max(Y - B)  (Sec. 2.2)
+            lam = 1.0 / float(np.max(self.y - self.bg))
+        self.prior = Prior(lam, mu_sd, alpha_mean, alpha_sd, w_shape, w_rate, alpha_min)
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        return cls(inst.offsets, inst.pos, inst.inten, inst.x, inst.y, inst.bg, **kw)
+
+    @property
+    def eta(self):
+        return 1.0 / self.prior.lambda_
+
+    def _args(self):
+        return (self.K, _pi(self.off), _pd(self.pos), _pd(self.inten), self.N,
+                _pd(self.x), _pd(self.y), _pd(self.bg))
+
+    # ---- model -----------------------------------------------------------
+    def profile(self, theta):
+        """f[S, N] for physical parameters theta[S, K, 5]."""
+        theta = f64(theta)
+        S = theta.shape[0]
+        f = np.zeros((S, self.N))
+        lib().orc_profile(self.K, _pi(self.off), _pd(self.pos), _pd(self.inten), self.N,
+                          _pd(self.x), _pd(self.bg), S, _pd(theta), self.prior.alpha_min, _pd(f))
+        return f
+
+    def loglik(self, f, form="direct"):
+        f = f64(f)
+        if form == "direct":
+            return lib().orc_loglik_direct(self.N, _pd(self.y), _pd(f))
+        return lib().orc_loglik_deviance(self.N, _pd(self.y), _pd(f), None)
+
+    def data_constant(self):
+        """sum_i [y ln y - y - ln y!] (the data part of the deviance split)."""
+        c = ctypes.c_double(0.0)
+        lib().orc_loglik_deviance(self.N, _pd(self.y), _pd(self.bg), ctypes.byref(c))
+        return c.value
+
+    def theta(self, loc, raw, eps):
+        eps = f64(eps)
+        S = eps.shape[0]
+        u = np.zeros((S, self.K, 5))
+        th = np.zeros((S, self.K, 5))
+        lib().orc_theta(S, self.K, _pd(f64(loc)), _pd(f64(raw)), _pd(eps), _pd(u), _pd(th))
+        return u, th
+
+    def log_prior(self, th_k):
+        return lib().orc_log_prior(ctypes.byref(self.prior), _pd(f64(th_k)))
+
+    def elbo_grad(self, loc, raw, eps, want_f=False):
+        """ELBO estimate + per-sample LL, log prior+Jacobian and the gradient
+        [K, 10] (loc grads then raw grads) for injected noise eps[S, K, 5]."""
+        eps = f64(eps)
+        S = eps.shape[0]
+        elbo = ctypes.c_double(0.0)
+        ll = np.zeros(S)
+        lpj = np.zeros(S)
+        grad = np.zeros((self.K, 10))
+        f = np.zeros((S, self.N)) if want_f else None
+        lib().orc_elbo_grad(*self._args(), ctypes.byref(self.prior), S, _pd(f64(loc)),
+                            _pd(f64(raw)), _pd(eps), ctypes.byref(elbo), _pd(ll), _pd(lpj),
+                            _pd(grad), _pd(f) if want_f else None)
+        out = {"elbo": elbo.value, "ll": ll, "lpj": lpj, "grad": grad}
+        if want_f:
+            out["f"] = f
+        return out
+
+    def init_params(self, h_frac=0.1, sigma0=0.1):
+        """Initial variational state.  Reading: loc at h = h_frac * eta, mu = 0,
+        w = prior mean shape/rate, r = 1/2, alpha = prior mean; every sigma = sigma0."""
+        loc = np.zeros((self.K, 5))
+        loc[:, 0] = math.log(h_frac * self.eta)
+        loc[:, 1] = 0.0
+        loc[:, 2] = math.log(self.prior.w_shape / self.prior.w_rate)
+        loc[:, 3] = 0.0
+        loc[:, 4] = self.prior.alpha_mean
+        raw = np.full((self.K, 5), math.log(math.expm1(sigma0)))
+        return loc, raw
+
+    def fit(self, S, iters, seed, loc=None, raw=None, m=None, v=None, t0=0,
+            lr=0.01, b1=0.9, b2=0.999, adam_eps=1e-8):
+        if loc is None:
+            loc, raw = self.init_params()
+        loc, raw = f64(loc).copy(), f64(raw).copy()
+        m = np.zeros((self.K, 10)) if m is None else f64(m).copy()
+        v = np.zeros((self.K, 10)) if v is None else f64(v).copy()
+        trace = np.zeros(iters)
+        lib().orc_fit(*self._args(), ctypes.byref(self.prior), S, seed, t0, iters,
+                      lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
+        return {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
+
+
+def philox(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def normals(seed, tag, it, S, K):
+    eps = np.zeros((S, K, 5))
+    lib().orc_normals(seed, tag, it, S, K, _pd(eps))
+    return eps
+
+
+def softplus(x):
+    return lib().orc_softplus(float(x))
+
+
+def sigmoid(x):
+    return lib().orc_sigmoid(float(x))
+
+
+def components(d, w, alpha_c):
+    G, L = ctypes.c_double(), ctypes.c_double()
+    lib().orc_components(float(d), float(w), float(alpha_c), ctypes.byref(G), ctypes.byref(L))
+    return G.value, L.value
+
+
+def pvoigt(d, w, r, alpha_c):
+    return lib().orc_pvoigt(float(d), float(w), float(r), float(alpha_c))
+
+
+def entropy(raw):
+    raw = f64(raw)
+    return lib().orc_entropy(raw.shape[0], _pd(raw))
+
+
+def adam_step(params, grad, m, v, t, lr=0.01, b1=0.9, b2=0.999, eps=1e-8):
+    params, m, v = f64(params).copy(), f64(m).copy(), f64(v).copy()
+    lib().orc_adam_step(params.size, _pd(params), _pd(f64(grad)), _pd(m), _pd(v), t, lr, b1, b2, eps)
+    return params, m, v
+
+
+def max_threads():
+    return lib().orc_max_threads()

@@ -1,0 +1,177 @@
+"""Pins of the oracle's Monte-Carlo ELBO, gradient, optimiser and noise stream
+(no GPU)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+import oracle
+from oracle import posterior as post
+from paper_2501_09308_gb300 import synth
+
+
+def _fd_grad(P, loc, raw, eps, h=1e-6):
+    num = np.zeros((P.K, 10))
+    for k in range(P.K):
+        for j in range(5):
+            for which in (0, 1):
+                L, R = loc.copy(), raw.copy()
+                A = L if which == 0 else R
+                A[k, j] += h
+                ep = P.elbo_grad(L, R, eps)["elbo"]
+                A[k, j] -= 2 * h
+                em = P.elbo_grad(L, R, eps)["elbo"]
+                num[k, j + 5 * which] = (ep - em) / (2 * h)
+    return num
+
+
+def test_gradient_against_central_differences():
+    """Analytic reparameterisation gradient vs FP64 central differences (h=1e-6)
+    on the K=6, N=600 sub-instance with fixed noise; every block (loc and raw
+    of h, mu, w, r, alpha) within 1e-5 of its max-norm."""
+    inst = synth.config(2)
+    P = oracle.Problem.from_instance(inst)
+    loc, raw = P.init_params()
+    rng = np.random.default_rng(0)
+    loc = loc + rng.normal(0, 0.05, loc.shape)
+    raw = raw + rng.normal(0, 0.1, raw.shape)
+    eps = synth.normals(5, 2, P.K).astype(np.float64)
+    g = P.elbo_grad(loc, raw, eps)["grad"]
+    num = _fd_grad(P, loc, raw, eps)
+    rel = np.max(np.abs(num - g), axis=0) / np.max(np.abs(g), axis=0)
+    assert np.all(rel < 1e-5), rel
+
+
+def test_gradient_with_alpha_clamped_is_zero_in_alpha_likelihood():
+    """Below the clamp the profile no longer depends on alpha: only the prior
+    gradient -(alpha - 1)/0.2^2 remains for the alpha component."""
+    P = oracle.Problem.from_instance(synth.small_problem(K=2, N=200))
+    loc, raw = P.init_params()
+    loc[:, 4] = -0.5
+    raw[:, 4] = -60.0  # sigma ~ 0: alpha = -0.5 exactly, below the clamp
+    eps = np.zeros((1, P.K, 5))
+    g = P.elbo_grad(loc, raw, eps)["grad"]
+    np.testing.assert_allclose(g[:, 4], -(-0.5 - 1.0) / 0.2 ** 2, rtol=1e-12)
+
+
+def _conjugate_setup():
+    """K = 1, Lorentzian (r -> 1), mu, w, alpha held fixed (sigma ~ 0), B = 0:
+    the intensity h has an Exp(lambda) prior and a Poisson likelihood with mean
+    h C_i, so p(Y) has a closed form (gamma-Poisson conjugacy)."""
+    rng = np.random.default_rng(11)
+    x = np.linspace(30, 40, 301)
+    pos, inten = np.array([32.0, 35.2, 38.7]), np.array([1.0, 0.45, 0.7])
+    mu0, w0, a0 = 0.01, 0.08, 1.1
+    C = np.zeros_like(x)
+    for p, I in zip(pos, inten):
+        d = x - (p + mu0)
+        side = np.where(d >= 0, a0 * w0, w0)
+        C += I * stats.cauchy.pdf(d, scale=side / 2) / stats.cauchy.pdf(0, scale=side / 2)
+    y = rng.poisson(2500.0 * C).astype(np.float64)
+    P = oracle.Problem([0, 3], pos, inten, x, y, np.zeros_like(x))
+    lam = P.prior.lambda_
+    sy, sC = y.sum(), C.sum()
+    lnZ = (np.sum(special.xlogy(y, C)) - np.sum(special.gammaln(y + 1)) + math.log(lam)
+           + special.gammaln(1 + sy) - (1 + sy) * math.log(lam + sC))
+    a, b = 1 + sy, lam + sC
+    loc = np.array([[math.log(a / b), mu0, math.log(w0), 40.0, a0]])
+    raw = np.array([[math.log(math.expm1(1 / math.sqrt(a))), -60.0, -60.0, -60.0, -60.0]])
+    sig0 = float(np.logaddexp(0.0, -60.0))
+    # fixed parameters' deterministic contribution to ELBO: log prior + log Jacobian + entropy
+    fixed_lpj = (stats.norm.logpdf(mu0, 0, 0.03) + stats.norm.logpdf(a0, 1.0, 0.2)
+                 + stats.gamma.logpdf(w0, 3.0, scale=0.01) + math.log(w0)
+                 - np.logaddexp(0.0, -40.0) - np.logaddexp(0.0, 40.0))
+    fixed_H = 4 * (math.log(sig0) + 0.5 * (1 + math.log(2 * math.pi)))
+    return P, loc, raw, lnZ, fixed_lpj, fixed_H, sig0
+
+
+def test_elbo_is_a_tight_lower_bound_in_the_conjugate_case():
+    """Sec. 3.2: ln p(Y) = L[q] + KL >= L[q].  With q at the (log-normal)
+    approximation of the exact gamma posterior, the ELBO sits just below the
+    closed-form evidence; a shifted q sits well below it."""
+    P, loc, raw, lnZ, fixed_lpj, fixed_H, _ = _conjugate_setup()
+    # stratified standard-normal quantiles, rescaled to unit second moment, so
+    # the Monte-Carlo mean carries no sampling noise at the order tested
+    S = 4000
+    z = stats.norm.ppf((np.arange(S) + 0.5) / S)
+    z /= math.sqrt(np.mean(z * z))
+    eps = np.zeros((S, 1, 5))
+    eps[:, 0, 0] = z
+    e = P.elbo_grad(loc, raw, eps)["elbo"] - fixed_lpj - fixed_H
+    assert e <= lnZ + 1e-4
+    assert lnZ - e < 1e-3
+    loc2 = loc.copy()
+    loc2[0, 0] += 3.0 / math.sqrt(P.y.sum())
+    e2 = P.elbo_grad(loc2, raw, eps)["elbo"] - fixed_lpj - fixed_H
+    assert lnZ - e2 > 3.0
+
+
+def test_importance_sampled_evidence_in_the_conjugate_case():
+    P, loc, raw, lnZ, fixed_lpj, _, sig0 = _conjugate_setup()
+    rng = np.random.default_rng(6)
+    S = 256
+    eps = np.zeros((S, 1, 5))
+    eps[:, 0, 0] = rng.standard_normal(S)
+    res = post.posterior(P, loc, raw, S, eps=eps, top_m=1)
+    lq_fixed = 4 * (-math.log(sig0) - 0.5 * math.log(2 * math.pi))
+    est = res["log_evidence"] - fixed_lpj + lq_fixed
+    assert est == pytest.approx(lnZ, abs=1e-3)
+    assert res["ess"] > 0.9 * S
+
+
+def test_adam_step_matches_torch():
+    """One Adam step on -ELBO equals torch.optim.Adam (library routine)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2)
+    p0 = rng.normal(size=40)
+    m = np.zeros(40)
+    v = np.zeros(40)
+    tp = torch.tensor(p0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=0.01, betas=(0.9, 0.999), eps=1e-8)
+    p = p0.copy()
+    for t in range(1, 6):
+        g = rng.normal(size=40) * 10 ** rng.uniform(-3, 3, size=40)
+        p, m, v = oracle.adam_step(p, g, m, v, t)
+        tp.grad = torch.tensor(-g)
+        opt.step()
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_philox_noise_is_standard_normal_and_counter_keyed():
+    """Box-Muller normals from the Philox stream: KS test against N(0,1), per-bit
+    balance of the raw words, and distinct streams per (s, k, step, tag)."""
+    z = oracle.normals(123, 0, 0, 4000, 5).ravel()
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
+    words = np.array([oracle.philox([i, 7, 3, 0], [99, 1]) for i in range(2000)], dtype=np.uint64).ravel()
+    bits = (words[:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)
+    frac = bits.mean(axis=0)
+    assert np.all(np.abs(frac - 0.5) < 5 * 0.5 / math.sqrt(words.size))
+    a = oracle.normals(123, 0, 0, 3, 4)
+    b = oracle.normals(123, 0, 1, 3, 4)
+    c = oracle.normals(123, 1, 0, 3, 4)
+    d = oracle.normals(124, 0, 0, 3, 4)
+    for other in (b, c, d):
+        assert not np.any(np.isclose(a, other))
+    assert len(np.unique(a.ravel())) == a.size
+    np.testing.assert_array_equal(a, oracle.normals(123, 0, 0, 3, 4))
+
+
+def test_elbo_components_add_up():
+    """ELBO = mean_s [LL_s + ln p(theta_s) + ln|J_s|] + H(q); LL_s from the
+    profile and the library Poisson log-pmf."""
+    inst = synth.small_problem(K=3, N=250, S=3)
+    P = oracle.Problem.from_instance(inst)
+    loc, raw = P.init_params()
+    eps = synth.normals(1, 3, P.K).astype(np.float64)
+    r = P.elbo_grad(loc, raw, eps, want_f=True)
+    u, th = P.theta(loc, raw, eps)
+    f = P.profile(th)
+    np.testing.assert_allclose(r["f"], f, rtol=1e-14)
+    for s in range(3):
+        assert r["ll"][s] == pytest.approx(stats.poisson.logpmf(P.y, f[s]).sum(), rel=1e-11)
+    sig = np.logaddexp(0.0, raw)
+    H = np.sum(stats.norm(scale=sig).entropy())
+    assert r["elbo"] == pytest.approx(np.mean(r["ll"] + r["lpj"]) + H, rel=1e-14)
