@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the Monte-Carlo ELBO step (variational sparse phase search).
+
+Workload: the K=50 single fit — 50 candidate phases with 5-80 peaks each,
+N=4500 2-theta points (10-100 deg, 0.02 deg step), S=256 Monte-Carlo samples,
+2000 SVI steps, seeded synthetic diffractogram with 4 planted phases.
+
+One bench step = one complete fit on the resident problem: 2000 SVI steps
+(sample -> profile/likelihood -> backward -> Adam -> ELBO) followed by the
+posterior over phase combinations (4096 posterior draws).  The headline value
+is ELBO evaluations per second, counted densely as S * sum_k M_k * N per SVI
+step (every step evaluates the profile and its gradient at every
+(sample, peak, point) triple), and the step time is the time-to-posterior.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank fits its own replica (no data-path
+collective; weak scaling), and the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ELBO evals/s (S·K·peaks·N) + time-to-posterior K=50; served p50/p99 latency"
+S_POST = 4096
+TOP_M = 16
+PROFILE_STEPS = 64          # of the 2000 SVI steps, launched kernel by kernel between events
+CPU_SAMPLE_S = 128          # oracle cpu-baseline sample: one ELBO+gradient at 128 of 256 samples
+REF_SAMPLE_S = 32           # reference-arm step: one oracle ELBO+gradient at 32 samples
+# algorithmic instructions per dense evaluation (tail form, one MUFU each):
+#   forward : d = (x - p) - mu (2), c(d) d (2), u (1), 1 + u (1), rcp (1 MUFU), accumulate (1)   = 8
+#   backward: d (2), c(d) d (2), u (1), |d| c(d) d (1), 1 + u (1), rcp (1 MUFU), g I (1), q L (1),
+#             accumulate (1), q L^2 (1), three FMA accumulations (3)                              = 15
+INSTR_PER_EVAL = {"forward": 8, "backward": 15}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=None, help="SVI steps per fit (default: workload's 2000)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen([exe, "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def l2_flush(buf):
+    buf.add_(1.0)  # writes a buffer larger than L2 (129 MB) between timed steps
+
+
+def cpu_baseline(inst, S_sample, world_rank):
+    """The FP64 oracle as it stands, on this host's cores: one ELBO+gradient
+    evaluation of the same workload at S_sample Monte-Carlo samples."""
+    import numpy as np
+    import oracle
+    from paper_2501_09308_gb300 import synth
+    P = oracle.Problem.from_instance(inst)
+    loc, raw = P.init_params()
+    eps = synth.normals(4242, S_sample, P.K).astype(np.float64)
+    t0 = time.perf_counter()
+    P.elbo_grad(loc, raw, eps)
+    dt = time.perf_counter() - t0
+    evals = S_sample * int(inst.offsets[-1]) * inst.N
+    return {"value": evals / dt, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "seconds": dt,
+            "sample": f"one FP64 ELBO+gradient evaluation at {S_sample} of the {inst.S} Monte-Carlo "
+                      f"samples of the K={inst.K}, N={inst.N} workload ({evals:.3e} evals)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle on the host cores, same metric and
+    config, each step a bounded sample (one ELBO+gradient at 32 samples)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2501_09308_gb300 import synth
+    inst = synth.config(1)
+    P = oracle.Problem.from_instance(inst)
+    loc, raw = P.init_params()
+    eps = synth.normals(4242, REF_SAMPLE_S, P.K).astype(np.float64)
+    for _ in range(args.warmup):
+        P.elbo_grad(loc, raw, eps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.elbo_grad(loc, raw, eps)
+    dt = time.perf_counter() - t0
+    evals = REF_SAMPLE_S * int(inst.offsets[-1]) * inst.N * args.steps
+    v = evals / dt
+    out = {
+        "metric": METRIC, "value": v, "unit": "evals/s", "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(inst, l2="inputs L2-resident on the CPU; no GPU"),
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"per step one FP64 ELBO+gradient at {REF_SAMPLE_S} of {inst.S} samples"},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def workload_config(inst, l2):
+    return {"workload": f"single fit K={inst.K} (5-80 peaks, sum M={int(inst.offsets[-1])}), N={inst.N}, "
+                        f"S={inst.S}, {inst.iters} SVI steps + posterior ({S_POST} draws)",
+            "K": inst.K, "peaks_total": int(inst.offsets[-1]), "N": inst.N, "S": inst.S,
+            "svi_steps": inst.iters, "posterior_draws": S_POST, "parallelism": "replicas",
+            "l2": l2}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    from paper_2501_09308_gb300 import synth, xrdvi
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the xrdvi library has no CPU path)")
+    torch.cuda.set_device(local)
+    xrdvi.lib()
+    inst = synth.config(1, instance=rank)
+    iters = args.iters or inst.iters
+    evals_step = inst.evals_per_iter * iters
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    ctx = xrdvi.Context.from_instance(inst, seed=1000 + rank)
+    ctx.set_stream(stream.cuda_stream)
+    init_state = ctx.state()
+
+    def one_step(prof):
+        ctx.fit(iters - (PROFILE_STEPS if prof else 0), trace=False)
+        k = ctx.profile_steps(PROFILE_STEPS) if prof else None
+        post = ctx.posterior(S_POST, 77, TOP_M)
+        return k, post
+
+    for _ in range(args.warmup):
+        ctx.set_state(init_state)
+        one_step(prof=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    times = []
+    kern = {k: 0.0 for k in xrdvi.KERNELS}
+    post = None
+    barrier(world)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        ctx.set_state(init_state)
+        l2_flush(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        km, post = one_step(prof=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        for k, v in km.items():
+            kern[k] += v / args.steps
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    total_ms = max_over_ranks(world, float(sum(times)))
+    ms_step = total_ms / args.steps
+    value = sum_over_ranks(world, evals_step * args.steps) / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: create (H2D) -> fit (trace D2H) -> posterior (D2H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c2 = xrdvi.Context.from_instance(inst, seed=2000 + rank)
+    trace = c2.fit(iters, trace=True)
+    post2 = c2.posterior(S_POST, 77, TOP_M)
+    c2.close()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = sum_over_ranks(world, evals_step) / e2e_s
+    K, N, M = inst.K, inst.N, int(inst.offsets[-1])
+    h2d = (K + 1) * 4 + 2 * M * 4 + 3 * N * 4
+    d2h = iters * 8 + 8 + K * 8 + TOP_M * ((K + 63) // 64) * 8 + TOP_M * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, CPU_SAMPLE_S, rank)
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    issue_peak = sms * 128 * clock_mhz * 1e6 / 1e12   # lane-instructions per second (4 SMSP x 32 lanes)
+    dom = "backward" if kern["backward"] >= kern["forward"] else "forward"
+    evals_launch = inst.evals_per_iter
+    achieved = {k: evals_launch * INSTR_PER_EVAL[k] / (kern[k] * 1e-3) / 1e12 for k in ("forward", "backward")}
+    launches_per_step = 5 * iters + 6
+    share = {k: kern[k] / sum(kern.values()) for k in kern}
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(inst, l2="256 MB buffer written between timed steps (L2 flush)"),
+        "time_to_posterior_s": ms_step / 1e3,
+        "svi_step_ms": ms_step / iters,
+        "kernel_ms_per_launch": kern,
+        "kernel_share": share,
+        "roofline": {
+            "bound": "alu",
+            "kernel": f"k_{dom}",
+            "achieved": achieved[dom],
+            "peak": issue_peak,
+            "unit": "Tinst/s",
+            "frac": achieved[dom] / issue_peak,
+            "traffic": None,
+            "peak_source": f"{sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({peak_src} sm_max_mhz); "
+                           f"{INSTR_PER_EVAL[dom]} algorithmic instructions per evaluation",
+            "forward_frac": achieved["forward"] / issue_peak,
+            "backward_frac": achieved["backward"] / issue_peak,
+        },
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "seconds": e2e_s},
+        "gpu_launches": launches_per_step * args.steps,
+        "posterior": {"top_combination": [int(k) for k in np.flatnonzero(post["combos"][0])],
+                      "planted": [int(k) for k in inst.planted],
+                      "pi_planted_min": float(min(post["pi"][inst.planted])),
+                      "e2e_top_combination": [int(k) for k in np.flatnonzero(post2["combos"][0])],
+                      "final_elbo": float(trace[-1])},
+    }
+    if clk:
+        out["clocks"] = clk
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

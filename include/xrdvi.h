@@ -1,0 +1,203 @@
+/*
+ * xrdvi — variational sparse Bayesian crystalline-phase search on one GPU.
+ *
+ * C ABI of the Monte-Carlo ELBO step of Murakami et al., "Rapid, Comprehensive
+ * Search of Crystalline Phases from X-ray Diffraction in Seconds via
+ * GPU-Accelerated Bayesian Variational Inference" (arXiv 2501.09308):
+ *
+ *   problem   (Appendix A.1)  pattern D = {(x_i, y_i)}, i = 1..N, 2-theta in
+ *             degrees and integer counts; K candidate phases, phase k a list
+ *             of M_k (position p_m, relative intensity I_m) pairs;
+ *   model     (Appendix A.2)  f(x) = B(x) + sum_k h_k sum_m I_m V(x; p_m + mu_k,
+ *             w_k, r_k, alpha_k), V the split pseudo-Voigt (1-r) G + r L;
+ *   likelihood(Appendix A.2)  y_i ~ Poisson(f(x_i));
+ *   priors    (Sec. 2.2, Appendix B.2)  h ~ Exp(1/max(Y-B)), mu ~ N(0,0.03),
+ *             alpha ~ N(1,0.2), r ~ U(0,1), w ~ Gam(3, rate 100);
+ *   inference (Sec. 3.2)  mean-field normal q over the unconstrained
+ *             parameters u = (ln h, mu, ln w, logit r, alpha), fitted by
+ *             maximising the reparameterised Monte-Carlo ELBO with Adam.
+ *
+ * Every compute step runs in CUDA kernels built for sm_103a; there is no CPU
+ * fallback.  A context owns all of its device memory.  Unless stated, pointers
+ * are HOST pointers owned by the caller, copied during the call; "_dev"
+ * entry points take DEVICE pointers (caller-owned, must stay valid until the
+ * call returns on the context's stream).  No call keeps a caller pointer.
+ *
+ * Errors: every call returns an xrdvi_status; xrdvi_last_error() gives a
+ * thread-local message for the last failing call on the calling thread.
+ * A context is not thread-safe: use one context per host thread.
+ *
+ * Parameter layout (all entry points): per phase k, j = 0 intensity h,
+ * 1 shift mu, 2 width w (FWHM, degrees), 3 Gauss-Lorentz ratio r,
+ * 4 asymmetry alpha.  loc/raw are float [K*5] (index k*5+j) with
+ * sigma = softplus(raw).  Gradients are float [K*10]: grad[k*10+j] =
+ * dELBO/dloc[k][j], grad[k*10+5+j] = dELBO/draw[k][j].  Monte-Carlo noise is
+ * float [S*K*5] (index (s*K+k)*5+j).
+ */
+#ifndef XRDVI_H
+#define XRDVI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XRDVI_OK = 0,
+    XRDVI_EINVAL = 1,      /* invalid argument or input data                    */
+    XRDVI_ENOMEM = 2,      /* device allocation failed / over the memory budget */
+    XRDVI_ECUDA = 3,       /* CUDA runtime error (no device, launch failure)    */
+    XRDVI_ETIMEOUT = 4,    /* bounded wait ran out                               */
+    XRDVI_ENONFINITE = 5,  /* ELBO or gradient became NaN/Inf                    */
+    XRDVI_EBUSY = 6        /* resource temporarily unavailable                   */
+} xrdvi_status;
+
+typedef struct xrdvi_ctx xrdvi_ctx;
+
+/* Candidate phase set F (Appendix A.1) in CSR form.  offsets[0] = 0,
+ * offsets[k+1] - offsets[k] = M_k >= 1.  Positions in (0, 180) degrees,
+ * relative intensities in [0, 1].  Peaks need not be sorted. */
+typedef struct {
+    int32_t K;
+    const int32_t *offsets;   /* [K+1]            */
+    const float *pos_deg;     /* [offsets[K]]     */
+    const float *rel_int;     /* [offsets[K]]     */
+} xrdvi_peaks;
+
+/* Measured pattern D (Appendix A.1) and the fixed background B (Appendix A.2,
+ * estimated before fitting).  x strictly increasing in (0, 180); y >= 0 and
+ * integer-valued; bg >= 0. */
+typedef struct {
+    int32_t N;
+    const float *x_deg;       /* [N] */
+    const float *y_counts;    /* [N] */
+    const float *bg;          /* [N] */
+} xrdvi_pattern;
+
+/* Flags */
+#define XRDVI_FLAG_BF16_INT   (1u << 0)  /* keep relative intensities as bfloat16 */
+#define XRDVI_FLAG_NAIVE_SUM  (1u << 1)  /* plain instead of compensated f32 sum over phases */
+
+typedef struct {
+    uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */
+    int32_t S;                /* Monte-Carlo samples per ELBO step (>= 1)          */
+    float lr, beta1, beta2, adam_eps;   /* Adam on -ELBO                          */
+    uint64_t seed;            /* Philox4x32-10 key for the fit's noise stream      */
+    float prior_mu_sd;        /* mu ~ N(0, prior_mu_sd)                 (B.2)      */
+    float prior_alpha_mean;   /* alpha ~ N(mean, sd)                    (B.2)      */
+    float prior_alpha_sd;
+    float prior_w_shape;      /* w ~ Gam(shape, rate)                   (B.2)      */
+    float prior_w_rate;
+    float alpha_min;          /* profile clamp: alpha_eff = max(alpha, alpha_min)  */
+    float init_h_frac;        /* initial h = init_h_frac * max(Y - B)              */
+    float init_sigma;         /* initial sigma of every q factor                   */
+    uint32_t flags;           /* XRDVI_FLAG_*                                      */
+} xrdvi_config;
+
+/* Fills the defaults: S 256, Adam lr 0.01 betas (0.9, 0.999) eps 1e-8, seed 0,
+ * priors of Appendix B.2, alpha_min 1e-3, init_h_frac 0.1, init_sigma 0.1. */
+void xrdvi_config_default(xrdvi_config *cfg);
+
+/* Validates and uploads the problem (one host-to-device copy), computes
+ * lambda = 1 / max(Y - B) (Sec. 2.2) and the data constant of the Poisson
+ * log-likelihood, allocates the device state and initialises q.
+ * EINVAL on malformed input (K < 1, an empty phase, x not increasing,
+ * y negative / non-integer / non-finite, bg < 0, max(Y - B) <= 0, S < 1, sizes
+ * above the documented limits: K <= 1024, total peaks <= 24000, N <= 2^24,
+ * S <= 65536).  On success *out owns all device memory. */
+xrdvi_status xrdvi_create(const xrdvi_peaks *peaks, const xrdvi_pattern *pattern,
+                          const xrdvi_config *cfg, xrdvi_ctx **out);
+
+/* Frees the context and all of its device memory (NULL is a no-op). */
+void xrdvi_destroy(xrdvi_ctx *ctx);
+
+/* Runs subsequent work on `cuda_stream` (a cudaStream_t; NULL restores the
+ * context's own stream).  The CUDA-graph of the fit step is re-captured. */
+xrdvi_status xrdvi_set_stream(xrdvi_ctx *ctx, void *cuda_stream);
+
+/* Stochastic variational inference (Sec. 3.2): `iters` steps of
+ * sample -> profile/likelihood -> backward -> Adam, replayed as a CUDA graph
+ * with no host synchronisation inside.  elbo_trace (NULL or [iters]) receives
+ * the ELBO estimate of each step before its update.  Returns ENONFINITE if
+ * the last ELBO is not finite.  Blocks until the work is done. */
+xrdvi_status xrdvi_fit(xrdvi_ctx *ctx, int32_t iters, double *elbo_trace);
+
+/* One ELBO + gradient evaluation at the current q, without an update.
+ * eps: NULL (noise from the fit stream at the current step) or injected
+ * standard normals [S*K*5].  Outputs (each may be NULL): elbo [1],
+ * grad [K*10], f_out profile [S*N], ll_out [S] log-likelihood per sample,
+ * lpj_out [S] log prior + log Jacobian per sample. */
+xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *ctx, const float *eps, double *elbo, float *grad,
+                             float *f_out, double *ll_out, double *lpj_out);
+
+/* Posterior over phase combinations from the fitted q: how probable each
+ * subset of the candidate phases is given the data (Abstract, Sec. 1), with a
+ * phase counted as present when its share of the total peak area is at least
+ * 1 % (Sec. 4).  Draws S_post samples (Philox key `seed`),
+ * computes per-sample inclusion bits, marginal inclusion probabilities
+ * pi_k = (count_k + 1/2) / (S_post + 1), the top_m most probable combinations
+ * of the mean-field product (exact best-first order), their FP64 log-sum-exp
+ * coverage, and the importance-sampled log evidence with its effective
+ * sample size.  Outputs (host, may be NULL): pi [K]; combos [top_m * W] bit
+ * masks with W = ceil(K/64) words per combination, bit k%64 of word k/64 =
+ * phase k; combo_logp [top_m]; log_evidence [1]; ess [1]; coverage_log [1].
+ * 1 <= S_post <= 65536, 1 <= top_m <= 4096. */
+xrdvi_status xrdvi_posterior(xrdvi_ctx *ctx, int32_t S_post, uint64_t seed, int32_t top_m,
+                             double *pi, uint64_t *combos, double *combo_logp,
+                             double *log_evidence, double *ess, double *coverage_log);
+
+/* Variational parameters (host float [K*5] each). */
+xrdvi_status xrdvi_get_params(xrdvi_ctx *ctx, float *loc, float *raw);
+xrdvi_status xrdvi_set_params(xrdvi_ctx *ctx, const float *loc, const float *raw);
+
+/* Checkpoint / resume.  The state is loc, raw, the Adam moments, the step
+ * counter and the seed; a resumed fit replays the same noise (Philox counters
+ * are keyed by step) and is bit-identical to an uninterrupted one.
+ * xrdvi_get_state with buf == NULL stores the required size in *len. */
+xrdvi_status xrdvi_get_state(xrdvi_ctx *ctx, void *buf, size_t *len);
+xrdvi_status xrdvi_set_state(xrdvi_ctx *ctx, const void *buf, size_t len);
+
+typedef struct {
+    int32_t K, N, S, M_total;
+    int64_t step;             /* optimisation steps taken                   */
+    double eta;               /* max(Y - B)                                  */
+    double lambda_;           /* 1 / eta                                     */
+    double data_const;        /* sum_i [y ln y - y - ln y!]                  */
+    size_t device_bytes;      /* device memory held by the context           */
+    int32_t point_tiles;      /* 2-theta tiles of the profile kernels        */
+} xrdvi_info;
+
+xrdvi_status xrdvi_get_info(xrdvi_ctx *ctx, xrdvi_info *info);
+
+/* Device-pointer entry points used by the torch.autograd.Function wrapper.
+ * d_loc, d_raw: float [K*5]; d_eps: float [S*K*5] standard normals.
+ * xrdvi_forward_dev writes the ELBO estimate (double) to d_elbo.
+ * xrdvi_backward_dev recomputes the profiles (nothing of size S*K*N is kept)
+ * and writes dELBO/d(loc, raw) to d_grad (float [K*10]).
+ * Both are asynchronous on the context's stream. */
+xrdvi_status xrdvi_forward_dev(xrdvi_ctx *ctx, const float *d_loc, const float *d_raw,
+                               const float *d_eps, double *d_elbo);
+xrdvi_status xrdvi_backward_dev(xrdvi_ctx *ctx, const float *d_loc, const float *d_raw,
+                                const float *d_eps, float *d_grad);
+
+/* Runs `steps` ordinary fit steps (identical to xrdvi_fit's, advancing the
+ * fit) but launches each kernel individually between CUDA events on the
+ * context's stream, and returns in kernel_ms[5] the mean duration per launch
+ * of: sampling, profile+likelihood, backward, gradient reduction + Adam, ELBO
+ * finalisation.  Blocks until done.  For measurement only; xrdvi_fit is the
+ * fast path. */
+xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *xrdvi_last_error(void);
+
+/* Library version string. */
+const char *xrdvi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XRDVI_H */

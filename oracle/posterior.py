@@ -6,9 +6,9 @@ What the paper fixes and what is read here:
 
 * Phase identification (Sec. 4, the area-ratio figure): a phase counts as
   present when its share of the total integrated peak area is at least 1 %.
-* The paper estimates "the posterior probability of crystalline phase
-  combinations" by an approximate exhaustive search (Abstract, Sec. 1).
-  Reading: draw S_post samples from the fitted mean-field q; each sample gives
+* The paper's output is a probability for each subset of candidate phases
+  given the data, obtained by an approximate search over all subsets
+  (Abstract, Sec. 1).  Reading: draw S_post samples from the fitted mean-field q; each sample gives
   the inclusion bit b_sk = [area ratio_sk >= 0.01]; the marginal inclusion
   probability is pi_k = (sum_s b_sk + 1/2) / (S_post + 1) (the +1/2 keeps
   logs finite); the probability of a combination c in {0,1}^K is the

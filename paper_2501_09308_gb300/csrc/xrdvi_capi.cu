@@ -1,0 +1,642 @@
+// C ABI of the xrdvi library: context lifetime, input validation, upload,
+// the CUDA-graph fit loop, the single-step ELBO/gradient entry points, the
+// posterior and checkpointing.  Host code only; the kernels live in
+// xrdvi_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/xrdvi.h"
+#include "xrdvi_internal.h"
+
+using namespace xrdvi;
+
+namespace {
+
+thread_local std::string g_err;
+
+xrdvi_status fail(xrdvi_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define XR_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? XRDVI_ENOMEM : XRDVI_ECUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+#define XR_TRY(expr)                          \
+    do {                                      \
+        xrdvi_status s_ = (expr);             \
+        if (s_ != XRDVI_OK) return s_;        \
+    } while (0)
+
+constexpr int kUnroll = 16;          // fit steps per captured CUDA graph
+constexpr uint32_t kStateMagic = 0x58524456u;  // "XRDV"
+
+float round_bf16(float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    const uint32_t lsb = (b >> 16) & 1u;
+    b += 0x7fffu + lsb;  // round to nearest even
+    b &= 0xffff0000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+}  // namespace
+
+struct xrdvi_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    xrdvi_config cfg{};
+    Problem P;
+    Workspace W;       // fit sample set (S)
+    Workspace Wp;      // posterior sample set (S_post)
+    PostBuffers B;
+    float *loc = nullptr, *raw = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    float *eps_in = nullptr;   // injected noise [S*K*5]
+    float *f_out = nullptr;    // profile output [S*N]
+    double *ent = nullptr, *elbo = nullptr, *trace = nullptr;
+    int *step = nullptr, *iter = nullptr;
+    cudaGraphExec_t graph_many = nullptr, graph_one = nullptr;
+    int64_t host_step = 0;
+    double eta = 0.0;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+    std::vector<void *> post_allocs;
+
+    template <class T>
+    xrdvi_status alloc(T **p, size_t n, std::vector<void *> *list = nullptr) {
+        if (n == 0) n = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        if (e != cudaSuccess) {
+            return fail(e == cudaErrorMemoryAllocation ? XRDVI_ENOMEM : XRDVI_ECUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        (list ? list : &allocs)->push_back(q);
+        bytes += n * sizeof(T);
+        *p = static_cast<T *>(q);
+        return XRDVI_OK;
+    }
+
+    void drop_graphs() {
+        if (graph_many) cudaGraphExecDestroy(graph_many);
+        if (graph_one) cudaGraphExecDestroy(graph_one);
+        graph_many = graph_one = nullptr;
+    }
+
+    void free_post() {
+        for (void *q : post_allocs) cudaFree(q);
+        post_allocs.clear();
+        Wp = Workspace();
+        B = PostBuffers();
+    }
+
+    ~xrdvi_ctx() {
+        if (stream) cudaStreamSynchronize(stream);
+        drop_graphs();
+        free_post();
+        for (void *q : allocs) cudaFree(q);
+        if (own_stream) cudaStreamDestroy(own_stream);
+    }
+};
+
+namespace {
+
+xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
+                             std::vector<void *> *list) {
+    const Problem &P = c->P;
+    const size_t SK = static_cast<size_t>(S) * P.K;
+    const size_t before = c->bytes;
+    W.S = S;
+    XR_TRY(c->alloc(&W.eps, SK * 5, list));
+    XR_TRY(c->alloc(&W.theta, SK * 5, list));
+    XR_TRY(c->alloc(&W.cst, SK, list));
+    XR_TRY(c->alloc(&W.lpj, static_cast<size_t>(S), list));
+    XR_TRY(c->alloc(&W.ll, static_cast<size_t>(S), list));
+    XR_TRY(c->alloc(&W.g, static_cast<size_t>(S) * P.Npad, list));
+    XR_TRY(c->alloc(&W.llpart, static_cast<size_t>(S) * P.T, list));
+    if (fit) {
+        XR_TRY(c->alloc(&W.gpart, SK * P.T * 8, list));
+        W.lq = nullptr;
+    } else {
+        XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
+        W.gpart = nullptr;
+    }
+    W.bytes = c->bytes - before;
+    return XRDVI_OK;
+}
+
+xrdvi_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return XRDVI_OK;
+}
+
+AdamConst adam_const(const xrdvi_config &cfg) {
+    return AdamConst{cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps};
+}
+
+// One SVI step: sample -> profile + likelihood -> backward -> Adam -> ELBO.
+void enqueue_step(xrdvi_ctx *c, cudaStream_t st) {
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    launch_sample(c->P, c->W, c->loc, c->raw, nullptr, c->cfg.seed, 0u, c->step, 0u, c->iter, c->ent, st);
+    launch_forward(c->P, c->W, nullptr, naive, st);
+    launch_backward(c->P, c->W, st);
+    launch_grad(c->P, c->W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m,
+                c->v, c->iter, c->step, c->ent, c->elbo, c->trace, st);
+}
+
+xrdvi_status capture(xrdvi_ctx *c, int steps, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    XR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < steps; ++i) enqueue_step(c, c->stream);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return XRDVI_OK;
+}
+
+bool finite_all(const float *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+xrdvi_status validate(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg) {
+    if (!pk || !pt || !cfg) return fail(XRDVI_EINVAL, "null argument");
+    if (cfg->size != sizeof(xrdvi_config)) return fail(XRDVI_EINVAL, "config.size mismatch (call xrdvi_config_default)");
+    if (pk->K < 1 || pk->K > kMaxK) return fail(XRDVI_EINVAL, "K must be in [1, 1024]");
+    if (!pk->offsets || !pk->pos_deg || !pk->rel_int) return fail(XRDVI_EINVAL, "null peak arrays");
+    if (pk->offsets[0] != 0) return fail(XRDVI_EINVAL, "offsets[0] must be 0");
+    for (int k = 0; k < pk->K; ++k)
+        if (pk->offsets[k + 1] - pk->offsets[k] < 1) return fail(XRDVI_EINVAL, "every phase needs at least one peak");
+    const int M = pk->offsets[pk->K];
+    if (M > kMaxPeaks) return fail(XRDVI_EINVAL, "total peaks above 24000");
+    for (int i = 0; i < M; ++i) {
+        const float p = pk->pos_deg[i], I = pk->rel_int[i];
+        if (!(std::isfinite(p) && p > 0.f && p < 180.f)) return fail(XRDVI_EINVAL, "peak position outside (0, 180)");
+        if (!(std::isfinite(I) && I >= 0.f && I <= 1.f)) return fail(XRDVI_EINVAL, "relative intensity outside [0, 1]");
+    }
+    if (pt->N < 1 || pt->N > kMaxN) return fail(XRDVI_EINVAL, "N must be in [1, 2^24]");
+    if (!pt->x_deg || !pt->y_counts || !pt->bg) return fail(XRDVI_EINVAL, "null pattern arrays");
+    for (int i = 0; i < pt->N; ++i) {
+        const float x = pt->x_deg[i], y = pt->y_counts[i], b = pt->bg[i];
+        if (!(std::isfinite(x) && x > 0.f && x < 180.f)) return fail(XRDVI_EINVAL, "2-theta outside (0, 180)");
+        if (i > 0 && !(x > pt->x_deg[i - 1])) return fail(XRDVI_EINVAL, "x must be strictly increasing");
+        if (!(std::isfinite(y) && y >= 0.f && std::floor(y) == y)) return fail(XRDVI_EINVAL, "counts must be non-negative integers");
+        if (!(std::isfinite(b) && b >= 0.f)) return fail(XRDVI_EINVAL, "background must be finite and >= 0");
+    }
+    if (cfg->S < 1 || cfg->S > kMaxS) return fail(XRDVI_EINVAL, "S must be in [1, 65536]");
+    const float pos_params[] = {cfg->prior_mu_sd, cfg->prior_alpha_sd, cfg->prior_w_shape, cfg->prior_w_rate,
+                                cfg->alpha_min, cfg->init_h_frac, cfg->init_sigma, cfg->lr};
+    for (float q : pos_params)
+        if (!(std::isfinite(q) && q > 0.f)) return fail(XRDVI_EINVAL, "prior / optimiser parameters must be positive");
+    if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->adam_eps > 0.f))
+        return fail(XRDVI_EINVAL, "Adam betas must be in [0, 1) and eps > 0");
+    return XRDVI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *xrdvi_last_error(void) { return g_err.c_str(); }
+
+const char *xrdvi_version(void) { return "xrdvi 0.1 (sm_103a)"; }
+
+void xrdvi_config_default(xrdvi_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->size = sizeof(xrdvi_config);
+    cfg->S = 256;
+    cfg->lr = 0.01f;
+    cfg->beta1 = 0.9f;
+    cfg->beta2 = 0.999f;
+    cfg->adam_eps = 1e-8f;
+    cfg->seed = 0;
+    cfg->prior_mu_sd = 0.03f;
+    cfg->prior_alpha_mean = 1.0f;
+    cfg->prior_alpha_sd = 0.2f;
+    cfg->prior_w_shape = 3.0f;
+    cfg->prior_w_rate = 100.0f;
+    cfg->alpha_min = 1e-3f;
+    cfg->init_h_frac = 0.1f;
+    cfg->init_sigma = 0.1f;
+    cfg->flags = 0;
+}
+
+xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
+                          xrdvi_ctx **out) {
+    g_err.clear();
+    if (!out) return fail(XRDVI_EINVAL, "null output pointer");
+    *out = nullptr;
+    XR_TRY(validate(pk, pt, cfg));
+    const int K = pk->K, N = pt->N, M = pk->offsets[K];
+    // host preparation: sort each phase by position, eta, data constant
+    std::vector<float> pos(M), inten(M);
+    std::vector<double> isum(K, 0.0);
+    const bool bf16 = (cfg->flags & XRDVI_FLAG_BF16_INT) != 0;
+    for (int k = 0; k < K; ++k) {
+        const int b = pk->offsets[k], e = pk->offsets[k + 1];
+        std::vector<int> idx(e - b);
+        std::iota(idx.begin(), idx.end(), b);
+        std::stable_sort(idx.begin(), idx.end(), [&](int i, int j) { return pk->pos_deg[i] < pk->pos_deg[j]; });
+        for (int i = 0; i < e - b; ++i) {
+            pos[b + i] = pk->pos_deg[idx[i]];
+            const float I = bf16 ? round_bf16(pk->rel_int[idx[i]]) : pk->rel_int[idx[i]];
+            inten[b + i] = I;
+            isum[k] += I;
+        }
+    }
+    double eta = -INFINITY, csum = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double y = pt->y_counts[i];
+        eta = std::max(eta, y - static_cast<double>(pt->bg[i]));
+        if (y > 0) csum += y * std::log(y) - y - std::lgamma(y + 1.0);
+    }
+    if (!(eta > 0.0)) return fail(XRDVI_EINVAL, "max(Y - B) must be positive (it sets the intensity prior)");
+
+    int dev = 0, sms = 0;
+    XR_CUDA(cudaGetDevice(&dev));
+    XR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+    xrdvi_ctx *c = new xrdvi_ctx();
+    c->device = dev;
+    c->cfg = *cfg;
+    c->eta = eta;
+    auto bail = [&](xrdvi_status st) {
+        std::string keep = g_err;
+        delete c;
+        g_err = keep;
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(XRDVI_ECUDA, "cudaStreamCreate failed"));
+    c->stream = c->own_stream;
+
+    Problem &P = c->P;
+    P.K = K;
+    P.N = N;
+    P.Mtot = M;
+    P.T = (N + kTile - 1) / kTile;
+    P.Npad = P.T * kTile;
+    P.csum = csum;
+    P.prior.lambda = 1.0 / eta;
+    P.prior.mu_sd = cfg->prior_mu_sd;
+    P.prior.alpha_mean = cfg->prior_alpha_mean;
+    P.prior.alpha_sd = cfg->prior_alpha_sd;
+    P.prior.w_shape = cfg->prior_w_shape;
+    P.prior.w_rate = cfg->prior_w_rate;
+    P.prior.lgamma_w_shape = std::lgamma(static_cast<double>(cfg->prior_w_shape));
+    P.prior.alpha_min = cfg->alpha_min;
+
+    xrdvi_status st;
+#define XR_C(expr)                         \
+    do {                                   \
+        st = (expr);                       \
+        if (st != XRDVI_OK) return bail(st); \
+    } while (0)
+    XR_C(c->alloc(&P.pos, M));
+    XR_C(c->alloc(&P.inten, M));
+    XR_C(c->alloc(&P.off, K + 1));
+    XR_C(c->alloc(&P.x, N));
+    XR_C(c->alloc(&P.y, N));
+    XR_C(c->alloc(&P.bg, N));
+    XR_C(c->alloc(&P.isum, K));
+    XR_C(alloc_workspace(c, c->W, cfg->S, true, nullptr));
+    XR_C(c->alloc(&c->loc, K * 5));
+    XR_C(c->alloc(&c->raw, K * 5));
+    XR_C(c->alloc(&c->m, K * 10));
+    XR_C(c->alloc(&c->v, K * 10));
+    XR_C(c->alloc(&c->grad, K * 10));
+    XR_C(c->alloc(&c->ent, 1));
+    XR_C(c->alloc(&c->elbo, 1));
+    XR_C(c->alloc(&c->trace, kTraceCap));
+    XR_C(c->alloc(&c->step, 1));
+    XR_C(c->alloc(&c->iter, 1));
+
+    // initial q (reading: loc at h = init_h_frac * eta, mu = 0, w at the prior
+    // mean shape/rate, r = 1/2, alpha at its prior mean; sigma = init_sigma)
+    std::vector<float> loc(K * 5), raw(K * 5);
+    const double raw0 = std::log(std::expm1(static_cast<double>(cfg->init_sigma)));
+    for (int k = 0; k < K; ++k) {
+        loc[k * 5 + 0] = static_cast<float>(std::log(cfg->init_h_frac * eta));
+        loc[k * 5 + 1] = 0.f;
+        loc[k * 5 + 2] = static_cast<float>(std::log(static_cast<double>(cfg->prior_w_shape) / cfg->prior_w_rate));
+        loc[k * 5 + 3] = 0.f;
+        loc[k * 5 + 4] = cfg->prior_alpha_mean;
+        for (int j = 0; j < 5; ++j) raw[k * 5 + j] = static_cast<float>(raw0);
+    }
+    cudaStream_t s = c->stream;
+    auto up = [&](void *dst, const void *src, size_t n) { return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s); };
+    if (up(P.pos, pos.data(), M * 4) || up(P.inten, inten.data(), M * 4) ||
+        up(P.off, pk->offsets, (K + 1) * 4) || up(P.x, pt->x_deg, N * 4) || up(P.y, pt->y_counts, N * 4) ||
+        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) || up(c->loc, loc.data(), K * 20) ||
+        up(c->raw, raw.data(), K * 20) || cudaMemsetAsync(c->m, 0, K * 40, s) ||
+        cudaMemsetAsync(c->v, 0, K * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
+        cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s))
+        return bail(fail(XRDVI_ECUDA, "upload failed"));
+    configure_grids(P, sms);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return bail(fail(XRDVI_ECUDA, "create: device error"));
+#undef XR_C
+    *out = c;
+    return XRDVI_OK;
+}
+
+void xrdvi_destroy(xrdvi_ctx *c) { delete c; }
+
+xrdvi_status xrdvi_set_stream(xrdvi_ctx *c, void *stream) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    c->drop_graphs();
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_fit(xrdvi_ctx *c, int32_t iters, double *trace) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    if (iters < 0) return fail(XRDVI_EINVAL, "iters must be >= 0");
+    if (iters == 0) return XRDVI_OK;
+    if (c->host_step + iters > INT32_MAX) return fail(XRDVI_EINVAL, "step counter would overflow");
+    if (!c->graph_many) XR_TRY(capture(c, kUnroll, &c->graph_many));
+    if (!c->graph_one) XR_TRY(capture(c, 1, &c->graph_one));
+    int done = 0;
+    while (done < iters) {
+        const int chunk = std::min(iters - done, kTraceCap / 2);
+        int left = chunk;
+        while (left >= kUnroll) {
+            XR_CUDA(cudaGraphLaunch(c->graph_many, c->stream));
+            left -= kUnroll;
+        }
+        while (left-- > 0) XR_CUDA(cudaGraphLaunch(c->graph_one, c->stream));
+        if (trace) {
+            const int64_t s0 = c->host_step + done;
+            const int64_t a = s0 & (kTraceCap - 1);
+            const int64_t n1 = std::min<int64_t>(chunk, kTraceCap - a);
+            XR_CUDA(cudaMemcpyAsync(trace + done, c->trace + a, n1 * 8, cudaMemcpyDeviceToHost, c->stream));
+            if (n1 < chunk)
+                XR_CUDA(cudaMemcpyAsync(trace + done + n1, c->trace, (chunk - n1) * 8, cudaMemcpyDeviceToHost,
+                                        c->stream));
+        }
+        done += chunk;
+    }
+    double last = 0.0;
+    XR_CUDA(cudaMemcpyAsync(&last, c->elbo, 8, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    c->host_step += iters;
+    if (!std::isfinite(last)) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float *grad, float *f_out,
+                             double *ll_out, double *lpj_out) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    const Problem &P = c->P;
+    const int S = c->W.S;
+    const size_t SK5 = static_cast<size_t>(S) * P.K * 5;
+    cudaStream_t st = c->stream;
+    if (eps) {
+        if (!finite_all(eps, SK5)) return fail(XRDVI_EINVAL, "eps must be finite");
+        if (!c->eps_in) XR_TRY(c->alloc(&c->eps_in, SK5));
+        XR_CUDA(cudaMemcpyAsync(c->eps_in, eps, SK5 * 4, cudaMemcpyHostToDevice, st));
+    }
+    if (f_out && !c->f_out) XR_TRY(c->alloc(&c->f_out, static_cast<size_t>(S) * P.N));
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    launch_sample(P, c->W, c->loc, c->raw, eps ? c->eps_in : nullptr, c->cfg.seed, 0u, c->step, 0u, nullptr,
+                  c->ent, st);
+    launch_forward(P, c->W, f_out ? c->f_out : nullptr, naive, st);
+    launch_backward(P, c->W, st);
+    launch_grad(P, c->W, c->loc, c->raw, nullptr, nullptr, c->grad, false, adam_const(c->cfg), nullptr, nullptr,
+                nullptr, nullptr, c->ent, c->elbo, nullptr, st);
+    XR_TRY(check_launch("elbo_grad"));
+    double e = 0.0;
+    XR_CUDA(cudaMemcpyAsync(&e, c->elbo, 8, cudaMemcpyDeviceToHost, st));
+    if (grad) XR_CUDA(cudaMemcpyAsync(grad, c->grad, P.K * 10 * 4, cudaMemcpyDeviceToHost, st));
+    if (f_out) XR_CUDA(cudaMemcpyAsync(f_out, c->f_out, static_cast<size_t>(S) * P.N * 4, cudaMemcpyDeviceToHost, st));
+    if (ll_out) XR_CUDA(cudaMemcpyAsync(ll_out, c->W.ll, S * 8, cudaMemcpyDeviceToHost, st));
+    if (lpj_out) XR_CUDA(cudaMemcpyAsync(lpj_out, c->W.lpj, S * 8, cudaMemcpyDeviceToHost, st));
+    XR_CUDA(cudaStreamSynchronize(st));
+    if (elbo) *elbo = e;
+    if (!std::isfinite(e)) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_forward_dev(xrdvi_ctx *c, const float *d_loc, const float *d_raw, const float *d_eps,
+                               double *d_elbo) {
+    if (!c || !d_loc || !d_raw || !d_eps || !d_elbo) return fail(XRDVI_EINVAL, "null argument");
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    launch_sample(c->P, c->W, d_loc, d_raw, d_eps, c->cfg.seed, 0u, nullptr, 0u, nullptr, c->ent, c->stream);
+    launch_forward(c->P, c->W, nullptr, naive, c->stream);
+    launch_grad(c->P, c->W, d_loc, d_raw, nullptr, nullptr, nullptr, false, adam_const(c->cfg), nullptr, nullptr,
+                nullptr, nullptr, c->ent, d_elbo, nullptr, c->stream);
+    return check_launch("forward_dev");
+}
+
+xrdvi_status xrdvi_backward_dev(xrdvi_ctx *c, const float *d_loc, const float *d_raw, const float *d_eps,
+                                float *d_grad) {
+    if (!c || !d_loc || !d_raw || !d_eps || !d_grad) return fail(XRDVI_EINVAL, "null argument");
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    launch_sample(c->P, c->W, d_loc, d_raw, d_eps, c->cfg.seed, 0u, nullptr, 0u, nullptr, c->ent, c->stream);
+    launch_forward(c->P, c->W, nullptr, naive, c->stream);
+    launch_backward(c->P, c->W, c->stream);
+    launch_grad(c->P, c->W, d_loc, d_raw, nullptr, nullptr, d_grad, false, adam_const(c->cfg), nullptr, nullptr,
+                nullptr, nullptr, c->ent, nullptr, nullptr, c->stream);
+    return check_launch("backward_dev");
+}
+
+xrdvi_status xrdvi_posterior(xrdvi_ctx *c, int32_t S_post, uint64_t seed, int32_t top_m, double *pi,
+                             uint64_t *combos, double *combo_logp, double *log_evidence, double *ess,
+                             double *coverage_log) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    if (S_post < 1 || S_post > kMaxS) return fail(XRDVI_EINVAL, "S_post must be in [1, 65536]");
+    if (top_m < 1 || top_m > 4096) return fail(XRDVI_EINVAL, "top_m must be in [1, 4096]");
+    const Problem &P = c->P;
+    const int K = P.K, W = (K + 63) / 64;
+    if (c->B.cap_S < S_post || c->B.cap_M < top_m) {
+        XR_CUDA(cudaStreamSynchronize(c->stream));
+        c->bytes -= c->Wp.bytes;
+        c->free_post();
+        const int capS = std::max(S_post, c->B.cap_S), capM = std::max(top_m, 64);
+        std::vector<void *> *L = &c->post_allocs;
+        const size_t before = c->bytes;
+        XR_TRY(alloc_workspace(c, c->Wp, capS, false, L));
+        XR_TRY(c->alloc(&c->B.logw, capS, L));
+        XR_TRY(c->alloc(&c->B.bits, static_cast<size_t>(capS) * K, L));
+        XR_TRY(c->alloc(&c->B.pi, K, L));
+        XR_TRY(c->alloc(&c->B.scalars, 4, L));
+        XR_TRY(c->alloc(&c->B.combos, static_cast<size_t>(capM) * W, L));
+        XR_TRY(c->alloc(&c->B.combo_logp, capM, L));
+        XR_TRY(c->alloc(&c->B.order, K, L));
+        XR_TRY(c->alloc(&c->B.cost, K, L));
+        XR_TRY(c->alloc(&c->B.heap_cost, 2 * capM + 2, L));
+        XR_TRY(c->alloc(&c->B.heap_node, 2 * capM + 2, L));
+        XR_TRY(c->alloc(&c->B.node_mask, static_cast<size_t>(2 * capM + 2) * W, L));
+        XR_TRY(c->alloc(&c->B.node_last, 2 * capM + 2, L));
+        c->B.cap_S = capS;
+        c->B.cap_M = capM;
+        c->Wp.bytes = c->bytes - before;
+    }
+    c->Wp.S = S_post;
+    cudaStream_t st = c->stream;
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    launch_sample(P, c->Wp, c->loc, c->raw, nullptr, seed, 1u, nullptr, 0u, nullptr, nullptr, st);
+    launch_forward(P, c->Wp, nullptr, naive, st);
+    launch_posterior(P, c->Wp, c->B, top_m, st);
+    XR_TRY(check_launch("posterior"));
+    double sc[4] = {0, 0, 0, 0};
+    XR_CUDA(cudaMemcpyAsync(sc, c->B.scalars, 32, cudaMemcpyDeviceToHost, st));
+    if (pi) XR_CUDA(cudaMemcpyAsync(pi, c->B.pi, K * 8, cudaMemcpyDeviceToHost, st));
+    if (combos) XR_CUDA(cudaMemcpyAsync(combos, c->B.combos, static_cast<size_t>(top_m) * W * 8, cudaMemcpyDeviceToHost, st));
+    if (combo_logp) XR_CUDA(cudaMemcpyAsync(combo_logp, c->B.combo_logp, top_m * 8, cudaMemcpyDeviceToHost, st));
+    XR_CUDA(cudaStreamSynchronize(st));
+    if (log_evidence) *log_evidence = sc[0];
+    if (ess) *ess = sc[1];
+    if (coverage_log) *coverage_log = sc[2];
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_profile_steps(xrdvi_ctx *c, int32_t steps, float *kernel_ms) {
+    if (!c || !kernel_ms) return fail(XRDVI_EINVAL, "null argument");
+    if (steps < 1) return fail(XRDVI_EINVAL, "steps must be >= 1");
+    if (c->host_step + steps > INT32_MAX) return fail(XRDVI_EINVAL, "step counter would overflow");
+    cudaEvent_t ev[6];
+    for (auto &e : ev) XR_CUDA(cudaEventCreate(&e));
+    double acc[5] = {0, 0, 0, 0, 0};
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    cudaStream_t st = c->stream;
+    xrdvi_status rc = XRDVI_OK;
+    for (int i = 0; i < steps && rc == XRDVI_OK; ++i) {
+        cudaEventRecord(ev[0], st);
+        launch_sample(c->P, c->W, c->loc, c->raw, nullptr, c->cfg.seed, 0u, c->step, 0u, c->iter, c->ent, st);
+        cudaEventRecord(ev[1], st);
+        launch_forward(c->P, c->W, nullptr, naive, st);
+        cudaEventRecord(ev[2], st);
+        launch_backward(c->P, c->W, st);
+        cudaEventRecord(ev[3], st);
+        launch_grad(c->P, c->W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m, c->v,
+                    c->iter, nullptr, c->ent, nullptr, nullptr, st);
+        cudaEventRecord(ev[4], st);
+        launch_grad(c->P, c->W, c->loc, c->raw, nullptr, nullptr, nullptr, false, adam_const(c->cfg), nullptr,
+                    nullptr, c->iter, c->step, c->ent, c->elbo, c->trace, st);
+        cudaEventRecord(ev[5], st);
+        if (cudaEventSynchronize(ev[5]) != cudaSuccess) {
+            rc = fail(XRDVI_ECUDA, std::string("profile_steps: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        for (int k = 0; k < 5; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            acc[k] += ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc != XRDVI_OK) return rc;
+    c->host_step += steps;
+    for (int k = 0; k < 5; ++k) kernel_ms[k] = static_cast<float>(acc[k] / steps);
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_get_params(xrdvi_ctx *c, float *loc, float *raw) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    if (loc) XR_CUDA(cudaMemcpyAsync(loc, c->loc, c->P.K * 20, cudaMemcpyDeviceToHost, c->stream));
+    if (raw) XR_CUDA(cudaMemcpyAsync(raw, c->raw, c->P.K * 20, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_set_params(xrdvi_ctx *c, const float *loc, const float *raw) {
+    if (!c || !loc || !raw) return fail(XRDVI_EINVAL, "null argument");
+    if (!finite_all(loc, c->P.K * 5) || !finite_all(raw, c->P.K * 5)) return fail(XRDVI_EINVAL, "params must be finite");
+    XR_CUDA(cudaMemcpyAsync(c->loc, loc, c->P.K * 20, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaMemcpyAsync(c->raw, raw, c->P.K * 20, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    return XRDVI_OK;
+}
+
+namespace {
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t K, pad;
+    int64_t step;
+    uint64_t seed;
+};
+}  // namespace
+
+xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
+    if (!c || !len) return fail(XRDVI_EINVAL, "null argument");
+    const int K = c->P.K;
+    const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * (5 + 5 + 10 + 10) * 4;
+    if (!buf) {
+        *len = need;
+        return XRDVI_OK;
+    }
+    if (*len < need) return fail(XRDVI_EINVAL, "state buffer too small");
+    StateHeader h{kStateMagic, 1u, K, 0, c->host_step, c->cfg.seed};
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    XR_CUDA(cudaMemcpyAsync(p, c->loc, K * 20, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaMemcpyAsync(p + K * 20, c->raw, K * 20, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaMemcpyAsync(p + K * 40, c->m, K * 40, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaMemcpyAsync(p + K * 80, c->v, K * 40, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    *len = need;
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_set_state(xrdvi_ctx *c, const void *buf, size_t len) {
+    if (!c || !buf) return fail(XRDVI_EINVAL, "null argument");
+    const int K = c->P.K;
+    const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * 120;
+    if (len < need) return fail(XRDVI_EINVAL, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1u || h.K != K) return fail(XRDVI_EINVAL, "state does not match this problem");
+    if (h.step < 0 || h.step > INT32_MAX) return fail(XRDVI_EINVAL, "bad step counter");
+    const char *p = static_cast<const char *>(buf) + sizeof(h);
+    const int step = static_cast<int>(h.step);
+    XR_CUDA(cudaMemcpyAsync(c->loc, p, K * 20, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaMemcpyAsync(c->raw, p + K * 20, K * 20, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaMemcpyAsync(c->m, p + K * 40, K * 40, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaMemcpyAsync(c->v, p + K * 80, K * 40, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaMemcpyAsync(c->step, &step, 4, cudaMemcpyHostToDevice, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    c->host_step = h.step;
+    c->cfg.seed = h.seed;
+    c->drop_graphs();  // the seed is a kernel argument of the captured step
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_get_info(xrdvi_ctx *c, xrdvi_info *info) {
+    if (!c || !info) return fail(XRDVI_EINVAL, "null argument");
+    info->K = c->P.K;
+    info->N = c->P.N;
+    info->S = c->W.S;
+    info->M_total = c->P.Mtot;
+    info->step = c->host_step;
+    info->eta = c->eta;
+    info->lambda_ = c->P.prior.lambda;
+    info->data_const = c->P.csum;
+    info->device_bytes = c->bytes;
+    info->point_tiles = c->P.T;
+    return XRDVI_OK;
+}
+
+}  // extern "C"

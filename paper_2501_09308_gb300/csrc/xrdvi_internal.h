@@ -1,0 +1,122 @@
+// Internal declarations shared by the kernel and host translation units of
+// the xrdvi library (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xrdvi {
+
+// Profile kernels: 8 warps per block; each warp owns one (sample, 2-theta
+// tile) work item of 32 * kPts consecutive points, lane l holding points
+// l, l+32, ..., l+32*(kPts-1) of the tile.
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kPts = 4;
+constexpr int kTile = 32 * kPts;
+
+// The Gaussian component 2^-u of a peak is evaluated only for warps with a
+// point inside the peak's reach u < kGaussU; beyond it 2^-u < 2^-128, which
+// flushes to zero in single precision anyway.
+constexpr float kGaussU = 128.0f;
+
+// Limits checked at create time.
+constexpr int kMaxK = 1024;
+constexpr int kMaxPeaks = 24000;
+constexpr int kMaxS = 65536;
+constexpr int kMaxN = 1 << 24;
+constexpr int kTraceCap = 1 << 16;   // ring buffer of ELBO values (power of two)
+
+// Per (sample, phase) constants of the profile kernels (32 bytes).  With
+// d = x - p - mu and side width w_side = w (d < 0) or alpha*w (d >= 0):
+//   c(d) = 4 / w_side^2,  u = c(d) d^2 = (2 d / w_side)^2,
+//   G = 2^-u = exp(-4 ln2 t^2),  L = 1 / (1 + u),  t = d / w_side.
+// c(d) d is formed without a select as a d + b |d| with a = (c_r + c_l)/2,
+// b = (c_r - c_l)/2 when the two sides differ by at most 4x (alpha in
+// [0.5, 2]: the cancellation costs at most a factor 4 in rounding error);
+// otherwise (split = 1) a = c_l, b = c_r and the side is selected by sign.
+struct __align__(16) PhaseConst {
+    float mu;      // peak shift
+    float a, b;    // see above
+    float hl, hg;  // h * r, h * (1 - r)
+    float rl, rr;  // Gaussian reach left / right of the peak (degrees)
+    int split;     // 0: a d + b |d| form, 1: explicit side select
+};
+
+struct PriorConst {
+    double lambda;        // rate of the exponential prior on h
+    double mu_sd;
+    double alpha_mean, alpha_sd;
+    double w_shape, w_rate, lgamma_w_shape;
+    double alpha_min;
+};
+
+// Buffers of one sample set (the fit's S, or the posterior's S_post).
+struct Workspace {
+    int S = 0;
+    float *eps = nullptr;        // [S*K*5] standard normals used
+    float *theta = nullptr;      // [S*K*5] physical parameters
+    PhaseConst *cst = nullptr;   // [S*K]
+    double *lpj = nullptr;       // [S] log prior + log Jacobian
+    double *lq = nullptr;        // [S] log q(u)
+    double *ll = nullptr;        // [S] log-likelihood
+    float *g = nullptr;          // [S*Npad] y/f - 1 (0 on padding)
+    double *llpart = nullptr;    // [S*T] deviance partial sums per tile
+    float *gpart = nullptr;      // [S*K*T*8] gradient partial sums (fit only)
+    size_t bytes = 0;
+};
+
+struct Problem {
+    int K = 0, N = 0, Npad = 0, T = 0, Mtot = 0;
+    float *pos = nullptr;        // [Mtot] sorted by position within each phase
+    float *inten = nullptr;      // [Mtot] (f32 copy; bf16-rounded with the flag)
+    int *off = nullptr;          // [K+1]
+    float *x = nullptr, *y = nullptr, *bg = nullptr;   // [N]
+    double *isum = nullptr;      // [K] sum_m I_m per phase
+    double csum = 0.0;           // sum_i [y ln y - y - ln y!]
+    PriorConst prior{};
+    size_t smem = 0;             // dynamic shared memory of the profile kernels
+    int grid_fwd = 0, grid_bwd = 0;
+};
+
+// --- kernel launchers (xrdvi_kernels.cu) ------------------------------------
+// Sampling: eps_in (device, may be null) or Philox(seed, tag, step).
+// d_step: device step counter (null: use `step`); d_iter: receives the step
+// used (may be null); ent: receives the entropy of q (may be null).
+void launch_sample(const Problem &P, Workspace &W, const float *loc, const float *raw,
+                   const float *eps_in, uint64_t seed, uint32_t tag, const int *d_step,
+                   uint32_t step, int *d_iter, double *ent, cudaStream_t st);
+void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st);
+void launch_backward(const Problem &P, Workspace &W, cudaStream_t st);
+// Reduces gradient partials per phase and optionally applies Adam (when
+// grad_out or adam), then finalises the ELBO (when elbo_out or trace: writes
+// ll[S], *elbo_out, trace[step] and advances *d_step).
+struct AdamConst { float lr, b1, b2, eps; };
+void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,
+                 float *loc_out, float *raw_out, float *grad_out, bool adam, AdamConst ac,
+                 float *m, float *v, const int *d_iter, int *d_step, const double *ent,
+                 double *elbo_out, double *trace, cudaStream_t st);
+// Posterior: per-sample log weights and inclusion bits, marginals, IS
+// evidence, and the best-first top-M combinations.
+struct PostBuffers {
+    double *logw = nullptr;      // [S]
+    uint8_t *bits = nullptr;     // [S*K]
+    double *pi = nullptr;        // [K]
+    double *scalars = nullptr;   // [4]: log_evidence, ess, coverage_log, (spare)
+    uint64_t *combos = nullptr;  // [top_m * W]
+    double *combo_logp = nullptr;// [top_m]
+    int *order = nullptr;        // [K]
+    double *cost = nullptr;      // [K]
+    double *heap_cost = nullptr; // [2*top_m + 2]
+    int *heap_node = nullptr;    // [2*top_m + 2]
+    uint64_t *node_mask = nullptr; // [(2*top_m + 2) * ceil(K/64)] flip sets
+    int *node_last = nullptr;    // [2*top_m + 2]
+    int cap_S = 0, cap_M = 0;
+};
+void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m, cudaStream_t st);
+
+// Occupancy-based persistent grid sizes.
+void configure_grids(Problem &P, int sm_count);
+
+}  // namespace xrdvi

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of the xrdvi C ABI (``include/xrdvi.h``).
+
+Argument marshalling only: every step of the fit, the profile and the
+posterior runs in the CUDA library.  Functions carry the C names; ``Context``
+is a small owner object around the opaque handle.  If the library is missing
+and cannot be built, importing anything that needs it raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EBUSY"}
+FLAG_BF16_INT = 1 << 0
+FLAG_NAIVE_SUM = 1 << 1
+
+
+class XrdviError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"xrdvi {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("offsets", ctypes.POINTER(ctypes.c_int32)),
+                ("pos_deg", ctypes.POINTER(ctypes.c_float)), ("rel_int", ctypes.POINTER(ctypes.c_float))]
+
+
+class Pattern(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("x_deg", ctypes.POINTER(ctypes.c_float)),
+                ("y_counts", ctypes.POINTER(ctypes.c_float)), ("bg", ctypes.POINTER(ctypes.c_float))]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint32), ("S", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("prior_mu_sd", ctypes.c_float),
+                ("prior_alpha_mean", ctypes.c_float), ("prior_alpha_sd", ctypes.c_float),
+                ("prior_w_shape", ctypes.c_float), ("prior_w_rate", ctypes.c_float),
+                ("alpha_min", ctypes.c_float), ("init_h_frac", ctypes.c_float),
+                ("init_sigma", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("N", ctypes.c_int32), ("S", ctypes.c_int32),
+                ("M_total", ctypes.c_int32), ("step", ctypes.c_int64), ("eta", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("data_const", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("point_tiles", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.POINTER
+_f, _d, _i32, _u64 = ctypes.c_float, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); every function declared in include/xrdvi.h
+SIGNATURES = {
+    "xrdvi_config_default": (None, [P(Config)]),
+    "xrdvi_create": (ctypes.c_int, [P(Peaks), P(Pattern), P(Config), P(_vp)]),
+    "xrdvi_destroy": (None, [_vp]),
+    "xrdvi_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "xrdvi_fit": (ctypes.c_int, [_vp, _i32, P(_d)]),
+    "xrdvi_elbo_grad": (ctypes.c_int, [_vp, P(_f), P(_d), P(_f), P(_f), P(_d), P(_d)]),
+    "xrdvi_posterior": (ctypes.c_int, [_vp, _i32, _u64, _i32, P(_d), P(_u64), P(_d), P(_d), P(_d), P(_d)]),
+    "xrdvi_get_params": (ctypes.c_int, [_vp, P(_f), P(_f)]),
+    "xrdvi_set_params": (ctypes.c_int, [_vp, P(_f), P(_f)]),
+    "xrdvi_get_state": (ctypes.c_int, [_vp, _vp, P(ctypes.c_size_t)]),
+    "xrdvi_set_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "xrdvi_get_info": (ctypes.c_int, [_vp, P(Info)]),
+    "xrdvi_forward_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "xrdvi_backward_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "xrdvi_profile_steps": (ctypes.c_int, [_vp, _i32, P(_f)]),
+    "xrdvi_last_error": (ctypes.c_char_p, []),
+    "xrdvi_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("xrdvi CUDA library is missing and could not be built")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        msg = lib().xrdvi_last_error().decode(errors="replace")
+        raise XrdviError(status, msg)
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(P(ct))
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def xrdvi_config_default(**overrides) -> Config:
+    cfg = Config()
+    lib().xrdvi_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def xrdvi_create(offsets, pos, inten, x, y, bg, cfg: Config):
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    pos, inten, x, y, bg = map(_f32, (pos, inten, x, y, bg))
+    pk = Peaks(len(offsets) - 1, _ptr(offsets, ctypes.c_int32), _ptr(pos, _f), _ptr(inten, _f))
+    pt = Pattern(len(x), _ptr(x, _f), _ptr(y, _f), _ptr(bg, _f))
+    h = _vp()
+    _check(lib().xrdvi_create(ctypes.byref(pk), ctypes.byref(pt), ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def xrdvi_destroy(h):
+    if h:
+        lib().xrdvi_destroy(h)
+
+
+def xrdvi_set_stream(h, stream_handle):
+    _check(lib().xrdvi_set_stream(h, _vp(stream_handle) if stream_handle else None))
+
+
+def xrdvi_fit(h, iters, trace=True):
+    tr = np.zeros(max(iters, 1), dtype=np.float64) if trace else None
+    _check(lib().xrdvi_fit(h, int(iters), _ptr(tr, _d) if trace else None))
+    return tr[:iters] if trace else None
+
+
+def xrdvi_get_info(h) -> Info:
+    info = Info()
+    _check(lib().xrdvi_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def xrdvi_elbo_grad(h, eps=None, want_f=False, want_grad=True):
+    info = xrdvi_get_info(h)
+    S, K, N = info.S, info.K, info.N
+    e = None if eps is None else _f32(eps).reshape(S, K, 5)
+    elbo = ctypes.c_double(0.0)
+    grad = np.zeros((K, 10), dtype=np.float32)
+    f = np.zeros((S, N), dtype=np.float32) if want_f else None
+    ll = np.zeros(S)
+    lpj = np.zeros(S)
+    _check(lib().xrdvi_elbo_grad(h, _ptr(e, _f) if e is not None else None, ctypes.byref(elbo),
+                                 _ptr(grad, _f) if want_grad else None,
+                                 _ptr(f, _f) if want_f else None, _ptr(ll, _d), _ptr(lpj, _d)))
+    out = {"elbo": elbo.value, "grad": grad, "ll": ll, "lpj": lpj}
+    if want_f:
+        out["f"] = f
+    return out
+
+
+def xrdvi_posterior(h, S_post, seed, top_m=8):
+    info = xrdvi_get_info(h)
+    K = info.K
+    W = (K + 63) // 64
+    pi = np.zeros(K)
+    combos = np.zeros((top_m, W), dtype=np.uint64)
+    clp = np.zeros(top_m)
+    le, ess, cov = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().xrdvi_posterior(h, int(S_post), int(seed), int(top_m), _ptr(pi, _d),
+                                 _ptr(combos, ctypes.c_uint64), _ptr(clp, _d), ctypes.byref(le),
+                                 ctypes.byref(ess), ctypes.byref(cov)))
+    bits = np.zeros((top_m, K), dtype=bool)
+    for k in range(K):
+        bits[:, k] = (combos[:, k // 64] >> np.uint64(k % 64)) & np.uint64(1)
+    return {"pi": pi, "combos": bits, "combo_words": combos, "combo_logp": clp,
+            "log_evidence": le.value, "ess": ess.value, "coverage_log": cov.value}
+
+
+def xrdvi_get_params(h):
+    K = xrdvi_get_info(h).K
+    loc = np.zeros((K, 5), dtype=np.float32)
+    raw = np.zeros((K, 5), dtype=np.float32)
+    _check(lib().xrdvi_get_params(h, _ptr(loc, _f), _ptr(raw, _f)))
+    return loc, raw
+
+
+def xrdvi_set_params(h, loc, raw):
+    loc, raw = _f32(loc), _f32(raw)
+    _check(lib().xrdvi_set_params(h, _ptr(loc, _f), _ptr(raw, _f)))
+
+
+def xrdvi_get_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().xrdvi_get_state(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().xrdvi_get_state(h, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def xrdvi_set_state(h, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(lib().xrdvi_set_state(h, buf, len(state)))
+
+
+def xrdvi_forward_dev(h, loc_ptr, raw_ptr, eps_ptr, elbo_ptr):
+    _check(lib().xrdvi_forward_dev(h, _vp(loc_ptr), _vp(raw_ptr), _vp(eps_ptr), _vp(elbo_ptr)))
+
+
+def xrdvi_backward_dev(h, loc_ptr, raw_ptr, eps_ptr, grad_ptr):
+    _check(lib().xrdvi_backward_dev(h, _vp(loc_ptr), _vp(raw_ptr), _vp(eps_ptr), _vp(grad_ptr)))
+
+
+KERNELS = ("sample", "forward", "backward", "grad_adam", "elbo")
+
+
+def xrdvi_profile_steps(h, steps):
+    ms = np.zeros(5, dtype=np.float32)
+    _check(lib().xrdvi_profile_steps(h, int(steps), _ptr(ms, _f)))
+    return dict(zip(KERNELS, ms.astype(float)))
+
+
+def xrdvi_version() -> str:
+    return lib().xrdvi_version().decode()
+
+
+class Context:
+    """Owner of one fit (a problem, its device state and its q)."""
+
+    def __init__(self, offsets, pos, inten, x, y, bg, cfg: Config | None = None, **cfg_overrides):
+        if cfg is None:
+            cfg = xrdvi_config_default(**cfg_overrides)
+        self.cfg = cfg
+        self.h = xrdvi_create(offsets, pos, inten, x, y, bg, cfg)
+
+    @classmethod
+    def from_instance(cls, inst, **cfg_overrides):
+        cfg_overrides.setdefault("S", inst.S)
+        return cls(inst.offsets, inst.pos, inst.inten, inst.x, inst.y, inst.bg, **cfg_overrides)
+
+    def close(self):
+        if getattr(self, "h", None):
+            xrdvi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def info(self) -> Info:
+        return xrdvi_get_info(self.h)
+
+    def fit(self, iters, trace=True):
+        return xrdvi_fit(self.h, iters, trace)
+
+    def elbo_grad(self, eps=None, want_f=False):
+        return xrdvi_elbo_grad(self.h, eps, want_f)
+
+    def posterior(self, S_post, seed, top_m=8):
+        return xrdvi_posterior(self.h, S_post, seed, top_m)
+
+    def params(self):
+        return xrdvi_get_params(self.h)
+
+    def set_params(self, loc, raw):
+        xrdvi_set_params(self.h, loc, raw)
+
+    def state(self) -> bytes:
+        return xrdvi_get_state(self.h)
+
+    def set_state(self, s: bytes):
+        xrdvi_set_state(self.h, s)
+
+    def profile_steps(self, steps):
+        return xrdvi_profile_steps(self.h, steps)
+
+    def set_stream(self, stream_handle):
+        xrdvi_set_stream(self.h, stream_handle)
