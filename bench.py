@@ -248,9 +248,11 @@ def main():
     ctx.set_stream(stream.cuda_stream)
     init_state = ctx.state()
 
+    n_prof = max(1, min(PROFILE_STEPS, iters // 2))
+
     def one_step(prof):
-        ctx.fit(iters - (PROFILE_STEPS if prof else 0), trace=False)
-        k = ctx.profile_steps(PROFILE_STEPS) if prof else None
+        ctx.fit(iters - (n_prof if prof else 0), trace=False)
+        k = ctx.profile_steps(n_prof) if prof else None
         post = ctx.posterior(S_POST, 77, TOP_M)
         return k, post
 

@@ -113,8 +113,9 @@ xrdvi_status xrdvi_create(const xrdvi_peaks *peaks, const xrdvi_pattern *pattern
 /* Frees the context and all of its device memory (NULL is a no-op). */
 void xrdvi_destroy(xrdvi_ctx *ctx);
 
-/* Runs subsequent work on `cuda_stream` (a cudaStream_t; NULL restores the
- * context's own stream).  The CUDA-graph of the fit step is re-captured. */
+/* Runs subsequent work on `cuda_stream`, a cudaStream_t (cudaStreamLegacy
+ * and cudaStreamPerThread are accepted); NULL selects the context's own
+ * non-blocking stream (the default).  Waits for the previous stream first. */
 xrdvi_status xrdvi_set_stream(xrdvi_ctx *ctx, void *cuda_stream);
 
 /* Stochastic variational inference (Sec. 3.2): `iters` steps of

@@ -160,11 +160,13 @@ void enqueue_step(xrdvi_ctx *c, cudaStream_t st) {
                 c->v, c->iter, c->step, c->ent, c->elbo, c->trace, st);
 }
 
+// Captured on the context's private stream (capturable in every case); the
+// executable graph is then launched onto whichever stream the context uses.
 xrdvi_status capture(xrdvi_ctx *c, int steps, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
-    XR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < steps; ++i) enqueue_step(c, c->stream);
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    XR_CUDA(cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < steps; ++i) enqueue_step(c, c->own_stream);
+    cudaError_t e = cudaStreamEndCapture(c->own_stream, &g);
     if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
@@ -365,7 +367,6 @@ void xrdvi_destroy(xrdvi_ctx *c) { delete c; }
 xrdvi_status xrdvi_set_stream(xrdvi_ctx *c, void *stream) {
     if (!c) return fail(XRDVI_EINVAL, "null context");
     XR_CUDA(cudaStreamSynchronize(c->stream));
-    c->drop_graphs();
     c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
     return XRDVI_OK;
 }

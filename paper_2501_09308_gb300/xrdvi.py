@@ -137,8 +137,17 @@ def xrdvi_destroy(h):
         lib().xrdvi_destroy(h)
 
 
+CUDA_STREAM_LEGACY = 0x1
+
+
 def xrdvi_set_stream(h, stream_handle):
-    _check(lib().xrdvi_set_stream(h, _vp(stream_handle) if stream_handle else None))
+    """stream_handle: a cudaStream_t as an int.  0 (the legacy default
+    stream, e.g. torch's default stream) maps to cudaStreamLegacy; None selects
+    the context's own stream."""
+    if stream_handle is None:
+        _check(lib().xrdvi_set_stream(h, None))
+    else:
+        _check(lib().xrdvi_set_stream(h, _vp(stream_handle or CUDA_STREAM_LEGACY)))
 
 
 def xrdvi_fit(h, iters, trace=True):
