@@ -784,9 +784,13 @@ __global__ void k_post_topm(PostArgs a) {
 // ---------------------------------------------------------------------------
 void configure_grids(Problem &P, int sm_count) {
     P.smem = static_cast<size_t>(P.Mtot) * sizeof(float2) + static_cast<size_t>(P.K + 1) * sizeof(int);
-    cudaFuncSetAttribute(k_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P.smem));
-    cudaFuncSetAttribute(k_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P.smem));
-    cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P.smem));
+    // The attribute is per function, shared by every context: always allow the
+    // largest table any context may have, never the current problem's size.
+    const int smax = static_cast<int>(static_cast<size_t>(kMaxPeaks) * sizeof(float2) +
+                                      static_cast<size_t>(kMaxK + 1) * sizeof(int));
+    cudaFuncSetAttribute(k_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     int bf = 1, bb = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward<false>, kThreads, P.smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_backward, kThreads, P.smem);

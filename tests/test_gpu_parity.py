@@ -250,3 +250,18 @@ def test_recovery_tiny_config():
     ctx.close()
     top = set(np.flatnonzero(res["combos"][0]).tolist())
     assert top == set(inst.planted.tolist()), (res["pi"], inst.planted)
+
+
+def test_contexts_with_different_table_sizes_coexist():
+    """A context with a large peak table keeps working after a context with a
+    small table is created (the kernels' shared-memory limit is global)."""
+    big = synth.small_problem(K=40, M=60, N=500, S=4, seed=41)
+    small = synth.small_problem(K=2, M=3, N=200, S=4, seed=42)
+    cb = xrdvi.Context.from_instance(big, S=4)
+    e1 = cb.elbo_grad(synth.normals(1, 4, big.K))["elbo"]
+    cs = xrdvi.Context.from_instance(small, S=4)
+    cs.elbo_grad(synth.normals(2, 4, small.K))
+    e2 = cb.elbo_grad(synth.normals(1, 4, big.K))["elbo"]
+    cb.close()
+    cs.close()
+    assert e1 == e2
