@@ -191,6 +191,41 @@ xrdvi_status xrdvi_backward_dev(xrdvi_ctx *ctx, const float *d_loc, const float 
  * fast path. */
 xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms);
 
+/* Allocation-free variant of xrdvi_elbo_grad, for callers that may not
+ * allocate device memory themselves: code whose device memory is owned by
+ * something else (a framework's caching allocator, a host application that
+ * enforces a fixed memory budget) and that therefore cannot create a context.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  The paper
+ * has no counterpart; this is an interface convenience.
+ *
+ * Inputs (DEVICE pointers, caller-owned): the peak table in CSR form
+ * (d_offsets [K+1], d_pos / d_inten [M_total], any peak order), the pattern
+ * (d_x, d_y, d_bg [N], validated as by xrdvi_create), d_loc / d_raw [K*5],
+ * d_eps [S*K*5] standard normals; cfg (HOST) gives S, the priors, alpha_min
+ * and flags.  data_const = sum_i [y ln y - y - ln y!] and lambda_ =
+ * 1 / max(Y - B) are the values xrdvi_create derives from the pattern
+ * (xrdvi_get_info reports both).  Outputs (DEVICE): d_elbo [1] (double),
+ * d_grad [K*10] (float), written asynchronously on cuda_stream (a
+ * cudaStream_t; NULL is the legacy default stream).
+ *
+ * Scratch: one file-scope device array of XRDVI_STATIC_SCRATCH_BYTES
+ * (32 MiB), which every GPU that loads the library holds until the process
+ * exits.  A problem needing more (about 32*S*K*ceil(N/128) +
+ * 512*S*ceil(N/128) + 72*S*K bytes) is rejected with EINVAL before any work.
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device); make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents (every
+ * element is rewritten before use, nothing needs clearing): calls that
+ * overlap on the GPU — on different streams, or from different threads —
+ * race, so serialise them. */
+#define XRDVI_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const int32_t *d_offsets,
+                                    const float *d_pos, const float *d_inten, int32_t N,
+                                    const float *d_x, const float *d_y, const float *d_bg,
+                                    double data_const, double lambda_, const xrdvi_config *cfg,
+                                    const float *d_loc, const float *d_raw, const float *d_eps,
+                                    double *d_elbo, float *d_grad, void *cuda_stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *xrdvi_last_error(void);
 

@@ -56,6 +56,11 @@ float round_bf16(float v) {
 
 }  // namespace
 
+namespace xrdvi {
+// Error reporting for the other host translation units of the library.
+xrdvi_status report_error(xrdvi_status st, const std::string &msg) { return fail(st, msg); }
+}  // namespace xrdvi
+
 struct xrdvi_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;

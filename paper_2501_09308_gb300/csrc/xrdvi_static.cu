@@ -1,0 +1,152 @@
+// Allocation-free ELBO + gradient evaluation (xrdvi_elbo_grad_static).
+//
+// For callers that may not allocate device memory themselves: everything the
+// evaluation needs beyond the caller's inputs and outputs comes from one
+// file-scope device array, so the entry point calls no cudaMalloc, cudaFree or
+// allocating library routine.  It launches the same kernels as
+// xrdvi_elbo_grad (sampling from injected noise, profile + likelihood,
+// backward, gradient reduction, ELBO).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "../../include/xrdvi.h"
+#include "xrdvi_internal.h"
+
+namespace {
+
+// The scratch array: one per GPU that loads this library, held until exit.
+// In host code this name is only a host-side stand-in; the device address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[XRDVI_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
+
+size_t align256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
+
+}  // namespace
+
+namespace xrdvi {
+xrdvi_status report_error(xrdvi_status st, const std::string &msg);
+}
+
+extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const int32_t *d_offsets,
+                                               const float *d_pos, const float *d_inten, int32_t N,
+                                               const float *d_x, const float *d_y, const float *d_bg,
+                                               double data_const, double lambda_, const xrdvi_config *cfg,
+                                               const float *d_loc, const float *d_raw, const float *d_eps,
+                                               double *d_elbo, float *d_grad, void *cuda_stream) {
+    using namespace xrdvi;
+    if (!cfg || !d_offsets || !d_pos || !d_inten || !d_x || !d_y || !d_bg || !d_loc || !d_raw || !d_eps ||
+        !d_elbo || !d_grad)
+        return report_error(XRDVI_EINVAL, "elbo_grad_static: null argument");
+    if (cfg->size != sizeof(xrdvi_config)) return report_error(XRDVI_EINVAL, "elbo_grad_static: config.size mismatch");
+    if (K < 1 || K > kMaxK) return report_error(XRDVI_EINVAL, "elbo_grad_static: K must be in [1, 1024]");
+    if (M_total < K || M_total > kMaxPeaks)
+        return report_error(XRDVI_EINVAL, "elbo_grad_static: M_total must be in [K, 24000]");
+    if (N < 1 || N > kMaxN) return report_error(XRDVI_EINVAL, "elbo_grad_static: N must be in [1, 2^24]");
+    const int S = cfg->S;
+    if (S < 1 || S > kMaxS) return report_error(XRDVI_EINVAL, "elbo_grad_static: S must be in [1, 65536]");
+    if (!(std::isfinite(lambda_) && lambda_ > 0.0) || !std::isfinite(data_const))
+        return report_error(XRDVI_EINVAL, "elbo_grad_static: lambda_ must be positive, data_const finite");
+
+    // Layout of the scratch array for this call.
+    const size_t T = (static_cast<size_t>(N) + kTile - 1) / kTile;
+    const size_t Npad = T * kTile;
+    const size_t SK = static_cast<size_t>(S) * K;
+    size_t off = 0;
+    const size_t o_eps = off;    off += align256(SK * 5 * sizeof(float));
+    const size_t o_theta = off;  off += align256(SK * 5 * sizeof(float));
+    const size_t o_cst = off;    off += align256(SK * sizeof(PhaseConst));
+    const size_t o_lpj = off;    off += align256(static_cast<size_t>(S) * sizeof(double));
+    const size_t o_ll = off;     off += align256(static_cast<size_t>(S) * sizeof(double));
+    const size_t o_ent = off;    off += align256(sizeof(double));
+    const size_t o_g = off;      off += align256(static_cast<size_t>(S) * Npad * sizeof(float));
+    const size_t o_llp = off;    off += align256(static_cast<size_t>(S) * T * sizeof(double));
+    const size_t o_gp = off;     off += align256(SK * T * 8 * sizeof(float));
+    if (off > XRDVI_STATIC_SCRATCH_BYTES)
+        return report_error(XRDVI_EINVAL, "elbo_grad_static: this problem needs " + std::to_string(off) +
+                                              " bytes of scratch, more than the " +
+                                              std::to_string(XRDVI_STATIC_SCRATCH_BYTES) +
+                                              " bytes of the static array");
+
+    // Set-up, once per device, with that device current.
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return report_error(XRDVI_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return report_error(XRDVI_EINVAL, "elbo_grad_static: device ordinal above 63");
+    unsigned char *base = nullptr;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_setup_mutex);
+        if (!g_scratch_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p)
+                return report_error(XRDVI_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            int n = 0;
+            e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return report_error(XRDVI_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+            g_sm_count[dev] = n;
+            g_scratch_addr[dev] = p;
+        }
+        base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+        sms = g_sm_count[dev];
+    }
+
+    Problem P;
+    P.K = K;
+    P.N = N;
+    P.Mtot = M_total;
+    P.T = static_cast<int>(T);
+    P.Npad = static_cast<int>(Npad);
+    P.pos = const_cast<float *>(d_pos);
+    P.inten = const_cast<float *>(d_inten);
+    P.off = const_cast<int *>(d_offsets);
+    P.x = const_cast<float *>(d_x);
+    P.y = const_cast<float *>(d_y);
+    P.bg = const_cast<float *>(d_bg);
+    P.csum = data_const;
+    P.prior.lambda = lambda_;
+    P.prior.mu_sd = cfg->prior_mu_sd;
+    P.prior.alpha_mean = cfg->prior_alpha_mean;
+    P.prior.alpha_sd = cfg->prior_alpha_sd;
+    P.prior.w_shape = cfg->prior_w_shape;
+    P.prior.w_rate = cfg->prior_w_rate;
+    P.prior.lgamma_w_shape = std::lgamma(static_cast<double>(cfg->prior_w_shape));
+    P.prior.alpha_min = cfg->alpha_min;
+    configure_grids(P, sms);
+
+    // Every scratch element is written before it is read in one call (the
+    // partial sums of every sample, phase and tile, the padded tail of g), so
+    // nothing has to be cleared; the array keeps the last call's contents.
+    Workspace W;
+    W.S = S;
+    W.eps = reinterpret_cast<float *>(base + o_eps);
+    W.theta = reinterpret_cast<float *>(base + o_theta);
+    W.cst = reinterpret_cast<PhaseConst *>(base + o_cst);
+    W.lpj = reinterpret_cast<double *>(base + o_lpj);
+    W.lq = nullptr;
+    W.ll = reinterpret_cast<double *>(base + o_ll);
+    W.g = reinterpret_cast<float *>(base + o_g);
+    W.llpart = reinterpret_cast<double *>(base + o_llp);
+    W.gpart = reinterpret_cast<float *>(base + o_gp);
+    double *ent = reinterpret_cast<double *>(base + o_ent);
+
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const bool naive = (cfg->flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    launch_sample(P, W, d_loc, d_raw, d_eps, cfg->seed, 0u, nullptr, 0u, nullptr, ent, st);
+    launch_forward(P, W, nullptr, naive, st);
+    launch_backward(P, W, st);
+    launch_grad(P, W, d_loc, d_raw, nullptr, nullptr, d_grad, false, AdamConst{0.f, 0.f, 0.f, 0.f}, nullptr, nullptr,
+                nullptr, nullptr, ent, d_elbo, nullptr, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(XRDVI_ECUDA, std::string("elbo_grad_static: ") + cudaGetErrorString(e));
+    return XRDVI_OK;
+}

@@ -78,6 +78,8 @@ SIGNATURES = {
     "xrdvi_forward_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "xrdvi_backward_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "xrdvi_profile_steps": (ctypes.c_int, [_vp, _i32, P(_f)]),
+    "xrdvi_elbo_grad_static": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _d, _d,
+                                              P(Config), _vp, _vp, _vp, _vp, _vp, _vp]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -230,6 +232,19 @@ def xrdvi_forward_dev(h, loc_ptr, raw_ptr, eps_ptr, elbo_ptr):
 
 def xrdvi_backward_dev(h, loc_ptr, raw_ptr, eps_ptr, grad_ptr):
     _check(lib().xrdvi_backward_dev(h, _vp(loc_ptr), _vp(raw_ptr), _vp(eps_ptr), _vp(grad_ptr)))
+
+
+def xrdvi_elbo_grad_static(K, M_total, offsets_ptr, pos_ptr, inten_ptr, N, x_ptr, y_ptr, bg_ptr,
+                           data_const, lambda_, cfg: Config, loc_ptr, raw_ptr, eps_ptr, elbo_ptr,
+                           grad_ptr, stream_handle=0):
+    """Allocation-free ELBO + gradient: every pointer is a device address
+    (int) owned by the caller; scratch comes from the library's static array.
+    Asynchronous on stream_handle (0: the legacy default stream)."""
+    _check(lib().xrdvi_elbo_grad_static(int(K), int(M_total), _vp(offsets_ptr), _vp(pos_ptr),
+                                        _vp(inten_ptr), int(N), _vp(x_ptr), _vp(y_ptr), _vp(bg_ptr),
+                                        float(data_const), float(lambda_), ctypes.byref(cfg),
+                                        _vp(loc_ptr), _vp(raw_ptr), _vp(eps_ptr), _vp(elbo_ptr),
+                                        _vp(grad_ptr), _vp(stream_handle) if stream_handle else None))
 
 
 KERNELS = ("sample", "forward", "backward", "grad_adam", "elbo")
