@@ -210,8 +210,8 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms
  *
  * Scratch: one file-scope device array of XRDVI_STATIC_SCRATCH_BYTES
  * (32 MiB), which every GPU that loads the library holds until the process
- * exits.  A problem needing more (about 32*S*K*ceil(N/128) +
- * 512*S*ceil(N/128) + 72*S*K bytes) is rejected with EINVAL before any work.
+ * exits.  A problem needing more (about 40*S*K*ceil(N/256) +
+ * 1032*S*ceil(N/256) + 72*S*K bytes) is rejected with EINVAL before any work.
  * The first call on a device looks up the array's device address (a one-time
  * set-up per device); make that first call before any stream capture.  All
  * calls share the one array and it keeps the last call's contents (every

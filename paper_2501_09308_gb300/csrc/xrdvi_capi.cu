@@ -81,6 +81,7 @@ struct xrdvi_ctx {
     size_t bytes = 0;
     std::vector<void *> allocs;
     std::vector<void *> post_allocs;
+    std::vector<int> host_off;   // CSR offsets (host copy, for work partitioning)
 
     template <class T>
     xrdvi_status alloc(T **p, size_t n, std::vector<void *> *list = nullptr) {
@@ -135,12 +136,16 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
     XR_TRY(c->alloc(&W.g, static_cast<size_t>(S) * P.Npad, list));
     XR_TRY(c->alloc(&W.llpart, static_cast<size_t>(S) * P.T, list));
     if (fit) {
-        XR_TRY(c->alloc(&W.gpart, SK * P.T * 8, list));
+        XR_TRY(c->alloc(&W.gpart, SK * P.T * kGradSums, list));
         W.lq = nullptr;
     } else {
         XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
         W.gpart = nullptr;
     }
+    choose_chunks(P, c->host_off.data(), S, W);
+    W.fpart_cap = static_cast<size_t>(W.C) * S * P.Npad;
+    XR_TRY(c->alloc(&W.fpart, W.fpart_cap, list));
+    XR_TRY(c->alloc(&W.counters, 2, list));
     W.bytes = c->bytes - before;
     return XRDVI_OK;
 }
@@ -326,6 +331,8 @@ xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const 
     XR_C(c->alloc(&P.y, N));
     XR_C(c->alloc(&P.bg, N));
     XR_C(c->alloc(&P.isum, K));
+    configure_grids(P, sms);
+    c->host_off.assign(pk->offsets, pk->offsets + K + 1);
     XR_C(alloc_workspace(c, c->W, cfg->S, true, nullptr));
     XR_C(c->alloc(&c->loc, K * 5));
     XR_C(c->alloc(&c->raw, K * 5));
@@ -359,7 +366,6 @@ xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const 
         cudaMemsetAsync(c->v, 0, K * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
         cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s))
         return bail(fail(XRDVI_ECUDA, "upload failed"));
-    configure_grids(P, sms);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return bail(fail(XRDVI_ECUDA, "create: device error"));
 #undef XR_C
@@ -500,6 +506,10 @@ xrdvi_status xrdvi_posterior(xrdvi_ctx *c, int32_t S_post, uint64_t seed, int32_
         c->Wp.bytes = c->bytes - before;
     }
     c->Wp.S = S_post;
+    {
+        const size_t per_chunk = static_cast<size_t>(S_post) * P.Npad;
+        choose_chunks(P, c->host_off.data(), S_post, c->Wp, static_cast<int>(c->Wp.fpart_cap / per_chunk));
+    }
     cudaStream_t st = c->stream;
     const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     launch_sample(P, c->Wp, c->loc, c->raw, nullptr, seed, 1u, nullptr, 0u, nullptr, nullptr, st);

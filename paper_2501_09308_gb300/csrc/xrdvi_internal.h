@@ -13,8 +13,13 @@ namespace xrdvi {
 // l, l+32, ..., l+32*(kPts-1) of the tile.
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kPts = 4;
+constexpr int kPts = 8;
 constexpr int kTile = 32 * kPts;
+// Gradient partial sums per (sample, phase, tile) written by the backward.
+constexpr int kGradSums = 10;
+// Phases are split into up to kMaxChunks chunks of similar peak count so that
+// the profile kernels have enough equal-sized work items to fill the GPU.
+constexpr int kMaxChunks = 8;
 
 // The Gaussian component 2^-u of a peak is evaluated only for warps with a
 // point inside the peak's reach u < kGaussU; beyond it 2^-u < 2^-128, which
@@ -28,20 +33,19 @@ constexpr int kMaxS = 65536;
 constexpr int kMaxN = 1 << 24;
 constexpr int kTraceCap = 1 << 16;   // ring buffer of ELBO values (power of two)
 
-// Per (sample, phase) constants of the profile kernels (32 bytes).  With
+// Per (sample, phase) constants of the profile kernels (64 bytes).  With
 // d = x - p - mu and side width w_side = w (d < 0) or alpha*w (d >= 0):
-//   c(d) = 4 / w_side^2,  u = c(d) d^2 = (2 d / w_side)^2,
-//   G = 2^-u = exp(-4 ln2 t^2),  L = 1 / (1 + u),  t = d / w_side.
-// c(d) d is formed without a select as a d + b |d| with a = (c_r + c_l)/2,
-// b = (c_r - c_l)/2 when the two sides differ by at most 4x (alpha in
-// [0.5, 2]: the cancellation costs at most a factor 4 in rounding error);
-// otherwise (split = 1) a = c_l, b = c_r and the side is selected by sign.
+//   s(d) = 2 / w_side,  t = s(d) d,  u = t^2 = (2 d / w_side)^2,
+//   G = 2^-u = exp(-4 ln2 (d/w_side)^2),  L = 1 / (1 + u).
+// On ranges where every point lies on one side of the peak,
+// t = s_side (x - p) + (-s_side mu) with the side's sl / sr and nslmu / nsrmu.
 struct __align__(16) PhaseConst {
-    float mu;      // peak shift
-    float a, b;    // see above
-    float hl, hg;  // h * r, h * (1 - r)
-    float rl, rr;  // Gaussian reach left / right of the peak (degrees)
-    int split;     // 0: a d + b |d| form, 1: explicit side select
+    float mu;            // peak shift
+    float hl, hg;        // h * r, h * (1 - r)
+    float rl, rr;        // Gaussian reach left / right of the peak (degrees)
+    float sl, sr;        // 2 / w (d < 0), 2 / (alpha w) (d >= 0)
+    float nslmu, nsrmu;  // -sl * mu, -sr * mu
+    float pad[7];
 };
 
 struct PriorConst {
@@ -63,7 +67,12 @@ struct Workspace {
     double *ll = nullptr;        // [S] log-likelihood
     float *g = nullptr;          // [S*Npad] y/f - 1 (0 on padding)
     double *llpart = nullptr;    // [S*T] deviance partial sums per tile
-    float *gpart = nullptr;      // [S*K*T*8] gradient partial sums (fit only)
+    float *gpart = nullptr;      // [S*K*T*kGradSums] gradient partial sums (fit only)
+    float *fpart = nullptr;      // [C*S*Npad] partial profiles per phase chunk
+    int *counters = nullptr;     // [2] work counters of the profile kernels
+    size_t fpart_cap = 0;        // elements allocated for fpart
+    int C = 1;                   // phase chunks
+    int chunk[kMaxChunks + 1] = {0};
     size_t bytes = 0;
 };
 
@@ -118,5 +127,9 @@ void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m,
 
 // Occupancy-based persistent grid sizes.
 void configure_grids(Problem &P, int sm_count);
+// Phase chunks for a sample set of S samples: enough work items for about
+// four per resident warp, chunk boundaries balancing the peak counts
+// (offsets: host copy of the CSR offsets, K+1 entries).
+void choose_chunks(const Problem &P, const int *offsets, int S, Workspace &W, int max_chunks = kMaxChunks);
 
 }  // namespace xrdvi

@@ -136,13 +136,18 @@ struct SampleArgs {
     float *eps, *theta;
     PhaseConst *cst;
     double *lpj, *lq;
+    int *counters;
 };
 
 __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
     __shared__ double sh[4];
     const int s = blockIdx.x;
     const uint32_t step = a.d_step ? static_cast<uint32_t>(*a.d_step) : a.step;
-    if (s == 0 && threadIdx.x == 0 && a.d_iter) *a.d_iter = static_cast<int>(step);
+    if (s == 0 && threadIdx.x == 0) {
+        if (a.d_iter) *a.d_iter = static_cast<int>(step);
+        a.counters[0] = 0;  // work counters of the profile kernels that follow
+        a.counters[1] = 0;
+    }
     const float sq = sqrtf(kGaussU);
     double acc = 0.0, accq = 0.0;
     for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
@@ -187,16 +192,18 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         a.theta[base + 4] = al;
         const float ac = al > static_cast<float>(a.pr.alpha_min) ? al : static_cast<float>(a.pr.alpha_min);
         const float wl = w, wr = ac * w;
-        const float cl = 4.0f / (wl * wl), cr = 4.0f / (wr * wr);
+        const float sl = 2.0f / wl, sr = 2.0f / wr;
         PhaseConst pc;
         pc.mu = mu;
-        pc.split = (ac >= 0.5f && ac <= 2.0f) ? 0 : 1;
-        pc.a = pc.split ? cl : 0.5f * (cr + cl);
-        pc.b = pc.split ? cr : 0.5f * (cr - cl);
         pc.hl = h * r;
         pc.hg = h * (1.0f - r);
         pc.rl = 0.5f * sq * wl;
         pc.rr = 0.5f * sq * wr;
+        pc.sl = sl;
+        pc.sr = sr;
+        pc.nslmu = -sl * mu;
+        pc.nsrmu = -sr * mu;
+        pc.pad[0] = pc.pad[1] = pc.pad[2] = pc.pad[3] = pc.pad[4] = pc.pad[5] = pc.pad[6] = 0.f;
         a.cst[static_cast<size_t>(s) * a.K + k] = pc;
         // log prior (Sec. 2.2, Appendix B.2) + log Jacobian of the transform
         const double hd = h, mud = mu, wd = w, ald = al;
@@ -234,8 +241,27 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
 // ---------------------------------------------------------------------------
 // Profile kernels
 // ---------------------------------------------------------------------------
+//
+// Work item: one warp owns (sample s, tile of kTile consecutive points, chunk
+// c of the phases); lane l holds points i0 + l + 32 j, j < kPts, as kPts/2
+// packed pairs (points 2q and 2q+1 of the lane in one 64-bit register).
+// Items are taken from an atomic work counter (reset by k_sample), so every SM
+// stays busy until the queue drains.
+//
+// With d = x - p - mu and s(d) = 2 / w_side, t = s(d) d, u = t^2,
+// L = 1 / (1 + u), G = 2^-u.  Peaks are sorted by position within a phase, so
+// for one tile [xlo, xhi] the peaks of a phase fall into three contiguous
+// index ranges: peaks left of every point (all d > 0, the right-hand width
+// applies), peaks among the points (side decided per point), peaks right of
+// every point (all d < 0).  On the side-uniform ranges s is a constant and
+//   t = fma(s, x - p, -s mu)
+// (x - p is exact near the peak, so t keeps full precision there); on the
+// mixed range d = (x - p) - mu and the side's scale is selected per point.  The
+// Gaussian is evaluated only on the peaks within its reach of the tile (found
+// by binary search), beyond which 2^-u < 2^-128 is zero in FP32.
 struct ProfArgs {
-    int S, K, N, Npad, T, Mtot;
+    int S, K, N, Npad, T, Mtot, C;
+    int chunk[kMaxChunks + 1];  // phase boundaries of the C chunks
     const float *pos, *inten;
     const int *off;
     const float *x, *y, *bg;
@@ -243,13 +269,261 @@ struct ProfArgs {
     float *g;          // [S*Npad]
     float *f_out;      // [S*N] or null
     double *llpart;    // [S*T]
-    float *gpart;      // [S*K*T*8]
+    float *gpart;      // [S*K*T*kGradSums]
+    float *fpart;      // [C*S*Npad] partial profiles per chunk
+    int *counter;      // work counter of this kernel (zeroed by k_sample)
 };
 
+typedef unsigned long long f2_t;   // two packed floats
+
+__device__ __forceinline__ f2_t pk2(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2_t bc2(float v) { return pk2(v, v); }
+
+__device__ __forceinline__ f2_t rcp2(f2_t v) {
+    float a, b;
+    up2(v, a, b);
+    return pk2(rcp_approx(a), rcp_approx(b));
+}
+
+__device__ __forceinline__ f2_t ex2neg2(f2_t u) {
+    float a, b;
+    up2(u, a, b);
+    return pk2(ex2_approx(-a), ex2_approx(-b));
+}
+
+constexpr int kPairs = kPts / 2;
+
+// Shared-memory table entry: (-p, I) so that x + (-p) is one packed add.
 __device__ __forceinline__ void load_table(const ProfArgs &a, float2 *s_pk, int *s_off) {
-    for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) s_pk[i] = make_float2(a.pos[i], a.inten[i]);
+    for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) s_pk[i] = make_float2(-a.pos[i], a.inten[i]);
     for (int i = threadIdx.x; i <= a.K; i += blockDim.x) s_off[i] = a.off[i];
     __syncthreads();
+}
+
+// First m in [lo, hi) whose position p satisfies p > bound (strict) or
+// p >= bound (kInclusive); positions ascend, so -p descends.
+template <bool kInclusive>
+__device__ __forceinline__ int first_beyond(const float2 *s_pk, int lo, int hi, float bound) {
+    const float nb = -bound;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float np = s_pk[mid].x;
+        const bool beyond = kInclusive ? (np <= nb) : (np < nb);
+        if (beyond) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Peak index ranges of one phase for one tile (see the header comment).
+struct Ranges {
+    int mb, m1, m2, me;   // [mb,m1) all d > 0, [m1,m2) mixed, [m2,me) all d < 0
+    int nb, ne;           // Gaussian reach
+};
+
+// Margin (degrees) keeping the side-uniform ranges clear of d = 0.
+constexpr float kSideMargin = 1e-4f;
+
+__device__ __forceinline__ Ranges phase_ranges(const float2 *s_pk, int mb, int me, const PhaseConst &c,
+                                               float xlo, float xhi) {
+    Ranges r;
+    r.mb = mb;
+    r.me = me;
+    r.m1 = first_beyond<true>(s_pk, mb, me, xlo - c.mu - kSideMargin);
+    r.m2 = first_beyond<false>(s_pk, r.m1, me, xhi - c.mu + kSideMargin);
+    // a peak's Gaussian reaches [xlo, xhi] iff xlo - mu - rr < p < xhi - mu + rl
+    r.nb = first_beyond<false>(s_pk, mb, me, xlo - c.mu - c.rr);
+    r.ne = first_beyond<true>(s_pk, r.nb, me, xhi - c.mu + c.rl);
+    return r;
+}
+
+// t = s(d) d for a packed pair on the mixed range: the side's scale is
+// selected per point (exact for any asymmetry).
+__device__ __forceinline__ f2_t t_mixed(f2_t x2, f2_t np, f2_t nmu2, float sl, float sr) {
+    const f2_t d2 = add2(add2(x2, np), nmu2);
+    float d0, d1;
+    up2(d2, d0, d1);
+    return mul2(d2, pk2(d0 >= 0.f ? sr : sl, d1 >= 0.f ? sr : sl));
+}
+
+// --- forward helpers --------------------------------------------------------
+// Lorentzian sums on a side-uniform range, one reciprocal per two peaks:
+// I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1)  (d = 1 + t^2; d0 d1 stays finite
+// while s |d| < 1e9).
+__device__ __forceinline__ void fwdL_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu,
+                                             const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs]) {
+    const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
+    int m = m0;
+    for (; m + 1 < m1; m += 2) {
+        const float2 pa = s_pk[m], pb = s_pk[m + 1];
+        const f2_t np0 = bc2(pa.x), I0 = bc2(pa.y), np1 = bc2(pb.x), I1 = bc2(pb.y);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t0 = fma2(s2, add2(x2[q], np0), c2);
+            const f2_t t1 = fma2(s2, add2(x2[q], np1), c2);
+            const f2_t d0 = fma2(t0, t0, one2), d1 = fma2(t1, t1, one2);
+            const f2_t num = fma2(I0, d1, mul2(I1, d0));
+            sl[q] = fma2(num, rcp2(mul2(d0, d1)), sl[q]);
+        }
+    }
+    if (m < m1) {
+        const float2 pa = s_pk[m];
+        const f2_t np = bc2(pa.x), I = bc2(pa.y);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+            sl[q] = fma2(I, rcp2(fma2(t, t, one2)), sl[q]);
+        }
+    }
+}
+
+// Lorentzian and Gaussian sums on the mixed range (peaks among the points).
+__device__ __forceinline__ void fwd_mixed(const float2 *s_pk, int m0, int m1, const PhaseConst &c,
+                                          const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
+    const f2_t nmu2 = bc2(-c.mu), one2 = bc2(1.f);
+    for (int m = m0; m < m1; ++m) {
+        const float2 pa = s_pk[m];
+        const f2_t np = bc2(pa.x), I = bc2(pa.y);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = t_mixed(x2[q], np, nmu2, c.sl, c.sr);
+            const f2_t u = mul2(t, t);
+            sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
+            sg[q] = fma2(I, ex2neg2(u), sg[q]);
+        }
+    }
+}
+
+__device__ __forceinline__ void fwdG_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu,
+                                             const f2_t (&x2)[kPairs], f2_t (&sg)[kPairs]) {
+    const f2_t s2 = bc2(sc), c2 = bc2(cmu);
+    for (int m = m0; m < m1; ++m) {
+        const float2 pa = s_pk[m];
+        const f2_t np = bc2(pa.x), I = bc2(pa.y);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+            sg[q] = fma2(I, ex2neg2(mul2(t, t)), sg[q]);
+        }
+    }
+}
+
+// One phase: the Lorentzian over every peak, the Gaussian over the peaks
+// within reach.  Each loop body exists once; the two side-uniform ranges run
+// the same body with their own constants, which keeps the kernel small.
+__device__ __forceinline__ void fwd_phase(const float2 *s_pk, const Ranges &r, const PhaseConst &c,
+                                          const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int m0 = side ? r.m2 : r.mb, m1 = side ? r.me : r.m1;
+        fwdL_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, x2, sl);
+    }
+    fwd_mixed(s_pk, r.m1, r.m2, c, x2, sl, sg);
+    if (r.nb < r.m1 || r.m2 < r.ne) {  // warp-uniform
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
+            fwdG_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, x2, sg);
+        }
+    }
+}
+
+__device__ __forceinline__ void item_points(const ProfArgs &a, int i0, int lane, f2_t (&x2)[kPairs],
+                                            float &xlo, float &xhi) {
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        const int i_a = min(i0 + (2 * q) * 32 + lane, a.N - 1);
+        const int i_b = min(i0 + (2 * q + 1) * 32 + lane, a.N - 1);
+        x2[q] = pk2(a.x[i_a], a.x[i_b]);
+    }
+    xlo = a.x[i0];
+    xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
+}
+
+__device__ __forceinline__ int next_item(int *counter, int lane) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// Partial profile of one phase chunk: fpart[c][s][i] = sum over the chunk's
+// phases of h_k sum_m I_m V (Neumaier-compensated over phases).
+template <bool kNaive>
+__global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
+    extern __shared__ float2 s_pk[];
+    int *s_off = reinterpret_cast<int *>(s_pk + a.Mtot);
+    load_table(a, s_pk, s_off);
+    const int lane = threadIdx.x & 31;
+    const int items = a.S * a.T * a.C;
+    for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
+        const int c = item % a.C;
+        const int st = item / a.C;
+        const int s = st / a.T, tile = st - s * a.T;
+        const int i0 = tile * kTile;
+        f2_t x2[kPairs];
+        float xlo, xhi;
+        item_points(a, i0, lane, x2, xlo, xhi);
+        float fs[kPts], fc[kPts];
+#pragma unroll
+        for (int j = 0; j < kPts; ++j) fs[j] = fc[j] = 0.f;
+        const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
+        const int kb = a.chunk[c], ke = a.chunk[c + 1];
+        for (int k = kb; k < ke; ++k) {
+            const PhaseConst cp = cs[k];
+            const Ranges r = phase_ranges(s_pk, s_off[k], s_off[k + 1], cp, xlo, xhi);
+            f2_t sl[kPairs], sg[kPairs];
+#pragma unroll
+            for (int q = 0; q < kPairs; ++q) sl[q] = sg[q] = 0ull;
+            fwd_phase(s_pk, r, cp, x2, sl, sg);
+            const f2_t hl2 = bc2(cp.hl), hg2 = bc2(cp.hg);
+#pragma unroll
+            for (int q = 0; q < kPairs; ++q) {
+                float v[2];
+                up2(fma2(hl2, sl[q], mul2(hg2, sg[q])), v[0], v[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * q + h;
+                    if (kNaive) {
+                        fs[j] += v[h];
+                    } else {
+                        // Neumaier compensated summation over phases
+                        const float t = fs[j] + v[h];
+                        fc[j] += (fabsf(fs[j]) >= fabsf(v[h])) ? ((fs[j] - t) + v[h]) : ((v[h] - t) + fs[j]);
+                        fs[j] = t;
+                    }
+                }
+            }
+        }
+        float *dst = a.fpart + (static_cast<size_t>(c) * a.S + s) * a.Npad + i0 + lane;
+#pragma unroll
+        for (int j = 0; j < kPts; ++j) dst[j * 32] = fs[j] + fc[j];
+    }
 }
 
 // Poisson log-likelihood term minus its data constant, D(y, f) =
@@ -271,188 +545,196 @@ __device__ __forceinline__ float deviance_term(float y, float f) {
     return -(y * logf(__fdiv_rn(y, f)) - dif);
 }
 
-// c(d) * d for one side-width form (see PhaseConst).
-template <bool kSplit>
-__device__ __forceinline__ float cd_of(const PhaseConst &c, float d) {
-    if (kSplit) return (d >= 0.f ? c.b : c.a) * d;
-    return fmaf(c.b, fabsf(d), c.a * d);
+// f = B + sum of the chunk partials (FP64, fixed order), then the deviance
+// term, g = y/f - 1 and the per-tile FP64 deviance sum.  One block per
+// (sample, tile); kTile == blockDim.x.
+__global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
+    __shared__ double sh[kTile / 32];
+    const int s = blockIdx.x / a.T, tile = blockIdx.x - s * a.T;
+    const int i = tile * kTile + threadIdx.x;
+    double dev = 0.0;
+    float gv = 0.f;
+    if (i < a.N) {
+        double fd = a.bg[i];
+        for (int c = 0; c < a.C; ++c) fd += a.fpart[(static_cast<size_t>(c) * a.S + s) * a.Npad + i];
+        const float f = static_cast<float>(fd);
+        const float yv = a.y[i];
+        dev = static_cast<double>(deviance_term(yv, f));
+        gv = (yv > 0.f) ? __fdiv_rn(yv, f) - 1.0f : -1.0f;
+        if (a.f_out) a.f_out[static_cast<size_t>(s) * a.N + i] = f;
+    }
+    a.g[static_cast<size_t>(s) * a.Npad + i] = gv;
+    dev = block_sum(dev, sh);
+    if (threadIdx.x == 0) a.llpart[static_cast<size_t>(s) * a.T + tile] = dev;
 }
 
-// Forward sums over the peaks [mb, me) of one phase: sl += I L, sg += I G.
-template <bool kSplit>
-__device__ __forceinline__ void fwd_phase(const float2 *s_pk, int mb, int me, const PhaseConst &c,
-                                          float plo, float phi, const float (&xj)[kPts],
-                                          float (&sl)[kPts], float (&sg)[kPts]) {
-    for (int m = mb; m < me; ++m) {
-        const float2 pk = s_pk[m];
-        float u[kPts];
+// --- backward helpers -------------------------------------------------------
+// Accumulators (packed pairs, per lane), with q = (y/f - 1) I:
+//   0 S1G = sum q G          1 S1L = sum q L
+//   2 AG  = sum q G t        3 AL  = sum q L^2 t
+//   4 AGs = sum q G |t|      5 ALs = sum q L^2 |t|
+//   6 BG  = sum q G t^2      7 BL  = sum q L^2 t^2
+//   8 BGs = sum q G t|t|     9 BLs = sum q L^2 t|t|
+// (t carries the sign of d, so the |t| sums separate the two sides; on a
+// side-uniform range |t| = +-t and those sums follow from the plain ones).
+
+// Lorentzian part on a side-uniform range (sgn = +1: all d > 0, -1: all d < 0).
+__device__ __forceinline__ void bwdL_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu, bool right,
+                                             const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
+                                             f2_t (&acc)[kGradSums]) {
+    if (m0 >= m1) return;
+    const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
+    f2_t S1 = 0ull, A = 0ull, B = 0ull;
+    for (int m = m0; m < m1; ++m) {
+        const float2 pa = s_pk[m];
+        const f2_t np = bc2(pa.x), I = bc2(pa.y);
 #pragma unroll
-        for (int j = 0; j < kPts; ++j) {
-            const float d = (xj[j] - pk.x) - c.mu;
-            u[j] = d * cd_of<kSplit>(c, d);
-            sl[j] = fmaf(pk.y, rcp_approx(u[j] + 1.0f), sl[j]);
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+            const f2_t L = rcp2(fma2(t, t, one2));
+            const f2_t q1 = mul2(mul2(g2[q], I), L);
+            S1 = add2(S1, q1);
+            const f2_t q2 = mul2(q1, L);
+            A = fma2(q2, t, A);
+            B = fma2(mul2(q2, t), t, B);
         }
-        if (pk.x > plo && pk.x < phi) {  // warp-uniform
+    }
+    acc[1] = add2(acc[1], S1);
+    acc[3] = add2(acc[3], A);
+    acc[7] = add2(acc[7], B);
+    acc[5] = right ? add2(acc[5], A) : sub2(acc[5], A);
+    acc[9] = right ? add2(acc[9], B) : sub2(acc[9], B);
+}
+
+// Accumulate v * |t| into a packed pair of sums (scalar FMAs: |t| is a free
+// operand modifier of the scalar instruction).
+__device__ __forceinline__ f2_t fma_abs2(f2_t v, f2_t t, f2_t acc) {
+    float t0, t1, v0, v1, a0, a1;
+    up2(t, t0, t1);
+    up2(v, v0, v1);
+    up2(acc, a0, a1);
+    return pk2(fmaf(v0, fabsf(t0), a0), fmaf(v1, fabsf(t1), a1));
+}
+
+// Both components on the mixed range (peaks among the points).
+__device__ __forceinline__ void bwd_mixed(const float2 *s_pk, int m0, int m1, const PhaseConst &c,
+                                          const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
+                                          f2_t (&acc)[kGradSums]) {
+    const f2_t nmu2 = bc2(-c.mu), one2 = bc2(1.f);
+    for (int m = m0; m < m1; ++m) {
+        const float2 pa = s_pk[m];
+        const f2_t np = bc2(pa.x), I = bc2(pa.y);
 #pragma unroll
-            for (int j = 0; j < kPts; ++j) sg[j] = fmaf(pk.y, ex2_approx(-u[j]), sg[j]);
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = t_mixed(x2[q], np, nmu2, c.sl, c.sr);
+            const f2_t u = mul2(t, t);
+            const f2_t L = rcp2(add2(u, one2));
+            const f2_t gI = mul2(g2[q], I);
+            const f2_t q1 = mul2(gI, L);
+            acc[1] = add2(acc[1], q1);
+            const f2_t q2 = mul2(q1, L);
+            acc[3] = fma2(q2, t, acc[3]);
+            acc[5] = fma_abs2(q2, t, acc[5]);
+            const f2_t q3 = mul2(q2, t);
+            acc[7] = fma2(q3, t, acc[7]);
+            acc[9] = fma_abs2(q3, t, acc[9]);
+            const f2_t qg = mul2(gI, ex2neg2(u));
+            acc[0] = add2(acc[0], qg);
+            acc[2] = fma2(qg, t, acc[2]);
+            acc[4] = fma_abs2(qg, t, acc[4]);
+            const f2_t q3g = mul2(qg, t);
+            acc[6] = fma2(q3g, t, acc[6]);
+            acc[8] = fma_abs2(q3g, t, acc[8]);
         }
     }
 }
 
-// Backward sums over the peaks of one phase (layout of k_backward's acc).
-template <bool kSplit>
-__device__ __forceinline__ bool bwd_phase(const float2 *s_pk, int mb, int me, const PhaseConst &c,
-                                          float plo, float phi, const float (&xj)[kPts],
-                                          const float (&gj)[kPts], float (&acc)[8]) {
-    bool anyg = false;
-    for (int m = mb; m < me; ++m) {
-        const float2 pk = s_pk[m];
-        float u[kPts], cd[kPts], ud[kPts], q[kPts];
+__device__ __forceinline__ void bwdG_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu, bool right,
+                                             const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
+                                             f2_t (&acc)[kGradSums]) {
+    if (m0 >= m1) return;
+    const f2_t s2 = bc2(sc), c2 = bc2(cmu);
+    f2_t S1 = 0ull, A = 0ull, B = 0ull;
+    for (int m = m0; m < m1; ++m) {
+        const float2 pa = s_pk[m];
+        const f2_t np = bc2(pa.x), I = bc2(pa.y);
 #pragma unroll
-        for (int j = 0; j < kPts; ++j) {
-            const float d = (xj[j] - pk.x) - c.mu;
-            cd[j] = cd_of<kSplit>(c, d);
-            u[j] = d * cd[j];
-            ud[j] = fabsf(d) * cd[j];
-            q[j] = gj[j] * pk.y;
-            const float L = rcp_approx(u[j] + 1.0f);
-            const float q1 = q[j] * L;
-            acc[1] += q1;
-            const float q2 = q1 * L;
-            acc[3] = fmaf(q2, cd[j], acc[3]);
-            acc[5] = fmaf(q2, u[j], acc[5]);
-            acc[7] = fmaf(q2, ud[j], acc[7]);
-        }
-        if (pk.x > plo && pk.x < phi) {  // warp-uniform
-            anyg = true;
-#pragma unroll
-            for (int j = 0; j < kPts; ++j) {
-                const float qg = q[j] * ex2_approx(-u[j]);
-                acc[0] += qg;
-                acc[2] = fmaf(qg, cd[j], acc[2]);
-                acc[4] = fmaf(qg, u[j], acc[4]);
-                acc[6] = fmaf(qg, ud[j], acc[6]);
-            }
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+            const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(mul2(t, t)));
+            S1 = add2(S1, qg);
+            A = fma2(qg, t, A);
+            B = fma2(mul2(qg, t), t, B);
         }
     }
-    return anyg;
+    acc[0] = add2(acc[0], S1);
+    acc[2] = add2(acc[2], A);
+    acc[6] = add2(acc[6], B);
+    acc[4] = right ? add2(acc[4], A) : sub2(acc[4], A);
+    acc[8] = right ? add2(acc[8], B) : sub2(acc[8], B);
 }
 
-template <bool kNaive>
-__global__ void __launch_bounds__(kThreads) k_forward(ProfArgs a) {
-    extern __shared__ float2 s_pk[];
-    int *s_off = reinterpret_cast<int *>(s_pk + a.Mtot);
-    load_table(a, s_pk, s_off);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int items = a.S * a.T;
-    for (int item = blockIdx.x * kWarps + warp; item < items; item += gridDim.x * kWarps) {
-        const int s = item / a.T, tile = item - s * a.T;
-        const int i0 = tile * kTile;
-        float xj[kPts], fs[kPts], fc[kPts];
-#pragma unroll
-        for (int j = 0; j < kPts; ++j) {
-            const int ic = min(i0 + j * 32 + lane, a.N - 1);
-            xj[j] = a.x[ic];
-            fs[j] = a.bg[ic];
-            fc[j] = 0.f;
+__device__ __forceinline__ void bwd_phase(const float2 *s_pk, const Ranges &r, const PhaseConst &c,
+                                          const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
+                                          f2_t (&acc)[kGradSums]) {
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int m0 = side ? r.m2 : r.mb, m1 = side ? r.me : r.m1;
+        bwdL_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, side == 0, x2, g2, acc);
+    }
+    bwd_mixed(s_pk, r.m1, r.m2, c, x2, g2, acc);
+    if (r.nb < r.m1 || r.m2 < r.ne) {  // warp-uniform
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
+            bwdG_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, side == 0, x2, g2, acc);
         }
-        const float xlo = a.x[i0];
-        const float xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
-        const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
-        for (int k = 0; k < a.K; ++k) {
-            const PhaseConst c = cs[k];
-            const float plo = xlo - c.mu - c.rr;   // peak p is "near" iff plo < p < phi
-            const float phi = xhi - c.mu + c.rl;
-            float sl[kPts], sg[kPts];
-#pragma unroll
-            for (int j = 0; j < kPts; ++j) sl[j] = sg[j] = 0.f;
-            if (c.split)
-                fwd_phase<true>(s_pk, s_off[k], s_off[k + 1], c, plo, phi, xj, sl, sg);
-            else
-                fwd_phase<false>(s_pk, s_off[k], s_off[k + 1], c, plo, phi, xj, sl, sg);
-#pragma unroll
-            for (int j = 0; j < kPts; ++j) {
-                const float v = fmaf(c.hl, sl[j], c.hg * sg[j]);
-                if (kNaive) {
-                    fs[j] += v;
-                } else {
-                    // Neumaier compensated summation over phases
-                    const float t = fs[j] + v;
-                    fc[j] += (fabsf(fs[j]) >= fabsf(v)) ? ((fs[j] - t) + v) : ((v - t) + fs[j]);
-                    fs[j] = t;
-                }
-            }
-        }
-        double dev = 0.0;
-#pragma unroll
-        for (int j = 0; j < kPts; ++j) {
-            const int i = i0 + j * 32 + lane;
-            float gv = 0.f;
-            if (i < a.N) {
-                const float f = fs[j] + fc[j];
-                const float yv = a.y[i];
-                dev += static_cast<double>(deviance_term(yv, f));
-                gv = (yv > 0.f) ? __fdiv_rn(yv, f) - 1.0f : -1.0f;
-                if (a.f_out) a.f_out[static_cast<size_t>(s) * a.N + i] = f;
-            }
-            a.g[static_cast<size_t>(s) * a.Npad + i] = gv;
-        }
-        dev = warp_sum(dev);
-        if (lane == 0) a.llpart[static_cast<size_t>(s) * a.T + tile] = dev;
     }
 }
 
-// Gradient sums per (s, k, tile), with q = (y/f - 1) I_m, t = c(d) d, u = t d:
-//   0 S1G = sum q G        1 S1L = sum q L
-//   2 S2G = sum q G t      3 S2L = sum q L^2 t
-//   4 S3G = sum q G u      5 S3L = sum q L^2 u
-//   6 S4G = sum q G u sgn  7 S4L = sum q L^2 u sgn      (sgn = sign(d))
 __global__ void __launch_bounds__(kThreads) k_backward(ProfArgs a) {
     extern __shared__ float2 s_pk[];
     int *s_off = reinterpret_cast<int *>(s_pk + a.Mtot);
     load_table(a, s_pk, s_off);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int items = a.S * a.T;
-    for (int item = blockIdx.x * kWarps + warp; item < items; item += gridDim.x * kWarps) {
-        const int s = item / a.T, tile = item - s * a.T;
+    const int lane = threadIdx.x & 31;
+    const int items = a.S * a.T * a.C;
+    for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
+        const int c = item % a.C;
+        const int st = item / a.C;
+        const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
-        float xj[kPts], gj[kPts];
+        f2_t x2[kPairs], g2[kPairs];
+        float xlo, xhi;
+        item_points(a, i0, lane, x2, xlo, xhi);
+        const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
 #pragma unroll
-        for (int j = 0; j < kPts; ++j) {
-            const int i = i0 + j * 32 + lane;
-            xj[j] = a.x[min(i, a.N - 1)];
-            gj[j] = a.g[static_cast<size_t>(s) * a.Npad + i];
-        }
-        const float xlo = a.x[i0];
-        const float xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
+        for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
-        for (int k = 0; k < a.K; ++k) {
-            const PhaseConst c = cs[k];
-            const float plo = xlo - c.mu - c.rr;
-            const float phi = xhi - c.mu + c.rl;
-            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool anyg;
-            if (c.split)
-                anyg = bwd_phase<true>(s_pk, s_off[k], s_off[k + 1], c, plo, phi, xj, gj, acc);
-            else
-                anyg = bwd_phase<false>(s_pk, s_off[k], s_off[k + 1], c, plo, phi, xj, gj, acc);
-            float s1l = acc[1], s2l = acc[3], s3l = acc[5], s4l = acc[7];
-            float s1g = acc[0], s2g = acc[2], s3g = acc[4], s4g = acc[6];
-            s1l = warp_sumf(s1l);
-            s2l = warp_sumf(s2l);
-            s3l = warp_sumf(s3l);
-            s4l = warp_sumf(s4l);
-            if (anyg) {  // warp-uniform
-                s1g = warp_sumf(s1g);
-                s2g = warp_sumf(s2g);
-                s3g = warp_sumf(s3g);
-                s4g = warp_sumf(s4g);
+        const int kb = a.chunk[c], ke = a.chunk[c + 1];
+        for (int k = kb; k < ke; ++k) {
+            const PhaseConst cp = cs[k];
+            const Ranges r = phase_ranges(s_pk, s_off[k], s_off[k + 1], cp, xlo, xhi);
+            f2_t acc[kGradSums];
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) acc[j] = 0ull;
+            bwd_phase(s_pk, r, cp, x2, g2, acc);
+            float rr[kGradSums];
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) {
+                float lo, hi;
+                up2(acc[j], lo, hi);
+                rr[j] = lo + hi;
+            }
+            const bool anyg = r.nb < r.ne || r.m1 < r.m2;  // warp-uniform
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) {
+                if ((j & 1) || anyg) rr[j] = warp_sumf(rr[j]);
             }
             if (lane == 0) {
-                float4 *dst = reinterpret_cast<float4 *>(
-                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * 8);
-                dst[0] = make_float4(s1g, s1l, s2g, s2l);
-                dst[1] = make_float4(s3g, s3l, s4g, s4l);
+                float2 *dst = reinterpret_cast<float2 *>(
+                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
+#pragma unroll
+                for (int j = 0; j < kGradSums; j += 2) dst[j / 2] = make_float2(rr[j], rr[j + 1]);
             }
         }
     }
@@ -509,27 +791,34 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
     const double ln2 = kLn2;
     for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
         const size_t sk = static_cast<size_t>(s) * a.K + k;
-        const float *gp = a.gpart + sk * a.T * 8;
-        double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const float2 *gp = reinterpret_cast<const float2 *>(a.gpart + sk * a.T * kGradSums);
+        double q[kGradSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int t = 0; t < a.T; ++t) {
-            const float4 v0 = reinterpret_cast<const float4 *>(gp + t * 8)[0];
-            const float4 v1 = reinterpret_cast<const float4 *>(gp + t * 8)[1];
-            q[0] += v0.x; q[1] += v0.y; q[2] += v0.z; q[3] += v0.w;
-            q[4] += v1.x; q[5] += v1.y; q[6] += v1.z; q[7] += v1.w;
+#pragma unroll
+            for (int j = 0; j < kGradSums / 2; ++j) {
+                const float2 v = gp[t * (kGradSums / 2) + j];
+                q[2 * j] += v.x;
+                q[2 * j + 1] += v.y;
+            }
         }
         const float *th = a.theta + sk * 5;
         const float *ep = a.eps + sk * 5;
         const double h = th[0], mu = th[1], w = th[2], r = th[3], al = th[4];
         const bool clamped = !(th[4] > static_cast<float>(a.pr.alpha_min));
         const double acl = clamped ? static_cast<double>(static_cast<float>(a.pr.alpha_min)) : al;
+        const double sl = 2.0 / w, sr = 2.0 / (acl * w);
+        // side splits: X+ = (X + Xs)/2 (d >= 0), X- = (X - Xs)/2 (d < 0)
+        const double AGp = 0.5 * (q[2] + q[4]), AGm = 0.5 * (q[2] - q[4]);
+        const double ALp = 0.5 * (q[3] + q[5]), ALm = 0.5 * (q[3] - q[5]);
+        const double BGp = 0.5 * (q[6] + q[8]), BLp = 0.5 * (q[7] + q[9]);
         double G[5];
-        // likelihood part (chain to u) + prior/Jacobian part
+        // likelihood part (chained to u) + prior/Jacobian part
         G[0] = h * ((1.0 - r) * q[0] + r * q[1]) + (1.0 - a.pr.lambda * h);
-        G[1] = 2.0 * h * ((1.0 - r) * ln2 * q[2] + r * q[3]) - mu / (a.pr.mu_sd * a.pr.mu_sd);
-        G[2] = 2.0 * h * ((1.0 - r) * ln2 * q[4] + r * q[5]) + (a.pr.w_shape - a.pr.w_rate * w);
+        G[1] = 2.0 * h * ((1.0 - r) * ln2 * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
+               mu / (a.pr.mu_sd * a.pr.mu_sd);
+        G[2] = 2.0 * h * ((1.0 - r) * ln2 * q[6] + r * q[7]) + (a.pr.w_shape - a.pr.w_rate * w);
         G[3] = r * (1.0 - r) * h * (q[1] - q[0]) + (1.0 - 2.0 * r);
-        const double gal = clamped ? 0.0
-                                   : (h / acl) * ((1.0 - r) * ln2 * (q[4] + q[6]) + r * (q[5] + q[7]));
+        const double gal = clamped ? 0.0 : (2.0 * h / acl) * ((1.0 - r) * ln2 * BGp + r * BLp);
         G[4] = gal - (al - a.pr.alpha_mean) / (a.pr.alpha_sd * a.pr.alpha_sd);
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
@@ -802,16 +1091,43 @@ void configure_grids(Problem &P, int sm_count) {
 
 static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     ProfArgs a;
-    a.S = W.S; a.K = P.K; a.N = P.N; a.Npad = P.Npad; a.T = P.T; a.Mtot = P.Mtot;
+    a.S = W.S; a.K = P.K; a.N = P.N; a.Npad = P.Npad; a.T = P.T; a.Mtot = P.Mtot; a.C = W.C;
+    for (int c = 0; c <= kMaxChunks; ++c) a.chunk[c] = c <= W.C ? W.chunk[c] : P.K;
     a.pos = P.pos; a.inten = P.inten; a.off = P.off;
     a.x = P.x; a.y = P.y; a.bg = P.bg;
     a.cst = W.cst; a.g = W.g; a.f_out = f_out; a.llpart = W.llpart; a.gpart = W.gpart;
+    a.fpart = W.fpart; a.counter = W.counters;
     return a;
 }
 
 static int grid_for(int grid_max, int items) {
     const int need = (items + kWarps - 1) / kWarps;
     return need < grid_max ? need : grid_max;
+}
+
+void choose_chunks(const Problem &P, const int *offsets, int S, Workspace &W, int max_chunks) {
+    const long long base = static_cast<long long>(S) * P.T;
+    const long long resident = static_cast<long long>(P.grid_fwd) * kWarps;
+    int C = static_cast<int>((4 * resident + base - 1) / base);
+    C = C < 1 ? 1 : C;
+    C = C > kMaxChunks ? kMaxChunks : C;
+    C = C > max_chunks ? max_chunks : C;
+    C = C < 1 ? 1 : C;
+    C = C > P.K ? P.K : C;
+    // cut at the first phase boundary reaching c * Mtot / C peaks, leaving at
+    // least one phase for every later chunk
+    W.chunk[0] = 0;
+    int k = 0;
+    for (int c = 1; c < C; ++c) {
+        const long long target = static_cast<long long>(P.Mtot) * c / C;
+        const int kmax = P.K - (C - c);
+        int kk = k + 1;
+        while (kk < kmax && offsets[kk] < target) ++kk;
+        W.chunk[c] = kk;
+        k = kk;
+    }
+    W.chunk[C] = P.K;
+    W.C = C;
 }
 
 void launch_sample(const Problem &P, Workspace &W, const float *loc, const float *raw,
@@ -823,21 +1139,24 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.key1 = static_cast<uint32_t>(seed >> 32);
     a.tag = tag; a.step = step; a.d_step = d_step; a.d_iter = d_iter; a.ent = ent;
     a.pr = P.prior; a.eps = W.eps; a.theta = W.theta; a.cst = W.cst; a.lpj = W.lpj; a.lq = W.lq;
+    a.counters = W.counters;
     k_sample<<<W.S, 128, 0, st>>>(a);
 }
 
 void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st) {
     ProfArgs a = prof_args(P, W, f_out);
-    const int grid = grid_for(P.grid_fwd, W.S * P.T);
+    const int grid = grid_for(P.grid_fwd, W.S * P.T * W.C);
     if (naive)
         k_forward<true><<<grid, kThreads, P.smem, st>>>(a);
     else
         k_forward<false><<<grid, kThreads, P.smem, st>>>(a);
+    k_lik<<<W.S * P.T, kTile, 0, st>>>(a);
 }
 
 void launch_backward(const Problem &P, Workspace &W, cudaStream_t st) {
     ProfArgs a = prof_args(P, W, nullptr);
-    const int grid = grid_for(P.grid_bwd, W.S * P.T);
+    a.counter = W.counters + 1;
+    const int grid = grid_for(P.grid_bwd, W.S * P.T * W.C);
     k_backward<<<grid, kThreads, P.smem, st>>>(a);
 }
 

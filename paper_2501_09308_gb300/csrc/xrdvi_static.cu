@@ -69,7 +69,9 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     const size_t o_ent = off;    off += align256(sizeof(double));
     const size_t o_g = off;      off += align256(static_cast<size_t>(S) * Npad * sizeof(float));
     const size_t o_llp = off;    off += align256(static_cast<size_t>(S) * T * sizeof(double));
-    const size_t o_gp = off;     off += align256(SK * T * 8 * sizeof(float));
+    const size_t o_gp = off;     off += align256(SK * T * kGradSums * sizeof(float));
+    const size_t o_fp = off;     off += align256(static_cast<size_t>(S) * Npad * sizeof(float));
+    const size_t o_cnt = off;    off += align256(2 * sizeof(int));
     if (off > XRDVI_STATIC_SCRATCH_BYTES)
         return report_error(XRDVI_EINVAL, "elbo_grad_static: this problem needs " + std::to_string(off) +
                                               " bytes of scratch, more than the " +
@@ -124,8 +126,9 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     configure_grids(P, sms);
 
     // Every scratch element is written before it is read in one call (the
-    // partial sums of every sample, phase and tile, the padded tail of g), so
-    // nothing has to be cleared; the array keeps the last call's contents.
+    // partial sums of every sample, phase and tile, the padded tail of g, the
+    // work counters, which the sampling kernel zeroes), so nothing has to be
+    // cleared here; the array keeps the last call's contents.
     Workspace W;
     W.S = S;
     W.eps = reinterpret_cast<float *>(base + o_eps);
@@ -137,6 +140,11 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     W.g = reinterpret_cast<float *>(base + o_g);
     W.llpart = reinterpret_cast<double *>(base + o_llp);
     W.gpart = reinterpret_cast<float *>(base + o_gp);
+    W.fpart = reinterpret_cast<float *>(base + o_fp);     // one phase chunk
+    W.counters = reinterpret_cast<int *>(base + o_cnt);   // zeroed by the sampling kernel
+    W.C = 1;
+    W.chunk[0] = 0;
+    W.chunk[1] = K;
     double *ent = reinterpret_cast<double *>(base + o_ent);
 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
