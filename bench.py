@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=None, help="SVI steps per fit (default: workload's 2000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=6,
+                    help="requests of the serving leg (0: skip); the first is the K=50 fit")
     return ap.parse_args()
 
 
@@ -220,6 +222,36 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def serving_leg(n_requests, plain_ms):
+    """Continuous batching: the K=50 fit followed by serving-workload requests
+    (K ~ U{10..200}, N ~ U{2000..9000}, 5-100 peaks per phase, S=256, 1000
+    steps) arriving as a Poisson stream at 200 requests/s, on a server with 4
+    slots and a 32 GB device-memory budget.  Reports time-to-posterior
+    (completion - arrival) percentiles, fits/s and the K=50 request's served
+    time-to-posterior beside the plain single-fit path's."""
+    import numpy as np
+    from paper_2501_09308_gb300 import serving, synth
+    reqs = [synth.config(1)] + [synth.config(4, instance=i) for i in range(1, n_requests)]
+    arrivals = synth.arrival_times(n_requests, 200.0, seed=synth.SEED_BASE + 4000)
+    srv = serving.Server(hbm_budget=32 << 30, max_slots=4)
+    res = serving.replay_arrivals(srv, reqs, arrivals, S_post=S_POST, post_seed=77, top_m=TOP_M)
+    stats = srv.stats()
+    srv.close()
+    evals = [r_.evals_per_iter * r_.iters for r_ in reqs]
+    out = serving.summarize(res, evals)
+    out.update({
+        "slots": 4, "hbm_budget_bytes": 32 << 30, "arrival_rate_per_s": 200.0,
+        "peak_bytes_in_use": stats["peak_bytes"],
+        "k50_served_time_to_posterior_s": res[0]["latency"],
+        "k50_plain_time_to_posterior_s": plain_ms / 1e3,
+        "k50_top_combination": [int(k) for k in np.flatnonzero(res[0]["combos"][0])],
+        "requests_K": [int(r_.K) for r_ in reqs], "requests_N": [int(r_.N) for r_ in reqs],
+        "note": f"{n_requests} requests of the 4096-request stream: at ~8e12 evaluations per fit the full "
+                "stream would take hours on one GPU (queueing-dominated latency)",
+    })
+    return out
+
+
 def workload_config(inst, l2):
     return {"workload": f"single fit K={inst.K} (5-80 peaks, sum M={int(inst.offsets[-1])}), N={inst.N}, "
                         f"S={inst.S}, {inst.iters} SVI steps + posterior ({S_POST} draws)",
@@ -303,6 +335,10 @@ def main():
     h2d = (K + 1) * 4 + 2 * M * 4 + 3 * N * 4
     d2h = iters * 8 + 8 + K * 8 + TOP_M * ((K + 63) // 64) * 8 + TOP_M * 8
 
+    serve = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serve = serving_leg(args.serve_requests, ms_step)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(inst, CPU_SAMPLE_S, rank)
@@ -365,6 +401,8 @@ def main():
                       "e2e_top_combination": [int(k) for k in np.flatnonzero(post2["combos"][0])],
                       "final_elbo": float(trace[-1])},
     }
+    if serve:
+        out["serving"] = serve
     if clk:
         out["clocks"] = clk
     if cpu:

@@ -51,7 +51,8 @@ typedef enum {
     XRDVI_ECUDA = 3,       /* CUDA runtime error (no device, launch failure)    */
     XRDVI_ETIMEOUT = 4,    /* bounded wait ran out                               */
     XRDVI_ENONFINITE = 5,  /* ELBO or gradient became NaN/Inf                    */
-    XRDVI_EBUSY = 6        /* resource temporarily unavailable                   */
+    XRDVI_EBUSY = 6,       /* resource temporarily unavailable                   */
+    XRDVI_ECANCELED = 7    /* served request cancelled before it ran             */
 } xrdvi_status;
 
 typedef struct xrdvi_ctx xrdvi_ctx;
@@ -225,6 +226,81 @@ xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const int32_t *d
                                     double data_const, double lambda_, const xrdvi_config *cfg,
                                     const float *d_loc, const float *d_raw, const float *d_eps,
                                     double *d_elbo, float *d_grad, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of fits (a runtime around the fit kernels; the
+ * paper runs one fit at a time).
+ *
+ * A server owns a FIFO request queue, max_slots worker threads with one CUDA
+ * stream each, and a stream-ordered device memory pool.  A worker takes the
+ * head request as soon as its device footprint (xrdvi_footprint_bytes) fits
+ * into hbm_budget next to the fits already running, so requests arriving
+ * while others run are admitted as slots and memory free up, and fits in
+ * different slots overlap on the GPU.  Each fit keeps its whole state on the
+ * device from creation to posterior and runs the same deterministic kernels
+ * as a standalone context, so its result is the same alone and in the mix.
+ * All server calls are thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct xrdvi_server xrdvi_server;
+
+typedef struct {
+    int32_t iters;        /* SVI steps of the fit (>= 0)                       */
+    int32_t S_post;       /* posterior draws (0: no posterior)                 */
+    uint64_t post_seed;   /* Philox key of the posterior draws                 */
+    int32_t top_m;        /* combinations reported (1..4096 when S_post > 0)   */
+} xrdvi_request_opts;
+
+/* Result of a served fit.  The pointer fields are CALLER buffers (NULL to
+ * skip): pi [K], combos [top_m * ceil(K/64)] (layout of xrdvi_posterior),
+ * combo_logp [top_m], loc / raw [K*5] (fitted q). */
+typedef struct {
+    int32_t status;            /* xrdvi_status of the fit itself              */
+    int32_t K;
+    double t_submit, t_admit, t_done;  /* seconds since xrdvi_server_create    */
+    double final_elbo, log_evidence, ess, coverage_log;
+    size_t footprint_bytes;
+    double *pi;
+    uint64_t *combos;
+    double *combo_logp;
+    float *loc, *raw;
+} xrdvi_result;
+
+typedef struct {
+    int64_t queued, running, completed;
+    size_t bytes_in_use, peak_bytes, budget;
+    int32_t slots;
+} xrdvi_server_stats;
+
+/* Upper bound of the device bytes one fit of this size holds (problem,
+ * sample workspaces, state, posterior buffers).  Host arithmetic only; 0 on
+ * invalid sizes. */
+size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t S_post,
+                             int32_t top_m);
+
+/* Creates a server on the current device.  hbm_budget: device bytes the
+ * admitted fits may hold together; max_slots in [1, 64]. */
+xrdvi_status xrdvi_server_create(size_t hbm_budget, int32_t max_slots, xrdvi_server **out);
+
+/* Queues a fit; inputs are copied and validated when the fit runs (a bad
+ * problem completes with status EINVAL).  ENOMEM if the request alone exceeds
+ * the budget.  *req_id identifies it for poll / cancel. */
+xrdvi_status xrdvi_server_submit(xrdvi_server *srv, const xrdvi_peaks *peaks, const xrdvi_pattern *pattern,
+                                 const xrdvi_config *cfg, const xrdvi_request_opts *opts, uint64_t *req_id);
+
+/* Waits up to timeout_ms for the request; on completion copies the result
+ * into *res (res->status is the fit's own status), forgets the request and
+ * returns OK.  ETIMEOUT if it is still queued or running; EINVAL for an
+ * unknown or already collected id. */
+xrdvi_status xrdvi_server_poll(xrdvi_server *srv, uint64_t req_id, int32_t timeout_ms, xrdvi_result *res);
+
+/* Cancels a request that has not started (its poll reports ECANCELED);
+ * EBUSY if it is running or done. */
+xrdvi_status xrdvi_server_cancel(xrdvi_server *srv, uint64_t req_id);
+
+xrdvi_status xrdvi_server_get_stats(xrdvi_server *srv, xrdvi_server_stats *stats);
+
+/* Cancels queued requests, waits for running fits, frees everything. */
+void xrdvi_server_destroy(xrdvi_server *srv);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *xrdvi_last_error(void);

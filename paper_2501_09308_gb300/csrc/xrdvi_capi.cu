@@ -63,8 +63,10 @@ xrdvi_status report_error(xrdvi_status st, const std::string &msg) { return fail
 
 struct xrdvi_ctx {
     int device = 0;
-    cudaStream_t own_stream = nullptr;
+    cudaStream_t own_stream = nullptr;   // private stream (graph capture; default work stream)
+    bool owns_stream = true;             // false when the stream was lent by a server slot
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;        // stream-ordered allocation from this pool when set
     xrdvi_config cfg{};
     Problem P;
     Workspace W;       // fit sample set (S)
@@ -87,10 +89,11 @@ struct xrdvi_ctx {
     xrdvi_status alloc(T **p, size_t n, std::vector<void *> *list = nullptr) {
         if (n == 0) n = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, n * sizeof(T), pool, own_stream)
+                             : cudaMalloc(&q, n * sizeof(T));
         if (e != cudaSuccess) {
             return fail(e == cudaErrorMemoryAllocation ? XRDVI_ENOMEM : XRDVI_ECUDA,
-                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+                        std::string("device allocation: ") + cudaGetErrorString(e));
         }
         (list ? list : &allocs)->push_back(q);
         bytes += n * sizeof(T);
@@ -104,8 +107,15 @@ struct xrdvi_ctx {
         graph_many = graph_one = nullptr;
     }
 
+    void release(void *q) {
+        if (pool)
+            cudaFreeAsync(q, own_stream);
+        else
+            cudaFree(q);
+    }
+
     void free_post() {
-        for (void *q : post_allocs) cudaFree(q);
+        for (void *q : post_allocs) release(q);
         post_allocs.clear();
         Wp = Workspace();
         B = PostBuffers();
@@ -113,10 +123,11 @@ struct xrdvi_ctx {
 
     ~xrdvi_ctx() {
         if (stream) cudaStreamSynchronize(stream);
+        if (own_stream && own_stream != stream) cudaStreamSynchronize(own_stream);
         drop_graphs();
         free_post();
-        for (void *q : allocs) cudaFree(q);
-        if (own_stream) cudaStreamDestroy(own_stream);
+        for (void *q : allocs) release(q);
+        if (own_stream && owns_stream) cudaStreamDestroy(own_stream);
     }
 };
 
@@ -255,6 +266,13 @@ void xrdvi_config_default(xrdvi_config *cfg) {
 
 xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
                           xrdvi_ctx **out) {
+    return xrdvi::create_context(pk, pt, cfg, nullptr, nullptr, out);
+}
+
+}  // extern "C"
+
+xrdvi_status xrdvi::create_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
+                                   cudaMemPool_t pool, cudaStream_t stream, xrdvi_ctx **out) {
     g_err.clear();
     if (!out) return fail(XRDVI_EINVAL, "null output pointer");
     *out = nullptr;
@@ -298,9 +316,14 @@ xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const 
         g_err = keep;
         return st;
     };
-    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    if (stream) {
+        c->own_stream = stream;
+        c->owns_stream = false;
+    } else if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         return bail(fail(XRDVI_ECUDA, "cudaStreamCreate failed"));
+    }
     c->stream = c->own_stream;
+    c->pool = pool;
 
     Problem &P = c->P;
     P.K = K;
@@ -372,6 +395,8 @@ xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const 
     *out = c;
     return XRDVI_OK;
 }
+
+extern "C" {
 
 void xrdvi_destroy(xrdvi_ctx *c) { delete c; }
 

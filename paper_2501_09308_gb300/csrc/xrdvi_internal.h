@@ -4,7 +4,10 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
+
+#include "../../include/xrdvi.h"
 
 namespace xrdvi {
 
@@ -124,6 +127,16 @@ struct PostBuffers {
     int cap_S = 0, cap_M = 0;
 };
 void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m, cudaStream_t st);
+
+// Error reporting shared by the host translation units (sets the thread-local
+// message returned by xrdvi_last_error).
+xrdvi_status report_error(xrdvi_status st, const std::string &msg);
+
+// Context creation; with a pool, every device buffer comes from the pool by
+// stream-ordered allocation on `stream` (which the context then uses and does
+// not own), so creating and destroying contexts never synchronises the device.
+xrdvi_status create_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
+                            cudaMemPool_t pool, cudaStream_t stream, xrdvi_ctx **out);
 
 // Occupancy-based persistent grid sizes.
 void configure_grids(Problem &P, int sm_count);

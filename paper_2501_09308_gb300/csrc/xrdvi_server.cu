@@ -1,0 +1,336 @@
+// Continuous-batching fit server (xrdvi_server_*): host runtime around the
+// fit kernels.
+//
+// Requests (a problem + fit options) enter a FIFO queue.  max_slots worker
+// threads, each with its own CUDA stream, take the head request whenever it
+// fits into the device-memory budget next to the fits already running
+// (admission by HBM footprint), so requests that arrive while others run are
+// admitted as slots and memory free up, and the fits of different slots
+// overlap on the GPU.  A fit's whole state (tables, variational parameters,
+// Adam moments, sample workspaces) stays on the device from creation to its
+// posterior; all of it comes from one stream-ordered memory pool, so starting
+// and finishing fits never synchronises the device.  Each fit runs the same
+// deterministic kernels as a standalone context, so its result does not
+// depend on what else is running.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/xrdvi.h"
+#include "xrdvi_internal.h"
+
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t id = 0;
+    std::vector<int32_t> off;
+    std::vector<float> pos, inten, x, y, bg;
+    xrdvi_config cfg{};
+    xrdvi_request_opts opts{};
+    size_t footprint = 0;
+    double t_submit = 0, t_admit = -1, t_done = -1;
+    bool done = false;
+    xrdvi_status status = XRDVI_OK;
+    std::string error;
+    std::vector<double> pi, combo_logp;
+    std::vector<uint64_t> combos;
+    std::vector<float> loc, raw;
+    double final_elbo = 0, log_evidence = 0, ess = 0, coverage_log = 0;
+};
+
+size_t a256(size_t n) { return (n + 511) & ~static_cast<size_t>(511); }  // pool granularity allowance
+
+}  // namespace
+
+struct xrdvi_server {
+    int device = 0;
+    size_t budget = 0;
+    int slots = 0;
+    cudaMemPool_t pool = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
+    size_t in_use = 0, peak = 0;
+    int64_t running = 0, completed = 0;
+    uint64_t next_id = 1;
+    bool stopping = false;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    Clock::time_point t0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+    void worker(int slot);
+    void run(Request &r, cudaStream_t st);
+};
+
+extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t S_post,
+                                        int32_t top_m) {
+    using namespace xrdvi;
+    if (K < 1 || N < 1 || M_total < 1 || S < 1 || S_post < 0 || top_m < 0) return 0;
+    const size_t T = (static_cast<size_t>(N) + kTile - 1) / kTile, Npad = T * kTile;
+    // phase chunks: the rule of choose_chunks with an upper bound on resident
+    // warps (up to 160 SMs x 4 blocks x 8 warps), so C is never underestimated
+    auto chunks = [&](size_t s) {
+        const size_t resident = 160 * 4 * kWarps, items = s * T;
+        size_t c = (4 * resident + items - 1) / items;
+        c = std::min<size_t>(c, kMaxChunks);
+        c = std::min<size_t>(c, static_cast<size_t>(K));
+        return std::max<size_t>(c, 1);
+    };
+    auto ws = [&](size_t s, bool fit) {
+        const size_t sk = s * K, C = chunks(s);
+        size_t b = 0;
+        b += a256(sk * 5 * 4) * 2 + a256(sk * sizeof(PhaseConst)) + a256(s * 8) * 2 + a256(s * Npad * 4) +
+             a256(s * T * 8) + a256(C * s * Npad * 4) + a256(8);
+        b += fit ? a256(sk * T * kGradSums * 4) : a256(s * 8);
+        return b;
+    };
+    size_t b = a256(M_total * 4) * 2 + a256((K + 1) * 4) + a256(N * 4) * 3 + a256(K * 8);
+    b += ws(S, true);
+    b += a256(K * 20) * 2 + a256(K * 40) * 3 + a256(8) * 2 + a256(kTraceCap * 8) + a256(4) * 2;
+    if (S_post > 0) {
+        const size_t W = (K + 63) / 64, capM = std::max(top_m, 64);
+        b += ws(S_post, false);
+        b += a256(S_post * 8) + a256(static_cast<size_t>(S_post) * K) + a256(K * 8) + a256(32) +
+             a256(capM * W * 8) + a256(capM * 8) + a256(K * 4) + a256(K * 8) + a256((2 * capM + 2) * 8) +
+             a256((2 * capM + 2) * 4) + a256((2 * capM + 2) * W * 8) + a256((2 * capM + 2) * 4);
+    }
+    return b;
+}
+
+void xrdvi_server::run(Request &r, cudaStream_t st) {
+    xrdvi_peaks pk{static_cast<int32_t>(r.off.size() - 1), r.off.data(), r.pos.data(), r.inten.data()};
+    xrdvi_pattern pt{static_cast<int32_t>(r.x.size()), r.x.data(), r.y.data(), r.bg.data()};
+    xrdvi_ctx *c = nullptr;
+    xrdvi_status s = xrdvi::create_context(&pk, &pt, &r.cfg, pool, st, &c);
+    std::vector<double> trace(std::max(r.opts.iters, 1));
+    if (s == XRDVI_OK) s = xrdvi_fit(c, r.opts.iters, trace.data());
+    const int K = pk.K, W = (K + 63) / 64;
+    if (s == XRDVI_OK) {
+        r.final_elbo = r.opts.iters > 0 ? trace[r.opts.iters - 1] : 0.0;
+        if (r.opts.S_post > 0) {
+            r.pi.resize(K);
+            r.combos.resize(static_cast<size_t>(r.opts.top_m) * W);
+            r.combo_logp.resize(r.opts.top_m);
+            s = xrdvi_posterior(c, r.opts.S_post, r.opts.post_seed, r.opts.top_m, r.pi.data(), r.combos.data(),
+                                r.combo_logp.data(), &r.log_evidence, &r.ess, &r.coverage_log);
+        }
+    }
+    if (s == XRDVI_OK) {
+        r.loc.resize(K * 5);
+        r.raw.resize(K * 5);
+        s = xrdvi_get_params(c, r.loc.data(), r.raw.data());
+    }
+    if (s != XRDVI_OK) r.error = xrdvi_last_error();
+    r.status = s;
+    xrdvi_destroy(c);  // stream-ordered frees on the slot stream
+}
+
+void xrdvi_server::worker(int slot) {
+    cudaSetDevice(device);
+    cudaStream_t st = streams[slot];
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] {
+                return stopping || (!queue.empty() && queue.front()->footprint <= budget - in_use);
+            });
+            if (stopping) return;
+            r = queue.front();
+            queue.pop_front();
+            in_use += r->footprint;
+            peak = std::max(peak, in_use);
+            ++running;
+            r->t_admit = now();
+        }
+        run(*r, st);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            in_use -= r->footprint;
+            --running;
+            ++completed;
+            r->t_done = now();
+            r->done = true;
+        }
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+}
+
+extern "C" {
+
+xrdvi_status xrdvi_server_create(size_t hbm_budget, int32_t max_slots, xrdvi_server **out) {
+    if (!out) return xrdvi::report_error(XRDVI_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 64) return xrdvi::report_error(XRDVI_EINVAL, "max_slots must be in [1, 64]");
+    if (hbm_budget == 0) return xrdvi::report_error(XRDVI_EINVAL, "hbm_budget must be positive");
+    auto srv = std::make_unique<xrdvi_server>();
+    cudaError_t e = cudaGetDevice(&srv->device);
+    if (e != cudaSuccess) return xrdvi::report_error(XRDVI_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = srv->device;
+    e = cudaMemPoolCreate(&srv->pool, &props);
+    if (e != cudaSuccess) return xrdvi::report_error(XRDVI_ECUDA, std::string("cudaMemPoolCreate: ") + cudaGetErrorString(e));
+    uint64_t keep = UINT64_MAX;  // keep released memory reserved for the next fits
+    cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    srv->budget = hbm_budget;
+    srv->slots = max_slots;
+    srv->streams.resize(max_slots);
+    for (auto &st : srv->streams) {
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (auto &s2 : srv->streams)
+                if (s2) cudaStreamDestroy(s2);
+            cudaMemPoolDestroy(srv->pool);
+            return xrdvi::report_error(XRDVI_ECUDA, "cudaStreamCreate failed");
+        }
+    }
+    srv->t0 = Clock::now();
+    for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back([s = srv.get(), i] { s->worker(i); });
+    *out = srv.release();
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_server_submit(xrdvi_server *srv, const xrdvi_peaks *pk, const xrdvi_pattern *pt,
+                                 const xrdvi_config *cfg, const xrdvi_request_opts *opts, uint64_t *req_id) {
+    if (!srv || !pk || !pt || !cfg || !opts || !req_id) return xrdvi::report_error(XRDVI_EINVAL, "null argument");
+    if (opts->iters < 0 || opts->S_post < 0 || opts->S_post > 65536 || (opts->S_post > 0 && (opts->top_m < 1 || opts->top_m > 4096)))
+        return xrdvi::report_error(XRDVI_EINVAL, "bad request options");
+    if (!pk->offsets || pk->K < 1 || pk->K > xrdvi::kMaxK || !pt->x_deg || pt->N < 1)
+        return xrdvi::report_error(XRDVI_EINVAL, "bad problem sizes");
+    auto r = std::make_shared<Request>();
+    const int K = pk->K, N = pt->N, M = pk->offsets[K];
+    if (M < 1 || M > xrdvi::kMaxPeaks) return xrdvi::report_error(XRDVI_EINVAL, "bad peak count");
+    r->off.assign(pk->offsets, pk->offsets + K + 1);
+    r->pos.assign(pk->pos_deg, pk->pos_deg + M);
+    r->inten.assign(pk->rel_int, pk->rel_int + M);
+    r->x.assign(pt->x_deg, pt->x_deg + N);
+    r->y.assign(pt->y_counts, pt->y_counts + N);
+    r->bg.assign(pt->bg, pt->bg + N);
+    r->cfg = *cfg;
+    r->opts = *opts;
+    r->footprint = xrdvi_footprint_bytes(K, N, M, cfg->S, opts->S_post, opts->top_m);
+    if (r->footprint > srv->budget)
+        return xrdvi::report_error(XRDVI_ENOMEM, "request needs " + std::to_string(r->footprint) +
+                                                      " bytes, more than the server's budget");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stopping) return xrdvi::report_error(XRDVI_EBUSY, "server is shutting down");
+        r->id = srv->next_id++;
+        r->t_submit = srv->now();
+        srv->table[r->id] = r;
+        srv->queue.push_back(r);
+        *req_id = r->id;
+    }
+    srv->cv_work.notify_all();
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_server_poll(xrdvi_server *srv, uint64_t req_id, int32_t timeout_ms, xrdvi_result *res) {
+    if (!srv || !res) return xrdvi::report_error(XRDVI_EINVAL, "null argument");
+    std::shared_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lk(srv->mu);
+        auto it = srv->table.find(req_id);
+        if (it == srv->table.end()) return xrdvi::report_error(XRDVI_EINVAL, "unknown or already collected request");
+        r = it->second;
+        const auto deadline = Clock::now() + std::chrono::milliseconds(std::max(timeout_ms, 0));
+        if (!srv->cv_done.wait_until(lk, deadline, [&] { return r->done; }))
+            return xrdvi::report_error(XRDVI_ETIMEOUT, "request not finished yet");
+        srv->table.erase(it);
+    }
+    const int K = static_cast<int>(r->off.size()) - 1;
+    res->status = r->status;
+    res->K = K;
+    res->t_submit = r->t_submit;
+    res->t_admit = r->t_admit;
+    res->t_done = r->t_done;
+    res->final_elbo = r->final_elbo;
+    res->log_evidence = r->log_evidence;
+    res->ess = r->ess;
+    res->coverage_log = r->coverage_log;
+    res->footprint_bytes = r->footprint;
+    if (res->pi && !r->pi.empty()) std::memcpy(res->pi, r->pi.data(), r->pi.size() * 8);
+    if (res->combos && !r->combos.empty()) std::memcpy(res->combos, r->combos.data(), r->combos.size() * 8);
+    if (res->combo_logp && !r->combo_logp.empty())
+        std::memcpy(res->combo_logp, r->combo_logp.data(), r->combo_logp.size() * 8);
+    if (res->loc && !r->loc.empty()) std::memcpy(res->loc, r->loc.data(), r->loc.size() * 4);
+    if (res->raw && !r->raw.empty()) std::memcpy(res->raw, r->raw.data(), r->raw.size() * 4);
+    if (r->status != XRDVI_OK) xrdvi::report_error(static_cast<xrdvi_status>(r->status), r->error);
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_server_cancel(xrdvi_server *srv, uint64_t req_id) {
+    if (!srv) return xrdvi::report_error(XRDVI_EINVAL, "null argument");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = std::find_if(srv->queue.begin(), srv->queue.end(),
+                               [&](const std::shared_ptr<Request> &r) { return r->id == req_id; });
+        if (it == srv->queue.end()) return xrdvi::report_error(XRDVI_EBUSY, "request is not queued (running or done)");
+        (*it)->status = XRDVI_ECANCELED;
+        (*it)->error = "cancelled before it ran";
+        (*it)->t_done = srv->now();
+        (*it)->done = true;
+        srv->queue.erase(it);
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();  // the next request may fit now
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_server_get_stats(xrdvi_server *srv, xrdvi_server_stats *st) {
+    if (!srv || !st) return xrdvi::report_error(XRDVI_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    st->queued = static_cast<int64_t>(srv->queue.size());
+    st->running = srv->running;
+    st->completed = srv->completed;
+    st->bytes_in_use = srv->in_use;
+    st->peak_bytes = srv->peak;
+    st->budget = srv->budget;
+    st->slots = srv->slots;
+    return XRDVI_OK;
+}
+
+void xrdvi_server_destroy(xrdvi_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stopping = true;
+        for (auto &r : srv->queue) {
+            r->status = XRDVI_ECANCELED;
+            r->error = "server destroyed before the request ran";
+            r->t_done = srv->now();
+            r->done = true;
+        }
+        srv->queue.clear();
+    }
+    srv->cv_work.notify_all();
+    srv->cv_done.notify_all();
+    for (auto &t : srv->workers) t.join();  // running fits finish first
+    for (auto &s : srv->streams) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    cudaMemPoolDestroy(srv->pool);
+    delete srv;
+}
+
+}  // extern "C"

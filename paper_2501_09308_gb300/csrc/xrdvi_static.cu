@@ -32,9 +32,6 @@ size_t align256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
 
 }  // namespace
 
-namespace xrdvi {
-xrdvi_status report_error(xrdvi_status st, const std::string &msg);
-}
 
 extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const int32_t *d_offsets,
                                                const float *d_pos, const float *d_inten, int32_t N,

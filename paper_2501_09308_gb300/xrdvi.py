@@ -54,6 +54,26 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("point_tiles", ctypes.c_int32)]
 
 
+class RequestOpts(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("S_post", ctypes.c_int32), ("post_seed", ctypes.c_uint64),
+                ("top_m", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("K", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("final_elbo", ctypes.c_double),
+                ("log_evidence", ctypes.c_double), ("ess", ctypes.c_double), ("coverage_log", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_size_t), ("pi", ctypes.POINTER(ctypes.c_double)),
+                ("combos", ctypes.POINTER(ctypes.c_uint64)), ("combo_logp", ctypes.POINTER(ctypes.c_double)),
+                ("loc", ctypes.POINTER(ctypes.c_float)), ("raw", ctypes.POINTER(ctypes.c_float))]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("slots", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -80,6 +100,13 @@ SIGNATURES = {
     "xrdvi_profile_steps": (ctypes.c_int, [_vp, _i32, P(_f)]),
     "xrdvi_elbo_grad_static": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _d, _d,
                                               P(Config), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "xrdvi_footprint_bytes": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _i32, _i32]),
+    "xrdvi_server_create": (ctypes.c_int, [ctypes.c_size_t, _i32, P(_vp)]),
+    "xrdvi_server_submit": (ctypes.c_int, [_vp, P(Peaks), P(Pattern), P(Config), P(RequestOpts), P(_u64)]),
+    "xrdvi_server_poll": (ctypes.c_int, [_vp, _u64, _i32, P(Result)]),
+    "xrdvi_server_cancel": (ctypes.c_int, [_vp, _u64]),
+    "xrdvi_server_get_stats": (ctypes.c_int, [_vp, P(ServerStats)]),
+    "xrdvi_server_destroy": (None, [_vp]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -321,3 +348,68 @@ class Context:
 
     def set_stream(self, stream_handle):
         xrdvi_set_stream(self.h, stream_handle)
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+def xrdvi_footprint_bytes(K, N, M_total, S, S_post, top_m):
+    return int(lib().xrdvi_footprint_bytes(int(K), int(N), int(M_total), int(S), int(S_post), int(top_m)))
+
+
+def xrdvi_server_create(hbm_budget, max_slots):
+    h = _vp()
+    _check(lib().xrdvi_server_create(int(hbm_budget), int(max_slots), ctypes.byref(h)))
+    return h
+
+
+def xrdvi_server_submit(srv, offsets, pos, inten, x, y, bg, cfg: Config, iters, S_post=4096, post_seed=1,
+                        top_m=8):
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    pos, inten, x, y, bg = map(_f32, (pos, inten, x, y, bg))
+    pk = Peaks(len(offsets) - 1, _ptr(offsets, ctypes.c_int32), _ptr(pos, _f), _ptr(inten, _f))
+    pt = Pattern(len(x), _ptr(x, _f), _ptr(y, _f), _ptr(bg, _f))
+    opts = RequestOpts(int(iters), int(S_post), int(post_seed), int(top_m))
+    rid = ctypes.c_uint64(0)
+    _check(lib().xrdvi_server_submit(srv, ctypes.byref(pk), ctypes.byref(pt), ctypes.byref(cfg),
+                                     ctypes.byref(opts), ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def xrdvi_server_poll(srv, req_id, timeout_ms, K, top_m):
+    """Returns a dict, or None while the request is still queued / running."""
+    W = (K + 63) // 64
+    pi = np.zeros(K)
+    combos = np.zeros((top_m, W), dtype=np.uint64)
+    clp = np.zeros(top_m)
+    loc = np.zeros((K, 5), dtype=np.float32)
+    raw = np.zeros((K, 5), dtype=np.float32)
+    res = Result()
+    res.pi, res.combos, res.combo_logp = _ptr(pi, _d), _ptr(combos, ctypes.c_uint64), _ptr(clp, _d)
+    res.loc, res.raw = _ptr(loc, _f), _ptr(raw, _f)
+    st = lib().xrdvi_server_poll(srv, int(req_id), int(timeout_ms), ctypes.byref(res))
+    if st == 4:
+        return None
+    _check(st)
+    bits = np.zeros((top_m, K), dtype=bool)
+    for k in range(K):
+        bits[:, k] = (combos[:, k // 64] >> np.uint64(k % 64)) & np.uint64(1)
+    return {"status": res.status, "t_submit": res.t_submit, "t_admit": res.t_admit, "t_done": res.t_done,
+            "final_elbo": res.final_elbo, "log_evidence": res.log_evidence, "ess": res.ess,
+            "coverage_log": res.coverage_log, "footprint_bytes": res.footprint_bytes, "pi": pi,
+            "combos": bits, "combo_logp": clp, "loc": loc, "raw": raw}
+
+
+def xrdvi_server_cancel(srv, req_id):
+    _check(lib().xrdvi_server_cancel(srv, int(req_id)))
+
+
+def xrdvi_server_get_stats(srv) -> ServerStats:
+    st = ServerStats()
+    _check(lib().xrdvi_server_get_stats(srv, ctypes.byref(st)))
+    return st
+
+
+def xrdvi_server_destroy(srv):
+    if srv:
+        lib().xrdvi_server_destroy(srv)

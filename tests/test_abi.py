@@ -85,3 +85,15 @@ def test_invalid_config_is_rejected():
     with pytest.raises(xrdvi.XrdviError) as e:
         xrdvi.xrdvi_create(a["offsets"], a["pos"], a["inten"], a["x"], a["y"], a["bg"], cfg)
     assert e.value.status == 1
+
+
+def test_footprint_bound_is_monotone_and_rejects_bad_sizes():
+    f = xrdvi.xrdvi_footprint_bytes
+    base = f(50, 4500, 2194, 256, 4096, 16)
+    assert base > 0
+    assert f(50, 9000, 2194, 256, 4096, 16) > base
+    assert f(50, 4500, 4000, 256, 4096, 16) > base
+    assert f(50, 4500, 2194, 512, 4096, 16) > base
+    assert f(50, 4500, 2194, 256, 0, 16) < base
+    assert f(0, 4500, 2194, 256, 4096, 16) == 0
+    assert f(50, 0, 2194, 256, 4096, 16) == 0

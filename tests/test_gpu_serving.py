@@ -1,0 +1,111 @@
+"""Continuous-batching fit server: results equal to standalone fits, admission
+by device-memory footprint, continuous admission while fits run, cancellation."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2501_09308_gb300 import serving, synth, xrdvi
+
+pytestmark = pytest.mark.gpu
+
+ITERS = 150
+
+
+def _problems():
+    return [synth.small_problem(K=3, M=6, N=300, S=8, seed=71),
+            synth.small_problem(K=6, M=10, N=900, S=8, seed=72, x_step=0.03),
+            synth.small_problem(K=9, M=14, N=1500, S=8, seed=73, x_step=0.02)]
+
+
+def _alone(inst, seed):
+    c = xrdvi.Context.from_instance(inst, S=inst.S, seed=seed)
+    tr = c.fit(ITERS)
+    post = c.posterior(256, 5, top_m=4)
+    loc, raw = c.params()
+    c.close()
+    return tr[-1], post, loc, raw
+
+
+def test_served_results_equal_standalone_results():
+    """Each fit in the mix (three at once on three slots) equals the same fit
+    run alone: identical kernels, fixed reduction orders, no shared state."""
+    probs = _problems()
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=3)
+    ids = [srv.submit(p, iters=ITERS, S_post=256, post_seed=5, top_m=4, seed=100 + i) for i, p in enumerate(probs)]
+    served = [srv.wait(i) for i in ids]
+    srv.close()
+    spans = [(r["t_admit"], r["t_done"]) for r in served]
+    overlap = any(a[0] < b[1] and b[0] < a[1] for i, a in enumerate(spans) for b in spans[i + 1:])
+    assert overlap, spans
+    for i, (p, r) in enumerate(zip(probs, served)):
+        assert r["status"] == 0
+        e, post, loc, raw = _alone(p, 100 + i)
+        np.testing.assert_array_equal(r["loc"], loc)
+        np.testing.assert_array_equal(r["raw"], raw)
+        assert r["final_elbo"] == e
+        np.testing.assert_array_equal(r["pi"], post["pi"])
+        np.testing.assert_array_equal(r["combo_logp"], post["combo_logp"])
+
+
+def test_admission_by_footprint_serialises_when_only_one_fits():
+    """Three same-size requests, three free slots, but a budget of 1.5
+    footprints: they must run one after another."""
+    probs = [synth.small_problem(K=6, M=10, N=900, S=8, seed=80 + i, x_step=0.03) for i in range(3)]
+    fp = [xrdvi.xrdvi_footprint_bytes(p.K, p.N, int(p.offsets[-1]), p.S, 256, 4) for p in probs]
+    assert len(set(fp)) == 1
+    srv = serving.Server(hbm_budget=int(fp[0] * 1.5), max_slots=3)
+    ids = [srv.submit(p, iters=ITERS, S_post=256, post_seed=5, top_m=4) for p in probs]
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    spans = sorted((r["t_admit"], r["t_done"]) for r in res)
+    for a, b in zip(spans, spans[1:]):
+        assert a[1] <= b[0] + 1e-6, spans
+    assert st["peak_bytes"] <= int(fp[0] * 1.5)
+    assert [r["footprint_bytes"] for r in res] == fp
+
+
+def test_requests_arriving_during_a_fit_are_admitted_before_it_ends():
+    long = synth.small_problem(K=9, M=14, N=1500, S=8, seed=74, x_step=0.02)
+    short = synth.small_problem(K=3, M=6, N=300, S=8, seed=75)
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=2)
+    a = srv.submit(long, iters=3000, S_post=64, top_m=2)
+    while srv.stats()["running"] == 0:
+        time.sleep(0.005)
+    b = srv.submit(short, iters=50, S_post=64, top_m=2)
+    rb = srv.wait(b)
+    ra = srv.wait(a)
+    srv.close()
+    assert rb["t_admit"] < ra["t_done"] and rb["t_done"] < ra["t_done"]
+
+
+def test_request_over_budget_is_rejected():
+    p = _problems()[2]
+    srv = serving.Server(hbm_budget=1 << 20, max_slots=1)
+    with pytest.raises(xrdvi.XrdviError) as e:
+        srv.submit(p, iters=10)
+    srv.close()
+    assert e.value.status == 2
+
+
+def test_cancel_a_queued_request():
+    long = synth.small_problem(K=9, M=14, N=1500, S=8, seed=76, x_step=0.02)
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=1)
+    a = srv.submit(long, iters=2000, S_post=64, top_m=2)
+    b = srv.submit(long, iters=2000, S_post=64, top_m=2)
+    srv.cancel(b)
+    rb = srv.wait(b)
+    ra = srv.wait(a)
+    srv.close()
+    assert rb["status"] == 7 and ra["status"] == 0
+
+
+def test_footprint_bound_covers_the_context_allocation():
+    for p in _problems() + [synth.config(1)]:
+        c = xrdvi.Context.from_instance(p, S=p.S)
+        c.posterior(512, 1, top_m=8)
+        used = c.info.device_bytes
+        c.close()
+        bound = xrdvi.xrdvi_footprint_bytes(p.K, p.N, int(p.offsets[-1]), p.S, 512, 8)
+        assert used <= bound <= 2 * used + (8 << 20), (used, bound)
