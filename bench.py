@@ -37,8 +37,8 @@ METRIC = "ELBO evals/s (S·K·peaks·N) + time-to-posterior K=50; served p50/p99
 S_POST = 4096
 TOP_M = 16
 PROFILE_STEPS = 64          # of the 2000 SVI steps, launched kernel by kernel between events
-CPU_SAMPLE_S = 128          # oracle cpu-baseline sample: one ELBO+gradient at 128 of 256 samples
-REF_SAMPLE_S = 32           # reference-arm step: one oracle ELBO+gradient at 32 samples
+CPU_SAMPLE_STEPS = 4        # oracle cpu-baseline sample: 4 of the fit's 2000 SVI steps (S = 256)
+REF_STEP_ITERS = 1          # reference-arm step: one oracle SVI step (S = 256)
 # Algorithmic FP32-pipe operations (lane operations; an FMA counts once) per dense
 # evaluation, on the side-uniform peak ranges that hold almost all evaluations:
 #   forward : x - p, t = fma(s, ., -s mu), 1 + t^2 for two peaks, I0 d1 + I1 d0 (2),
@@ -170,53 +170,47 @@ def l2_flush(buf):
     buf.add_(1.0)  # writes a buffer larger than L2 (129 MB) between timed steps
 
 
-def cpu_baseline(inst, S_sample, world_rank):
-    """The FP64 oracle as it stands, on this host's cores: one ELBO+gradient
-    evaluation of the same workload at S_sample Monte-Carlo samples."""
-    import numpy as np
+def cpu_baseline(inst, steps):
+    """The FP64 oracle as it stands, on this host's cores: `steps` SVI steps
+    (sample, ELBO + gradient at all S samples, Adam) of the same fit."""
     import oracle
-    from paper_2501_09308_gb300 import synth
     P = oracle.Problem.from_instance(inst)
-    loc, raw = P.init_params()
-    eps = synth.normals(4242, S_sample, P.K).astype(np.float64)
     t0 = time.perf_counter()
-    P.elbo_grad(loc, raw, eps)
+    P.fit(inst.S, steps, 1000)
     dt = time.perf_counter() - t0
-    evals = S_sample * int(inst.offsets[-1]) * inst.N
+    evals = inst.evals_per_iter * steps
     return {"value": evals / dt, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
             "seconds": dt,
-            "sample": f"one FP64 ELBO+gradient evaluation at {S_sample} of the {inst.S} Monte-Carlo "
-                      f"samples of the K={inst.K}, N={inst.N} workload ({evals:.3e} evals)"}
+            "sample": f"{steps} of the {inst.iters} FP64 SVI steps (S={inst.S}) of the K={inst.K}, N={inst.N} "
+                      f"fit ({evals:.3e} evals)"}
 
 
 def run_reference(args, world, rank):
     """Reference arm: the FP64 oracle on the host cores, same metric and
-    config, each step a bounded sample (one ELBO+gradient at 32 samples)."""
+    config; each step is a bounded sample of the fit: one SVI step at S=256."""
     if rank != 0:
         return
-    import numpy as np
     import oracle
     from paper_2501_09308_gb300 import synth
     inst = synth.config(1)
     P = oracle.Problem.from_instance(inst)
-    loc, raw = P.init_params()
-    eps = synth.normals(4242, REF_SAMPLE_S, P.K).astype(np.float64)
-    for _ in range(args.warmup):
-        P.elbo_grad(loc, raw, eps)
+    state = P.fit(inst.S, args.warmup, 1000) if args.warmup > 0 else None
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        P.elbo_grad(loc, raw, eps)
+    for i in range(args.steps):
+        kw = {} if state is None else {"loc": state["loc"], "raw": state["raw"], "m": state["m"], "v": state["v"],
+                                       "t0": args.warmup + i}
+        state = P.fit(inst.S, REF_STEP_ITERS, 1000, **kw)
     dt = time.perf_counter() - t0
-    evals = REF_SAMPLE_S * int(inst.offsets[-1]) * inst.N * args.steps
+    evals = inst.evals_per_iter * REF_STEP_ITERS * args.steps
     v = evals / dt
     out = {
         "metric": METRIC, "value": v, "unit": "evals/s", "impl": "reference", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(inst, l2="inputs L2-resident on the CPU; no GPU"),
+        "config": workload_config(inst, l2="host caches; no GPU"),
         "cpu_baseline": {"value": v, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-                         "sample": f"per step one FP64 ELBO+gradient at {REF_SAMPLE_S} of {inst.S} samples"},
+                         "sample": f"per step {REF_STEP_ITERS} FP64 SVI step (S={inst.S}) of the {inst.iters}-step fit"},
         "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -341,7 +335,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(inst, CPU_SAMPLE_S, rank)
+        cpu = cpu_baseline(inst, CPU_SAMPLE_STEPS)
 
     if world > 1:
         import torch.distributed as dist
