@@ -43,10 +43,10 @@ REF_STEP_ITERS = 1          # reference-arm step: one oracle SVI step (S = 256)
 # evaluation, on the side-uniform peak ranges that hold almost all evaluations:
 #   forward : x - p, t = fma(s, ., -s mu), 1 + t^2 for two peaks, I0 d1 + I1 d0 (2),
 #             d0 d1, accumulate (num * rcp)  -> 10 per two evaluations = 5, and 0.5 MUFU (rcp)
-#   backward: x - p, t, 1 + t^2, g I, q L, sum q L, q L^2, sum q L^2 t, q L^2 t, sum q L^2 t^2
-#             -> 10, and 1 MUFU (rcp)
+#   backward: x - p, t, 1 + t^2, g I, q L, sum q L, q L^2, sum q L^2 t, sum q L^2
+#             -> 9 (sum q L^2 t^2 follows from sum q L - sum q L^2), and 1 MUFU (rcp)
 # Both kernels are bound by the FP32 pipe (128 lanes/clk/SM; MUFU 16/clk/SM).
-FP32_OPS_PER_EVAL = {"forward": 5, "backward": 10}
+FP32_OPS_PER_EVAL = {"forward": 5, "backward": 9}
 MUFU_PER_EVAL = {"forward": 0.5, "backward": 1.0}
 
 
@@ -351,7 +351,9 @@ def main():
     achieved = {k: evals_launch * FP32_OPS_PER_EVAL[k] / (kern[k] * 1e-3) / 1e12 for k in ("forward", "backward")}
     mufu_frac = {k: evals_launch * MUFU_PER_EVAL[k] / (kern[k] * 1e-3) / (sms * 16 * clock_mhz * 1e6)
                  for k in ("forward", "backward")}
-    launches_per_step = 6 * iters + 7
+    # per SVI step: sample, ranges, forward, lik, bwd_uniform, bwd_near, grad, elbo;
+    # posterior: sample, ranges, forward, lik, post_sample, post_reduce, post_sort, post_topm
+    launches_per_step = 8 * iters + 8
     share = {k: kern[k] / sum(kern.values()) for k in kern}
     out = {
         "metric": METRIC,

@@ -43,6 +43,13 @@ xrdvi_status fail(xrdvi_status st, const std::string &msg) {
 constexpr int kUnroll = 16;          // fit steps per captured CUDA graph
 constexpr uint32_t kStateMagic = 0x58524456u;  // "XRDV"
 
+// Parameter-free part of ln p(theta) for one phase (Sec. 2.2, Appendix B.2):
+// ln lambda - ln(mu_sd) - ln(alpha_sd) - ln(2 pi) + a ln b - lnGamma(a).
+double prior_constant(const PriorConst &p) {
+    return std::log(p.lambda) - std::log(p.mu_sd) - std::log(p.alpha_sd) - std::log(2.0 * M_PI) +
+           p.w_shape * std::log(p.w_rate) - p.lgamma_w_shape;
+}
+
 float round_bf16(float v) {
     uint32_t b;
     std::memcpy(&b, &v, 4);
@@ -148,6 +155,8 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
     XR_TRY(c->alloc(&W.llpart, static_cast<size_t>(S) * P.T, list));
     if (fit) {
         XR_TRY(c->alloc(&W.gpart, SK * P.T * kGradSums, list));
+        XR_TRY(c->alloc(&W.gred, static_cast<size_t>(P.K) * kGradBlocks * 10, list));
+        XR_TRY(c->alloc(&W.tickets, static_cast<size_t>(P.K), list));
         W.lq = nullptr;
     } else {
         XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
@@ -156,7 +165,8 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
     choose_chunks(P, c->host_off.data(), S, W);
     W.fpart_cap = static_cast<size_t>(W.C) * S * P.Npad;
     XR_TRY(c->alloc(&W.fpart, W.fpart_cap, list));
-    XR_TRY(c->alloc(&W.counters, 2, list));
+    XR_TRY(c->alloc(&W.ranges, SK * P.T, list));
+    XR_TRY(c->alloc(&W.counters, kCounters, list));
     W.bytes = c->bytes - before;
     return XRDVI_OK;
 }
@@ -340,6 +350,7 @@ xrdvi_status xrdvi::create_context(const xrdvi_peaks *pk, const xrdvi_pattern *p
     P.prior.w_rate = cfg->prior_w_rate;
     P.prior.lgamma_w_shape = std::lgamma(static_cast<double>(cfg->prior_w_shape));
     P.prior.alpha_min = cfg->alpha_min;
+    P.prior.lp_const = prior_constant(P.prior);
 
     xrdvi_status st;
 #define XR_C(expr)                         \

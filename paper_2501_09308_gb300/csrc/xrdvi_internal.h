@@ -23,6 +23,10 @@ constexpr int kGradSums = 10;
 // Phases are split into up to kMaxChunks chunks of similar peak count so that
 // the profile kernels have enough equal-sized work items to fill the GPU.
 constexpr int kMaxChunks = 8;
+// Work counters of the profile kernels of one sample set.
+constexpr int kCounters = 4;
+// Sample blocks per phase in the gradient reduction.
+constexpr int kGradBlocks = 16;
 
 // The Gaussian component 2^-u of a peak is evaluated only for warps with a
 // point inside the peak's reach u < kGaussU; beyond it 2^-u < 2^-128, which
@@ -57,6 +61,7 @@ struct PriorConst {
     double alpha_mean, alpha_sd;
     double w_shape, w_rate, lgamma_w_shape;
     double alpha_min;
+    double lp_const;      // parameter-free part of ln p(theta) per phase
 };
 
 // Buffers of one sample set (the fit's S, or the posterior's S_post).
@@ -72,7 +77,10 @@ struct Workspace {
     double *llpart = nullptr;    // [S*T] deviance partial sums per tile
     float *gpart = nullptr;      // [S*K*T*kGradSums] gradient partial sums (fit only)
     float *fpart = nullptr;      // [C*S*Npad] partial profiles per phase chunk
-    int *counters = nullptr;     // [2] work counters of the profile kernels
+    ushort4 *ranges = nullptr;   // [S*K*T] peak index ranges per (sample, phase, tile)
+    int *counters = nullptr;     // [kCounters] work counters of the profile kernels
+    double *gred = nullptr;      // [K*kGradBlocks*10] gradient partials per sample block (fit only)
+    int *tickets = nullptr;      // [K] arrival tickets of the gradient reduction (fit only)
     size_t fpart_cap = 0;        // elements allocated for fpart
     int C = 1;                   // phase chunks
     int chunk[kMaxChunks + 1] = {0};
@@ -88,7 +96,9 @@ struct Problem {
     double *isum = nullptr;      // [K] sum_m I_m per phase
     double csum = 0.0;           // sum_i [y ln y - y - ln y!]
     PriorConst prior{};
-    size_t smem = 0;             // dynamic shared memory of the profile kernels
+    size_t smem = 0;             // dynamic shared memory of the backward profile kernels
+    size_t smem_fwd = 0;         // ... of the forward kernel (compact table)
+    bool wide = false;           // backward peak table stored as (-p, -p, I, I) float4
     int grid_fwd = 0, grid_bwd = 0;
 };
 

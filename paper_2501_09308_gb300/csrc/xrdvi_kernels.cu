@@ -94,6 +94,12 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
+__device__ __forceinline__ double warp_sumd(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Block-wide FP64 sum with a fixed reduction tree (deterministic).  `sh`
 // holds blockDim.x/32 doubles.  Result valid in every thread.
 __device__ double block_sum(double v, double *sh) {
@@ -137,6 +143,9 @@ struct SampleArgs {
     PhaseConst *cst;
     double *lpj, *lq;
     int *counters;
+    int *tickets;   // [K] arrival tickets of k_grad, zeroed here
+    // FP32 copies of the prior constants used per (s, k)
+    float pr_lambda, pr_mu_isd, pr_alpha_mean, pr_alpha_isd, pr_wsm1, pr_wrate;
 };
 
 __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
@@ -145,8 +154,7 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
     const uint32_t step = a.d_step ? static_cast<uint32_t>(*a.d_step) : a.step;
     if (s == 0 && threadIdx.x == 0) {
         if (a.d_iter) *a.d_iter = static_cast<int>(step);
-        a.counters[0] = 0;  // work counters of the profile kernels that follow
-        a.counters[1] = 0;
+        for (int i = 0; i < kCounters; ++i) a.counters[i] = 0;  // work counters of the profile kernels
     }
     const float sq = sqrtf(kGaussU);
     double acc = 0.0, accq = 0.0;
@@ -205,24 +213,23 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         pc.nsrmu = -sr * mu;
         pc.pad[0] = pc.pad[1] = pc.pad[2] = pc.pad[3] = pc.pad[4] = pc.pad[5] = pc.pad[6] = 0.f;
         a.cst[static_cast<size_t>(s) * a.K + k] = pc;
-        // log prior (Sec. 2.2, Appendix B.2) + log Jacobian of the transform
-        const double hd = h, mud = mu, wd = w, ald = al;
-        double lp = log(a.pr.lambda) - a.pr.lambda * hd;
-        const double zm = mud / a.pr.mu_sd;
-        lp += -0.5 * zm * zm - log(a.pr.mu_sd) - 0.5 * kLog2Pi;
-        const double za = (ald - a.pr.alpha_mean) / a.pr.alpha_sd;
-        lp += -0.5 * za * za - log(a.pr.alpha_sd) - 0.5 * kLog2Pi;
-        lp += a.pr.w_shape * log(a.pr.w_rate) - a.pr.lgamma_w_shape +
-              (a.pr.w_shape - 1.0) * log(wd) - a.pr.w_rate * wd;
-        const double lj = static_cast<double>(u[0]) + static_cast<double>(u[2]) -
-                          softplusd(-static_cast<double>(u[3])) - softplusd(static_cast<double>(u[3]));
-        acc += lp + lj;
+        // log prior (Sec. 2.2, Appendix B.2) + log Jacobian of the transform:
+        // the parameter-free part is the host constant lp_const; the rest is
+        // O(1) per phase and evaluated in FP32 (ln w = u_w exactly), summed in FP64.
+        const float zm = mu * a.pr_mu_isd;
+        const float za = (al - a.pr_alpha_mean) * a.pr_alpha_isd;
+        const float lpf = -a.pr_lambda * h - 0.5f * zm * zm - 0.5f * za * za + a.pr_wsm1 * u[2] - a.pr_wrate * w;
+        const float ljf = u[0] + u[2] - softplusf(-u[3]) - softplusf(u[3]);
+        acc += a.pr.lp_const + static_cast<double>(lpf) + static_cast<double>(ljf);
         if (a.lq) {
+            float q = 0.f;
 #pragma unroll
-            for (int j = 0; j < 5; ++j)
-                accq += -0.5 * static_cast<double>(e[j]) * e[j] - log(static_cast<double>(sig[j])) - 0.5 * kLog2Pi;
+            for (int j = 0; j < 5; ++j) q += -0.5f * e[j] * e[j] - logf(sig[j]);
+            accq += static_cast<double>(q) - 2.5 * kLog2Pi;
         }
     }
+    if (s == 0 && a.tickets)
+        for (int k = threadIdx.x; k < a.K; k += blockDim.x) a.tickets[k] = 0;
     const double tot = block_sum(acc, sh);
     const double totq = a.lq ? block_sum(accq, sh) : 0.0;
     if (threadIdx.x == 0) {
@@ -242,23 +249,30 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
 // Profile kernels
 // ---------------------------------------------------------------------------
 //
+// With d = x - p - mu and s(d) = 2 / w_side, t = s(d) d, u = t^2,
+// L = 1 / (1 + u), G = 2^-u.  Peaks are sorted by position within a phase,
+// so for one tile of points [xlo, xhi] the peaks of a phase fall into three
+// contiguous index ranges: peaks left of every point (all d > 0, the
+// right-hand width applies), peaks among the points, peaks right of every
+// point (all d < 0).  k_ranges finds them once per step for every (sample,
+// phase, tile), together with the range of peaks whose Gaussian reaches the
+// tile (beyond it 2^-u < 2^-128 is zero in FP32).
+//
+// The Lorentzian over the two side-uniform ranges is almost all of the work
+// (the mixed range holds the few peaks inside the tile); there s is a
+// constant and
+//   t = fma(s, x - p, -s mu)
+// (x - p is exact near the peak, so t keeps full precision there).  The
+// mixed range (side chosen per point, both components) and the Gaussian on
+// the uniform ranges form the near part.  The forward does both in one
+// kernel; the backward's heavier near part runs in its own kernel
+// (k_bwd_near), which keeps the hot kernel's code small.
+//
 // Work item: one warp owns (sample s, tile of kTile consecutive points, chunk
 // c of the phases); lane l holds points i0 + l + 32 j, j < kPts, as kPts/2
-// packed pairs (points 2q and 2q+1 of the lane in one 64-bit register).
-// Items are taken from an atomic work counter (reset by k_sample), so every SM
-// stays busy until the queue drains.
-//
-// With d = x - p - mu and s(d) = 2 / w_side, t = s(d) d, u = t^2,
-// L = 1 / (1 + u), G = 2^-u.  Peaks are sorted by position within a phase, so
-// for one tile [xlo, xhi] the peaks of a phase fall into three contiguous
-// index ranges: peaks left of every point (all d > 0, the right-hand width
-// applies), peaks among the points (side decided per point), peaks right of
-// every point (all d < 0).  On the side-uniform ranges s is a constant and
-//   t = fma(s, x - p, -s mu)
-// (x - p is exact near the peak, so t keeps full precision there); on the
-// mixed range d = (x - p) - mu and the side's scale is selected per point.  The
-// Gaussian is evaluated only on the peaks within its reach of the tile (found
-// by binary search), beyond which 2^-u < 2^-128 is zero in FP32.
+// packed pairs (points 2q and 2q+1 of the lane in one 64-bit register;
+// arithmetic without an |x| operand runs as packed f32x2 instructions).
+// Items are taken from an atomic work counter (zeroed by k_sample).
 struct ProfArgs {
     int S, K, N, Npad, T, Mtot, C;
     int chunk[kMaxChunks + 1];  // phase boundaries of the C chunks
@@ -266,11 +280,12 @@ struct ProfArgs {
     const int *off;
     const float *x, *y, *bg;
     const PhaseConst *cst;
+    ushort4 *ranges;   // [S*K*T] (m1, m2, nb, ne) relative to the phase's first peak
     float *g;          // [S*Npad]
     float *f_out;      // [S*N] or null
     double *llpart;    // [S*T]
     float *gpart;      // [S*K*T*kGradSums]
-    float *fpart;      // [C*S*Npad] partial profiles per chunk
+    float *fpart;      // [C*S*Npad] partial profiles per phase chunk
     int *counter;      // work counter of this kernel (zeroed by k_sample)
 };
 
@@ -305,6 +320,11 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
     return r;
 }
 __device__ __forceinline__ f2_t bc2(float v) { return pk2(v, v); }
+__device__ __forceinline__ float sum2(f2_t v) {
+    float a, b;
+    up2(v, a, b);
+    return a + b;
+}
 
 __device__ __forceinline__ f2_t rcp2(f2_t v) {
     float a, b;
@@ -320,47 +340,109 @@ __device__ __forceinline__ f2_t ex2neg2(f2_t u) {
 
 constexpr int kPairs = kPts / 2;
 
-// Shared-memory table entry: (-p, I) so that x + (-p) is one packed add.
-__device__ __forceinline__ void load_table(const ProfArgs &a, float2 *s_pk, int *s_off) {
-    for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) s_pk[i] = make_float2(-a.pos[i], a.inten[i]);
-    for (int i = threadIdx.x; i <= a.K; i += blockDim.x) s_off[i] = a.off[i];
-    __syncthreads();
-}
+// Margin (degrees) keeping the side-uniform ranges clear of d = 0.
+constexpr float kSideMargin = 1e-4f;
 
-// First m in [lo, hi) whose position p satisfies p > bound (strict) or
-// p >= bound (kInclusive); positions ascend, so -p descends.
+// First m in [lo, hi) with pos[m] > bound (strict) or >= bound (kInclusive).
 template <bool kInclusive>
-__device__ __forceinline__ int first_beyond(const float2 *s_pk, int lo, int hi, float bound) {
-    const float nb = -bound;
+__device__ __forceinline__ int first_beyond(const float *pos, int lo, int hi, float bound) {
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        const float np = s_pk[mid].x;
-        const bool beyond = kInclusive ? (np <= nb) : (np < nb);
+        const float p = pos[mid];
+        const bool beyond = kInclusive ? (p >= bound) : (p > bound);
         if (beyond) hi = mid; else lo = mid + 1;
     }
     return lo;
 }
 
-// Peak index ranges of one phase for one tile (see the header comment).
-struct Ranges {
-    int mb, m1, m2, me;   // [mb,m1) all d > 0, [m1,m2) mixed, [m2,me) all d < 0
-    int nb, ne;           // Gaussian reach
+// Peak index ranges of every (sample, phase, tile):
+//   [mb, m1) all d > 0,  [m1, m2) mixed,  [m2, me) all d < 0,  [nb, ne) Gaussian reach.
+__global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
+    const int total = a.S * a.K * a.T;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int tile = idx % a.T;
+        const int sk = idx / a.T;
+        const int k = sk % a.K;
+        const PhaseConst c = a.cst[sk];
+        const float xlo = a.x[tile * kTile];
+        const float xhi = a.x[min(tile * kTile + kTile - 1, a.N - 1)];
+        const int mb = a.off[k], me = a.off[k + 1];
+        const int m1 = first_beyond<true>(a.pos, mb, me, xlo - c.mu - kSideMargin);
+        const int m2 = first_beyond<false>(a.pos, m1, me, xhi - c.mu + kSideMargin);
+        const int nb = first_beyond<false>(a.pos, mb, me, xlo - c.mu - c.rr);
+        const int ne = first_beyond<true>(a.pos, nb, me, xhi - c.mu + c.rl);
+        a.ranges[idx] = make_ushort4(static_cast<unsigned short>(m1 - mb), static_cast<unsigned short>(m2 - mb),
+                                     static_cast<unsigned short>(nb - mb), static_cast<unsigned short>(ne - mb));
+    }
+}
+
+// Shared-memory peak table.  Entries hold -p (so that x + (-p) is one packed
+// add) and I.  The wide layout stores each value twice, (-p, -p, I, I), so a
+// single 16-byte load yields both packed pairs; it is used when the table is
+// small enough not to limit occupancy.
+template <bool kWide>
+struct PeakTable;
+template <>
+struct PeakTable<false> {
+    const float2 *p;
+    __device__ __forceinline__ void get(int m, f2_t &np, f2_t &I) const {
+        const float2 v = p[m];
+        np = bc2(v.x);
+        I = bc2(v.y);
+    }
+};
+template <>
+struct PeakTable<true> {
+    const float4 *p;
+    __device__ __forceinline__ void get(int m, f2_t &np, f2_t &I) const {
+        const float4 v = p[m];
+        np = pk2(v.x, v.y);
+        I = pk2(v.z, v.w);
+    }
 };
 
-// Margin (degrees) keeping the side-uniform ranges clear of d = 0.
-constexpr float kSideMargin = 1e-4f;
+template <bool kWide>
+__device__ __forceinline__ PeakTable<kWide> load_table(const ProfArgs &a, float4 *s_raw, int *&s_off) {
+    PeakTable<kWide> t;
+    if constexpr (kWide) {
+        float4 *q = s_raw;
+        for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) {
+            const float np = -a.pos[i], I = a.inten[i];
+            q[i] = make_float4(np, np, I, I);
+        }
+        t.p = q;
+        s_off = reinterpret_cast<int *>(q + a.Mtot);
+    } else {
+        float2 *q = reinterpret_cast<float2 *>(s_raw);
+        for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) q[i] = make_float2(-a.pos[i], a.inten[i]);
+        t.p = q;
+        s_off = reinterpret_cast<int *>(q + a.Mtot);
+    }
+    for (int i = threadIdx.x; i <= a.K; i += blockDim.x) s_off[i] = a.off[i];
+    __syncthreads();
+    return t;
+}
 
-__device__ __forceinline__ Ranges phase_ranges(const float2 *s_pk, int mb, int me, const PhaseConst &c,
-                                               float xlo, float xhi) {
-    Ranges r;
-    r.mb = mb;
-    r.me = me;
-    r.m1 = first_beyond<true>(s_pk, mb, me, xlo - c.mu - kSideMargin);
-    r.m2 = first_beyond<false>(s_pk, r.m1, me, xhi - c.mu + kSideMargin);
-    // a peak's Gaussian reaches [xlo, xhi] iff xlo - mu - rr < p < xhi - mu + rl
-    r.nb = first_beyond<false>(s_pk, mb, me, xlo - c.mu - c.rr);
-    r.ne = first_beyond<true>(s_pk, r.nb, me, xhi - c.mu + c.rl);
-    return r;
+struct Ranges {
+    int mb, m1, m2, me, nb, ne;
+};
+
+__device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_off, int s, int k, int tile) {
+    const ushort4 r = a.ranges[(static_cast<size_t>(s) * a.K + k) * a.T + tile];
+    Ranges o;
+    o.mb = s_off[k];
+    o.me = s_off[k + 1];
+    o.m1 = o.mb + r.x;
+    o.m2 = o.mb + r.y;
+    o.nb = o.mb + r.z;
+    o.ne = o.mb + r.w;
+    return o;
+}
+
+// Is there any work for the near kernels (mixed range, or Gaussian reach
+// beyond it)?  Warp-uniform.
+__device__ __forceinline__ bool near_work(const Ranges &r) {
+    return r.m1 < r.m2 || r.nb < r.m1 || r.m2 < r.ne;
 }
 
 // t = s(d) d for a packed pair on the mixed range: the side's scale is
@@ -372,17 +454,55 @@ __device__ __forceinline__ f2_t t_mixed(f2_t x2, f2_t np, f2_t nmu2, float sl, f
     return mul2(d2, pk2(d0 >= 0.f ? sr : sl, d1 >= 0.f ? sr : sl));
 }
 
-// --- forward helpers --------------------------------------------------------
+__device__ __forceinline__ void item_points(const ProfArgs &a, int i0, int lane, f2_t (&x2)[kPairs]) {
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        const int i_a = min(i0 + (2 * q) * 32 + lane, a.N - 1);
+        const int i_b = min(i0 + (2 * q + 1) * 32 + lane, a.N - 1);
+        x2[q] = pk2(a.x[i_a], a.x[i_b]);
+    }
+}
+
+__device__ __forceinline__ int next_item(int *counter, int lane) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// Neumaier-compensated accumulation of packed per-point values.
+template <bool kNaive>
+__device__ __forceinline__ void acc_points(float (&fs)[kPts], float (&fc)[kPts], const f2_t (&v2)[kPairs]) {
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        float v[2];
+        up2(v2[q], v[0], v[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * q + h;
+            if (kNaive) {
+                fs[j] += v[h];
+            } else {
+                const float t = fs[j] + v[h];
+                fc[j] += (fabsf(fs[j]) >= fabsf(v[h])) ? ((fs[j] - t) + v[h]) : ((v[h] - t) + fs[j]);
+                fs[j] = t;
+            }
+        }
+    }
+}
+
+// --- forward ------------------------------------------------------------------
 // Lorentzian sums on a side-uniform range, one reciprocal per two peaks:
 // I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1)  (d = 1 + t^2; d0 d1 stays finite
 // while s |d| < 1e9).
-__device__ __forceinline__ void fwdL_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu,
+template <class Tab>
+__device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
                                              const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs]) {
     const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
     int m = m0;
     for (; m + 1 < m1; m += 2) {
-        const float2 pa = s_pk[m], pb = s_pk[m + 1];
-        const f2_t np0 = bc2(pa.x), I0 = bc2(pa.y), np1 = bc2(pb.x), I1 = bc2(pb.y);
+        f2_t np0, I0, np1, I1;
+        tab.get(m, np0, I0);
+        tab.get(m + 1, np1, I1);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
             const f2_t t0 = fma2(s2, add2(x2[q], np0), c2);
@@ -393,8 +513,8 @@ __device__ __forceinline__ void fwdL_uniform(const float2 *s_pk, int m0, int m1,
         }
     }
     if (m < m1) {
-        const float2 pa = s_pk[m];
-        const f2_t np = bc2(pa.x), I = bc2(pa.y);
+        f2_t np, I;
+        tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
             const f2_t t = fma2(s2, add2(x2[q], np), c2);
@@ -403,82 +523,47 @@ __device__ __forceinline__ void fwdL_uniform(const float2 *s_pk, int m0, int m1,
     }
 }
 
-// Lorentzian and Gaussian sums on the mixed range (peaks among the points).
-__device__ __forceinline__ void fwd_mixed(const float2 *s_pk, int m0, int m1, const PhaseConst &c,
-                                          const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
-    const f2_t nmu2 = bc2(-c.mu), one2 = bc2(1.f);
-    for (int m = m0; m < m1; ++m) {
-        const float2 pa = s_pk[m];
-        const f2_t np = bc2(pa.x), I = bc2(pa.y);
+// Near part of one phase's profile on the tile: the mixed range (both
+// components, side chosen per point) and the Gaussian on the side-uniform
+// ranges within its reach.
+template <class Tab>
+__device__ __forceinline__ void fwd_near(const Tab &tab, const Ranges &r, const PhaseConst &cp,
+                                         const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
+    const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
+    for (int m = r.m1; m < r.m2; ++m) {
+        f2_t np, I;
+        tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = t_mixed(x2[q], np, nmu2, c.sl, c.sr);
+            const f2_t t = t_mixed(x2[q], np, nmu2, cp.sl, cp.sr);
             const f2_t u = mul2(t, t);
             sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
             sg[q] = fma2(I, ex2neg2(u), sg[q]);
         }
     }
-}
-
-__device__ __forceinline__ void fwdG_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu,
-                                             const f2_t (&x2)[kPairs], f2_t (&sg)[kPairs]) {
-    const f2_t s2 = bc2(sc), c2 = bc2(cmu);
-    for (int m = m0; m < m1; ++m) {
-        const float2 pa = s_pk[m];
-        const f2_t np = bc2(pa.x), I = bc2(pa.y);
-#pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = fma2(s2, add2(x2[q], np), c2);
-            sg[q] = fma2(I, ex2neg2(mul2(t, t)), sg[q]);
-        }
-    }
-}
-
-// One phase: the Lorentzian over every peak, the Gaussian over the peaks
-// within reach.  Each loop body exists once; the two side-uniform ranges run
-// the same body with their own constants, which keeps the kernel small.
-__device__ __forceinline__ void fwd_phase(const float2 *s_pk, const Ranges &r, const PhaseConst &c,
-                                          const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
-        const int m0 = side ? r.m2 : r.mb, m1 = side ? r.me : r.m1;
-        fwdL_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, x2, sl);
-    }
-    fwd_mixed(s_pk, r.m1, r.m2, c, x2, sl, sg);
-    if (r.nb < r.m1 || r.m2 < r.ne) {  // warp-uniform
-#pragma unroll 1
-        for (int side = 0; side < 2; ++side) {
-            const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
-            fwdG_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, x2, sg);
+        const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
+        const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
+        for (int m = m0; m < m1; ++m) {
+            f2_t np, I;
+            tab.get(m, np, I);
+#pragma unroll
+            for (int q = 0; q < kPairs; ++q) {
+                const f2_t t = fma2(s2, add2(x2[q], np), c2);
+                sg[q] = fma2(I, ex2neg2(mul2(t, t)), sg[q]);
+            }
         }
     }
-}
-
-__device__ __forceinline__ void item_points(const ProfArgs &a, int i0, int lane, f2_t (&x2)[kPairs],
-                                            float &xlo, float &xhi) {
-#pragma unroll
-    for (int q = 0; q < kPairs; ++q) {
-        const int i_a = min(i0 + (2 * q) * 32 + lane, a.N - 1);
-        const int i_b = min(i0 + (2 * q + 1) * 32 + lane, a.N - 1);
-        x2[q] = pk2(a.x[i_a], a.x[i_b]);
-    }
-    xlo = a.x[i0];
-    xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
-}
-
-__device__ __forceinline__ int next_item(int *counter, int lane) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(counter, 1);
-    return __shfl_sync(0xffffffffu, it, 0);
 }
 
 // Partial profile of one phase chunk: fpart[c][s][i] = sum over the chunk's
-// phases of h_k sum_m I_m V (Neumaier-compensated over phases).
-template <bool kNaive>
+// phases of h sum_m I_m [(1 - r) G + r L] (Neumaier-compensated over phases).
+template <bool kNaive, bool kWide>
 __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
-    extern __shared__ float2 s_pk[];
-    int *s_off = reinterpret_cast<int *>(s_pk + a.Mtot);
-    load_table(a, s_pk, s_off);
+    extern __shared__ float4 s_raw[];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
     const int lane = threadIdx.x & 31;
     const int items = a.S * a.T * a.C;
     for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
@@ -487,38 +572,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
         const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
         f2_t x2[kPairs];
-        float xlo, xhi;
-        item_points(a, i0, lane, x2, xlo, xhi);
+        item_points(a, i0, lane, x2);
         float fs[kPts], fc[kPts];
 #pragma unroll
         for (int j = 0; j < kPts; ++j) fs[j] = fc[j] = 0.f;
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
-        const int kb = a.chunk[c], ke = a.chunk[c + 1];
-        for (int k = kb; k < ke; ++k) {
+        for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
             const PhaseConst cp = cs[k];
-            const Ranges r = phase_ranges(s_pk, s_off[k], s_off[k + 1], cp, xlo, xhi);
+            const Ranges r = load_ranges(a, s_off, s, k, tile);
             f2_t sl[kPairs], sg[kPairs];
 #pragma unroll
             for (int q = 0; q < kPairs; ++q) sl[q] = sg[q] = 0ull;
-            fwd_phase(s_pk, r, cp, x2, sl, sg);
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                fwdL_uniform(tab, side ? r.m2 : r.mb, side ? r.me : r.m1, side ? cp.sl : cp.sr,
+                             side ? cp.nslmu : cp.nsrmu, x2, sl);
+            }
+            if (near_work(r)) fwd_near(tab, r, cp, x2, sl, sg);  // warp-uniform
             const f2_t hl2 = bc2(cp.hl), hg2 = bc2(cp.hg);
 #pragma unroll
-            for (int q = 0; q < kPairs; ++q) {
-                float v[2];
-                up2(fma2(hl2, sl[q], mul2(hg2, sg[q])), v[0], v[1]);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = 2 * q + h;
-                    if (kNaive) {
-                        fs[j] += v[h];
-                    } else {
-                        // Neumaier compensated summation over phases
-                        const float t = fs[j] + v[h];
-                        fc[j] += (fabsf(fs[j]) >= fabsf(v[h])) ? ((fs[j] - t) + v[h]) : ((v[h] - t) + fs[j]);
-                        fs[j] = t;
-                    }
-                }
-            }
+            for (int q = 0; q < kPairs; ++q) sl[q] = fma2(hl2, sl[q], mul2(hg2, sg[q]));
+            acc_points<kNaive>(fs, fc, sl);
         }
         float *dst = a.fpart + (static_cast<size_t>(c) * a.S + s) * a.Npad + i0 + lane;
 #pragma unroll
@@ -545,31 +619,39 @@ __device__ __forceinline__ float deviance_term(float y, float f) {
     return -(y * logf(__fdiv_rn(y, f)) - dif);
 }
 
-// f = B + sum of the chunk partials (FP64, fixed order), then the deviance
-// term, g = y/f - 1 and the per-tile FP64 deviance sum.  One block per
-// (sample, tile); kTile == blockDim.x.
+// f = B + sum of the C chunk partials (fixed order; all terms are positive,
+// so the FP32 sum errs by at most C ulps), then the deviance term, g = y/f - 1
+// and the per-tile deviance sum (all terms <= 0: an FP32 tree sum without
+// cancellation, stored in FP64).  One block per (sample, tile);
+// kTile == blockDim.x.
 __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
-    __shared__ double sh[kTile / 32];
+    __shared__ float shf[kTile / 32];
     const int s = blockIdx.x / a.T, tile = blockIdx.x - s * a.T;
     const int i = tile * kTile + threadIdx.x;
-    double dev = 0.0;
+    float dev = 0.f;
     float gv = 0.f;
     if (i < a.N) {
-        double fd = a.bg[i];
-        for (int c = 0; c < a.C; ++c) fd += a.fpart[(static_cast<size_t>(c) * a.S + s) * a.Npad + i];
-        const float f = static_cast<float>(fd);
+        float f = a.bg[i];
+        for (int c = 0; c < a.C; ++c) f += a.fpart[(static_cast<size_t>(c) * a.S + s) * a.Npad + i];
         const float yv = a.y[i];
-        dev = static_cast<double>(deviance_term(yv, f));
+        dev = deviance_term(yv, f);
         gv = (yv > 0.f) ? __fdiv_rn(yv, f) - 1.0f : -1.0f;
         if (a.f_out) a.f_out[static_cast<size_t>(s) * a.N + i] = f;
     }
     a.g[static_cast<size_t>(s) * a.Npad + i] = gv;
-    dev = block_sum(dev, sh);
-    if (threadIdx.x == 0) a.llpart[static_cast<size_t>(s) * a.T + tile] = dev;
+    dev = warp_sumf(dev);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) shf[w] = dev;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < kTile / 32 ? shf[threadIdx.x] : 0.f;
+        t = warp_sumf(t);
+        if (threadIdx.x == 0) a.llpart[static_cast<size_t>(s) * a.T + tile] = static_cast<double>(t);
+    }
 }
 
-// --- backward helpers -------------------------------------------------------
-// Accumulators (packed pairs, per lane), with q = (y/f - 1) I:
+// --- backward -----------------------------------------------------------------
+// Gradient sums per (sample, phase, tile), with q = (y/f - 1) I:
 //   0 S1G = sum q G          1 S1L = sum q L
 //   2 AG  = sum q G t        3 AL  = sum q L^2 t
 //   4 AGs = sum q G |t|      5 ALs = sum q L^2 |t|
@@ -578,16 +660,17 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
 // (t carries the sign of d, so the |t| sums separate the two sides; on a
 // side-uniform range |t| = +-t and those sums follow from the plain ones).
 
-// Lorentzian part on a side-uniform range (sgn = +1: all d > 0, -1: all d < 0).
-__device__ __forceinline__ void bwdL_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu, bool right,
+// Lorentzian part on one side-uniform range: S1 += sum q L, A += sum q L^2 t,
+// C2 += sum q L^2.  Since L (1 + t^2) = 1, q L^2 t^2 = q L - q L^2, so the
+// range's sum q L^2 t^2 is S1 - C2 and needs no product of its own.
+template <class Tab>
+__device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
                                              const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
-                                             f2_t (&acc)[kGradSums]) {
-    if (m0 >= m1) return;
+                                             f2_t &S1, f2_t &A, f2_t &C2) {
     const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
-    f2_t S1 = 0ull, A = 0ull, B = 0ull;
     for (int m = m0; m < m1; ++m) {
-        const float2 pa = s_pk[m];
-        const f2_t np = bc2(pa.x), I = bc2(pa.y);
+        f2_t np, I;
+        tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
             const f2_t t = fma2(s2, add2(x2[q], np), c2);
@@ -596,14 +679,55 @@ __device__ __forceinline__ void bwdL_uniform(const float2 *s_pk, int m0, int m1,
             S1 = add2(S1, q1);
             const f2_t q2 = mul2(q1, L);
             A = fma2(q2, t, A);
-            B = fma2(mul2(q2, t), t, B);
+            C2 = add2(C2, q2);
         }
     }
-    acc[1] = add2(acc[1], S1);
-    acc[3] = add2(acc[3], A);
-    acc[7] = add2(acc[7], B);
-    acc[5] = right ? add2(acc[5], A) : sub2(acc[5], A);
-    acc[9] = right ? add2(acc[9], B) : sub2(acc[9], B);
+}
+
+template <bool kWide>
+__global__ void __launch_bounds__(kThreads, 4) k_bwd_uniform(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    const int lane = threadIdx.x & 31;
+    const int items = a.S * a.T * a.C;
+    for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
+        const int c = item % a.C;
+        const int st = item / a.C;
+        const int s = st / a.T, tile = st - s * a.T;
+        const int i0 = tile * kTile;
+        f2_t x2[kPairs], g2[kPairs];
+        item_points(a, i0, lane, x2);
+        const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
+        const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
+        for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
+            const PhaseConst cp = cs[k];
+            const Ranges r = load_ranges(a, s_off, s, k, tile);
+            f2_t S1 = 0ull, A[2] = {0ull, 0ull}, B[2] = {0ull, 0ull};
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                f2_t S1s = 0ull, As = 0ull, C2s = 0ull;
+                bwdL_uniform(tab, side ? r.m2 : r.mb, side ? r.me : r.m1, side ? cp.sl : cp.sr,
+                             side ? cp.nslmu : cp.nsrmu, x2, g2, S1s, As, C2s);
+                S1 = add2(S1, S1s);
+                const f2_t Bs = sub2(S1s, C2s);
+                if (side) { A[1] = As; B[1] = Bs; } else { A[0] = As; B[0] = Bs; }
+            }
+            // side 0: all d > 0 (|t| = t); side 1: all d < 0 (|t| = -t)
+            float v[5] = {sum2(S1), sum2(add2(A[0], A[1])), sum2(sub2(A[0], A[1])), sum2(add2(B[0], B[1])),
+                          sum2(sub2(B[0], B[1]))};
+#pragma unroll
+            for (int j = 0; j < 5; ++j) v[j] = warp_sumf(v[j]);
+            if (lane == 0) {
+                float2 *dst = reinterpret_cast<float2 *>(
+                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) dst[j] = make_float2(0.f, v[j]);
+            }
+        }
+    }
 }
 
 // Accumulate v * |t| into a packed pair of sums (scalar FMAs: |t| is a free
@@ -616,86 +740,15 @@ __device__ __forceinline__ f2_t fma_abs2(f2_t v, f2_t t, f2_t acc) {
     return pk2(fmaf(v0, fabsf(t0), a0), fmaf(v1, fabsf(t1), a1));
 }
 
-// Both components on the mixed range (peaks among the points).
-__device__ __forceinline__ void bwd_mixed(const float2 *s_pk, int m0, int m1, const PhaseConst &c,
-                                          const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
-                                          f2_t (&acc)[kGradSums]) {
-    const f2_t nmu2 = bc2(-c.mu), one2 = bc2(1.f);
-    for (int m = m0; m < m1; ++m) {
-        const float2 pa = s_pk[m];
-        const f2_t np = bc2(pa.x), I = bc2(pa.y);
-#pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = t_mixed(x2[q], np, nmu2, c.sl, c.sr);
-            const f2_t u = mul2(t, t);
-            const f2_t L = rcp2(add2(u, one2));
-            const f2_t gI = mul2(g2[q], I);
-            const f2_t q1 = mul2(gI, L);
-            acc[1] = add2(acc[1], q1);
-            const f2_t q2 = mul2(q1, L);
-            acc[3] = fma2(q2, t, acc[3]);
-            acc[5] = fma_abs2(q2, t, acc[5]);
-            const f2_t q3 = mul2(q2, t);
-            acc[7] = fma2(q3, t, acc[7]);
-            acc[9] = fma_abs2(q3, t, acc[9]);
-            const f2_t qg = mul2(gI, ex2neg2(u));
-            acc[0] = add2(acc[0], qg);
-            acc[2] = fma2(qg, t, acc[2]);
-            acc[4] = fma_abs2(qg, t, acc[4]);
-            const f2_t q3g = mul2(qg, t);
-            acc[6] = fma2(q3g, t, acc[6]);
-            acc[8] = fma_abs2(q3g, t, acc[8]);
-        }
-    }
-}
-
-__device__ __forceinline__ void bwdG_uniform(const float2 *s_pk, int m0, int m1, float sc, float cmu, bool right,
-                                             const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
-                                             f2_t (&acc)[kGradSums]) {
-    if (m0 >= m1) return;
-    const f2_t s2 = bc2(sc), c2 = bc2(cmu);
-    f2_t S1 = 0ull, A = 0ull, B = 0ull;
-    for (int m = m0; m < m1; ++m) {
-        const float2 pa = s_pk[m];
-        const f2_t np = bc2(pa.x), I = bc2(pa.y);
-#pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = fma2(s2, add2(x2[q], np), c2);
-            const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(mul2(t, t)));
-            S1 = add2(S1, qg);
-            A = fma2(qg, t, A);
-            B = fma2(mul2(qg, t), t, B);
-        }
-    }
-    acc[0] = add2(acc[0], S1);
-    acc[2] = add2(acc[2], A);
-    acc[6] = add2(acc[6], B);
-    acc[4] = right ? add2(acc[4], A) : sub2(acc[4], A);
-    acc[8] = right ? add2(acc[8], B) : sub2(acc[8], B);
-}
-
-__device__ __forceinline__ void bwd_phase(const float2 *s_pk, const Ranges &r, const PhaseConst &c,
-                                          const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
-                                          f2_t (&acc)[kGradSums]) {
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-        const int m0 = side ? r.m2 : r.mb, m1 = side ? r.me : r.m1;
-        bwdL_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, side == 0, x2, g2, acc);
-    }
-    bwd_mixed(s_pk, r.m1, r.m2, c, x2, g2, acc);
-    if (r.nb < r.m1 || r.m2 < r.ne) {  // warp-uniform
-#pragma unroll 1
-        for (int side = 0; side < 2; ++side) {
-            const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
-            bwdG_uniform(s_pk, m0, m1, side ? c.sl : c.sr, side ? c.nslmu : c.nsrmu, side == 0, x2, g2, acc);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_backward(ProfArgs a) {
-    extern __shared__ float2 s_pk[];
-    int *s_off = reinterpret_cast<int *>(s_pk + a.Mtot);
-    load_table(a, s_pk, s_off);
+// Near part of the gradient sums (mixed range: both components; Gaussian on
+// the side-uniform ranges), added to the sums k_bwd_uniform wrote.  The
+// ranges of 32 phases are loaded at once, one per lane, and only the phases
+// with near work on this tile (a warp ballot) are visited.
+template <bool kWide>
+__global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
     const int lane = threadIdx.x & 31;
     const int items = a.S * a.T * a.C;
     for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
@@ -704,37 +757,102 @@ __global__ void __launch_bounds__(kThreads) k_backward(ProfArgs a) {
         const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
         f2_t x2[kPairs], g2[kPairs];
-        float xlo, xhi;
-        item_points(a, i0, lane, x2, xlo, xhi);
-        const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
-#pragma unroll
-        for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
+        bool loaded = false;
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
-        const int kb = a.chunk[c], ke = a.chunk[c + 1];
-        for (int k = kb; k < ke; ++k) {
-            const PhaseConst cp = cs[k];
-            const Ranges r = phase_ranges(s_pk, s_off[k], s_off[k + 1], cp, xlo, xhi);
-            f2_t acc[kGradSums];
-#pragma unroll
-            for (int j = 0; j < kGradSums; ++j) acc[j] = 0ull;
-            bwd_phase(s_pk, r, cp, x2, g2, acc);
-            float rr[kGradSums];
-#pragma unroll
-            for (int j = 0; j < kGradSums; ++j) {
-                float lo, hi;
-                up2(acc[j], lo, hi);
-                rr[j] = lo + hi;
+        const int kend = a.chunk[c + 1];
+        for (int kb = a.chunk[c]; kb < kend; kb += 32) {
+            const int kl = kb + lane;
+            Ranges rl;
+            bool work = false;
+            if (kl < kend) {
+                rl = load_ranges(a, s_off, s, kl, tile);
+                work = near_work(rl);
             }
-            const bool anyg = r.nb < r.ne || r.m1 < r.m2;  // warp-uniform
+            unsigned mask = __ballot_sync(0xffffffffu, work);
+            if (mask && !loaded) {
+                item_points(a, i0, lane, x2);
+                const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
 #pragma unroll
-            for (int j = 0; j < kGradSums; ++j) {
-                if ((j & 1) || anyg) rr[j] = warp_sumf(rr[j]);
+                for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
+                loaded = true;
             }
-            if (lane == 0) {
-                float2 *dst = reinterpret_cast<float2 *>(
-                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int k = kb + src;
+                Ranges r;
+                r.mb = __shfl_sync(0xffffffffu, rl.mb, src);
+                r.m1 = __shfl_sync(0xffffffffu, rl.m1, src);
+                r.m2 = __shfl_sync(0xffffffffu, rl.m2, src);
+                r.me = __shfl_sync(0xffffffffu, rl.me, src);
+                r.nb = __shfl_sync(0xffffffffu, rl.nb, src);
+                r.ne = __shfl_sync(0xffffffffu, rl.ne, src);
+                const PhaseConst cp = cs[k];
+                f2_t acc[kGradSums];
 #pragma unroll
-                for (int j = 0; j < kGradSums; j += 2) dst[j / 2] = make_float2(rr[j], rr[j + 1]);
+                for (int j = 0; j < kGradSums; ++j) acc[j] = 0ull;
+                const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
+                for (int m = r.m1; m < r.m2; ++m) {
+                    f2_t np, I;
+                    tab.get(m, np, I);
+#pragma unroll
+                    for (int q = 0; q < kPairs; ++q) {
+                        const f2_t t = t_mixed(x2[q], np, nmu2, cp.sl, cp.sr);
+                        const f2_t u = mul2(t, t);
+                        const f2_t L = rcp2(add2(u, one2));
+                        const f2_t gI = mul2(g2[q], I);
+                        const f2_t q1 = mul2(gI, L);
+                        acc[1] = add2(acc[1], q1);
+                        const f2_t q2 = mul2(q1, L);
+                        acc[3] = fma2(q2, t, acc[3]);
+                        acc[5] = fma_abs2(q2, t, acc[5]);
+                        const f2_t q3 = mul2(q2, t);
+                        acc[7] = fma2(q3, t, acc[7]);
+                        acc[9] = fma_abs2(q3, t, acc[9]);
+                        const f2_t qg = mul2(gI, ex2neg2(u));
+                        acc[0] = add2(acc[0], qg);
+                        acc[2] = fma2(qg, t, acc[2]);
+                        acc[4] = fma_abs2(qg, t, acc[4]);
+                        const f2_t q3g = mul2(qg, t);
+                        acc[6] = fma2(q3g, t, acc[6]);
+                        acc[8] = fma_abs2(q3g, t, acc[8]);
+                    }
+                }
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
+                    const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
+                    f2_t S1 = 0ull, A = 0ull, B = 0ull;
+                    for (int m = m0; m < m1; ++m) {
+                        f2_t np, I;
+                        tab.get(m, np, I);
+#pragma unroll
+                        for (int q = 0; q < kPairs; ++q) {
+                            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+                            const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(mul2(t, t)));
+                            S1 = add2(S1, qg);
+                            A = fma2(qg, t, A);
+                            B = fma2(mul2(qg, t), t, B);
+                        }
+                    }
+                    acc[0] = add2(acc[0], S1);
+                    acc[2] = add2(acc[2], A);
+                    acc[6] = add2(acc[6], B);
+                    acc[4] = side ? sub2(acc[4], A) : add2(acc[4], A);
+                    acc[8] = side ? sub2(acc[8], B) : add2(acc[8], B);
+                }
+                float v[kGradSums];
+#pragma unroll
+                for (int j = 0; j < kGradSums; ++j) v[j] = warp_sumf(sum2(acc[j]));
+                if (lane == 0) {
+                    float2 *dst = reinterpret_cast<float2 *>(
+                        a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
+#pragma unroll
+                    for (int j = 0; j < kGradSums; j += 2) {
+                        const float2 o = dst[j / 2];
+                        dst[j / 2] = make_float2(o.x + v[j], o.y + v[j + 1]);
+                    }
+                }
             }
         }
     }
@@ -757,6 +875,9 @@ struct GradArgs {
     int *d_step;
     const double *llpart, *lpj, *ent;
     double *ll, *elbo_out, *trace;
+    double *gred;   // [K*kGradBlocks*10] per-sample-block partial sums
+    int *tickets;   // [K] arrival tickets (zeroed by k_sample, reset by the last block)
+    int NB;         // sample blocks per phase
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -783,59 +904,109 @@ __global__ void __launch_bounds__(256) k_elbo(GradArgs a) {
     }
 }
 
+// Gradient of the ELBO for phase k = blockIdx.x over sample block
+// blockIdx.y, 32 samples at a time.  Stage 1: one warp per (sample, phase)
+// record, the lanes read the record's tiles (coalesced) and tree-sum the ten
+// partial sums in FP32 into shared memory.  Stage 2: warp 0, one sample per
+// lane, forms the per-sample gradient in FP64 and accumulates it; the lanes
+// are combined by a fixed shuffle tree.  The last block of the phase to
+// arrive adds the block totals in a fixed order (deterministic) and applies
+// Adam.
 __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
-    __shared__ double sh[8];
+    __shared__ float qs[32][kGradSums + 1];
     __shared__ double red[10];
-    const int k = blockIdx.x;
+    __shared__ int is_last;
+    const int k = blockIdx.x, b = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s0 = static_cast<int>((static_cast<long long>(a.S) * b) / a.NB);
+    const int s1 = static_cast<int>((static_cast<long long>(a.S) * (b + 1)) / a.NB);
     double accl[5] = {0, 0, 0, 0, 0}, acce[5] = {0, 0, 0, 0, 0};
     const double ln2 = kLn2;
-    for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
-        const size_t sk = static_cast<size_t>(s) * a.K + k;
-        const float2 *gp = reinterpret_cast<const float2 *>(a.gpart + sk * a.T * kGradSums);
-        double q[kGradSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int t = 0; t < a.T; ++t) {
+    for (int c0 = s0; c0 < s1; c0 += 32) {
+        const int nc = s1 - c0 < 32 ? s1 - c0 : 32;
+        for (int i = warp; i < nc; i += kWarps) {
+            const size_t sk = static_cast<size_t>(c0 + i) * a.K + k;
+            const float2 *gp = reinterpret_cast<const float2 *>(a.gpart + sk * a.T * kGradSums);
+            float qf[kGradSums];
 #pragma unroll
-            for (int j = 0; j < kGradSums / 2; ++j) {
-                const float2 v = gp[t * (kGradSums / 2) + j];
-                q[2 * j] += v.x;
-                q[2 * j + 1] += v.y;
+            for (int j = 0; j < kGradSums; ++j) qf[j] = 0.f;
+            for (int t = lane; t < a.T; t += 32) {
+#pragma unroll
+                for (int j = 0; j < kGradSums / 2; ++j) {
+                    const float2 v = gp[t * (kGradSums / 2) + j];
+                    qf[2 * j] += v.x;
+                    qf[2 * j + 1] += v.y;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) qf[j] = warp_sumf(qf[j]);
+            if (lane < kGradSums) {
+                float v = qf[0];
+#pragma unroll
+                for (int j = 1; j < kGradSums; ++j) v = lane == j ? qf[j] : v;
+                qs[i][lane] = v;
             }
         }
-        const float *th = a.theta + sk * 5;
-        const float *ep = a.eps + sk * 5;
-        const double h = th[0], mu = th[1], w = th[2], r = th[3], al = th[4];
-        const bool clamped = !(th[4] > static_cast<float>(a.pr.alpha_min));
-        const double acl = clamped ? static_cast<double>(static_cast<float>(a.pr.alpha_min)) : al;
-        const double sl = 2.0 / w, sr = 2.0 / (acl * w);
-        // side splits: X+ = (X + Xs)/2 (d >= 0), X- = (X - Xs)/2 (d < 0)
-        const double AGp = 0.5 * (q[2] + q[4]), AGm = 0.5 * (q[2] - q[4]);
-        const double ALp = 0.5 * (q[3] + q[5]), ALm = 0.5 * (q[3] - q[5]);
-        const double BGp = 0.5 * (q[6] + q[8]), BLp = 0.5 * (q[7] + q[9]);
-        double G[5];
-        // likelihood part (chained to u) + prior/Jacobian part
-        G[0] = h * ((1.0 - r) * q[0] + r * q[1]) + (1.0 - a.pr.lambda * h);
-        G[1] = 2.0 * h * ((1.0 - r) * ln2 * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
-               mu / (a.pr.mu_sd * a.pr.mu_sd);
-        G[2] = 2.0 * h * ((1.0 - r) * ln2 * q[6] + r * q[7]) + (a.pr.w_shape - a.pr.w_rate * w);
-        G[3] = r * (1.0 - r) * h * (q[1] - q[0]) + (1.0 - 2.0 * r);
-        const double gal = clamped ? 0.0 : (2.0 * h / acl) * ((1.0 - r) * ln2 * BGp + r * BLp);
-        G[4] = gal - (al - a.pr.alpha_mean) / (a.pr.alpha_sd * a.pr.alpha_sd);
+        __syncthreads();
+        if (warp == 0 && lane < nc) {
+            double q[kGradSums];
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) q[j] = qs[lane][j];
+            const size_t sk = static_cast<size_t>(c0 + lane) * a.K + k;
+            const float *th = a.theta + sk * 5;
+            const float *ep = a.eps + sk * 5;
+            const double h = th[0], mu = th[1], w = th[2], r = th[3], al = th[4];
+            const bool clamped = !(th[4] > static_cast<float>(a.pr.alpha_min));
+            const double acl = clamped ? static_cast<double>(static_cast<float>(a.pr.alpha_min)) : al;
+            const double sl = 2.0 / w, sr = 2.0 / (acl * w);
+            // side splits: X+ = (X + Xs)/2 (d >= 0), X- = (X - Xs)/2 (d < 0)
+            const double AGp = 0.5 * (q[2] + q[4]), AGm = 0.5 * (q[2] - q[4]);
+            const double ALp = 0.5 * (q[3] + q[5]), ALm = 0.5 * (q[3] - q[5]);
+            const double BGp = 0.5 * (q[6] + q[8]), BLp = 0.5 * (q[7] + q[9]);
+            double G[5];
+            // likelihood part (chained to u) + prior/Jacobian part
+            G[0] = h * ((1.0 - r) * q[0] + r * q[1]) + (1.0 - a.pr.lambda * h);
+            G[1] = 2.0 * h * ((1.0 - r) * ln2 * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
+                   mu / (a.pr.mu_sd * a.pr.mu_sd);
+            G[2] = 2.0 * h * ((1.0 - r) * ln2 * q[6] + r * q[7]) + (a.pr.w_shape - a.pr.w_rate * w);
+            G[3] = r * (1.0 - r) * h * (q[1] - q[0]) + (1.0 - 2.0 * r);
+            const double gal = clamped ? 0.0 : (2.0 * h / acl) * ((1.0 - r) * ln2 * BGp + r * BLp);
+            G[4] = gal - (al - a.pr.alpha_mean) / (a.pr.alpha_sd * a.pr.alpha_sd);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                accl[j] += G[j];
+                acce[j] += G[j] * static_cast<double>(ep[j]);
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            accl[j] += G[j];
-            acce[j] += G[j] * static_cast<double>(ep[j]);
+            accl[j] = warp_sumd(accl[j]);
+            acce[j] = warp_sumd(acce[j]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                a.gred[(static_cast<size_t>(k) * a.NB + b) * 10 + j] = accl[j];
+                a.gred[(static_cast<size_t>(k) * a.NB + b) * 10 + 5 + j] = acce[j];
+            }
         }
     }
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const double v1 = block_sum(accl[j], sh);
-        const double v2 = block_sum(acce[j], sh);
-        if (threadIdx.x == 0) {
-            red[j] = v1;
-            red[5 + j] = v2;
-        }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.tickets[k], 1) == a.NB - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x < 10) {
+        double tot = 0.0;
+        for (int bb = 0; bb < a.NB; ++bb) tot += __ldcg(&a.gred[(static_cast<size_t>(k) * a.NB + bb) * 10 + threadIdx.x]);
+        red[threadIdx.x] = tot;
     }
     __syncthreads();
+    if (threadIdx.x == 0) a.tickets[k] = 0;
     if (threadIdx.x < 10) {
         const int j = threadIdx.x % 5;
         const bool is_raw = threadIdx.x >= 5;
@@ -1071,18 +1242,36 @@ __global__ void k_post_topm(PostArgs a) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Largest table for which the wide layout is used (keeps four blocks per SM).
+constexpr size_t kWideTableBytes = 56 * 1024;
+
+template <class F>
+static void set_smem_attr(F f, int bytes) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 void configure_grids(Problem &P, int sm_count) {
-    P.smem = static_cast<size_t>(P.Mtot) * sizeof(float2) + static_cast<size_t>(P.K + 1) * sizeof(int);
+    const size_t offs = static_cast<size_t>(P.K + 1) * sizeof(int);
+    P.wide = static_cast<size_t>(P.Mtot) * sizeof(float4) + offs <= kWideTableBytes;
+    P.smem = static_cast<size_t>(P.Mtot) * (P.wide ? sizeof(float4) : sizeof(float2)) + offs;
+    P.smem_fwd = static_cast<size_t>(P.Mtot) * sizeof(float2) + offs;
     // The attribute is per function, shared by every context: always allow the
     // largest table any context may have, never the current problem's size.
     const int smax = static_cast<int>(static_cast<size_t>(kMaxPeaks) * sizeof(float2) +
                                       static_cast<size_t>(kMaxK + 1) * sizeof(int));
-    cudaFuncSetAttribute(k_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    cudaFuncSetAttribute(k_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    set_smem_attr(k_forward<false, false>, smax);
+    set_smem_attr(k_forward<true, false>, smax);
+
+    set_smem_attr(k_bwd_uniform<false>, smax);
+    set_smem_attr(k_bwd_uniform<true>, smax);
+    set_smem_attr(k_bwd_near<false>, smax);
+    set_smem_attr(k_bwd_near<true>, smax);
     int bf = 1, bb = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward<false>, kThreads, P.smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_backward, kThreads, P.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward<false, false>, kThreads, P.smem_fwd);
+    if (P.wide)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_bwd_uniform<true>, kThreads, P.smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_bwd_uniform<false>, kThreads, P.smem);
     if (bf < 1) bf = 1;
     if (bb < 1) bb = 1;
     P.grid_fwd = bf * sm_count;
@@ -1095,7 +1284,7 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     for (int c = 0; c <= kMaxChunks; ++c) a.chunk[c] = c <= W.C ? W.chunk[c] : P.K;
     a.pos = P.pos; a.inten = P.inten; a.off = P.off;
     a.x = P.x; a.y = P.y; a.bg = P.bg;
-    a.cst = W.cst; a.g = W.g; a.f_out = f_out; a.llpart = W.llpart; a.gpart = W.gpart;
+    a.cst = W.cst; a.ranges = W.ranges; a.g = W.g; a.f_out = f_out; a.llpart = W.llpart; a.gpart = W.gpart;
     a.fpart = W.fpart; a.counter = W.counters;
     return a;
 }
@@ -1140,24 +1329,42 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.tag = tag; a.step = step; a.d_step = d_step; a.d_iter = d_iter; a.ent = ent;
     a.pr = P.prior; a.eps = W.eps; a.theta = W.theta; a.cst = W.cst; a.lpj = W.lpj; a.lq = W.lq;
     a.counters = W.counters;
+    a.tickets = W.tickets;
+    a.pr_lambda = static_cast<float>(P.prior.lambda);
+    a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
+    a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
+    a.pr_alpha_isd = static_cast<float>(1.0 / P.prior.alpha_sd);
+    a.pr_wsm1 = static_cast<float>(P.prior.w_shape - 1.0);
+    a.pr_wrate = static_cast<float>(P.prior.w_rate);
     k_sample<<<W.S, 128, 0, st>>>(a);
 }
 
 void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st) {
     ProfArgs a = prof_args(P, W, f_out);
+    const int nr = W.S * P.K * P.T;
+    k_ranges<<<(nr + 255) / 256 < 4096 ? (nr + 255) / 256 : 4096, 256, 0, st>>>(a);
+    // the forward reads the compact table (measured faster than the wide one)
     const int grid = grid_for(P.grid_fwd, W.S * P.T * W.C);
     if (naive)
-        k_forward<true><<<grid, kThreads, P.smem, st>>>(a);
+        k_forward<true, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
     else
-        k_forward<false><<<grid, kThreads, P.smem, st>>>(a);
+        k_forward<false, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
     k_lik<<<W.S * P.T, kTile, 0, st>>>(a);
 }
 
 void launch_backward(const Problem &P, Workspace &W, cudaStream_t st) {
     ProfArgs a = prof_args(P, W, nullptr);
-    a.counter = W.counters + 1;
     const int grid = grid_for(P.grid_bwd, W.S * P.T * W.C);
-    k_backward<<<grid, kThreads, P.smem, st>>>(a);
+    a.counter = W.counters + 2;
+    if (P.wide)
+        k_bwd_uniform<true><<<grid, kThreads, P.smem, st>>>(a);
+    else
+        k_bwd_uniform<false><<<grid, kThreads, P.smem, st>>>(a);
+    a.counter = W.counters + 3;
+    if (P.wide)
+        k_bwd_near<true><<<grid, kThreads, P.smem, st>>>(a);
+    else
+        k_bwd_near<false><<<grid, kThreads, P.smem, st>>>(a);
 }
 
 void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,
@@ -1171,7 +1378,10 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.grad_out = grad_out; a.adam = adam ? 1 : 0; a.ac = ac; a.m = m; a.v = v;
     a.d_iter = d_iter; a.d_step = d_step; a.llpart = W.llpart; a.lpj = W.lpj; a.ent = ent;
     a.ll = W.ll; a.elbo_out = elbo_out; a.trace = trace;
-    if (grad_out || adam) k_grad<<<P.K, 256, 0, st>>>(a);
+    a.gred = W.gred; a.tickets = W.tickets;
+    a.NB = (W.S + 31) / 32;   // 32 samples (4 per warp) per block
+    a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
+    if (grad_out || adam) k_grad<<<dim3(P.K, a.NB), 256, 0, st>>>(a);
     if (elbo_out || trace) k_elbo<<<1, 256, 0, st>>>(a);
 }
 

@@ -95,8 +95,10 @@ extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, i
         const size_t sk = s * K, C = chunks(s);
         size_t b = 0;
         b += a256(sk * 5 * 4) * 2 + a256(sk * sizeof(PhaseConst)) + a256(s * 8) * 2 + a256(s * Npad * 4) +
-             a256(s * T * 8) + a256(C * s * Npad * 4) + a256(8);
-        b += fit ? a256(sk * T * kGradSums * 4) : a256(s * 8);
+             a256(s * T * 8) + a256(C * s * Npad * 4) + a256(sk * T * 8) + a256(kCounters * 4);
+        b += fit ? a256(sk * T * kGradSums * 4) + a256(static_cast<size_t>(K) * kGradBlocks * 80) +
+                       a256(static_cast<size_t>(K) * 4)
+                 : a256(s * 8);
         return b;
     };
     size_t b = a256(M_total * 4) * 2 + a256((K + 1) * 4) + a256(N * 4) * 3 + a256(K * 8);

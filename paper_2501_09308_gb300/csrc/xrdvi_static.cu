@@ -68,7 +68,10 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     const size_t o_llp = off;    off += align256(static_cast<size_t>(S) * T * sizeof(double));
     const size_t o_gp = off;     off += align256(SK * T * kGradSums * sizeof(float));
     const size_t o_fp = off;     off += align256(static_cast<size_t>(S) * Npad * sizeof(float));
-    const size_t o_cnt = off;    off += align256(2 * sizeof(int));
+    const size_t o_rg = off;     off += align256(SK * T * sizeof(ushort4));
+    const size_t o_cnt = off;    off += align256(kCounters * sizeof(int));
+    const size_t o_gred = off;   off += align256(static_cast<size_t>(K) * kGradBlocks * 10 * sizeof(double));
+    const size_t o_tk = off;     off += align256(static_cast<size_t>(K) * sizeof(int));
     if (off > XRDVI_STATIC_SCRATCH_BYTES)
         return report_error(XRDVI_EINVAL, "elbo_grad_static: this problem needs " + std::to_string(off) +
                                               " bytes of scratch, more than the " +
@@ -120,6 +123,10 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     P.prior.w_rate = cfg->prior_w_rate;
     P.prior.lgamma_w_shape = std::lgamma(static_cast<double>(cfg->prior_w_shape));
     P.prior.alpha_min = cfg->alpha_min;
+    P.prior.lp_const = std::log(lambda_) - std::log(static_cast<double>(cfg->prior_mu_sd)) -
+                       std::log(static_cast<double>(cfg->prior_alpha_sd)) - std::log(2.0 * M_PI) +
+                       cfg->prior_w_shape * std::log(static_cast<double>(cfg->prior_w_rate)) -
+                       P.prior.lgamma_w_shape;
     configure_grids(P, sms);
 
     // Every scratch element is written before it is read in one call (the
@@ -138,7 +145,10 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     W.llpart = reinterpret_cast<double *>(base + o_llp);
     W.gpart = reinterpret_cast<float *>(base + o_gp);
     W.fpart = reinterpret_cast<float *>(base + o_fp);     // one phase chunk
+    W.ranges = reinterpret_cast<ushort4 *>(base + o_rg);
     W.counters = reinterpret_cast<int *>(base + o_cnt);   // zeroed by the sampling kernel
+    W.gred = reinterpret_cast<double *>(base + o_gred);
+    W.tickets = reinterpret_cast<int *>(base + o_tk);     // zeroed by the sampling kernel
     W.C = 1;
     W.chunk[0] = 0;
     W.chunk[1] = K;
