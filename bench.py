@@ -43,10 +43,11 @@ REF_STEP_ITERS = 1          # reference-arm step: one oracle SVI step (S = 256)
 # evaluation, on the side-uniform peak ranges that hold almost all evaluations:
 #   forward : x - p, t = fma(s, ., -s mu), 1 + t^2 for two peaks, I0 d1 + I1 d0 (2),
 #             d0 d1, accumulate (num * rcp)  -> 10 per two evaluations = 5, and 0.5 MUFU (rcp)
-#   backward: x - p, t, 1 + t^2, g I, q L, sum q L, q L^2, sum q L^2 t, sum q L^2
-#             -> 9 (sum q L^2 t^2 follows from sum q L - sum q L^2), and 1 MUFU (rcp)
+#   backward: x - p, t, 1 + t^2, I L, sum I L, I L^2, sum I L^2 t, sum I L^2
+#             -> 8 (sum I L^2 t^2 follows from sum I L - sum I L^2; the point's factor
+#             g = y/f - 1 multiplies the per-point sums once per range), and 1 MUFU (rcp)
 # Both kernels are bound by the FP32 pipe (128 lanes/clk/SM; MUFU 16/clk/SM).
-FP32_OPS_PER_EVAL = {"forward": 5, "backward": 9}
+FP32_OPS_PER_EVAL = {"forward": 5, "backward": 8}
 MUFU_PER_EVAL = {"forward": 0.5, "backward": 1.0}
 
 

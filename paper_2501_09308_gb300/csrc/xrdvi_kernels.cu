@@ -338,6 +338,15 @@ __device__ __forceinline__ f2_t ex2neg2(f2_t u) {
     return pk2(ex2_approx(-a), ex2_approx(-b));
 }
 
+// Does any point of the warp's pair block lie inside the Gaussian's reach
+// (u < kGaussU)?  Beyond it ex2.approx.ftz returns exactly 0, so skipping the
+// Gaussian terms there leaves every sum bit-identical.  Warp-uniform.
+__device__ __forceinline__ bool any_gauss(f2_t u) {
+    float a, b;
+    up2(u, a, b);
+    return __any_sync(0xffffffffu, fminf(a, b) < kGaussU);
+}
+
 constexpr int kPairs = kPts / 2;
 
 // Margin (degrees) keeping the side-uniform ranges clear of d = 0.
@@ -662,12 +671,17 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
 
 // Lorentzian part on one side-uniform range: S1 += sum q L, A += sum q L^2 t,
 // C2 += sum q L^2.  Since L (1 + t^2) = 1, q L^2 t^2 = q L - q L^2, so the
-// range's sum q L^2 t^2 is S1 - C2 and needs no product of its own.
+// range's sum q L^2 t^2 is S1 - C2 and needs no product of its own.  The
+// sums over the range's peaks are taken per point without the point's factor
+// g = y/f - 1, which multiplies them once at the end (q = g I).
 template <class Tab>
 __device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
                                              const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
                                              f2_t &S1, f2_t &A, f2_t &C2) {
     const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
+    f2_t S1p[kPairs], Ap[kPairs], C2p[kPairs];
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) S1p[q] = Ap[q] = C2p[q] = 0ull;
     for (int m = m0; m < m1; ++m) {
         f2_t np, I;
         tab.get(m, np, I);
@@ -675,12 +689,18 @@ __device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, flo
         for (int q = 0; q < kPairs; ++q) {
             const f2_t t = fma2(s2, add2(x2[q], np), c2);
             const f2_t L = rcp2(fma2(t, t, one2));
-            const f2_t q1 = mul2(mul2(g2[q], I), L);
-            S1 = add2(S1, q1);
+            const f2_t q1 = mul2(I, L);
+            S1p[q] = add2(S1p[q], q1);
             const f2_t q2 = mul2(q1, L);
-            A = fma2(q2, t, A);
-            C2 = add2(C2, q2);
+            Ap[q] = fma2(q2, t, Ap[q]);
+            C2p[q] = add2(C2p[q], q2);
         }
+    }
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        S1 = fma2(g2[q], S1p[q], S1);
+        A = fma2(g2[q], Ap[q], A);
+        C2 = fma2(g2[q], C2p[q], C2);
     }
 }
 
@@ -809,13 +829,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
                         const f2_t q3 = mul2(q2, t);
                         acc[7] = fma2(q3, t, acc[7]);
                         acc[9] = fma_abs2(q3, t, acc[9]);
-                        const f2_t qg = mul2(gI, ex2neg2(u));
-                        acc[0] = add2(acc[0], qg);
-                        acc[2] = fma2(qg, t, acc[2]);
-                        acc[4] = fma_abs2(qg, t, acc[4]);
-                        const f2_t q3g = mul2(qg, t);
-                        acc[6] = fma2(q3g, t, acc[6]);
-                        acc[8] = fma_abs2(q3g, t, acc[8]);
+                        if (any_gauss(u)) {
+                            const f2_t qg = mul2(gI, ex2neg2(u));
+                            acc[0] = add2(acc[0], qg);
+                            acc[2] = fma2(qg, t, acc[2]);
+                            acc[4] = fma_abs2(qg, t, acc[4]);
+                            const f2_t q3g = mul2(qg, t);
+                            acc[6] = fma2(q3g, t, acc[6]);
+                            acc[8] = fma_abs2(q3g, t, acc[8]);
+                        }
                     }
                 }
 #pragma unroll 1
@@ -829,10 +851,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
 #pragma unroll
                         for (int q = 0; q < kPairs; ++q) {
                             const f2_t t = fma2(s2, add2(x2[q], np), c2);
-                            const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(mul2(t, t)));
-                            S1 = add2(S1, qg);
-                            A = fma2(qg, t, A);
-                            B = fma2(mul2(qg, t), t, B);
+                            const f2_t u = mul2(t, t);
+                            if (any_gauss(u)) {
+                                const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(u));
+                                S1 = add2(S1, qg);
+                                A = fma2(qg, t, A);
+                                B = fma2(mul2(qg, t), t, B);
+                            }
                         }
                     }
                     acc[0] = add2(acc[0], S1);
