@@ -211,8 +211,9 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms
  *
  * Scratch: one file-scope device array of XRDVI_STATIC_SCRATCH_BYTES
  * (32 MiB), which every GPU that loads the library holds until the process
- * exits.  A problem needing more (about 40*S*K*ceil(N/256) +
- * 1032*S*ceil(N/256) + 72*S*K bytes) is rejected with EINVAL before any work.
+ * exits.  A problem needing more (48*S*K*T + 2056*S*T + 104*S*K + 16*S +
+ * 1284*K bytes with T = ceil(N/256), plus 256-byte alignment of each of its 14
+ * arrays) is rejected with EINVAL before any work.
  * The first call on a device looks up the array's device address (a one-time
  * set-up per device); make that first call before any stream capture.  All
  * calls share the one array and it keeps the last call's contents (every
