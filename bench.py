@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=None, help="SVI steps per fit (default: workload's 2000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-enumeration", action="store_true", help="skip the K=8 exact-enumeration leg")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
     return ap.parse_args()
@@ -247,6 +248,32 @@ def serving_leg(n_requests, plain_ms):
     return out
 
 
+def enumeration_leg(iters=3000):
+    """Exact posterior over all 2^8 - 1 phase combinations of the tiny
+    workload (K = 8 candidates, 20 peaks each, N = 2000, S = 16): every
+    sub-model fitted to convergence in sub-model batches, FP64 log-sum-exp.
+    Timed with CUDA events around the call (host buffers in and out)."""
+    import numpy as np
+    import torch
+    from paper_2501_09308_gb300 import serving, synth
+    inst = synth.config(0)
+    serving.enumerate_combinations(inst, iters=20)   # warm-up (library load, first contexts)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    masks, elbo, p = serving.enumerate_combinations(inst, iters=iters)
+    ev1.record()
+    torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) / 1e3
+    M = np.diff(inst.offsets)
+    evals = sum(int(inst.S) * int(M[masks[i]].sum()) * int(inst.N) * iters for i in range(len(masks)))
+    best = masks[int(np.argmax(p))]
+    return {"K": inst.K, "sub_models": int(len(masks)), "svi_steps": iters, "S": inst.S, "N": inst.N,
+            "seconds": sec, "sub_model_fits_per_s": len(masks) / sec, "evals_per_s": evals / sec,
+            "best_combination": [int(k) for k in np.flatnonzero(best)], "p_best": float(p.max()),
+            "planted": [int(k) for k in inst.planted]}
+
+
 def workload_config(inst, l2):
     return {"workload": f"single fit K={inst.K} (5-80 peaks, sum M={int(inst.offsets[-1])}), N={inst.N}, "
                         f"S={inst.S}, {inst.iters} SVI steps + posterior ({S_POST} draws)",
@@ -333,6 +360,7 @@ def main():
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serve = serving_leg(args.serve_requests, ms_step)
+    enum = enumeration_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -376,7 +404,8 @@ def main():
         "kernel_share": share,
         "roofline": {
             "bound": "alu",
-            "kernel": f"k_{dom}",
+            "kernel": {"backward": "k_bwd_uniform + k_bwd_near",
+                       "forward": "k_ranges + k_forward + k_lik"}[dom],
             "achieved": achieved[dom],
             "peak": fp32_peak,
             "unit": "Top/s (FP32 lane ops)",
@@ -400,6 +429,8 @@ def main():
     }
     if serve:
         out["serving"] = serve
+    if enum is not None:
+        out["enumeration"] = enum
     if clk:
         out["clocks"] = clk
     if cpu:

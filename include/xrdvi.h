@@ -259,6 +259,8 @@ typedef struct {
     int32_t K;
     double t_submit, t_admit, t_done;  /* seconds since xrdvi_server_create    */
     double final_elbo, log_evidence, ess, coverage_log;
+    double elbo_tail_mean;     /* mean ELBO estimate over the last max(1, iters/4)
+                                  steps (the sub-model score of xrdvi_enumerate) */
     size_t footprint_bytes;
     double *pi;
     uint64_t *combos;
@@ -302,6 +304,37 @@ xrdvi_status xrdvi_server_get_stats(xrdvi_server *srv, xrdvi_server_stats *stats
 
 /* Cancels queued requests, waits for running fits, frees everything. */
 void xrdvi_server_destroy(xrdvi_server *srv);
+
+/* Exact posterior over phase combinations for small K, by enumeration (the
+ * small-K check of the method: every combination c of the K candidates is a
+ * sub-model with the phases outside c removed; the paper states the problem
+ * as a search over such combinations, Sec. 1 and App. A.1).
+ *
+ * Every non-empty combination c = 1 .. 2^K - 1 (bit k set = phase k kept,
+ * in input order) is fitted by the same SVI as xrdvi_fit: cfg (S, seed,
+ * priors, ...) for each, iters steps from the standard initialisation, the
+ * pattern and its rate lambda = 1/max(y - B) unchanged, the Monte-Carlo noise
+ * of a fit of the sub-model alone (Philox counters with the sample and phase
+ * indices local to the sub-model).  Its score is the mean ELBO estimate of
+ * the last max(1, iters/4) steps; under a uniform prior over combinations,
+ * log p(c | Y) = ELBO_c - logsumexp_c' ELBO_c' (FP64 log-sum-exp on the GPU).
+ *
+ * The sub-models are fitted in batches: one batch is one problem of
+ * B*S samples in which each block of S samples carries its sub-model's phase
+ * mask and variational state, so one SVI step advances the whole batch in the
+ * same eight kernels.  B is as large as 65536 samples and hbm_budget device
+ * bytes allow (xrdvi_enumerate_footprint_bytes).  Outputs are CALLER host
+ * buffers of 2^K - 1 doubles, entry c - 1 for combination c: elbo_c (may be
+ * NULL) and logp_c.  Blocks until done.  EINVAL for K outside [1, 16],
+ * iters < 1 or a bad problem (validated as by xrdvi_create); ENOMEM if one
+ * sub-model alone exceeds hbm_budget; ENONFINITE if a score is not finite.
+ * The paper has no GPU enumeration of its own. */
+xrdvi_status xrdvi_enumerate(const xrdvi_peaks *peaks, const xrdvi_pattern *pattern, const xrdvi_config *cfg,
+                             int32_t iters, size_t hbm_budget, double *elbo_c, double *logp_c);
+
+/* Device bytes of one enumeration batch of nsub sub-models (host arithmetic;
+ * 0 on invalid sizes). */
+size_t xrdvi_enumerate_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t nsub);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *xrdvi_last_error(void);

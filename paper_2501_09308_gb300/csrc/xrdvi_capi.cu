@@ -155,8 +155,8 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
     XR_TRY(c->alloc(&W.llpart, static_cast<size_t>(S) * P.T, list));
     if (fit) {
         XR_TRY(c->alloc(&W.gpart, SK * P.T * kGradSums, list));
-        XR_TRY(c->alloc(&W.gred, static_cast<size_t>(P.K) * kGradBlocks * 10, list));
-        XR_TRY(c->alloc(&W.tickets, static_cast<size_t>(P.K), list));
+        XR_TRY(c->alloc(&W.gred, static_cast<size_t>(W.B) * P.K * kGradBlocks * 10, list));
+        XR_TRY(c->alloc(&W.tickets, static_cast<size_t>(W.B) * P.K, list));
         W.lq = nullptr;
     } else {
         XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
@@ -247,6 +247,27 @@ xrdvi_status validate(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdv
 
 }  // namespace
 
+namespace xrdvi {
+xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg) {
+    return validate(pk, pt, cfg);
+}
+
+xrdvi_status batch_set_tail(xrdvi_ctx *c, int tail_start) {
+    if (!c || !c->W.tail_sum) return fail(XRDVI_EINVAL, "not a sub-model batch context");
+    c->W.tail_start = tail_start;
+    c->drop_graphs();   // kernel arguments are fixed at capture
+    return XRDVI_OK;
+}
+
+xrdvi_status batch_tail_sums(xrdvi_ctx *c, double *host) {
+    if (!c || !c->W.tail_sum || !host) return fail(XRDVI_EINVAL, "not a sub-model batch context");
+    XR_CUDA(cudaMemcpyAsync(host, c->W.tail_sum, static_cast<size_t>(c->W.B) * 8, cudaMemcpyDeviceToHost,
+                            c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    return XRDVI_OK;
+}
+}  // namespace xrdvi
+
 extern "C" {
 
 const char *xrdvi_last_error(void) { return g_err.c_str(); }
@@ -283,11 +304,28 @@ xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const 
 
 xrdvi_status xrdvi::create_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
                                    cudaMemPool_t pool, cudaStream_t stream, xrdvi_ctx **out) {
+    return create_batch_context(pk, pt, cfg, 1, nullptr, pool, stream, out);
+}
+
+xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
+                                         int nsub, const uint32_t *masks, cudaMemPool_t pool, cudaStream_t stream,
+                                         xrdvi_ctx **out) {
     g_err.clear();
     if (!out) return fail(XRDVI_EINVAL, "null output pointer");
     *out = nullptr;
     XR_TRY(validate(pk, pt, cfg));
     const int K = pk->K, N = pt->N, M = pk->offsets[K];
+    if (nsub < 1 || static_cast<int64_t>(nsub) * cfg->S > kMaxS)
+        return fail(XRDVI_EINVAL, "sub-model batch: B * S must be in [1, 65536]");
+    if (masks) {
+        if (K > 32) return fail(XRDVI_EINVAL, "sub-model batch: K must be <= 32");
+        for (int b = 0; b < nsub; ++b)
+            if (masks[b] == 0u || (K < 32 && (masks[b] >> K) != 0u))
+                return fail(XRDVI_EINVAL, "sub-model batch: masks must be non-empty subsets of the K phases");
+    } else if (nsub != 1) {
+        return fail(XRDVI_EINVAL, "sub-model batch needs masks");
+    }
+    const size_t KB = static_cast<size_t>(K) * nsub;
     // host preparation: sort each phase by position, eta, data constant
     std::vector<float> pos(M), inten(M);
     std::vector<double> isum(K, 0.0);
@@ -367,23 +405,32 @@ xrdvi_status xrdvi::create_context(const xrdvi_peaks *pk, const xrdvi_pattern *p
     XR_C(c->alloc(&P.isum, K));
     configure_grids(P, sms);
     c->host_off.assign(pk->offsets, pk->offsets + K + 1);
-    XR_C(alloc_workspace(c, c->W, cfg->S, true, nullptr));
-    XR_C(c->alloc(&c->loc, K * 5));
-    XR_C(c->alloc(&c->raw, K * 5));
-    XR_C(c->alloc(&c->m, K * 10));
-    XR_C(c->alloc(&c->v, K * 10));
-    XR_C(c->alloc(&c->grad, K * 10));
-    XR_C(c->alloc(&c->ent, 1));
-    XR_C(c->alloc(&c->elbo, 1));
+    c->W.B = nsub;
+    c->W.S_sub = cfg->S;
+    XR_C(alloc_workspace(c, c->W, cfg->S * nsub, true, nullptr));
+    uint32_t *d_mask = nullptr;
+    if (masks) {
+        XR_C(c->alloc(&d_mask, static_cast<size_t>(nsub)));
+        XR_C(c->alloc(&c->W.tail_sum, static_cast<size_t>(nsub)));
+        c->W.mask = d_mask;
+        c->cfg.S = cfg->S * nsub;
+    }
+    XR_C(c->alloc(&c->loc, KB * 5));
+    XR_C(c->alloc(&c->raw, KB * 5));
+    XR_C(c->alloc(&c->m, KB * 10));
+    XR_C(c->alloc(&c->v, KB * 10));
+    XR_C(c->alloc(&c->grad, KB * 10));
+    XR_C(c->alloc(&c->ent, static_cast<size_t>(nsub)));
+    XR_C(c->alloc(&c->elbo, static_cast<size_t>(nsub)));
     XR_C(c->alloc(&c->trace, kTraceCap));
     XR_C(c->alloc(&c->step, 1));
     XR_C(c->alloc(&c->iter, 1));
 
     // initial q (reading: loc at h = init_h_frac * eta, mu = 0, w at the prior
     // mean shape/rate, r = 1/2, alpha at its prior mean; sigma = init_sigma)
-    std::vector<float> loc(K * 5), raw(K * 5);
+    std::vector<float> loc(KB * 5), raw(KB * 5);
     const double raw0 = std::log(std::expm1(static_cast<double>(cfg->init_sigma)));
-    for (int k = 0; k < K; ++k) {
+    for (size_t k = 0; k < KB; ++k) {
         loc[k * 5 + 0] = static_cast<float>(std::log(cfg->init_h_frac * eta));
         loc[k * 5 + 1] = 0.f;
         loc[k * 5 + 2] = static_cast<float>(std::log(static_cast<double>(cfg->prior_w_shape) / cfg->prior_w_rate));
@@ -395,10 +442,12 @@ xrdvi_status xrdvi::create_context(const xrdvi_peaks *pk, const xrdvi_pattern *p
     auto up = [&](void *dst, const void *src, size_t n) { return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s); };
     if (up(P.pos, pos.data(), M * 4) || up(P.inten, inten.data(), M * 4) ||
         up(P.off, pk->offsets, (K + 1) * 4) || up(P.x, pt->x_deg, N * 4) || up(P.y, pt->y_counts, N * 4) ||
-        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) || up(c->loc, loc.data(), K * 20) ||
-        up(c->raw, raw.data(), K * 20) || cudaMemsetAsync(c->m, 0, K * 40, s) ||
-        cudaMemsetAsync(c->v, 0, K * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
-        cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s))
+        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) || up(c->loc, loc.data(), KB * 20) ||
+        up(c->raw, raw.data(), KB * 20) || cudaMemsetAsync(c->m, 0, KB * 40, s) ||
+        cudaMemsetAsync(c->v, 0, KB * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
+        cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s) ||
+        (d_mask && (up(d_mask, masks, static_cast<size_t>(nsub) * 4) ||
+                    cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))))
         return bail(fail(XRDVI_ECUDA, "upload failed"));
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return bail(fail(XRDVI_ECUDA, "create: device error"));

@@ -52,7 +52,8 @@ struct __align__(16) PhaseConst {
     float rl, rr;        // Gaussian reach left / right of the peak (degrees)
     float sl, sr;        // 2 / w (d < 0), 2 / (alpha w) (d >= 0)
     float nslmu, nsrmu;  // -sl * mu, -sr * mu
-    float pad[7];
+    float absent;        // 1: phase removed from this sample's sub-model (no peaks evaluated)
+    float pad[6];
 };
 
 struct PriorConst {
@@ -82,6 +83,14 @@ struct Workspace {
     double *gred = nullptr;      // [K*kGradBlocks*10] gradient partials per sample block (fit only)
     int *tickets = nullptr;      // [K] arrival tickets of the gradient reduction (fit only)
     size_t fpart_cap = 0;        // elements allocated for fpart
+    // Sub-model batch: the S samples form B blocks of S_sub, block b fits the
+    // sub-model keeping the phases set in mask[b] (bit k = phase k, K <= 32),
+    // with its own variational parameters and Adam state [B*K*...].  B = 1 and
+    // mask = null: one model over all phases.
+    int B = 1, S_sub = 0;
+    const uint32_t *mask = nullptr;   // [B] device
+    double *tail_sum = nullptr;       // [B] sum of the ELBO estimates from step tail_start on
+    int tail_start = 0;
     int C = 1;                   // phase chunks
     int chunk[kMaxChunks + 1] = {0};
     size_t bytes = 0;
@@ -147,6 +156,25 @@ xrdvi_status report_error(xrdvi_status st, const std::string &msg);
 // not own), so creating and destroying contexts never synchronises the device.
 xrdvi_status create_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
                             cudaMemPool_t pool, cudaStream_t stream, xrdvi_ctx **out);
+// A context fitting nsub sub-models of the problem at once: sub-model b keeps
+// the phases set in masks[b] (K <= 32) and gets its own variational
+// parameters, Adam state and cfg->S samples; one SVI step advances all of them
+// in the same kernels.  The ELBO estimates of every step from tail_start on
+// are summed per sub-model (tail sums, read by batch_tail_sums).  Only fit is
+// meaningful on such a context.
+xrdvi_status create_batch_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
+                                  int nsub, const uint32_t *masks, cudaMemPool_t pool, cudaStream_t stream,
+                                  xrdvi_ctx **out);
+xrdvi_status batch_set_tail(xrdvi_ctx *c, int tail_start);
+// Copies the nsub tail sums (FP64) to host memory.
+xrdvi_status batch_tail_sums(xrdvi_ctx *c, double *host);
+
+// Host validation of a problem and config (the checks of xrdvi_create).
+xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg);
+
+// logp[c] = elbo[c] - logsumexp(elbo[0..n)) in FP64 with a fixed reduction
+// order (one block).
+void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st);
 
 // Occupancy-based persistent grid sizes.
 void configure_grids(Problem &P, int sm_count);

@@ -143,7 +143,9 @@ struct SampleArgs {
     PhaseConst *cst;
     double *lpj, *lq;
     int *counters;
-    int *tickets;   // [K] arrival tickets of k_grad, zeroed here
+    int *tickets;   // [B*K] arrival tickets of k_grad, zeroed here
+    int B, S_sub;
+    const uint32_t *mask;  // [B] phases kept by each sub-model (null: all)
     // FP32 copies of the prior constants used per (s, k)
     float pr_lambda, pr_mu_isd, pr_alpha_mean, pr_alpha_isd, pr_wsm1, pr_wrate;
 };
@@ -157,9 +159,24 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         for (int i = 0; i < kCounters; ++i) a.counters[i] = 0;  // work counters of the profile kernels
     }
     const float sq = sqrtf(kGaussU);
+    // sub-model of this sample; the noise counters use the sample and phase
+    // indices local to the sub-model, as a fit of the sub-model alone would
+    const int b = s / a.S_sub, s_loc = s - b * a.S_sub;
+    const uint32_t mk = a.mask ? a.mask[b] : 0u;
+    const float *loc = a.loc + static_cast<size_t>(b) * a.K * 5;
+    const float *raw = a.raw + static_cast<size_t>(b) * a.K * 5;
     double acc = 0.0, accq = 0.0;
     for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
         const size_t base = (static_cast<size_t>(s) * a.K + k) * 5;
+        if (a.mask && !((mk >> k) & 1u)) {
+            PhaseConst pc = {};
+            pc.absent = 1.f;
+            a.cst[static_cast<size_t>(s) * a.K + k] = pc;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) a.theta[base + j] = 0.f;
+            continue;
+        }
+        const uint32_t kl = a.mask ? static_cast<uint32_t>(__popc(mk & ((1u << k) - 1u))) : static_cast<uint32_t>(k);
         float e[8];
         if (a.eps_in) {
 #pragma unroll
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         } else {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                uint32_t c[4] = {static_cast<uint32_t>(s), static_cast<uint32_t>(k), step,
+                uint32_t c[4] = {static_cast<uint32_t>(s_loc), kl, step,
                                  a.tag * 256u + static_cast<uint32_t>(j)};
                 philox4x32_10(c, a.key0, a.key1);
 #pragma unroll
@@ -184,8 +201,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         float u[5], sig[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            sig[j] = softplusf(a.raw[k * 5 + j]);
-            u[j] = fmaf(sig[j], e[j], a.loc[k * 5 + j]);
+            sig[j] = softplusf(raw[k * 5 + j]);
+            u[j] = fmaf(sig[j], e[j], loc[k * 5 + j]);
             a.eps[base + j] = e[j];
         }
         const float h = expf(u[0]);
@@ -211,7 +228,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         pc.sr = sr;
         pc.nslmu = -sl * mu;
         pc.nsrmu = -sr * mu;
-        pc.pad[0] = pc.pad[1] = pc.pad[2] = pc.pad[3] = pc.pad[4] = pc.pad[5] = pc.pad[6] = 0.f;
+        pc.absent = 0.f;
+        pc.pad[0] = pc.pad[1] = pc.pad[2] = pc.pad[3] = pc.pad[4] = pc.pad[5] = 0.f;
         a.cst[static_cast<size_t>(s) * a.K + k] = pc;
         // log prior (Sec. 2.2, Appendix B.2) + log Jacobian of the transform:
         // the parameter-free part is the host constant lp_const; the rest is
@@ -229,19 +247,20 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         }
     }
     if (s == 0 && a.tickets)
-        for (int k = threadIdx.x; k < a.K; k += blockDim.x) a.tickets[k] = 0;
+        for (int k = threadIdx.x; k < a.B * a.K; k += blockDim.x) a.tickets[k] = 0;
     const double tot = block_sum(acc, sh);
     const double totq = a.lq ? block_sum(accq, sh) : 0.0;
     if (threadIdx.x == 0) {
         a.lpj[s] = tot;
         if (a.lq) a.lq[s] = totq;
     }
-    if (s == 0 && a.ent) {
+    if (s_loc == 0 && a.ent) {
         double H = 0.0;
         for (int i = threadIdx.x; i < 5 * a.K; i += blockDim.x)
-            H += log(softplusd(static_cast<double>(a.raw[i]))) + 0.5 * (1.0 + kLog2Pi);
+            if (!a.mask || ((mk >> (i / 5)) & 1u))
+                H += log(softplusd(static_cast<double>(raw[i]))) + 0.5 * (1.0 + kLog2Pi);
         H = block_sum(H, sh);
-        if (threadIdx.x == 0) *a.ent = H;
+        if (threadIdx.x == 0) a.ent[b] = H;
     }
 }
 
@@ -349,6 +368,10 @@ __device__ __forceinline__ bool any_gauss(f2_t u) {
 
 constexpr int kPairs = kPts / 2;
 
+// Range marker of a phase removed from a sample's sub-model (peak offsets
+// stay below kMaxPeaks < 0xffff).
+constexpr unsigned short kAbsentRange = 0xffffu;
+
 // Margin (degrees) keeping the side-uniform ranges clear of d = 0.
 constexpr float kSideMargin = 1e-4f;
 
@@ -373,6 +396,10 @@ __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
         const int sk = idx / a.T;
         const int k = sk % a.K;
         const PhaseConst c = a.cst[sk];
+        if (c.absent != 0.f) {
+            a.ranges[idx] = make_ushort4(kAbsentRange, 0, 0, 0);
+            continue;
+        }
         const float xlo = a.x[tile * kTile];
         const float xhi = a.x[min(tile * kTile + kTile - 1, a.N - 1)];
         const int mb = a.off[k], me = a.off[k + 1];
@@ -440,6 +467,10 @@ __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_of
     const ushort4 r = a.ranges[(static_cast<size_t>(s) * a.K + k) * a.T + tile];
     Ranges o;
     o.mb = s_off[k];
+    if (r.x == kAbsentRange) {  // phase not in this sample's sub-model: every range empty
+        o.me = o.m1 = o.m2 = o.nb = o.ne = o.mb;
+        return o;
+    }
     o.me = s_off[k + 1];
     o.m1 = o.mb + r.x;
     o.m2 = o.mb + r.y;
@@ -900,17 +931,22 @@ struct GradArgs {
     int *d_step;
     const double *llpart, *lpj, *ent;
     double *ll, *elbo_out, *trace;
-    double *gred;   // [K*kGradBlocks*10] per-sample-block partial sums
-    int *tickets;   // [K] arrival tickets (zeroed by k_sample, reset by the last block)
+    double *gred;   // [B*K*kGradBlocks*10] per-sample-block partial sums
+    int *tickets;   // [B*K] arrival tickets (zeroed by k_sample, reset by the last block)
     int NB;         // sample blocks per phase
+    int B, S_sub;   // sub-model batch (B = 1, S_sub = S: one model)
+    const uint32_t *mask;
+    double *tail_sum;   // [B] (may be null): ELBO estimates summed from step tail_start on
+    int tail_start;
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
 // fixed summation order; also advances the step counter of the fit loop.
 __global__ void __launch_bounds__(256) k_elbo(GradArgs a) {
     __shared__ double sh[8];
+    const int b = blockIdx.x;   // sub-model
     double acc = 0.0;
-    for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
+    for (int s = b * a.S_sub + threadIdx.x; s < (b + 1) * a.S_sub; s += blockDim.x) {
         double ll = a.csum;
         const double *lp = a.llpart + static_cast<size_t>(s) * a.T;
         for (int t = 0; t < a.T; ++t) ll += lp[t];
@@ -919,12 +955,13 @@ __global__ void __launch_bounds__(256) k_elbo(GradArgs a) {
     }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) {
-        const double elbo = acc / a.S + *a.ent;
-        if (a.elbo_out) *a.elbo_out = elbo;
+        const double elbo = acc / a.S_sub + a.ent[b];
+        if (a.elbo_out) a.elbo_out[b] = elbo;
         if (a.d_iter) {
             const int it = *a.d_iter;
-            if (a.trace) a.trace[it & (kTraceCap - 1)] = elbo;
-            if (a.d_step) *a.d_step = it + 1;
+            if (a.trace && b == 0) a.trace[it & (kTraceCap - 1)] = elbo;
+            if (a.tail_sum && it >= a.tail_start) a.tail_sum[b] += elbo;
+            if (a.d_step && b == 0) *a.d_step = it + 1;
         }
     }
 }
@@ -941,10 +978,12 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
     __shared__ float qs[32][kGradSums + 1];
     __shared__ double red[10];
     __shared__ int is_last;
-    const int k = blockIdx.x, b = blockIdx.y;
+    const int bk = blockIdx.x, b = blockIdx.y;   // (sub-model, phase), sample block
+    const int sm = bk / a.K, k = bk - sm * a.K;
+    if (a.mask && !((a.mask[sm] >> k) & 1u)) return;   // phase not in this sub-model (whole block)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s0 = static_cast<int>((static_cast<long long>(a.S) * b) / a.NB);
-    const int s1 = static_cast<int>((static_cast<long long>(a.S) * (b + 1)) / a.NB);
+    const int s0 = sm * a.S_sub + static_cast<int>((static_cast<long long>(a.S_sub) * b) / a.NB);
+    const int s1 = sm * a.S_sub + static_cast<int>((static_cast<long long>(a.S_sub) * (b + 1)) / a.NB);
     double accl[5] = {0, 0, 0, 0, 0}, acce[5] = {0, 0, 0, 0, 0};
     const double ln2 = kLn2;
     for (int c0 = s0; c0 < s1; c0 += 32) {
@@ -1014,38 +1053,38 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         if (lane == 0) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
-                a.gred[(static_cast<size_t>(k) * a.NB + b) * 10 + j] = accl[j];
-                a.gred[(static_cast<size_t>(k) * a.NB + b) * 10 + 5 + j] = acce[j];
+                a.gred[(static_cast<size_t>(bk) * a.NB + b) * 10 + j] = accl[j];
+                a.gred[(static_cast<size_t>(bk) * a.NB + b) * 10 + 5 + j] = acce[j];
             }
         }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.tickets[k], 1) == a.NB - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.tickets[bk], 1) == a.NB - 1);
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     if (threadIdx.x < 10) {
         double tot = 0.0;
-        for (int bb = 0; bb < a.NB; ++bb) tot += __ldcg(&a.gred[(static_cast<size_t>(k) * a.NB + bb) * 10 + threadIdx.x]);
+        for (int bb = 0; bb < a.NB; ++bb) tot += __ldcg(&a.gred[(static_cast<size_t>(bk) * a.NB + bb) * 10 + threadIdx.x]);
         red[threadIdx.x] = tot;
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.tickets[k] = 0;
+    if (threadIdx.x == 0) a.tickets[bk] = 0;
     if (threadIdx.x < 10) {
         const int j = threadIdx.x % 5;
         const bool is_raw = threadIdx.x >= 5;
-        const double rw = a.raw_in[k * 5 + j];
+        const double rw = a.raw_in[bk * 5 + j];
         double grad;
         if (!is_raw) {
-            grad = red[j] / a.S;
+            grad = red[j] / a.S_sub;
         } else {
-            grad = (red[5 + j] / a.S + 1.0 / softplusd(rw)) * sigmoidd(rw);
+            grad = (red[5 + j] / a.S_sub + 1.0 / softplusd(rw)) * sigmoidd(rw);
         }
-        if (a.grad_out) a.grad_out[k * 10 + threadIdx.x] = static_cast<float>(grad);
+        if (a.grad_out) a.grad_out[bk * 10 + threadIdx.x] = static_cast<float>(grad);
         if (a.adam) {
             const int t = *a.d_iter + 1;
-            const int idx = k * 10 + threadIdx.x;
+            const int idx = bk * 10 + threadIdx.x;
             const double gm = -grad;  // minimise -ELBO
             const double mm = a.ac.b1 * static_cast<double>(a.m[idx]) + (1.0 - a.ac.b1) * gm;
             const double vv = a.ac.b2 * static_cast<double>(a.v[idx]) + (1.0 - a.ac.b2) * gm * gm;
@@ -1055,9 +1094,9 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             const double c2 = 1.0 - pow(static_cast<double>(a.ac.b2), t);
             const double step = a.ac.lr * (mm / c1) / (sqrt(vv / c2) + a.ac.eps);
             if (!is_raw) {
-                a.loc_out[k * 5 + j] = static_cast<float>(a.loc_in[k * 5 + j] - step);
+                a.loc_out[bk * 5 + j] = static_cast<float>(a.loc_in[bk * 5 + j] - step);
             } else {
-                a.raw_out[k * 5 + j] = static_cast<float>(rw - step);
+                a.raw_out[bk * 5 + j] = static_cast<float>(rw - step);
             }
         }
     }
@@ -1355,6 +1394,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.pr = P.prior; a.eps = W.eps; a.theta = W.theta; a.cst = W.cst; a.lpj = W.lpj; a.lq = W.lq;
     a.counters = W.counters;
     a.tickets = W.tickets;
+    a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1404,10 +1444,12 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.d_iter = d_iter; a.d_step = d_step; a.llpart = W.llpart; a.lpj = W.lpj; a.ent = ent;
     a.ll = W.ll; a.elbo_out = elbo_out; a.trace = trace;
     a.gred = W.gred; a.tickets = W.tickets;
-    a.NB = (W.S + 31) / 32;   // 32 samples (4 per warp) per block
+    a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
+    a.tail_sum = W.tail_sum; a.tail_start = W.tail_start;
+    a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
-    if (grad_out || adam) k_grad<<<dim3(P.K, a.NB), 256, 0, st>>>(a);
-    if (elbo_out || trace) k_elbo<<<1, 256, 0, st>>>(a);
+    if (grad_out || adam) k_grad<<<dim3(W.B * P.K, a.NB), 256, 0, st>>>(a);
+    if (elbo_out || trace || W.tail_sum) k_elbo<<<W.B, 256, 0, st>>>(a);
 }
 
 void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m, cudaStream_t st) {
@@ -1424,6 +1466,28 @@ void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m,
     k_post_reduce<<<P.K + 1, 256, 0, st>>>(a);
     k_post_sort<<<1, 1024, 0, st>>>(a);
     k_post_topm<<<1, 32, 0, st>>>(a);
+}
+
+
+namespace {
+// Normalised log-probabilities of enumerated combinations: logp = elbo -
+// logsumexp(elbo), FP64, strided per-thread partials combined by a fixed
+// tree (one block, deterministic).
+__global__ void __launch_bounds__(256) k_enum_lse(const double *elbo, int n, double *logp) {
+    __shared__ double sh[8];
+    double m = -CUDART_INF;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, elbo[i]);
+    m = block_max(m, sh);
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += exp(elbo[i] - m);
+    acc = block_sum(acc, sh);
+    const double lse = m + log(acc);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) logp[i] = elbo[i] - lse;
+}
+}  // namespace
+
+void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st) {
+    k_enum_lse<<<1, 256, 0, st>>>(elbo, n, logp);
 }
 
 }  // namespace xrdvi

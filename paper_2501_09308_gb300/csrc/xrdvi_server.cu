@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -48,10 +49,18 @@ struct Request {
     std::vector<double> pi, combo_logp;
     std::vector<uint64_t> combos;
     std::vector<float> loc, raw;
-    double final_elbo = 0, log_evidence = 0, ess = 0, coverage_log = 0;
+    double final_elbo = 0, log_evidence = 0, ess = 0, coverage_log = 0, elbo_tail_mean = 0;
 };
 
 size_t a256(size_t n) { return (n + 511) & ~static_cast<size_t>(511); }  // pool granularity allowance
+
+constexpr int kSliceSteps = 128;   // SVI steps a served fit queues at a time
+
+#define XR_TRY_STATUS(expr)                  \
+    do {                                     \
+        const xrdvi_status _s = (expr);      \
+        if (_s != XRDVI_OK) return _s;       \
+    } while (0)
 
 }  // namespace
 
@@ -120,10 +129,20 @@ void xrdvi_server::run(Request &r, cudaStream_t st) {
     xrdvi_ctx *c = nullptr;
     xrdvi_status s = xrdvi::create_context(&pk, &pt, &r.cfg, pool, st, &c);
     std::vector<double> trace(std::max(r.opts.iters, 1));
-    if (s == XRDVI_OK) s = xrdvi_fit(c, r.opts.iters, trace.data());
+    // Advance in slices with a wait between them: a fit never has more than
+    // kSliceSteps steps queued on its stream, so the kernels of fits admitted
+    // later interleave with it instead of queueing behind all of its steps.
+    for (int done = 0; s == XRDVI_OK && done < r.opts.iters; done += kSliceSteps)
+        s = xrdvi_fit(c, std::min(kSliceSteps, r.opts.iters - done), trace.data() + done);
     const int K = pk.K, W = (K + 63) / 64;
     if (s == XRDVI_OK) {
         r.final_elbo = r.opts.iters > 0 ? trace[r.opts.iters - 1] : 0.0;
+        if (r.opts.iters > 0) {
+            const int tail = std::max(1, r.opts.iters / 4);
+            double acc = 0.0;
+            for (int i = r.opts.iters - tail; i < r.opts.iters; ++i) acc += trace[i];
+            r.elbo_tail_mean = acc / tail;
+        }
         if (r.opts.S_post > 0) {
             r.pi.resize(K);
             r.combos.resize(static_cast<size_t>(r.opts.top_m) * W);
@@ -269,6 +288,7 @@ xrdvi_status xrdvi_server_poll(xrdvi_server *srv, uint64_t req_id, int32_t timeo
     res->log_evidence = r->log_evidence;
     res->ess = r->ess;
     res->coverage_log = r->coverage_log;
+    res->elbo_tail_mean = r->elbo_tail_mean;
     res->footprint_bytes = r->footprint;
     if (res->pi && !r->pi.empty()) std::memcpy(res->pi, r->pi.data(), r->pi.size() * 8);
     if (res->combos && !r->combos.empty()) std::memcpy(res->combos, r->combos.data(), r->combos.size() * 8);
@@ -333,6 +353,68 @@ void xrdvi_server_destroy(xrdvi_server *srv) {
     }
     cudaMemPoolDestroy(srv->pool);
     delete srv;
+}
+
+size_t xrdvi_enumerate_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t nsub) {
+    // a fit workspace of nsub*S samples plus per-sub-model state
+    if (nsub < 1) return 0;
+    const size_t base = xrdvi_footprint_bytes(K, N, M_total, S * nsub, 0, 0);
+    if (base == 0) return 0;
+    const size_t kb = static_cast<size_t>(K) * nsub;
+    return base + a256(kb * 20) * 2 + a256(kb * 40) * 3 + a256(kb * xrdvi::kGradBlocks * 80) + a256(kb * 4) +
+           a256(static_cast<size_t>(nsub) * 8) * 3 + a256(static_cast<size_t>(nsub) * 4);
+}
+
+xrdvi_status xrdvi_enumerate(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
+                             int32_t iters, size_t hbm_budget, double *elbo_c, double *logp_c) {
+    using xrdvi::report_error;
+    if (!pk || !pt || !cfg || !logp_c) return report_error(XRDVI_EINVAL, "null argument");
+    if (pk->K < 1 || pk->K > 16) return report_error(XRDVI_EINVAL, "enumeration needs K in [1, 16]");
+    if (iters < 1) return report_error(XRDVI_EINVAL, "iters must be >= 1");
+    XR_TRY_STATUS(xrdvi::validate_problem(pk, pt, cfg));
+    const int K = pk->K, n = (1 << K) - 1, S = cfg->S, M = pk->offsets[K];
+    // sub-models per batch: as many as the sample limit and the budget allow
+    int Bmax = std::min(n, xrdvi::kMaxS / S);
+    while (Bmax > 1 && xrdvi_enumerate_footprint_bytes(K, pt->N, M, S, Bmax) > hbm_budget) Bmax = (Bmax + 1) / 2;
+    if (Bmax < 1 || xrdvi_enumerate_footprint_bytes(K, pt->N, M, S, Bmax) > hbm_budget)
+        return report_error(XRDVI_ENOMEM, "one sub-model fit needs more than hbm_budget");
+    const int tail = std::max(1, iters / 4);
+    std::vector<double> score(n, 0.0);
+    std::vector<uint32_t> masks;
+    for (int first = 1; first <= n; first += Bmax) {
+        const int nb = std::min(Bmax, n - first + 1);
+        masks.resize(nb);
+        for (int i = 0; i < nb; ++i) masks[i] = static_cast<uint32_t>(first + i);
+        xrdvi_ctx *c = nullptr;
+        XR_TRY_STATUS(xrdvi::create_batch_context(pk, pt, cfg, nb, masks.data(), nullptr, nullptr, &c));
+        xrdvi_status st = xrdvi::batch_set_tail(c, iters - tail);
+        if (st == XRDVI_OK) st = xrdvi_fit(c, iters, nullptr);
+        if (st == XRDVI_OK) st = xrdvi::batch_tail_sums(c, score.data() + (first - 1));
+        xrdvi_destroy(c);
+        if (st != XRDVI_OK) return st;
+    }
+    for (double &v : score) {
+        v /= tail;
+        if (!std::isfinite(v)) return report_error(XRDVI_ENONFINITE, "enumeration: a sub-model ELBO is not finite");
+    }
+    // normalisation on the device (FP64 log-sum-exp)
+    double *d = nullptr;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d, sizeof(double) * 2 * n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, score.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        xrdvi::launch_enum_lse(d, n, d + n, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(logp_c, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (d) cudaFreeAsync(d, s);
+    const cudaError_t e2 = s ? cudaStreamSynchronize(s) : cudaSuccess;
+    if (s) cudaStreamDestroy(s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return report_error(XRDVI_ECUDA, std::string("enumeration: ") + cudaGetErrorString(e));
+    if (elbo_c) std::memcpy(elbo_c, score.data(), sizeof(double) * n);
+    return XRDVI_OK;
 }
 
 }  // extern "C"

@@ -62,6 +62,18 @@ class Server:
             pass
 
 
+def enumerate_combinations(inst, *, iters=None, hbm_budget=16 << 30, **cfg):
+    """Exact posterior over the 2^K - 1 non-empty phase combinations of a
+    small-K problem (K <= 16): every sub-model fitted by the same SVI in
+    sub-model batches on the GPU, scored by its tail-mean ELBO, normalised by
+    an FP64 log-sum-exp on the GPU.  Returns (masks, elbo_c, p_c)."""
+    cfg.setdefault("S", inst.S)
+    c = xrdvi.xrdvi_config_default(**cfg)
+    masks, elbo, logp = xrdvi.xrdvi_enumerate(inst.offsets, inst.pos, inst.inten, inst.x, inst.y, inst.bg, c,
+                                              inst.iters if iters is None else iters, hbm_budget)
+    return masks, elbo, np.exp(logp)
+
+
 def replay_arrivals(server: Server, requests, arrivals_s, **submit_kw):
     """Submit requests[i] at arrivals_s[i] seconds after the start, then wait
     for all.  Returns per-request dicts with 'latency' = done - submit."""

@@ -63,6 +63,7 @@ class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("K", ctypes.c_int32), ("t_submit", ctypes.c_double),
                 ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("final_elbo", ctypes.c_double),
                 ("log_evidence", ctypes.c_double), ("ess", ctypes.c_double), ("coverage_log", ctypes.c_double),
+                ("elbo_tail_mean", ctypes.c_double),
                 ("footprint_bytes", ctypes.c_size_t), ("pi", ctypes.POINTER(ctypes.c_double)),
                 ("combos", ctypes.POINTER(ctypes.c_uint64)), ("combo_logp", ctypes.POINTER(ctypes.c_double)),
                 ("loc", ctypes.POINTER(ctypes.c_float)), ("raw", ctypes.POINTER(ctypes.c_float))]
@@ -107,6 +108,8 @@ SIGNATURES = {
     "xrdvi_server_cancel": (ctypes.c_int, [_vp, _u64]),
     "xrdvi_server_get_stats": (ctypes.c_int, [_vp, P(ServerStats)]),
     "xrdvi_server_destroy": (None, [_vp]),
+    "xrdvi_enumerate": (ctypes.c_int, [P(Peaks), P(Pattern), P(Config), _i32, ctypes.c_size_t, P(_d), P(_d)]),
+    "xrdvi_enumerate_footprint_bytes": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _i32]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -396,7 +399,8 @@ def xrdvi_server_poll(srv, req_id, timeout_ms, K, top_m):
         bits[:, k] = (combos[:, k // 64] >> np.uint64(k % 64)) & np.uint64(1)
     return {"status": res.status, "t_submit": res.t_submit, "t_admit": res.t_admit, "t_done": res.t_done,
             "final_elbo": res.final_elbo, "log_evidence": res.log_evidence, "ess": res.ess,
-            "coverage_log": res.coverage_log, "footprint_bytes": res.footprint_bytes, "pi": pi,
+            "coverage_log": res.coverage_log, "elbo_tail_mean": res.elbo_tail_mean,
+            "footprint_bytes": res.footprint_bytes, "pi": pi,
             "combos": bits, "combo_logp": clp, "loc": loc, "raw": raw}
 
 
@@ -413,3 +417,25 @@ def xrdvi_server_get_stats(srv) -> ServerStats:
 def xrdvi_server_destroy(srv):
     if srv:
         lib().xrdvi_server_destroy(srv)
+
+
+def xrdvi_enumerate_footprint_bytes(K, N, M_total, S, nsub):
+    return int(lib().xrdvi_enumerate_footprint_bytes(int(K), int(N), int(M_total), int(S), int(nsub)))
+
+
+def xrdvi_enumerate(offsets, pos, inten, x, y, bg, cfg: Config, iters, hbm_budget):
+    """Fits all 2^K - 1 non-empty sub-models in sub-model batches; returns
+    (masks [2^K - 1, K] bool, elbo_c, logp_c), row c - 1 = combination c."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    pos, inten, x, y, bg = map(_f32, (pos, inten, x, y, bg))
+    K = len(offsets) - 1
+    n = max((1 << K) - 1, 0) if 0 < K <= 16 else 0
+    pk = Peaks(K, _ptr(offsets, ctypes.c_int32), _ptr(pos, _f), _ptr(inten, _f))
+    pt = Pattern(len(x), _ptr(x, _f), _ptr(y, _f), _ptr(bg, _f))
+    elbo = np.zeros(max(n, 1))
+    logp = np.zeros(max(n, 1))
+    _check(lib().xrdvi_enumerate(ctypes.byref(pk), ctypes.byref(pt), ctypes.byref(cfg), int(iters),
+                                 int(hbm_budget), _ptr(elbo, _d), _ptr(logp, _d)))
+    codes = np.arange(1, n + 1)
+    masks = ((codes[:, None] >> np.arange(K)[None, :]) & 1).astype(bool)
+    return masks, elbo[:n], logp[:n]

@@ -97,3 +97,19 @@ def test_footprint_bound_is_monotone_and_rejects_bad_sizes():
     assert f(50, 4500, 2194, 256, 0, 16) < base
     assert f(0, 4500, 2194, 256, 4096, 16) == 0
     assert f(50, 0, 2194, 256, 4096, 16) == 0
+
+
+def test_enumerate_rejects_bad_sizes_before_device_work():
+    a = _base()
+    cfg = xrdvi.xrdvi_config_default()
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.xrdvi_enumerate(a["offsets"], a["pos"], a["inten"], a["x"], a["y"], a["bg"], cfg, 0, 1 << 30)
+    assert e.value.status == 1
+    big = synth.small_problem(K=17, M=3, N=64)
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.xrdvi_enumerate(big.offsets, big.pos, big.inten, big.x, big.y, big.bg, cfg, 10, 1 << 30)
+    assert e.value.status == 1
+    a["y"][3] = -1.0
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.xrdvi_enumerate(a["offsets"], a["pos"], a["inten"], a["x"], a["y"], a["bg"], cfg, 10, 1 << 30)
+    assert e.value.status == 1
