@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=None, help="SVI steps per fit (default: workload's 2000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-enumeration", action="store_true", help="skip the K=8 exact-enumeration leg")
+    ap.add_argument("--no-enumeration", action="store_true", help="skip the K=8 exact-enumeration and estimator-variant legs")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
     return ap.parse_args()
@@ -274,6 +274,22 @@ def enumeration_leg(iters=3000):
             "planted": [int(k) for k in inst.planted]}
 
 
+def variants_leg(steps=32):
+    """Estimator variants on the K=50 workload: per-kernel CUDA-event times of
+    `steps` SVI steps with the Gaussian likelihood and with the
+    importance-weighted objective, beside the plain path's."""
+    from paper_2501_09308_gb300 import synth, xrdvi
+    inst = synth.config(1)
+    out = {}
+    for name, flags in (("gauss_lik", xrdvi.FLAG_GAUSS_LIK), ("iw_elbo", xrdvi.FLAG_IW_ELBO)):
+        c = xrdvi.Context.from_instance(inst, S=inst.S, flags=flags)
+        c.fit(16, trace=False)
+        k = c.profile_steps(steps)
+        c.close()
+        out[name] = {"kernel_ms_per_launch": k, "svi_step_ms": sum(k.values())}
+    return out
+
+
 def workload_config(inst, l2):
     return {"workload": f"single fit K={inst.K} (5-80 peaks, sum M={int(inst.offsets[-1])}), N={inst.N}, "
                         f"S={inst.S}, {inst.iters} SVI steps + posterior ({S_POST} draws)",
@@ -361,6 +377,7 @@ def main():
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serve = serving_leg(args.serve_requests, ms_step)
     enum = enumeration_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
+    variants = variants_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -431,6 +448,8 @@ def main():
         out["serving"] = serve
     if enum is not None:
         out["enumeration"] = enum
+    if variants is not None:
+        out["variants"] = variants
     if clk:
         out["clocks"] = clk
     if cpu:

@@ -80,6 +80,16 @@ typedef struct {
 /* Flags */
 #define XRDVI_FLAG_BF16_INT   (1u << 0)  /* keep relative intensities as bfloat16 */
 #define XRDVI_FLAG_NAIVE_SUM  (1u << 1)  /* plain instead of compensated f32 sum over phases */
+/* Estimator variants (the paper's model is the Poisson likelihood and the ELBO):
+ * GAUSS_LIK replaces the Poisson likelihood by a Gaussian with variance
+ * max(y_i, 1), ln p(Y|Phi) = sum_i [-(y_i - f_i)^2 / (2 v_i) - ln(2 pi v_i)/2]
+ * (a weighted residual sum of squares); IW_ELBO makes the fit maximise the
+ * importance-weighted bound ln (1/S) sum_s w_s over the S draws of a step
+ * (Burda, Grosse & Salakhutdinov, ICLR 2016), whose gradient weights each
+ * draw by w_s / sum w instead of 1/S; the ELBO values reported (trace,
+ * xrdvi_elbo_grad, forward_dev) are then that bound. */
+#define XRDVI_FLAG_GAUSS_LIK  (1u << 2)
+#define XRDVI_FLAG_IW_ELBO    (1u << 3)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */
@@ -166,7 +176,8 @@ typedef struct {
     int64_t step;             /* optimisation steps taken                   */
     double eta;               /* max(Y - B)                                  */
     double lambda_;           /* 1 / eta                                     */
-    double data_const;        /* sum_i [y ln y - y - ln y!]                  */
+    double data_const;        /* sum_i [y ln y - y - ln y!] (Gaussian variant:
+                                 -sum_i ln(2 pi max(y_i, 1)) / 2)            */
     size_t device_bytes;      /* device memory held by the context           */
     int32_t point_tiles;      /* 2-theta tiles of the profile kernels        */
 } xrdvi_info;
@@ -203,9 +214,10 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms
  * (d_offsets [K+1], d_pos / d_inten [M_total], any peak order), the pattern
  * (d_x, d_y, d_bg [N], validated as by xrdvi_create), d_loc / d_raw [K*5],
  * d_eps [S*K*5] standard normals; cfg (HOST) gives S, the priors, alpha_min
- * and flags.  data_const = sum_i [y ln y - y - ln y!] and lambda_ =
- * 1 / max(Y - B) are the values xrdvi_create derives from the pattern
- * (xrdvi_get_info reports both).  Outputs (DEVICE): d_elbo [1] (double),
+ * and flags (XRDVI_FLAG_IW_ELBO: EINVAL).  data_const = sum_i [y ln y - y -
+ * ln y!] (with XRDVI_FLAG_GAUSS_LIK: -sum_i ln(2 pi max(y_i, 1)) / 2) and
+ * lambda_ = 1 / max(Y - B) are the values xrdvi_create derives from the
+ * pattern (xrdvi_get_info reports both).  Outputs (DEVICE): d_elbo [1] (double),
  * d_grad [K*10] (float), written asynchronously on cuda_stream (a
  * cudaStream_t; NULL is the legacy default stream).
  *

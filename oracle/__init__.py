@@ -95,6 +95,14 @@ def lib():
             L.orc_entropy.argtypes = [i32, pd]
             L.orc_elbo_grad.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32,
                                         pd, pd, pd, pd, pd, pd, pd, pd]
+            L.orc_elbo_grad_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32,
+                                           pd, pd, pd, pd, pd, pd, pd, pd]
+            L.orc_fit_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32, u64, i32, i32,
+                                     d, d, d, d, pd, pd, pd, pd, pd]
+            L.orc_loglik_gauss.restype = d
+            L.orc_loglik_gauss.argtypes = [i32, pd, pd]
+            L.orc_iw_weights.restype = d
+            L.orc_iw_weights.argtypes = [i32, i32, pd, pd, pd, pd, pd]
             L.orc_adam_step.argtypes = [i32, pd, pd, pd, pd, i32, d, d, d, d]
             L.orc_fit.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, u64, i32, i32,
                                   d, d, d, d, pd, pd, pd, pd, pd]
@@ -120,7 +128,13 @@ class Problem:
 
     def __init__(self, offsets, pos, inten, x, y, bg, *, lam=None,
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
-                 w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN):
+                 w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
+                 likelihood="poisson", objective="elbo"):
+        # variants: likelihood "poisson" (the paper's) or "gauss" (variance
+        # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound)
+        assert likelihood in ("poisson", "gauss") and objective in ("elbo", "iw")
+        self.lik = 1 if likelihood == "gauss" else 0
+        self.iw = 1 if objective == "iw" else 0
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -154,6 +168,8 @@ class Problem:
 
     def loglik(self, f, form="direct"):
         f = f64(f)
+        if form == "gauss":
+            return lib().orc_loglik_gauss(self.N, _pd(self.y), _pd(f))
         if form == "direct":
             return lib().orc_loglik_direct(self.N, _pd(self.y), _pd(f))
         return lib().orc_loglik_deviance(self.N, _pd(self.y), _pd(f), None)
@@ -185,9 +201,9 @@ class Problem:
         lpj = np.zeros(S)
         grad = np.zeros((self.K, 10))
         f = np.zeros((S, self.N)) if want_f else None
-        lib().orc_elbo_grad(*self._args(), ctypes.byref(self.prior), S, _pd(f64(loc)),
-                            _pd(f64(raw)), _pd(eps), ctypes.byref(elbo), _pd(ll), _pd(lpj),
-                            _pd(grad), _pd(f) if want_f else None)
+        lib().orc_elbo_grad_ex(*self._args(), ctypes.byref(self.prior), self.lik, self.iw, S, _pd(f64(loc)),
+                               _pd(f64(raw)), _pd(eps), ctypes.byref(elbo), _pd(ll), _pd(lpj),
+                               _pd(grad), _pd(f) if want_f else None)
         out = {"elbo": elbo.value, "ll": ll, "lpj": lpj, "grad": grad}
         if want_f:
             out["f"] = f
@@ -213,9 +229,18 @@ class Problem:
         m = np.zeros((self.K, 10)) if m is None else f64(m).copy()
         v = np.zeros((self.K, 10)) if v is None else f64(v).copy()
         trace = np.zeros(iters)
-        lib().orc_fit(*self._args(), ctypes.byref(self.prior), S, seed, t0, iters,
-                      lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
+        lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), self.lik, self.iw, S, seed, t0, iters,
+                         lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
         return {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
+
+
+def iw_weights(raw, eps, ll, lpj):
+    """(L_S, normalised weights[S]) of the importance-weighted bound."""
+    eps = f64(eps)
+    S, K = eps.shape[0], eps.shape[1]
+    wt = np.zeros(S)
+    L = lib().orc_iw_weights(K, S, _pd(f64(raw)), _pd(eps), _pd(f64(ll)), _pd(f64(lpj)), _pd(wt))
+    return L, wt
 
 
 def philox(ctr, key):

@@ -214,6 +214,25 @@ double orc_loglik_deviance(int N, const double *y, const double *f, double *csum
     return c + dsum;
 }
 
+/*
+ * Likelihood variant: Gaussian with variance v_i = max(y_i, 1), a weighted
+ * residual sum of squares (not the paper's model, which is Poisson,
+ * Appendix A.2; v_i is the Poisson variance where counts are large):
+ *   ln p(Y|Phi) = sum_i [ -(y_i - f_i)^2 / (2 v_i) - ln(2 pi v_i) / 2 ],
+ * with d/df_i = (y_i - f_i) / v_i.
+ */
+double orc_gauss_var(double y) { return y > 1.0 ? y : 1.0; }
+
+double orc_loglik_gauss(int N, const double *y, const double *f)
+{
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double v = orc_gauss_var(y[i]), r = y[i] - f[i];
+        s += -0.5 * r * r / v - 0.5 * log(2.0 * ORC_PI * v);
+    }
+    return s;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Priors (Sec. 2.2, Appendix B.2) and the log-Jacobian of the transform     */
 /* ------------------------------------------------------------------------ */
@@ -265,6 +284,44 @@ double orc_entropy(int K, const double *raw)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Importance-weighted bound (estimator variant)                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * The importance-weighted bound of Burda, Grosse & Salakhutdinov
+ * ("Importance Weighted Autoencoders", ICLR 2016) on the S draws of one step:
+ *   L_S = ln (1/S) sum_s w_s,
+ *   ln w_s = ln p(Y|theta_s) + ln p(theta_s) + ln|J_s| - ln q(u_s),
+ *   ln q(u_s) = sum_kj [ -eps_skj^2 / 2 - ln sigma_kj - ln(2 pi) / 2 ].
+ * L_1 is the single-draw ELBO with the entropy replaced by -ln q(u_1), and
+ * L_S >= mean_s ln w_s.  With wt_s = w_s / sum_s' w_s' and G_s as for the
+ * ELBO, its reparameterisation gradient (eps fixed) is
+ *   dL_S/dloc = sum_s wt_s G_s,
+ *   dL_S/draw = [ sum_s wt_s G_s eps_s + 1/sigma ] sigmoid(raw),
+ * the 1/sigma being the derivative of -ln q(u_s) with u_s = loc + sigma eps_s.
+ * Returns L_S and writes wt[S]; ll and lpj are the per-draw terms.
+ */
+double orc_iw_weights(int K, int S, const double *raw, const double *eps, const double *ll,
+                      const double *lpj, double *wt)
+{
+    double *lw = (double *)malloc((size_t)S * sizeof(double));
+    double mx = -INFINITY;
+    for (int s = 0; s < S; ++s) {
+        double lq = 0.0;
+        for (int i = 0; i < 5 * K; ++i) {
+            double e = eps[(size_t)s * K * 5 + i];
+            lq += -0.5 * e * e - log(orc_softplus(raw[i])) - 0.5 * log(2.0 * ORC_PI);
+        }
+        lw[s] = ll[s] + lpj[s] - lq;
+        if (lw[s] > mx) mx = lw[s];
+    }
+    double sum = 0.0;
+    for (int s = 0; s < S; ++s) sum += exp(lw[s] - mx);
+    for (int s = 0; s < S; ++s) wt[s] = exp(lw[s] - mx) / sum;
+    free(lw);
+    return mx + log(sum) - log((double)S);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Monte-Carlo ELBO and its gradient (Sec. 3.2)                               */
 /* ------------------------------------------------------------------------ */
 /*
@@ -282,12 +339,17 @@ double orc_entropy(int K, const double *raw)
  *
  * Outputs: elbo; ll[S], lpj[S] (log prior + log Jacobian) if non-NULL;
  * grad[K*10] if non-NULL; f[S*N] if non-NULL.
+ *
+ * orc_elbo_grad_ex also takes the likelihood (lik: 0 Poisson, 1 the Gaussian
+ * variant, whose g_i = (y_i - f_i)/v_i replaces y_i/f_i - 1) and the
+ * objective (iw: 0 this ELBO, 1 the importance-weighted bound, whose weights
+ * replace the 1/S of the sample means); `elbo` then receives that objective.
  */
-void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten,
-                   int N, const double *x, const double *y, const double *bg,
-                   const orc_prior *pr, int S, const double *loc, const double *raw,
-                   const double *eps, double *elbo, double *ll, double *lpj,
-                   double *grad, double *f_out)
+void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *inten,
+                      int N, const double *x, const double *y, const double *bg,
+                      const orc_prior *pr, int lik, int iw, int S, const double *loc, const double *raw,
+                      const double *eps, double *elbo, double *ll, double *lpj,
+                      double *grad, double *f_out)
 {
     size_t SK5 = (size_t)S * K * 5;
     double *u = (double *)malloc(SK5 * sizeof(double));
@@ -315,10 +377,10 @@ void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten
                 acc += t[0] * C;
             }
             f[i] = acc;
-            gi[i] = y[i] / acc - 1.0;
+            gi[i] = lik ? (y[i] - acc) / orc_gauss_var(y[i]) : y[i] / acc - 1.0;
         }
         if (f_out) memcpy(f_out + (size_t)s * N, f, (size_t)N * sizeof(double));
-        lls[s] = orc_loglik_direct(N, y, f);
+        lls[s] = lik ? orc_loglik_gauss(N, y, f) : orc_loglik_direct(N, y, f);
         double lp = 0.0;
         for (int k = 0; k < K; ++k) lp += orc_log_prior(pr, ths + k * 5) + orc_log_jac(us + k * 5);
         lps[s] = lp;
@@ -366,10 +428,17 @@ void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten
         free(gi);
     }
 
-    double acc = 0.0;
-    for (int s = 0; s < S; ++s) acc += lls[s] + lps[s];
-    double H = orc_entropy(K, raw);
-    *elbo = acc / S + H;
+    /* sample weights: 1/S for the ELBO; for the importance-weighted bound the
+       normalised weights w_s / sum w (Burda et al.), see orc_iw_weights */
+    double *wt = (double *)malloc((size_t)S * sizeof(double));
+    if (iw) {
+        *elbo = orc_iw_weights(K, S, raw, eps, lls, lps, wt);
+    } else {
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += lls[s] + lps[s];
+        *elbo = acc / S + orc_entropy(K, raw);
+        for (int s = 0; s < S; ++s) wt[s] = 1.0 / S;
+    }
     if (ll) memcpy(ll, lls, (size_t)S * sizeof(double));
     if (lpj) memcpy(lpj, lps, (size_t)S * sizeof(double));
     if (grad) {
@@ -378,15 +447,24 @@ void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten
                 double gl = 0.0, ge = 0.0;
                 for (int s = 0; s < S; ++s) {
                     size_t i = ((size_t)s * K + k) * 5 + j;
-                    gl += G[i];
-                    ge += G[i] * eps[i];
+                    gl += wt[s] * G[i];
+                    ge += wt[s] * G[i] * eps[i];
                 }
                 double rw = raw[k * 5 + j];
-                grad[k * 10 + j] = gl / S;
-                grad[k * 10 + 5 + j] = (ge / S + 1.0 / orc_softplus(rw)) * orc_sigmoid(rw);
+                grad[k * 10 + j] = gl;
+                grad[k * 10 + 5 + j] = (ge + 1.0 / orc_softplus(rw)) * orc_sigmoid(rw);
             }
     }
-    free(u); free(th); free(G); free(lls); free(lps);
+    free(u); free(th); free(G); free(lls); free(lps); free(wt);
+}
+
+void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten,
+                   int N, const double *x, const double *y, const double *bg,
+                   const orc_prior *pr, int S, const double *loc, const double *raw,
+                   const double *eps, double *elbo, double *ll, double *lpj,
+                   double *grad, double *f_out)
+{
+    orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, S, loc, raw, eps, elbo, ll, lpj, grad, f_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -415,13 +493,14 @@ void orc_adam_step(int n, double *params, const double *grad, double *m, double 
  * noise of step t drawn by orc_normals(seed, 0, t0 + t, ...).  loc/raw ([K*5])
  * are updated in place; m, v ([K*10], layout as grad) carry the Adam moments;
  * t0 is the number of steps already taken.  trace[iters] receives the ELBO
- * estimate of each step (evaluated before that step's update).
+ * estimate of each step (evaluated before that step's update).  orc_fit_ex
+ * takes lik and iw as orc_elbo_grad_ex does (trace then holds that objective).
  */
-void orc_fit(int K, const int *off, const double *pos, const double *inten,
-             int N, const double *x, const double *y, const double *bg,
-             const orc_prior *pr, int S, uint64_t seed, int t0, int iters,
-             double lr, double b1, double b2, double adam_eps,
-             double *loc, double *raw, double *m, double *v, double *trace)
+void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
+                int N, const double *x, const double *y, const double *bg,
+                const orc_prior *pr, int lik, int iw, int S, uint64_t seed, int t0, int iters,
+                double lr, double b1, double b2, double adam_eps,
+                double *loc, double *raw, double *m, double *v, double *trace)
 {
     double *eps = (double *)malloc((size_t)S * K * 5 * sizeof(double));
     double *grad = (double *)malloc((size_t)K * 10 * sizeof(double));
@@ -429,7 +508,8 @@ void orc_fit(int K, const int *off, const double *pos, const double *inten,
     for (int t = 0; t < iters; ++t) {
         orc_normals(seed, 0u, (uint32_t)(t0 + t), S, K, eps);
         double elbo;
-        orc_elbo_grad(K, off, pos, inten, N, x, y, bg, pr, S, loc, raw, eps, &elbo, NULL, NULL, grad, NULL);
+        orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, lik, iw, S, loc, raw, eps, &elbo, NULL, NULL, grad,
+                         NULL);
         if (trace) trace[t] = elbo;
         for (int k = 0; k < K; ++k)
             for (int j = 0; j < 5; ++j) {
@@ -444,6 +524,16 @@ void orc_fit(int K, const int *off, const double *pos, const double *inten,
             }
     }
     free(eps); free(grad); free(par);
+}
+
+void orc_fit(int K, const int *off, const double *pos, const double *inten,
+             int N, const double *x, const double *y, const double *bg,
+             const orc_prior *pr, int S, uint64_t seed, int t0, int iters,
+             double lr, double b1, double b2, double adam_eps,
+             double *loc, double *raw, double *m, double *v, double *trace)
+{
+    orc_fit_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, S, seed, t0, iters, lr, b1, b2, adam_eps,
+               loc, raw, m, v, trace);
 }
 
 int orc_max_threads(void)

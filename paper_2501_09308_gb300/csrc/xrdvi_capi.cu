@@ -158,6 +158,11 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
         XR_TRY(c->alloc(&W.gred, static_cast<size_t>(W.B) * P.K * kGradBlocks * 10, list));
         XR_TRY(c->alloc(&W.tickets, static_cast<size_t>(W.B) * P.K, list));
         W.lq = nullptr;
+        W.iw = nullptr;
+        if (c->cfg.flags & XRDVI_FLAG_IW_ELBO) {   // ln q(u_s) and the normalised weights
+            XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
+            XR_TRY(c->alloc(&W.iw, static_cast<size_t>(S), list));
+        }
     } else {
         XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
         W.gpart = nullptr;
@@ -349,6 +354,12 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         if (y > 0) csum += y * std::log(y) - y - std::lgamma(y + 1.0);
     }
     if (!(eta > 0.0)) return fail(XRDVI_EINVAL, "max(Y - B) must be positive (it sets the intensity prior)");
+    const bool gauss = (cfg->flags & XRDVI_FLAG_GAUSS_LIK) != 0;
+    if (gauss) {   // Gaussian variant: the data part is -ln(2 pi v_i)/2, v_i = max(y_i, 1)
+        csum = 0.0;
+        for (int i = 0; i < N; ++i)
+            csum -= 0.5 * std::log(2.0 * M_PI * std::max(1.0, static_cast<double>(pt->y_counts[i])));
+    }
 
     int dev = 0, sms = 0;
     XR_CUDA(cudaGetDevice(&dev));
@@ -380,6 +391,7 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     P.T = (N + kTile - 1) / kTile;
     P.Npad = P.T * kTile;
     P.csum = csum;
+    P.gauss = gauss;
     P.prior.lambda = 1.0 / eta;
     P.prior.mu_sd = cfg->prior_mu_sd;
     P.prior.alpha_mean = cfg->prior_alpha_mean;

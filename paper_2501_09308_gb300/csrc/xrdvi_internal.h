@@ -90,6 +90,8 @@ struct Workspace {
     int B = 1, S_sub = 0;
     const uint32_t *mask = nullptr;   // [B] device
     double *tail_sum = nullptr;       // [B] sum of the ELBO estimates from step tail_start on
+    double *iw = nullptr;             // [S] normalised importance weights (importance-weighted
+                                      //     objective; null: the ELBO, weights 1/S)
     int tail_start = 0;
     int C = 1;                   // phase chunks
     int chunk[kMaxChunks + 1] = {0};
@@ -108,6 +110,7 @@ struct Problem {
     size_t smem = 0;             // dynamic shared memory of the backward profile kernels
     size_t smem_fwd = 0;         // ... of the forward kernel (compact table)
     bool wide = false;           // backward peak table stored as (-p, -p, I, I) float4
+    bool gauss = false;          // Gaussian likelihood variant (variance max(y, 1))
     int grid_fwd = 0, grid_bwd = 0;
 };
 

@@ -306,6 +306,7 @@ struct ProfArgs {
     float *gpart;      // [S*K*T*kGradSums]
     float *fpart;      // [C*S*Npad] partial profiles per phase chunk
     int *counter;      // work counter of this kernel (zeroed by k_sample)
+    int gauss;         // Gaussian likelihood variant
 };
 
 typedef unsigned long long f2_t;   // two packed floats
@@ -674,8 +675,15 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
         float f = a.bg[i];
         for (int c = 0; c < a.C; ++c) f += a.fpart[(static_cast<size_t>(c) * a.S + s) * a.Npad + i];
         const float yv = a.y[i];
-        dev = deviance_term(yv, f);
-        gv = (yv > 0.f) ? __fdiv_rn(yv, f) - 1.0f : -1.0f;
+        if (a.gauss) {
+            // Gaussian variant: -(y - f)^2 / (2 v), d/df = (y - f) / v, v = max(y, 1)
+            const float v = fmaxf(yv, 1.f), r = yv - f;
+            gv = __fdiv_rn(r, v);
+            dev = -0.5f * r * gv;
+        } else {
+            dev = deviance_term(yv, f);
+            gv = (yv > 0.f) ? __fdiv_rn(yv, f) - 1.0f : -1.0f;
+        }
         if (a.f_out) a.f_out[static_cast<size_t>(s) * a.N + i] = f;
     }
     a.g[static_cast<size_t>(s) * a.Npad + i] = gv;
@@ -938,6 +946,8 @@ struct GradArgs {
     const uint32_t *mask;
     double *tail_sum;   // [B] (may be null): ELBO estimates summed from step tail_start on
     int tail_start;
+    const double *lq;   // [S] ln q(u_s) (importance-weighted objective)
+    double *iw;         // [S] normalised importance weights (null: the ELBO)
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -953,9 +963,26 @@ __global__ void __launch_bounds__(256) k_elbo(GradArgs a) {
         a.ll[s] = ll;
         acc += ll + a.lpj[s];
     }
+    double iw_bound = 0.0;
+    if (a.iw) {
+        // importance-weighted bound (Burda et al. 2016): ln w_s = LL + ln p + ln|J| - ln q,
+        // L = logsumexp(ln w) - ln S; the normalised weights drive k_grad
+        __syncthreads();   // a.ll of this block written
+        double mx = -CUDART_INF;
+        for (int s = b * a.S_sub + threadIdx.x; s < (b + 1) * a.S_sub; s += blockDim.x)
+            mx = fmax(mx, a.ll[s] + a.lpj[s] - a.lq[s]);
+        mx = block_max(mx, sh);
+        double se = 0.0;
+        for (int s = b * a.S_sub + threadIdx.x; s < (b + 1) * a.S_sub; s += blockDim.x)
+            se += exp(a.ll[s] + a.lpj[s] - a.lq[s] - mx);
+        se = block_sum(se, sh);
+        for (int s = b * a.S_sub + threadIdx.x; s < (b + 1) * a.S_sub; s += blockDim.x)
+            a.iw[s] = exp(a.ll[s] + a.lpj[s] - a.lq[s] - mx) / se;
+        iw_bound = mx + log(se) - log(static_cast<double>(a.S_sub));
+    }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) {
-        const double elbo = acc / a.S_sub + a.ent[b];
+        const double elbo = a.iw ? iw_bound : acc / a.S_sub + a.ent[b];
         if (a.elbo_out) a.elbo_out[b] = elbo;
         if (a.d_iter) {
             const int it = *a.d_iter;
@@ -1036,6 +1063,11 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             G[3] = r * (1.0 - r) * h * (q[1] - q[0]) + (1.0 - 2.0 * r);
             const double gal = clamped ? 0.0 : (2.0 * h / acl) * ((1.0 - r) * ln2 * BGp + r * BLp);
             G[4] = gal - (al - a.pr.alpha_mean) / (a.pr.alpha_sd * a.pr.alpha_sd);
+            if (a.iw) {   // importance-weighted objective: weight w_s / sum w
+                const double wt = __ldcg(&a.iw[c0 + lane]);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) G[j] *= wt;
+            }
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
                 accl[j] += G[j];
@@ -1076,10 +1108,11 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         const bool is_raw = threadIdx.x >= 5;
         const double rw = a.raw_in[bk * 5 + j];
         double grad;
+        // importance weights are already normalised; the ELBO takes the sample mean
         if (!is_raw) {
-            grad = red[j] / a.S_sub;
+            grad = a.iw ? red[j] : red[j] / a.S_sub;
         } else {
-            grad = (red[5 + j] / a.S_sub + 1.0 / softplusd(rw)) * sigmoidd(rw);
+            grad = ((a.iw ? red[5 + j] : red[5 + j] / a.S_sub) + 1.0 / softplusd(rw)) * sigmoidd(rw);
         }
         if (a.grad_out) a.grad_out[bk * 10 + threadIdx.x] = static_cast<float>(grad);
         if (a.adam) {
@@ -1350,6 +1383,7 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     a.x = P.x; a.y = P.y; a.bg = P.bg;
     a.cst = W.cst; a.ranges = W.ranges; a.g = W.g; a.f_out = f_out; a.llpart = W.llpart; a.gpart = W.gpart;
     a.fpart = W.fpart; a.counter = W.counters;
+    a.gauss = P.gauss ? 1 : 0;
     return a;
 }
 
@@ -1446,10 +1480,18 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.gred = W.gred; a.tickets = W.tickets;
     a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
     a.tail_sum = W.tail_sum; a.tail_start = W.tail_start;
+    a.lq = W.lq; a.iw = W.iw;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
-    if (grad_out || adam) k_grad<<<dim3(W.B * P.K, a.NB), 256, 0, st>>>(a);
-    if (elbo_out || trace || W.tail_sum) k_elbo<<<W.B, 256, 0, st>>>(a);
+    const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;
+    if (W.iw) {
+        // the importance weights (k_elbo) come before the weighted gradient
+        k_elbo<<<W.B, 256, 0, st>>>(a);
+        if (want_grad) k_grad<<<dim3(W.B * P.K, a.NB), 256, 0, st>>>(a);
+    } else {
+        if (want_grad) k_grad<<<dim3(W.B * P.K, a.NB), 256, 0, st>>>(a);
+        if (want_elbo) k_elbo<<<W.B, 256, 0, st>>>(a);
+    }
 }
 
 void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m, cudaStream_t st) {

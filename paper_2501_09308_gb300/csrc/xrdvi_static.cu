@@ -52,6 +52,8 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     if (S < 1 || S > kMaxS) return report_error(XRDVI_EINVAL, "elbo_grad_static: S must be in [1, 65536]");
     if (!(std::isfinite(lambda_) && lambda_ > 0.0) || !std::isfinite(data_const))
         return report_error(XRDVI_EINVAL, "elbo_grad_static: lambda_ must be positive, data_const finite");
+    if (cfg->flags & XRDVI_FLAG_IW_ELBO)
+        return report_error(XRDVI_EINVAL, "elbo_grad_static: the importance-weighted objective is not supported");
 
     // Layout of the scratch array for this call.
     const size_t T = (static_cast<size_t>(N) + kTile - 1) / kTile;
@@ -115,6 +117,7 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     P.y = const_cast<float *>(d_y);
     P.bg = const_cast<float *>(d_bg);
     P.csum = data_const;
+    P.gauss = (cfg->flags & XRDVI_FLAG_GAUSS_LIK) != 0;
     P.prior.lambda = lambda_;
     P.prior.mu_sd = cfg->prior_mu_sd;
     P.prior.alpha_mean = cfg->prior_alpha_mean;

@@ -19,6 +19,8 @@ from . import build as _build
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EBUSY"}
 FLAG_BF16_INT = 1 << 0
 FLAG_NAIVE_SUM = 1 << 1
+FLAG_GAUSS_LIK = 1 << 2   # Gaussian likelihood, variance max(y, 1)
+FLAG_IW_ELBO = 1 << 3     # importance-weighted objective
 
 
 class XrdviError(RuntimeError):

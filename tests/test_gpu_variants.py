@@ -1,0 +1,106 @@
+"""Estimator and likelihood variants on the GPU against the FP64 oracle on
+the same inputs and injected noise: the Gaussian likelihood (variance
+max(y, 1)) and the importance-weighted objective (Burda et al., ICLR 2016).
+
+Tolerances as for the plain path (profile, LL, ELBO 1e-5; gradient blocks
+1e-4 of their max-norm), except the importance-weighted gradient: its
+weights exp(ln w_s - max) turn an absolute error d in the per-draw log
+weights into a relative error of about 2d in the weights, and the FP32
+path's per-draw log-likelihood carries an absolute error of about
+|LL_s| * 4e-8, so that gradient is held to 1e-4 + 4 * max_s |dLL_s|."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_09308_gb300 import synth, xrdvi
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+G_TOL = 1e-4
+
+
+def _run(inst, S, flags, seed, **okw):
+    ctx = xrdvi.Context.from_instance(inst, S=S, flags=flags)
+    loc, raw = ctx.params()
+    rng = np.random.default_rng(seed)
+    loc = loc + rng.normal(0, 0.05, loc.shape).astype(np.float32)
+    raw = raw + rng.normal(0, 0.1, raw.shape).astype(np.float32)
+    ctx.set_params(loc, raw)
+    eps = synth.normals(2000 + seed, S, inst.K)
+    g = ctx.elbo_grad(eps, want_f=True)
+    ctx.close()
+    P = oracle.Problem.from_instance(inst, **okw)
+    o = P.elbo_grad(loc.astype(np.float64), raw.astype(np.float64), eps.astype(np.float64), want_f=True)
+    return g, o
+
+
+def _check(g, o, g_tol=G_TOL):
+    assert np.max(np.abs(g["f"] - o["f"]) / np.abs(o["f"])) <= F_TOL
+    np.testing.assert_allclose(g["ll"], o["ll"], rtol=F_TOL)
+    assert abs(g["elbo"] - o["elbo"]) <= F_TOL * abs(o["elbo"])
+    for b in range(10):
+        ref = np.max(np.abs(o["grad"][:, b]))
+        err = np.max(np.abs(g["grad"][:, b] - o["grad"][:, b]))
+        assert err <= g_tol * ref, (b, err, ref)
+
+
+@pytest.mark.parametrize("K,M,N,S,seed", [(3, 6, 300, 4, 1), (8, 20, 1000, 8, 2), (1, 1, 1, 1, 3)])
+def test_gaussian_likelihood_parity(K, M, N, S, seed):
+    inst = synth.small_problem(K=K, M=M, N=N, S=S, seed=seed, x_step=max(0.02, 15.0 / N))
+    g, o = _run(inst, S, xrdvi.FLAG_GAUSS_LIK, seed, likelihood="gauss")
+    _check(g, o)
+
+
+@pytest.mark.parametrize("K,M,N,S,seed", [(3, 6, 300, 4, 4), (8, 20, 1000, 8, 5), (4, 10, 700, 64, 6)])
+def test_importance_weighted_objective_parity(K, M, N, S, seed):
+    inst = synth.small_problem(K=K, M=M, N=N, S=S, seed=seed, x_step=max(0.02, 15.0 / N))
+    g, o = _run(inst, S, xrdvi.FLAG_IW_ELBO, seed, objective="iw")
+    dll = float(np.max(np.abs(g["ll"] - o["ll"])))
+    gerr = max(float(np.max(np.abs(g["grad"][:, b] - o["grad"][:, b])) / np.max(np.abs(o["grad"][:, b])))
+               for b in range(10))
+    print(f"\nIW K={K} S={S}: max |dLL_s| = {dll:.2e}, gradient error {gerr:.2e} (max-norm per block), "
+          f"bound {o['elbo']:.6e}")
+    _check(g, o, g_tol=G_TOL + 4 * dll)
+
+
+def test_importance_weighted_gradient_at_one_draw_is_the_elbo_gradient():
+    """One draw: the weight is exactly 1, so the two objectives give the
+    same gradient bit for bit (the oracle pins the identity in FP64)."""
+    inst = synth.small_problem(K=3, M=6, N=300, S=1, seed=7)
+    eps = synth.normals(77, 1, inst.K)
+    out = []
+    for flags in (0, xrdvi.FLAG_IW_ELBO):
+        c = xrdvi.Context.from_instance(inst, S=1, flags=flags)
+        out.append(c.elbo_grad(eps)["grad"])
+        c.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("flags,okw", [(xrdvi.FLAG_GAUSS_LIK, {"likelihood": "gauss"}),
+                                       (xrdvi.FLAG_IW_ELBO, {"objective": "iw"})])
+def test_variant_fit_steps_match_oracle(flags, okw):
+    """Three fused SVI steps (Philox noise, Adam) against the oracle's fit
+    loop with the same variant."""
+    inst = synth.small_problem(K=3, M=6, N=300, S=8, seed=14)
+    ctx = xrdvi.Context.from_instance(inst, S=8, seed=4242, flags=flags)
+    loc0, raw0 = ctx.params()
+    trace = ctx.fit(3)
+    loc1, raw1 = ctx.params()
+    ctx.close()
+    ref = oracle.Problem.from_instance(inst, **okw).fit(8, 3, 4242, loc=loc0.astype(np.float64),
+                                                         raw=raw0.astype(np.float64))
+    np.testing.assert_allclose(trace, ref["trace"], rtol=F_TOL)
+    np.testing.assert_allclose(loc1, ref["loc"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(raw1, ref["raw"], rtol=1e-5, atol=1e-5)
+
+
+def test_gaussian_variant_recovers_planted_phases():
+    """The tiny workload fitted with the Gaussian likelihood: the planted
+    phases carry the area."""
+    inst = synth.config(0)
+    c = xrdvi.Context.from_instance(inst, S=inst.S, flags=xrdvi.FLAG_GAUSS_LIK)
+    c.fit(1000)
+    post = c.posterior(512, 3, top_m=1)
+    c.close()
+    assert set(np.flatnonzero(post["combos"][0]).tolist()) == set(inst.planted.tolist())

@@ -1,0 +1,125 @@
+"""Pins of the oracle's estimator and likelihood variants (no GPU): the
+Gaussian likelihood against scipy's normal density and central differences;
+the importance-weighted bound (Burda et al., ICLR 2016) against its
+definition written with scipy, its one-draw reduction, central differences,
+the posterior module's importance-sampled evidence and the gamma-Poisson
+closed form."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+import oracle
+from oracle import posterior as post
+from paper_2501_09308_gb300 import synth
+
+from test_oracle_elbo import _conjugate_setup
+
+
+def _fd_grad(P, loc, raw, eps, h=1e-6):
+    num = np.zeros((P.K, 10))
+    for k in range(P.K):
+        for j in range(5):
+            for which in (0, 1):
+                L, R = loc.copy(), raw.copy()
+                A = L if which == 0 else R
+                A[k, j] += h
+                ep = P.elbo_grad(L, R, eps)["elbo"]
+                A[k, j] -= 2 * h
+                em = P.elbo_grad(L, R, eps)["elbo"]
+                num[k, j + 5 * which] = (ep - em) / (2 * h)
+    return num
+
+
+def _perturbed(P, seed):
+    loc, raw = P.init_params()
+    rng = np.random.default_rng(seed)
+    return loc + rng.normal(0, 0.05, loc.shape), raw + rng.normal(0, 0.1, raw.shape)
+
+
+def _problem(**kw):
+    inst = synth.small_problem(K=3, M=6, N=240, seed=4)
+    return inst, oracle.Problem.from_instance(inst, **kw)
+
+
+def test_gaussian_loglik_is_the_normal_density_with_variance_max_y_1():
+    inst, P = _problem(likelihood="gauss")
+    rng = np.random.default_rng(1)
+    f = P.y + rng.normal(0, 30.0, P.N) + 5.0
+    ref = stats.norm.logpdf(P.y, loc=f, scale=np.sqrt(np.maximum(P.y, 1.0))).sum()
+    assert P.loglik(f, "gauss") == pytest.approx(ref, rel=1e-12)
+
+
+def test_gaussian_likelihood_terms_and_gradient():
+    """The per-draw LL is the Gaussian log density at the draw's profile, and
+    the analytic gradient matches FP64 central differences (h = 1e-6)."""
+    inst, P = _problem(likelihood="gauss")
+    loc, raw = _perturbed(P, 2)
+    eps = synth.normals(7, 2, P.K).astype(np.float64)
+    r = P.elbo_grad(loc, raw, eps, want_f=True)
+    for s in range(2):
+        assert r["ll"][s] == pytest.approx(P.loglik(r["f"][s], "gauss"), rel=1e-12)
+    num = _fd_grad(P, loc, raw, eps)
+    rel = np.max(np.abs(num - r["grad"]), axis=0) / np.max(np.abs(r["grad"]), axis=0)
+    assert np.all(rel < 1e-5), rel
+
+
+def test_iw_bound_is_its_definition():
+    """L_S = logsumexp_s(ln p(Y, theta_s) + ln|J_s| - ln q(u_s)) - ln S, with
+    ln q written as scipy normal log densities of u = loc + sigma eps."""
+    inst, P = _problem(objective="iw")
+    loc, raw = _perturbed(P, 3)
+    eps = synth.normals(8, 6, P.K).astype(np.float64)
+    r = P.elbo_grad(loc, raw, eps)
+    sig = np.logaddexp(0.0, raw)
+    u = loc[None] + sig[None] * eps
+    lq = stats.norm.logpdf(u, loc=loc[None], scale=sig[None]).sum(axis=(1, 2))
+    lw = r["ll"] + r["lpj"] - lq
+    assert r["elbo"] == pytest.approx(special.logsumexp(lw) - math.log(6), rel=1e-12)
+    # Jensen: the bound is above the mean log weight
+    assert r["elbo"] >= np.mean(lw)
+
+
+def test_iw_gradient_at_one_draw_is_the_elbo_gradient():
+    """With one draw the weight is 1 and -ln q differs from the analytic
+    entropy by a constant in loc and by the same 1/sigma in raw, so the two
+    objectives have the same gradient."""
+    inst, P_iw = _problem(objective="iw")
+    P_e = oracle.Problem.from_instance(inst)
+    loc, raw = _perturbed(P_e, 4)
+    eps = synth.normals(9, 1, P_e.K).astype(np.float64)
+    np.testing.assert_allclose(P_iw.elbo_grad(loc, raw, eps)["grad"], P_e.elbo_grad(loc, raw, eps)["grad"],
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_iw_gradient_against_central_differences():
+    inst, P = _problem(objective="iw")
+    loc, raw = _perturbed(P, 5)
+    eps = synth.normals(10, 4, P.K).astype(np.float64)
+    g = P.elbo_grad(loc, raw, eps)["grad"]
+    num = _fd_grad(P, loc, raw, eps)
+    rel = np.max(np.abs(num - g), axis=0) / np.max(np.abs(g), axis=0)
+    assert np.all(rel < 1e-5), rel
+
+
+def test_iw_bound_between_elbo_and_evidence_in_the_conjugate_case():
+    """Gamma-Poisson case with q shifted 1.5 posterior standard deviations off:
+    the ELBO is well below the closed-form ln p(Y), the importance-weighted
+    bound with 2048 draws is within a few hundredths of it, and it equals the
+    posterior module's importance-sampled evidence for the same draws."""
+    P, loc, raw, lnZ, fixed_lpj, fixed_H, sig0 = _conjugate_setup()
+    loc = loc.copy()
+    loc[0, 0] += 1.5 / math.sqrt(P.y.sum())
+    rng = np.random.default_rng(12)
+    S = 2048
+    eps = np.zeros((S, 1, 5))
+    eps[:, 0, 0] = rng.standard_normal(S)
+    P_iw = oracle.Problem(P.off, P.pos, P.inten, P.x, P.y, P.bg, objective="iw")
+    lq_fixed = 4 * (-math.log(sig0) - 0.5 * math.log(2 * math.pi))
+    l_iw = P_iw.elbo_grad(loc, raw, eps)["elbo"] - fixed_lpj + lq_fixed
+    l_elbo = P.elbo_grad(loc, raw, eps)["elbo"] - fixed_lpj - fixed_H
+    assert lnZ - l_elbo > 0.5
+    assert abs(lnZ - l_iw) < 0.05
+    res = post.posterior(P, loc, raw, S, eps=eps, top_m=1)
+    assert P_iw.elbo_grad(loc, raw, eps)["elbo"] == pytest.approx(res["log_evidence"], rel=1e-12)
