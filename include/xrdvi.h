@@ -348,6 +348,20 @@ xrdvi_status xrdvi_enumerate(const xrdvi_peaks *peaks, const xrdvi_pattern *patt
  * 0 on invalid sizes). */
 size_t xrdvi_enumerate_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t nsub);
 
+/* Tensor-core GEMM used by the shared-shape variant (XRDVI_FLAG_SHARED_SHAPES),
+ * exported for testing: C[M x N] = A[M x K] . B[N x K]^T with A, B, C DEVICE
+ * row-major FP32 matrices (K contiguous in A and B; leading dimensions lda,
+ * ldb, ldc in elements), computed on the 5th-generation tensor cores
+ * (tcgen05.mma kind::tf32, accumulators in tensor memory) with the 3xTF32
+ * split a = a_hi + a_lo (a_hi = a truncated to TF32): a b ~ a_hi b_hi +
+ * a_hi b_lo + a_lo b_hi, FP32 accumulation, split-K partials added in a
+ * fixed order (deterministic).  K, lda and ldb must be multiples of 4 with
+ * lda, ldb >= K, ldc >= N, and A, B 16-byte aligned (EINVAL otherwise).
+ * Allocates its scratch on cuda_stream (stream-ordered) and synchronises it;
+ * ETIMEOUT if a pipeline wait gave up.  No counterpart in the paper. */
+xrdvi_status xrdvi_gemm_nt_tf32x3(int32_t M, int32_t N, int32_t K, const float *d_A, int32_t lda,
+                                  const float *d_B, int32_t ldb, float *d_C, int32_t ldc, void *cuda_stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *xrdvi_last_error(void);
 

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libxrdvi.so")
-SOURCES = ["xrdvi_kernels.cu", "xrdvi_capi.cu", "xrdvi_static.cu", "xrdvi_server.cu"]
+SOURCES = ["xrdvi_kernels.cu", "xrdvi_capi.cu", "xrdvi_static.cu", "xrdvi_server.cu", "xrdvi_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -179,6 +179,17 @@ xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, co
 // order (one block).
 void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st);
 
+// Tensor-core GEMM (xrdvi_tc.cu): out[M x N] = A[M x K] . B[N x K]^T, A and B
+// row-major with K contiguous (K, lda, ldb multiples of 4, 16-byte aligned),
+// 3xTF32 on tcgen05 with FP32 accumulation; split-K partials (work,
+// gemm_workspace_floats) are added in a fixed order.  err (device int) is set
+// if an mbarrier wait gives up.
+size_t gemm_smem_bytes();
+int gemm_splits(int M, int N, int K, int sm_count);
+size_t gemm_workspace_floats(int M, int N, int splits);
+void launch_gemm_nt_tf32x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *out,
+                           int ldo, int splits, float *work, int *err, cudaStream_t st);
+
 // Occupancy-based persistent grid sizes.
 void configure_grids(Problem &P, int sm_count);
 // Phase chunks for a sample set of S samples: enough work items for about

@@ -112,6 +112,7 @@ SIGNATURES = {
     "xrdvi_server_destroy": (None, [_vp]),
     "xrdvi_enumerate": (ctypes.c_int, [P(Peaks), P(Pattern), P(Config), _i32, ctypes.c_size_t, P(_d), P(_d)]),
     "xrdvi_enumerate_footprint_bytes": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _i32]),
+    "xrdvi_gemm_nt_tf32x3": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -441,3 +442,9 @@ def xrdvi_enumerate(offsets, pos, inten, x, y, bg, cfg: Config, iters, hbm_budge
     codes = np.arange(1, n + 1)
     masks = ((codes[:, None] >> np.arange(K)[None, :]) & 1).astype(bool)
     return masks, elbo[:n], logp[:n]
+
+
+def xrdvi_gemm_nt_tf32x3(M, N, K, d_A, lda, d_B, ldb, d_C, ldc, stream=None):
+    """Device-pointer GEMM C = A . B^T on the tensor cores (3xTF32)."""
+    _check(lib().xrdvi_gemm_nt_tf32x3(int(M), int(N), int(K), _vp(d_A), int(lda), _vp(d_B), int(ldb), _vp(d_C),
+                                      int(ldc), _vp(stream or CUDA_STREAM_LEGACY)))
