@@ -274,19 +274,49 @@ def enumeration_leg(iters=3000):
             "planted": [int(k) for k in inst.planted]}
 
 
-def variants_leg(steps=32):
+def variants_leg(peaks, steps=32):
     """Estimator variants on the K=50 workload: per-kernel CUDA-event times of
-    `steps` SVI steps with the Gaussian likelihood and with the
-    importance-weighted objective, beside the plain path's."""
+    `steps` SVI steps with the Gaussian likelihood, the importance-weighted
+    objective and the shared-shape estimator; for the last also the whole fit
+    + posterior (time-to-posterior, CUDA events) and the roofline of its
+    backward contraction on the tensor cores."""
+    import numpy as np
+    import torch
     from paper_2501_09308_gb300 import synth, xrdvi
     inst = synth.config(1)
     out = {}
-    for name, flags in (("gauss_lik", xrdvi.FLAG_GAUSS_LIK), ("iw_elbo", xrdvi.FLAG_IW_ELBO)):
+    for name, flags in (("gauss_lik", xrdvi.FLAG_GAUSS_LIK), ("iw_elbo", xrdvi.FLAG_IW_ELBO),
+                        ("shared_shapes", xrdvi.FLAG_SHARED_SHAPES)):
         c = xrdvi.Context.from_instance(inst, S=inst.S, flags=flags)
         c.fit(16, trace=False)
         k = c.profile_steps(steps)
-        c.close()
         out[name] = {"kernel_ms_per_launch": k, "svi_step_ms": sum(k.values())}
+        if flags == xrdvi.FLAG_SHARED_SHAPES:
+            c.close()
+            c = xrdvi.Context.from_instance(inst, S=inst.S, flags=flags)
+            init = c.state()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c.fit(inst.iters, trace=False)   # warm-up fit (graphs captured)
+            c.set_state(init)
+            torch.cuda.synchronize()
+            ev0.record()
+            c.fit(inst.iters, trace=False)
+            post = c.posterior(S_POST, 77, TOP_M)
+            ev1.record()
+            torch.cuda.synchronize()
+            ttp = ev0.elapsed_time(ev1) / 1e3
+            Npad = (inst.N + 255) // 256 * 256
+            flop = 2.0 * inst.S * 10 * inst.K * Npad          # backward contraction, FP32-equivalent
+            tflops = flop / (k["backward"] * 1e-3) / 1e12
+            tf32_peak = float(peaks.get("bf16_tflops", 1965.0)) * 1.1 / 2.25
+            out[name].update({
+                "time_to_posterior_s": ttp, "svi_steps": inst.iters,
+                "top_combination": [int(v) for v in np.flatnonzero(post["combos"][0])],
+                "backward_gemm": {"shape": [inst.S, 10 * inst.K, Npad], "achieved_tflops": tflops,
+                                  "tensor_tflops_3xtf32": 3 * tflops, "tf32_peak_tflops": tf32_peak,
+                                  "frac_of_tf32_peak": 3 * tflops / tf32_peak,
+                                  "peak_source": "measured bf16 cuBLAS burst x nominal TF32/BF16 ratio 1.1/2.25"}})
+        c.close()
     return out
 
 
@@ -377,7 +407,7 @@ def main():
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serve = serving_leg(args.serve_requests, ms_step)
     enum = enumeration_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
-    variants = variants_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
+    variants = variants_leg(measured_peaks()[0]) if rank == 0 and world == 1 and not args.no_enumeration else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

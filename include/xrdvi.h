@@ -90,6 +90,15 @@ typedef struct {
  * xrdvi_elbo_grad, forward_dev) are then that bound. */
 #define XRDVI_FLAG_GAUSS_LIK  (1u << 2)
 #define XRDVI_FLAG_IW_ELBO    (1u << 3)
+/* Shared-shape estimator: the shapes (mu, w, r, alpha) of all S samples of a
+ * step take sample 0's noise, the intensities h each sample's own (an
+ * unbiased estimator of the same ELBO; with injected noise, eps[s][k][1..4]
+ * is replaced by eps[0][k][1..4]).  The profile then factors into phase
+ * profiles evaluated once per step, and both the forward contraction over
+ * phases and the backward's per-(sample, phase) sums run as GEMMs on the
+ * tensor cores (xrdvi_gemm_nt_tf32x3).  Not with sub-model batches or the
+ * static entry. */
+#define XRDVI_FLAG_SHARED_SHAPES (1u << 4)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */

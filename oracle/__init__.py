@@ -97,8 +97,9 @@ def lib():
                                         pd, pd, pd, pd, pd, pd, pd, pd]
             L.orc_elbo_grad_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32,
                                            pd, pd, pd, pd, pd, pd, pd, pd]
-            L.orc_fit_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32, u64, i32, i32,
+            L.orc_fit_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32, i32, u64, i32, i32,
                                      d, d, d, d, pd, pd, pd, pd, pd]
+            L.orc_tie_shapes.argtypes = [i32, i32, pd]
             L.orc_loglik_gauss.restype = d
             L.orc_loglik_gauss.argtypes = [i32, pd, pd]
             L.orc_iw_weights.restype = d
@@ -129,12 +130,15 @@ class Problem:
     def __init__(self, offsets, pos, inten, x, y, bg, *, lam=None,
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
                  w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
-                 likelihood="poisson", objective="elbo"):
+                 likelihood="poisson", objective="elbo", shapes="independent"):
         # variants: likelihood "poisson" (the paper's) or "gauss" (variance
-        # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound)
+        # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound);
+        # shapes "independent" or "shared" (one shape draw per step)
         assert likelihood in ("poisson", "gauss") and objective in ("elbo", "iw")
+        assert shapes in ("independent", "shared")
         self.lik = 1 if likelihood == "gauss" else 0
         self.iw = 1 if objective == "iw" else 0
+        self.shared = 1 if shapes == "shared" else 0
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -194,8 +198,10 @@ class Problem:
     def elbo_grad(self, loc, raw, eps, want_f=False):
         """ELBO estimate + per-sample LL, log prior+Jacobian and the gradient
         [K, 10] (loc grads then raw grads) for injected noise eps[S, K, 5]."""
-        eps = f64(eps)
+        eps = f64(eps).copy()
         S = eps.shape[0]
+        if self.shared:
+            lib().orc_tie_shapes(S, self.K, _pd(eps))
         elbo = ctypes.c_double(0.0)
         ll = np.zeros(S)
         lpj = np.zeros(S)
@@ -229,7 +235,8 @@ class Problem:
         m = np.zeros((self.K, 10)) if m is None else f64(m).copy()
         v = np.zeros((self.K, 10)) if v is None else f64(v).copy()
         trace = np.zeros(iters)
-        lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), self.lik, self.iw, S, seed, t0, iters,
+        lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), self.lik, self.iw, self.shared, S, seed, t0,
+                         iters,
                          lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
         return {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
 

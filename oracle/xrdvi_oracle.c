@@ -467,6 +467,20 @@ void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten
     orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, S, loc, raw, eps, elbo, ll, lpj, grad, f_out);
 }
 
+/*
+ * Shared-shape estimator (Reading: one draw of the shape parameters per step
+ * for all samples, each sample its own intensity): the noise of the shapes
+ * j = 1..4 of every sample becomes sample 0's.  The estimator of the ELBO is
+ * the plain one on this noise, so it stays unbiased; only its variance
+ * changes.
+ */
+void orc_tie_shapes(int S, int K, double *eps)
+{
+    for (int s = 1; s < S; ++s)
+        for (int k = 0; k < K; ++k)
+            for (int j = 1; j < 5; ++j) eps[((size_t)s * K + k) * 5 + j] = eps[(size_t)k * 5 + j];
+}
+
 /* ------------------------------------------------------------------------ */
 /* Optimiser (Reading: the paper names a gradient method; Adam is used)       */
 /* ------------------------------------------------------------------------ */
@@ -494,11 +508,12 @@ void orc_adam_step(int n, double *params, const double *grad, double *m, double 
  * are updated in place; m, v ([K*10], layout as grad) carry the Adam moments;
  * t0 is the number of steps already taken.  trace[iters] receives the ELBO
  * estimate of each step (evaluated before that step's update).  orc_fit_ex
- * takes lik and iw as orc_elbo_grad_ex does (trace then holds that objective).
+ * takes lik and iw as orc_elbo_grad_ex does (trace then holds that objective)
+ * and, with shared != 0, the shared-shape noise of orc_tie_shapes.
  */
 void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
                 int N, const double *x, const double *y, const double *bg,
-                const orc_prior *pr, int lik, int iw, int S, uint64_t seed, int t0, int iters,
+                const orc_prior *pr, int lik, int iw, int shared, int S, uint64_t seed, int t0, int iters,
                 double lr, double b1, double b2, double adam_eps,
                 double *loc, double *raw, double *m, double *v, double *trace)
 {
@@ -507,6 +522,7 @@ void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
     double *par = (double *)malloc((size_t)K * 10 * sizeof(double));
     for (int t = 0; t < iters; ++t) {
         orc_normals(seed, 0u, (uint32_t)(t0 + t), S, K, eps);
+        if (shared) orc_tie_shapes(S, K, eps);
         double elbo;
         orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, lik, iw, S, loc, raw, eps, &elbo, NULL, NULL, grad,
                          NULL);
@@ -532,7 +548,7 @@ void orc_fit(int K, const int *off, const double *pos, const double *inten,
              double lr, double b1, double b2, double adam_eps,
              double *loc, double *raw, double *m, double *v, double *trace)
 {
-    orc_fit_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, S, seed, t0, iters, lr, b1, b2, adam_eps,
+    orc_fit_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, 0, S, seed, t0, iters, lr, b1, b2, adam_eps,
                loc, raw, m, v, trace);
 }
 

@@ -186,12 +186,28 @@ AdamConst adam_const(const xrdvi_config &cfg) {
     return AdamConst{cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps};
 }
 
+// Profile + likelihood, and the backward's gradient sums, of the fit's sample
+// set: the dense profile kernels, or the tensor-core contractions of the
+// shared-shape variant.
+void fwd_pass(xrdvi_ctx *c, float *f_out, cudaStream_t st) {
+    if (c->W.shared)
+        launch_shared_forward(c->P, c->W, f_out, st);
+    else
+        launch_forward(c->P, c->W, f_out, (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0, st);
+}
+
+void bwd_pass(xrdvi_ctx *c, cudaStream_t st) {
+    if (c->W.shared)
+        launch_shared_backward(c->P, c->W, st);
+    else
+        launch_backward(c->P, c->W, st);
+}
+
 // One SVI step: sample -> profile + likelihood -> backward -> Adam -> ELBO.
 void enqueue_step(xrdvi_ctx *c, cudaStream_t st) {
-    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     launch_sample(c->P, c->W, c->loc, c->raw, nullptr, c->cfg.seed, 0u, c->step, 0u, c->iter, c->ent, st);
-    launch_forward(c->P, c->W, nullptr, naive, st);
-    launch_backward(c->P, c->W, st);
+    fwd_pass(c, nullptr, st);
+    bwd_pass(c, st);
     launch_grad(c->P, c->W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m,
                 c->v, c->iter, c->step, c->ent, c->elbo, c->trace, st);
 }
@@ -322,6 +338,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     const int K = pk->K, N = pt->N, M = pk->offsets[K];
     if (nsub < 1 || static_cast<int64_t>(nsub) * cfg->S > kMaxS)
         return fail(XRDVI_EINVAL, "sub-model batch: B * S must be in [1, 65536]");
+    if (masks && (cfg->flags & XRDVI_FLAG_SHARED_SHAPES))
+        return fail(XRDVI_EINVAL, "the shared-shape variant does not run in sub-model batches");
     if (masks) {
         if (K > 32) return fail(XRDVI_EINVAL, "sub-model batch: K must be <= 32");
         for (int b = 0; b < nsub; ++b)
@@ -434,6 +452,20 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     XR_C(c->alloc(&c->grad, KB * 10));
     XR_C(c->alloc(&c->ent, static_cast<size_t>(nsub)));
     XR_C(c->alloc(&c->elbo, static_cast<size_t>(nsub)));
+    Workspace &W = c->W;
+    if (cfg->flags & XRDVI_FLAG_SHARED_SHAPES) {
+        // shared-shape variant: GEMM operands and scratch of the tensor-core contractions
+        W.shared = true;
+        W.Kpad = (K + 31) / 32 * 32;
+        const int nk = K * kGradSums;
+        W.gemm_splits = gemm_splits(W.S, nk, P.Npad, sms);
+        XR_C(c->alloc(&W.H, static_cast<size_t>(W.S) * W.Kpad));
+        XR_C(c->alloc(&W.Ct, static_cast<size_t>(P.Npad) * W.Kpad));
+        XR_C(c->alloc(&W.D, static_cast<size_t>(nk) * P.Npad));
+        XR_C(c->alloc(&W.gemm_work, gemm_workspace_floats(W.S, nk, W.gemm_splits)));
+        XR_C(c->alloc(&W.gemm_err, 1));
+        if (gemm_configure() != cudaSuccess) return bail(fail(XRDVI_ECUDA, "tensor-core GEMM set-up failed"));
+    }
     XR_C(c->alloc(&c->trace, kTraceCap));
     XR_C(c->alloc(&c->step, 1));
     XR_C(c->alloc(&c->iter, 1));
@@ -459,7 +491,10 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         cudaMemsetAsync(c->v, 0, KB * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
         cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s) ||
         (d_mask && (up(d_mask, masks, static_cast<size_t>(nsub) * 4) ||
-                    cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))))
+                    cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))) ||
+        (W.shared && (cudaMemsetAsync(W.H, 0, static_cast<size_t>(W.S) * W.Kpad * 4, s) ||
+                      cudaMemsetAsync(W.Ct, 0, static_cast<size_t>(P.Npad) * W.Kpad * 4, s) ||
+                      cudaMemsetAsync(W.gemm_err, 0, 4, s))))
         return bail(fail(XRDVI_ECUDA, "upload failed"));
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return bail(fail(XRDVI_ECUDA, "create: device error"));
@@ -507,9 +542,12 @@ xrdvi_status xrdvi_fit(xrdvi_ctx *c, int32_t iters, double *trace) {
         done += chunk;
     }
     double last = 0.0;
+    int gerr = 0;
     XR_CUDA(cudaMemcpyAsync(&last, c->elbo, 8, cudaMemcpyDeviceToHost, c->stream));
+    if (c->W.gemm_err) XR_CUDA(cudaMemcpyAsync(&gerr, c->W.gemm_err, 4, cudaMemcpyDeviceToHost, c->stream));
     XR_CUDA(cudaStreamSynchronize(c->stream));
     c->host_step += iters;
+    if (gerr) return fail(XRDVI_ETIMEOUT, "tensor-core pipeline wait gave up");
     if (!std::isfinite(last)) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
     return XRDVI_OK;
 }
@@ -527,11 +565,10 @@ xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float
         XR_CUDA(cudaMemcpyAsync(c->eps_in, eps, SK5 * 4, cudaMemcpyHostToDevice, st));
     }
     if (f_out && !c->f_out) XR_TRY(c->alloc(&c->f_out, static_cast<size_t>(S) * P.N));
-    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     launch_sample(P, c->W, c->loc, c->raw, eps ? c->eps_in : nullptr, c->cfg.seed, 0u, c->step, 0u, nullptr,
                   c->ent, st);
-    launch_forward(P, c->W, f_out ? c->f_out : nullptr, naive, st);
-    launch_backward(P, c->W, st);
+    fwd_pass(c, f_out ? c->f_out : nullptr, st);
+    bwd_pass(c, st);
     launch_grad(P, c->W, c->loc, c->raw, nullptr, nullptr, c->grad, false, adam_const(c->cfg), nullptr, nullptr,
                 nullptr, nullptr, c->ent, c->elbo, nullptr, st);
     XR_TRY(check_launch("elbo_grad"));
@@ -550,9 +587,8 @@ xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float
 xrdvi_status xrdvi_forward_dev(xrdvi_ctx *c, const float *d_loc, const float *d_raw, const float *d_eps,
                                double *d_elbo) {
     if (!c || !d_loc || !d_raw || !d_eps || !d_elbo) return fail(XRDVI_EINVAL, "null argument");
-    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     launch_sample(c->P, c->W, d_loc, d_raw, d_eps, c->cfg.seed, 0u, nullptr, 0u, nullptr, c->ent, c->stream);
-    launch_forward(c->P, c->W, nullptr, naive, c->stream);
+    fwd_pass(c, nullptr, c->stream);
     launch_grad(c->P, c->W, d_loc, d_raw, nullptr, nullptr, nullptr, false, adam_const(c->cfg), nullptr, nullptr,
                 nullptr, nullptr, c->ent, d_elbo, nullptr, c->stream);
     return check_launch("forward_dev");
@@ -561,10 +597,9 @@ xrdvi_status xrdvi_forward_dev(xrdvi_ctx *c, const float *d_loc, const float *d_
 xrdvi_status xrdvi_backward_dev(xrdvi_ctx *c, const float *d_loc, const float *d_raw, const float *d_eps,
                                 float *d_grad) {
     if (!c || !d_loc || !d_raw || !d_eps || !d_grad) return fail(XRDVI_EINVAL, "null argument");
-    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     launch_sample(c->P, c->W, d_loc, d_raw, d_eps, c->cfg.seed, 0u, nullptr, 0u, nullptr, c->ent, c->stream);
-    launch_forward(c->P, c->W, nullptr, naive, c->stream);
-    launch_backward(c->P, c->W, c->stream);
+    fwd_pass(c, nullptr, c->stream);
+    bwd_pass(c, c->stream);
     launch_grad(c->P, c->W, d_loc, d_raw, nullptr, nullptr, d_grad, false, adam_const(c->cfg), nullptr, nullptr,
                 nullptr, nullptr, c->ent, nullptr, nullptr, c->stream);
     return check_launch("backward_dev");
@@ -632,16 +667,15 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *c, int32_t steps, float *kernel_ms) 
     cudaEvent_t ev[6];
     for (auto &e : ev) XR_CUDA(cudaEventCreate(&e));
     double acc[5] = {0, 0, 0, 0, 0};
-    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     cudaStream_t st = c->stream;
     xrdvi_status rc = XRDVI_OK;
     for (int i = 0; i < steps && rc == XRDVI_OK; ++i) {
         cudaEventRecord(ev[0], st);
         launch_sample(c->P, c->W, c->loc, c->raw, nullptr, c->cfg.seed, 0u, c->step, 0u, c->iter, c->ent, st);
         cudaEventRecord(ev[1], st);
-        launch_forward(c->P, c->W, nullptr, naive, st);
+        fwd_pass(c, nullptr, st);
         cudaEventRecord(ev[2], st);
-        launch_backward(c->P, c->W, st);
+        bwd_pass(c, st);
         cudaEventRecord(ev[3], st);
         launch_grad(c->P, c->W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m, c->v,
                     c->iter, nullptr, c->ent, nullptr, nullptr, st);

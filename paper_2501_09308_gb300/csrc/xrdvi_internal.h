@@ -92,6 +92,16 @@ struct Workspace {
     double *tail_sum = nullptr;       // [B] sum of the ELBO estimates from step tail_start on
     double *iw = nullptr;             // [S] normalised importance weights (importance-weighted
                                       //     objective; null: the ELBO, weights 1/S)
+    // Shared-shape variant (one shape draw per step for all samples): the
+    // profile and the backward's sums become GEMMs over phase profiles.
+    bool shared = false;
+    int Kpad = 0;                     // phases padded to a multiple of 32
+    float *H = nullptr;               // [S*Kpad] intensities h_sk (GEMM A of the forward)
+    float *Ct = nullptr;              // [Npad*Kpad] phase profiles C_k(x_i), point-major
+    float *D = nullptr;               // [K*10*Npad] derivative profiles D_jk(x_i) (GEMM B of the backward)
+    float *gemm_work = nullptr;       // split-K partials of the backward GEMM
+    int gemm_splits = 1;
+    int *gemm_err = nullptr;          // set if a tensor-core pipeline wait gives up
     int tail_start = 0;
     int C = 1;                   // phase chunks
     int chunk[kMaxChunks + 1] = {0};
@@ -179,12 +189,21 @@ xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, co
 // order (one block).
 void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st);
 
+// k_lik alone (f = B + chunk partials, deviance, g), over the first C chunks.
+void launch_lik(const Problem &P, Workspace &W, float *f_out, int C, cudaStream_t st);
+// Shared-shape variant (xrdvi_tc.cu): phase and derivative profiles of sample
+// 0's shapes, the forward GEMM into fpart and k_lik; the backward GEMM into
+// gpart (one tile per (sample, phase)).
+void launch_shared_forward(const Problem &P, Workspace &W, float *f_out, cudaStream_t st);
+void launch_shared_backward(const Problem &P, Workspace &W, cudaStream_t st);
+
 // Tensor-core GEMM (xrdvi_tc.cu): out[M x N] = A[M x K] . B[N x K]^T, A and B
 // row-major with K contiguous (K, lda, ldb multiples of 4, 16-byte aligned),
 // 3xTF32 on tcgen05 with FP32 accumulation; split-K partials (work,
 // gemm_workspace_floats) are added in a fixed order.  err (device int) is set
 // if an mbarrier wait gives up.
 size_t gemm_smem_bytes();
+cudaError_t gemm_configure();   // shared-memory attribute of the GEMM kernel (call before capture)
 int gemm_splits(int M, int N, int K, int sm_count);
 size_t gemm_workspace_floats(int M, int N, int splits);
 void launch_gemm_nt_tf32x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *out,

@@ -146,6 +146,9 @@ struct SampleArgs {
     int *tickets;   // [B*K] arrival tickets of k_grad, zeroed here
     int B, S_sub;
     const uint32_t *mask;  // [B] phases kept by each sub-model (null: all)
+    int shared;            // shape noise of every sample = sample 0's (shared-shape variant)
+    float *H;              // [S*Kpad] h_sk for the forward GEMM (shared-shape variant)
+    int Kpad;
     // FP32 copies of the prior constants used per (s, k)
     float pr_lambda, pr_mu_isd, pr_alpha_mean, pr_alpha_isd, pr_wsm1, pr_wrate;
 };
@@ -178,9 +181,12 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         }
         const uint32_t kl = a.mask ? static_cast<uint32_t>(__popc(mk & ((1u << k) - 1u))) : static_cast<uint32_t>(k);
         float e[8];
+        // shared-shape variant: h takes this sample's noise, the shapes sample 0's
+        const size_t sh_base = a.shared ? (static_cast<size_t>(b) * a.S_sub * a.K + k) * 5 : base;
         if (a.eps_in) {
+            e[0] = a.eps_in[base];
 #pragma unroll
-            for (int j = 0; j < 5; ++j) e[j] = a.eps_in[base + j];
+            for (int j = 1; j < 5; ++j) e[j] = a.eps_in[sh_base + j];
         } else {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -197,6 +203,24 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
                     e[4 * j + 2 * q + 1] = rad * sn;
                 }
             }
+            if (a.shared && s_loc != 0) {
+                const float e0 = e[0];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    uint32_t c[4] = {0u, kl, step, a.tag * 256u + static_cast<uint32_t>(j)};
+                    philox4x32_10(c, a.key0, a.key1);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float r1 = u01(c[2 * q]), r2 = u01(c[2 * q + 1]);
+                        const float rad = sqrtf(-2.0f * logf(r1));
+                        float sn, cs;
+                        sincospif(2.0f * r2, &sn, &cs);
+                        e[4 * j + 2 * q] = rad * cs;
+                        e[4 * j + 2 * q + 1] = rad * sn;
+                    }
+                }
+                e[0] = e0;
+            }
         }
         float u[5], sig[5];
 #pragma unroll
@@ -206,6 +230,7 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
             a.eps[base + j] = e[j];
         }
         const float h = expf(u[0]);
+        if (a.H) a.H[static_cast<size_t>(s) * a.Kpad + k] = h;
         const float mu = u[1];
         const float w = expf(u[2]);
         const float r = sigmoidf(u[3]);
@@ -948,6 +973,7 @@ struct GradArgs {
     int tail_start;
     const double *lq;   // [S] ln q(u_s) (importance-weighted objective)
     double *iw;         // [S] normalised importance weights (null: the ELBO)
+    int Tg;             // tiles per (sample, phase) record of gpart (T, or 1 for the shared-shape variant)
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -1017,11 +1043,11 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         const int nc = s1 - c0 < 32 ? s1 - c0 : 32;
         for (int i = warp; i < nc; i += kWarps) {
             const size_t sk = static_cast<size_t>(c0 + i) * a.K + k;
-            const float2 *gp = reinterpret_cast<const float2 *>(a.gpart + sk * a.T * kGradSums);
+            const float2 *gp = reinterpret_cast<const float2 *>(a.gpart + sk * a.Tg * kGradSums);
             float qf[kGradSums];
 #pragma unroll
             for (int j = 0; j < kGradSums; ++j) qf[j] = 0.f;
-            for (int t = lane; t < a.T; t += 32) {
+            for (int t = lane; t < a.Tg; t += 32) {
 #pragma unroll
                 for (int j = 0; j < kGradSums / 2; ++j) {
                     const float2 v = gp[t * (kGradSums / 2) + j];
@@ -1429,6 +1455,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.counters = W.counters;
     a.tickets = W.tickets;
     a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
+    a.shared = W.shared ? 1 : 0; a.H = W.H; a.Kpad = W.Kpad;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1436,6 +1463,12 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.pr_wsm1 = static_cast<float>(P.prior.w_shape - 1.0);
     a.pr_wrate = static_cast<float>(P.prior.w_rate);
     k_sample<<<W.S, 128, 0, st>>>(a);
+}
+
+void launch_lik(const Problem &P, Workspace &W, float *f_out, int C, cudaStream_t st) {
+    ProfArgs a = prof_args(P, W, f_out);
+    a.C = C;
+    k_lik<<<W.S * P.T, kTile, 0, st>>>(a);
 }
 
 void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st) {
@@ -1481,6 +1514,7 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
     a.tail_sum = W.tail_sum; a.tail_start = W.tail_start;
     a.lq = W.lq; a.iw = W.iw;
+    a.Tg = W.shared ? 1 : P.T;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
     const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;

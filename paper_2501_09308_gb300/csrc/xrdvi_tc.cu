@@ -241,7 +241,83 @@ __global__ void k_splitk_reduce(const float *part, int splits, size_t split_stri
     }
 }
 
+// Phase profiles and derivative profiles of the shared shapes (sample 0's
+// draw), one thread per (phase k = blockIdx.y, point i).  With d = x - p - mu,
+// s = 2 / w_side, t = s d, u = t^2, G = 2^-u, L = 1 / (1 + u), the ten sums
+// over the phase's peaks, in the order of the backward's gradient sums, are
+//   I G, I L, I G t, I L^2 t, I G |t|, I L^2 |t|, I G t^2, I L^2 t^2,
+//   I G t|t|, I L^2 t|t|,
+// and C_k = r sum I L + (1 - r) sum I G.  Beyond the Gaussian's reach
+// (u >= 128) its terms are zero in FP32 and are skipped.
+struct ShapeArgs {
+    int N, Npad, K, Kpad;
+    const float *x, *pos, *inten;
+    const int *off;
+    const PhaseConst *cst;   // sample 0's row [K]
+    const float *theta;      // sample 0's row [K*5]
+    float *D;                // [K*10*Npad]
+    float *Ct;               // [Npad*Kpad]
+};
+
+__global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
+    const int k = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.Npad) return;
+    const PhaseConst c = a.cst[k];
+    const float r = a.theta[k * 5 + 3];
+    float acc[kGradSums];
+#pragma unroll
+    for (int j = 0; j < kGradSums; ++j) acc[j] = 0.f;
+    if (i < a.N) {
+        const float x = a.x[i];
+        for (int m = a.off[k]; m < a.off[k + 1]; ++m) {
+            const float d = (x - __ldg(&a.pos[m])) - c.mu;
+            const float t = (d >= 0.f ? c.sr : c.sl) * d;
+            const float at = fabsf(t), u = t * t;
+            float L;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(L) : "f"(1.f + u));
+            const float I = __ldg(&a.inten[m]);
+            const float IL = I * L, IL2 = IL * L;
+            acc[1] += IL;
+            acc[3] = fmaf(IL2, t, acc[3]);
+            acc[5] = fmaf(IL2, at, acc[5]);
+            acc[7] = fmaf(IL2, u, acc[7]);
+            acc[9] = fmaf(IL2 * t, at, acc[9]);
+            if (u < kGaussU) {
+                float G;
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(-u));
+                const float IG = I * G;
+                acc[0] += IG;
+                acc[2] = fmaf(IG, t, acc[2]);
+                acc[4] = fmaf(IG, at, acc[4]);
+                acc[6] = fmaf(IG, u, acc[6]);
+                acc[8] = fmaf(IG * t, at, acc[8]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kGradSums; ++j) a.D[(static_cast<size_t>(k) * kGradSums + j) * a.Npad + i] = acc[j];
+    a.Ct[static_cast<size_t>(i) * a.Kpad + k] = fmaf(r, acc[1], (1.f - r) * acc[0]);
+}
+
 }  // namespace
+
+void launch_shared_forward(const Problem &P, Workspace &W, float *f_out, cudaStream_t st) {
+    ShapeArgs s;
+    s.N = P.N; s.Npad = P.Npad; s.K = P.K; s.Kpad = W.Kpad;
+    s.x = P.x; s.pos = P.pos; s.inten = P.inten; s.off = P.off;
+    s.cst = W.cst; s.theta = W.theta; s.D = W.D; s.Ct = W.Ct;
+    k_shapes<<<dim3(P.T, P.K), 256, 0, st>>>(s);
+    // f_s - B = sum_k h_sk C_k: [S x N] = H [S x Kpad] . Ct [N x Kpad]^T, into the first chunk slot
+    launch_gemm_nt_tf32x3(W.S, P.N, W.Kpad, W.H, W.Kpad, W.Ct, W.Kpad, W.fpart, P.Npad, 1, nullptr, W.gemm_err, st);
+    launch_lik(P, W, f_out, 1, st);
+}
+
+void launch_shared_backward(const Problem &P, Workspace &W, cudaStream_t st) {
+    // per (s, k) sums: [S x 10K] = g [S x Npad] . D [10K x Npad]^T  (g = 0 on padding)
+    const int nk = P.K * kGradSums;
+    launch_gemm_nt_tf32x3(W.S, nk, P.Npad, W.g, P.Npad, W.D, P.Npad, W.gpart, nk, W.gemm_splits, W.gemm_work,
+                          W.gemm_err, st);
+}
 
 size_t gemm_smem_bytes() { return kStages * kStage + 1024; }
 
@@ -257,14 +333,13 @@ size_t gemm_workspace_floats(int M, int N, int splits) {
     return splits > 1 ? static_cast<size_t>(splits) * M * N : 0;
 }
 
+cudaError_t gemm_configure() {
+    return cudaFuncSetAttribute(k_gemm_nt_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(gemm_smem_bytes()));
+}
+
 void launch_gemm_nt_tf32x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *out,
                            int ldo, int splits, float *work, int *err, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_gemm_nt_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(gemm_smem_bytes()));
-        attr_set = true;
-    }
     GemmArgs a;
     a.M = M; a.N = N; a.K = K; a.A = A; a.B = B; a.lda = lda; a.ldb = ldb; a.err = err;
     a.nkb = (K + kGKB - 1) / kGKB;
@@ -305,7 +380,8 @@ extern "C" xrdvi_status xrdvi_gemm_nt_tf32x3(int32_t M, int32_t N, int32_t K, co
     const int splits = xrdvi::gemm_splits(M, N, K, sms);
     float *work = nullptr;
     int *err = nullptr;
-    cudaError_t e = cudaMallocAsync(&err, sizeof(int), st);
+    cudaError_t e = xrdvi::gemm_configure();
+    if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
     const size_t wf = xrdvi::gemm_workspace_floats(M, N, splits);
     if (e == cudaSuccess && wf) e = cudaMallocAsync(&work, wf * sizeof(float), st);

@@ -123,3 +123,47 @@ def test_iw_bound_between_elbo_and_evidence_in_the_conjugate_case():
     assert abs(lnZ - l_iw) < 0.05
     res = post.posterior(P, loc, raw, S, eps=eps, top_m=1)
     assert P_iw.elbo_grad(loc, raw, eps)["elbo"] == pytest.approx(res["log_evidence"], rel=1e-12)
+
+
+def test_shared_shape_noise_ties_the_shape_columns_to_sample_zero():
+    """The shared-shape estimator is the plain one on noise whose shape
+    columns (mu, w, r, alpha) are sample 0's and whose intensity column is
+    each sample's own; with one sample nothing changes."""
+    inst, P = _problem()
+    P_sh = oracle.Problem.from_instance(inst, shapes="shared")
+    loc, raw = _perturbed(P, 6)
+    eps = synth.normals(11, 5, P.K).astype(np.float64)
+    tied = eps.copy()
+    tied[1:, :, 1:] = eps[0, :, 1:]
+    a, b = P_sh.elbo_grad(loc, raw, eps), P.elbo_grad(loc, raw, tied)
+    assert a["elbo"] == b["elbo"]
+    np.testing.assert_array_equal(a["grad"], b["grad"])
+    one = eps[:1]
+    assert P_sh.elbo_grad(loc, raw, one)["elbo"] == P.elbo_grad(loc, raw, one)["elbo"]
+
+
+def test_shared_shape_estimator_is_unbiased():
+    """Averaged over independent noise, the shared-shape estimate of the
+    ELBO and of its gradient agrees with the plain estimator's average (both
+    estimate the same expectation) within four standard errors."""
+    inst, P = _problem()
+    P_sh = oracle.Problem.from_instance(inst, shapes="shared")
+    loc, raw = _perturbed(P, 7)
+    rng = np.random.default_rng(13)
+    R, S = 300, 4
+    vals = {"plain": [], "shared": []}
+    grads = {"plain": [], "shared": []}
+    for _ in range(R):
+        eps = rng.standard_normal((S, P.K, 5))
+        for name, Q in (("plain", P), ("shared", P_sh)):
+            r = Q.elbo_grad(loc, raw, eps)
+            vals[name].append(r["elbo"])
+            grads[name].append(r["grad"])
+    for name in ("plain", "shared"):
+        vals[name] = np.array(vals[name])
+        grads[name] = np.array(grads[name])
+    se = math.sqrt(np.var(vals["plain"]) / R + np.var(vals["shared"]) / R)
+    assert abs(vals["plain"].mean() - vals["shared"].mean()) <= 4 * se
+    gse = np.sqrt(np.var(grads["plain"], axis=0) / R + np.var(grads["shared"], axis=0) / R)
+    z = np.abs(grads["plain"].mean(axis=0) - grads["shared"].mean(axis=0)) / np.maximum(gse, 1e-300)
+    assert np.mean(z <= 4) >= 0.97, np.sort(z.ravel())[-5:]
