@@ -275,9 +275,10 @@ def enumeration_leg(iters=3000):
 
 
 def variants_leg(peaks, steps=32):
-    """Estimator variants on the K=50 workload: per-kernel CUDA-event times of
-    `steps` SVI steps with the Gaussian likelihood, the importance-weighted
-    objective and the shared-shape estimator; for the last also the whole fit
+    """Estimator and model variants on the K=50 workload: per-kernel CUDA-event
+    times of `steps` SVI steps with the Gaussian likelihood, the
+    importance-weighted objective, the angle-dependent width and the
+    shared-shape estimator; for the last also the whole fit
     + posterior (time-to-posterior, CUDA events) and the roofline of its
     backward contraction on the tensor cores."""
     import numpy as np
@@ -286,7 +287,7 @@ def variants_leg(peaks, steps=32):
     inst = synth.config(1)
     out = {}
     for name, flags in (("gauss_lik", xrdvi.FLAG_GAUSS_LIK), ("iw_elbo", xrdvi.FLAG_IW_ELBO),
-                        ("shared_shapes", xrdvi.FLAG_SHARED_SHAPES)):
+                        ("sec_width", xrdvi.FLAG_SEC_WIDTH), ("shared_shapes", xrdvi.FLAG_SHARED_SHAPES)):
         c = xrdvi.Context.from_instance(inst, S=inst.S, flags=flags)
         c.fit(16, trace=False)
         k = c.profile_steps(steps)

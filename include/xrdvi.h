@@ -99,6 +99,11 @@ typedef struct {
  * tensor cores (xrdvi_gemm_nt_tf32x3).  Not with sub-model batches or the
  * static entry. */
 #define XRDVI_FLAG_SHARED_SHAPES (1u << 4)
+/* Angle-dependent width (model variant; the paper names a sec term in App.
+ * A.2 without a formula): every side width at point x is multiplied by
+ * sec(theta) with theta = x/2 (x the 2-theta of the point in degrees), so the
+ * peaks broaden towards high angles.  Needs every x below 174 degrees. */
+#define XRDVI_FLAG_SEC_WIDTH  (1u << 5)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */

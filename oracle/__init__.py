@@ -48,6 +48,11 @@ class Prior(ctypes.Structure):
                 ("alpha_min", ctypes.c_double)]
 
 
+class Variant(ctypes.Structure):
+    """orc_variant: likelihood, objective, shared shapes, angle-dependent width."""
+    _fields_ = [("lik", ctypes.c_int), ("iw", ctypes.c_int), ("shared", ctypes.c_int), ("sec", ctypes.c_int)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (no fast-math, no FMA
     contraction, so x86 and Arm builds round alike)."""
@@ -95,10 +100,13 @@ def lib():
             L.orc_entropy.argtypes = [i32, pd]
             L.orc_elbo_grad.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32,
                                         pd, pd, pd, pd, pd, pd, pd, pd]
-            L.orc_elbo_grad_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32,
+            L.orc_elbo_grad_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), P(Variant), i32,
                                            pd, pd, pd, pd, pd, pd, pd, pd]
-            L.orc_fit_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, i32, i32, i32, u64, i32, i32,
+            L.orc_fit_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), P(Variant), i32, u64, i32, i32,
                                      d, d, d, d, pd, pd, pd, pd, pd]
+            L.orc_profile_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, i32, pd, d, i32, pd]
+            L.orc_sec.restype = d
+            L.orc_sec.argtypes = [d]
             L.orc_tie_shapes.argtypes = [i32, i32, pd]
             L.orc_loglik_gauss.restype = d
             L.orc_loglik_gauss.argtypes = [i32, pd, pd]
@@ -130,15 +138,18 @@ class Problem:
     def __init__(self, offsets, pos, inten, x, y, bg, *, lam=None,
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
                  w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
-                 likelihood="poisson", objective="elbo", shapes="independent"):
+                 likelihood="poisson", objective="elbo", shapes="independent", width="constant"):
         # variants: likelihood "poisson" (the paper's) or "gauss" (variance
         # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound);
-        # shapes "independent" or "shared" (one shape draw per step)
+        # shapes "independent" or "shared" (one shape draw per step); width
+        # "constant" or "sec" (side widths times sec(2theta / 2) at each point)
         assert likelihood in ("poisson", "gauss") and objective in ("elbo", "iw")
-        assert shapes in ("independent", "shared")
+        assert shapes in ("independent", "shared") and width in ("constant", "sec")
         self.lik = 1 if likelihood == "gauss" else 0
         self.iw = 1 if objective == "iw" else 0
         self.shared = 1 if shapes == "shared" else 0
+        self.sec = 1 if width == "sec" else 0
+        self.variant = Variant(self.lik, self.iw, self.shared, self.sec)
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -166,8 +177,8 @@ class Problem:
         theta = f64(theta)
         S = theta.shape[0]
         f = np.zeros((S, self.N))
-        lib().orc_profile(self.K, _pi(self.off), _pd(self.pos), _pd(self.inten), self.N,
-                          _pd(self.x), _pd(self.bg), S, _pd(theta), self.prior.alpha_min, _pd(f))
+        lib().orc_profile_ex(self.K, _pi(self.off), _pd(self.pos), _pd(self.inten), self.N,
+                             _pd(self.x), _pd(self.bg), S, _pd(theta), self.prior.alpha_min, self.sec, _pd(f))
         return f
 
     def loglik(self, f, form="direct"):
@@ -207,7 +218,7 @@ class Problem:
         lpj = np.zeros(S)
         grad = np.zeros((self.K, 10))
         f = np.zeros((S, self.N)) if want_f else None
-        lib().orc_elbo_grad_ex(*self._args(), ctypes.byref(self.prior), self.lik, self.iw, S, _pd(f64(loc)),
+        lib().orc_elbo_grad_ex(*self._args(), ctypes.byref(self.prior), ctypes.byref(self.variant), S, _pd(f64(loc)),
                                _pd(f64(raw)), _pd(eps), ctypes.byref(elbo), _pd(ll), _pd(lpj),
                                _pd(grad), _pd(f) if want_f else None)
         out = {"elbo": elbo.value, "ll": ll, "lpj": lpj, "grad": grad}
@@ -235,8 +246,7 @@ class Problem:
         m = np.zeros((self.K, 10)) if m is None else f64(m).copy()
         v = np.zeros((self.K, 10)) if v is None else f64(v).copy()
         trace = np.zeros(iters)
-        lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), self.lik, self.iw, self.shared, S, seed, t0,
-                         iters,
+        lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), ctypes.byref(self.variant), S, seed, t0, iters,
                          lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
         return {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
 

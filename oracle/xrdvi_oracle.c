@@ -141,6 +141,10 @@ void orc_components(double d, double w, double alpha_c, double *G, double *L)
     *L = 1.0 / (1.0 + 4.0 * t * t);
 }
 
+/* Width factor of the angle-dependent variant at 2-theta x (degrees):
+ * sec(theta) with theta = x / 2, i.e. 1 / cos(x pi / 360). */
+double orc_sec(double x) { return 1.0 / cos(x * ORC_PI / 360.0); }
+
 /* Pseudo-Voigt V = (1 - r) G + r L (Appendix A.2, profile of one peak). */
 double orc_pvoigt(double d, double w, double r, double alpha_c)
 {
@@ -156,9 +160,9 @@ double orc_pvoigt(double d, double w, double r, double alpha_c)
  * [S][K][5]; f is [S][N].  alpha is clamped below at alpha_min (Reading: the
  * normal q and prior on alpha admit alpha <= 0, where the profile is undefined).
  */
-void orc_profile(int K, const int *off, const double *pos, const double *inten,
-                 int N, const double *x, const double *bg,
-                 int S, const double *theta, double alpha_min, double *f)
+void orc_profile_ex(int K, const int *off, const double *pos, const double *inten,
+                    int N, const double *x, const double *bg,
+                    int S, const double *theta, double alpha_min, int sec, double *f)
 {
 #pragma omp parallel for schedule(dynamic)
     for (int s = 0; s < S; ++s) {
@@ -168,16 +172,23 @@ void orc_profile(int K, const int *off, const double *pos, const double *inten,
                 const double *th = theta + ((size_t)s * K + k) * 5;
                 double h = th[0], mu = th[1], w = th[2], r = th[3];
                 double ac = th[4] > alpha_min ? th[4] : alpha_min;
-                double C = 0.0;
+                double C = 0.0, wx = sec ? w * orc_sec(x[i]) : w;
                 for (int m = off[k]; m < off[k + 1]; ++m) {
                     double d = x[i] - (pos[m] + mu);
-                    C += inten[m] * orc_pvoigt(d, w, r, ac);
+                    C += inten[m] * orc_pvoigt(d, wx, r, ac);
                 }
                 acc += h * C;
             }
             f[(size_t)s * N + i] = acc;
         }
     }
+}
+
+void orc_profile(int K, const int *off, const double *pos, const double *inten,
+                 int N, const double *x, const double *bg,
+                 int S, const double *theta, double alpha_min, double *f)
+{
+    orc_profile_ex(K, off, pos, inten, N, x, bg, S, theta, alpha_min, 0, f);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -245,6 +256,18 @@ typedef struct {
     double w_rate;
     double alpha_min;   /* profile clamp on alpha                               */
 } orc_prior;
+
+/*
+ * Model and estimator variants (none is the paper's model; all zero gives it):
+ *   lik     0 Poisson, 1 Gaussian with variance max(y, 1)   (orc_loglik_gauss)
+ *   iw      0 ELBO, 1 importance-weighted bound              (orc_iw_weights)
+ *   shared  1: one shape draw per step for all samples       (orc_tie_shapes)
+ *   sec     1: angle-dependent width, every side width at point x multiplied
+ *           by sec(theta), theta = x / 2 (x = 2-theta in degrees)   (orc_sec)
+ */
+typedef struct {
+    int lik, iw, shared, sec;
+} orc_variant;
 
 /* ln p(theta) for one phase: Exp(lambda) on h, normal on mu and alpha,
    Uni(0,1) on r (log density 0), gamma on w. */
@@ -340,17 +363,21 @@ double orc_iw_weights(int K, int S, const double *raw, const double *eps, const 
  * Outputs: elbo; ll[S], lpj[S] (log prior + log Jacobian) if non-NULL;
  * grad[K*10] if non-NULL; f[S*N] if non-NULL.
  *
- * orc_elbo_grad_ex also takes the likelihood (lik: 0 Poisson, 1 the Gaussian
- * variant, whose g_i = (y_i - f_i)/v_i replaces y_i/f_i - 1) and the
- * objective (iw: 0 this ELBO, 1 the importance-weighted bound, whose weights
- * replace the 1/S of the sample means); `elbo` then receives that objective.
+ * orc_elbo_grad_ex also takes the variants (orc_variant; NULL = none): the
+ * likelihood (lik: the Gaussian's g_i = (y_i - f_i)/v_i replaces
+ * y_i/f_i - 1), the objective (iw: the importance weights replace the 1/S of
+ * the sample means; `elbo` then receives that objective) and the
+ * angle-dependent width (sec: every side width at point x_i is multiplied by
+ * sec(x_i / 2), so t = d / side keeps its form and so do dt/dw = -t/w and
+ * dt/dalpha = -t/alpha, while dt/dmu = -1/side carries the factor).
  */
 void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *inten,
                       int N, const double *x, const double *y, const double *bg,
-                      const orc_prior *pr, int lik, int iw, int S, const double *loc, const double *raw,
+                      const orc_prior *pr, const orc_variant *var, int S, const double *loc, const double *raw,
                       const double *eps, double *elbo, double *ll, double *lpj,
                       double *grad, double *f_out)
 {
+    const int lik = var ? var->lik : 0, iw = var ? var->iw : 0, sec = var ? var->sec : 0;
     size_t SK5 = (size_t)S * K * 5;
     double *u = (double *)malloc(SK5 * sizeof(double));
     double *th = (double *)malloc(SK5 * sizeof(double));
@@ -372,8 +399,9 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 const double *t = ths + k * 5;
                 double ac = t[4] > pr->alpha_min ? t[4] : pr->alpha_min;
                 double C = 0.0;
+                double wx = sec ? t[2] * orc_sec(x[i]) : t[2];   /* width at this point */
                 for (int m = off[k]; m < off[k + 1]; ++m)
-                    C += inten[m] * orc_pvoigt(x[i] - (pos[m] + t[1]), t[2], t[3], ac);
+                    C += inten[m] * orc_pvoigt(x[i] - (pos[m] + t[1]), wx, t[3], ac);
                 acc += t[0] * C;
             }
             f[i] = acc;
@@ -395,7 +423,7 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 double C = 0, Cmu = 0, Cw = 0, Cr = 0, Cal = 0;
                 for (int m = off[k]; m < off[k + 1]; ++m) {
                     double d = x[i] - (pos[m] + mu);
-                    double side = d >= 0.0 ? ac * w : w;
+                    double side = (d >= 0.0 ? ac * w : w) * (sec ? orc_sec(x[i]) : 1.0);
                     double tt = d / side;
                     double Gc = exp(-4.0 * ORC_LN2 * tt * tt);
                     double Lc = 1.0 / (1.0 + 4.0 * tt * tt);
@@ -464,7 +492,7 @@ void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten
                    const double *eps, double *elbo, double *ll, double *lpj,
                    double *grad, double *f_out)
 {
-    orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, S, loc, raw, eps, elbo, ll, lpj, grad, f_out);
+    orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, NULL, S, loc, raw, eps, elbo, ll, lpj, grad, f_out);
 }
 
 /*
@@ -508,12 +536,12 @@ void orc_adam_step(int n, double *params, const double *grad, double *m, double 
  * are updated in place; m, v ([K*10], layout as grad) carry the Adam moments;
  * t0 is the number of steps already taken.  trace[iters] receives the ELBO
  * estimate of each step (evaluated before that step's update).  orc_fit_ex
- * takes lik and iw as orc_elbo_grad_ex does (trace then holds that objective)
- * and, with shared != 0, the shared-shape noise of orc_tie_shapes.
+ * takes the variants as orc_elbo_grad_ex does (trace then holds that
+ * objective; shared: the noise of orc_tie_shapes).
  */
 void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
                 int N, const double *x, const double *y, const double *bg,
-                const orc_prior *pr, int lik, int iw, int shared, int S, uint64_t seed, int t0, int iters,
+                const orc_prior *pr, const orc_variant *var, int S, uint64_t seed, int t0, int iters,
                 double lr, double b1, double b2, double adam_eps,
                 double *loc, double *raw, double *m, double *v, double *trace)
 {
@@ -522,10 +550,9 @@ void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
     double *par = (double *)malloc((size_t)K * 10 * sizeof(double));
     for (int t = 0; t < iters; ++t) {
         orc_normals(seed, 0u, (uint32_t)(t0 + t), S, K, eps);
-        if (shared) orc_tie_shapes(S, K, eps);
+        if (var && var->shared) orc_tie_shapes(S, K, eps);
         double elbo;
-        orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, lik, iw, S, loc, raw, eps, &elbo, NULL, NULL, grad,
-                         NULL);
+        orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, var, S, loc, raw, eps, &elbo, NULL, NULL, grad, NULL);
         if (trace) trace[t] = elbo;
         for (int k = 0; k < K; ++k)
             for (int j = 0; j < 5; ++j) {
@@ -548,7 +575,7 @@ void orc_fit(int K, const int *off, const double *pos, const double *inten,
              double lr, double b1, double b2, double adam_eps,
              double *loc, double *raw, double *m, double *v, double *trace)
 {
-    orc_fit_ex(K, off, pos, inten, N, x, y, bg, pr, 0, 0, 0, S, seed, t0, iters, lr, b1, b2, adam_eps,
+    orc_fit_ex(K, off, pos, inten, N, x, y, bg, pr, NULL, S, seed, t0, iters, lr, b1, b2, adam_eps,
                loc, raw, m, v, trace);
 }
 

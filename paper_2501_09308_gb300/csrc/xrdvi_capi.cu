@@ -372,6 +372,20 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         if (y > 0) csum += y * std::log(y) - y - std::lgamma(y + 1.0);
     }
     if (!(eta > 0.0)) return fail(XRDVI_EINVAL, "max(Y - B) must be positive (it sets the intensity prior)");
+    const bool sec = (cfg->flags & XRDVI_FLAG_SEC_WIDTH) != 0;
+    std::vector<float> csec;
+    float sec_max = 1.f;
+    if (sec) {   // angle-dependent width: cos(x/2) per point, x in degrees of 2-theta
+        csec.resize(N);
+        double mx = 1.0;
+        for (int i = 0; i < N; ++i) {
+            if (!(pt->x_deg[i] < 174.f)) return fail(XRDVI_EINVAL, "angle-dependent width needs every x < 174 deg");
+            const double cv = std::cos(static_cast<double>(pt->x_deg[i]) * M_PI / 360.0);
+            csec[i] = static_cast<float>(cv);
+            mx = std::max(mx, 1.0 / cv);
+        }
+        sec_max = static_cast<float>(mx * (1.0 + 1e-6));   // reach bound, rounded up
+    }
     const bool gauss = (cfg->flags & XRDVI_FLAG_GAUSS_LIK) != 0;
     if (gauss) {   // Gaussian variant: the data part is -ln(2 pi v_i)/2, v_i = max(y_i, 1)
         csum = 0.0;
@@ -410,6 +424,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     P.Npad = P.T * kTile;
     P.csum = csum;
     P.gauss = gauss;
+    P.sec = sec;
+    P.sec_max = sec_max;
     P.prior.lambda = 1.0 / eta;
     P.prior.mu_sd = cfg->prior_mu_sd;
     P.prior.alpha_mean = cfg->prior_alpha_mean;
@@ -433,6 +449,7 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     XR_C(c->alloc(&P.y, N));
     XR_C(c->alloc(&P.bg, N));
     XR_C(c->alloc(&P.isum, K));
+    if (sec) XR_C(c->alloc(&P.csec, N));
     configure_grids(P, sms);
     c->host_off.assign(pk->offsets, pk->offsets + K + 1);
     c->W.B = nsub;
@@ -486,7 +503,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     auto up = [&](void *dst, const void *src, size_t n) { return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s); };
     if (up(P.pos, pos.data(), M * 4) || up(P.inten, inten.data(), M * 4) ||
         up(P.off, pk->offsets, (K + 1) * 4) || up(P.x, pt->x_deg, N * 4) || up(P.y, pt->y_counts, N * 4) ||
-        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) || up(c->loc, loc.data(), KB * 20) ||
+        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) || (sec && up(P.csec, csec.data(), N * 4)) ||
+        up(c->loc, loc.data(), KB * 20) ||
         up(c->raw, raw.data(), KB * 20) || cudaMemsetAsync(c->m, 0, KB * 40, s) ||
         cudaMemsetAsync(c->v, 0, KB * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
         cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s) ||

@@ -146,6 +146,7 @@ struct SampleArgs {
     int *tickets;   // [B*K] arrival tickets of k_grad, zeroed here
     int B, S_sub;
     const uint32_t *mask;  // [B] phases kept by each sub-model (null: all)
+    float reach_scale;     // Gaussian reach factor: max sec(x/2) of the pattern (angle-dependent width), else 1
     int shared;            // shape noise of every sample = sample 0's (shared-shape variant)
     float *H;              // [S*Kpad] h_sk for the forward GEMM (shared-shape variant)
     int Kpad;
@@ -247,8 +248,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         pc.mu = mu;
         pc.hl = h * r;
         pc.hg = h * (1.0f - r);
-        pc.rl = 0.5f * sq * wl;
-        pc.rr = 0.5f * sq * wr;
+        pc.rl = 0.5f * sq * wl * a.reach_scale;
+        pc.rr = 0.5f * sq * wr * a.reach_scale;
         pc.sl = sl;
         pc.sr = sr;
         pc.nslmu = -sl * mu;
@@ -332,6 +333,7 @@ struct ProfArgs {
     float *fpart;      // [C*S*Npad] partial profiles per phase chunk
     int *counter;      // work counter of this kernel (zeroed by k_sample)
     int gauss;         // Gaussian likelihood variant
+    const float *csec; // [N] cos(x/2) of the angle-dependent width variant (null: constant width)
 };
 
 typedef unsigned long long f2_t;   // two packed floats
@@ -529,6 +531,29 @@ __device__ __forceinline__ void item_points(const ProfArgs &a, int i0, int lane,
     }
 }
 
+// Per-point width factor of the angle-dependent variant: the side width at
+// point x is w_side sec(x/2), so t = s d cos(x/2); the mu-gradient sums carry
+// one more factor cos(x/2) (dt/dmu = -s cos(x/2)), the other sums none.
+// PtScale<false> is the constant-width model and costs nothing.
+template <bool kSec>
+struct PtScale {
+    __device__ __forceinline__ void load(const ProfArgs &, int, int) {}
+    __device__ __forceinline__ f2_t operator()(f2_t t, int) const { return t; }
+};
+template <>
+struct PtScale<true> {
+    f2_t c[kPairs];
+    __device__ __forceinline__ void load(const ProfArgs &a, int i0, int lane) {
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const int i_a = min(i0 + (2 * q) * 32 + lane, a.N - 1);
+            const int i_b = min(i0 + (2 * q + 1) * 32 + lane, a.N - 1);
+            c[q] = pk2(a.csec[i_a], a.csec[i_b]);
+        }
+    }
+    __device__ __forceinline__ f2_t operator()(f2_t t, int q) const { return mul2(t, c[q]); }
+};
+
 __device__ __forceinline__ int next_item(int *counter, int lane) {
     int it = 0;
     if (lane == 0) it = atomicAdd(counter, 1);
@@ -560,9 +585,9 @@ __device__ __forceinline__ void acc_points(float (&fs)[kPts], float (&fc)[kPts],
 // Lorentzian sums on a side-uniform range, one reciprocal per two peaks:
 // I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1)  (d = 1 + t^2; d0 d1 stays finite
 // while s |d| < 1e9).
-template <class Tab>
+template <class Tab, class Sc>
 __device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
-                                             const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs]) {
+                                             const f2_t (&x2)[kPairs], const Sc &ps, f2_t (&sl)[kPairs]) {
     const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
     int m = m0;
     for (; m + 1 < m1; m += 2) {
@@ -571,8 +596,8 @@ __device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, flo
         tab.get(m + 1, np1, I1);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t0 = fma2(s2, add2(x2[q], np0), c2);
-            const f2_t t1 = fma2(s2, add2(x2[q], np1), c2);
+            const f2_t t0 = ps(fma2(s2, add2(x2[q], np0), c2), q);
+            const f2_t t1 = ps(fma2(s2, add2(x2[q], np1), c2), q);
             const f2_t d0 = fma2(t0, t0, one2), d1 = fma2(t1, t1, one2);
             const f2_t num = fma2(I0, d1, mul2(I1, d0));
             sl[q] = fma2(num, rcp2(mul2(d0, d1)), sl[q]);
@@ -583,7 +608,7 @@ __device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, flo
         tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
             sl[q] = fma2(I, rcp2(fma2(t, t, one2)), sl[q]);
         }
     }
@@ -592,16 +617,17 @@ __device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, flo
 // Near part of one phase's profile on the tile: the mixed range (both
 // components, side chosen per point) and the Gaussian on the side-uniform
 // ranges within its reach.
-template <class Tab>
+template <class Tab, class Sc>
 __device__ __forceinline__ void fwd_near(const Tab &tab, const Ranges &r, const PhaseConst &cp,
-                                         const f2_t (&x2)[kPairs], f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
+                                         const f2_t (&x2)[kPairs], const Sc &ps, f2_t (&sl)[kPairs],
+                                         f2_t (&sg)[kPairs]) {
     const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
     for (int m = r.m1; m < r.m2; ++m) {
         f2_t np, I;
         tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = t_mixed(x2[q], np, nmu2, cp.sl, cp.sr);
+            const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
             const f2_t u = mul2(t, t);
             sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
             sg[q] = fma2(I, ex2neg2(u), sg[q]);
@@ -616,7 +642,7 @@ __device__ __forceinline__ void fwd_near(const Tab &tab, const Ranges &r, const 
             tab.get(m, np, I);
 #pragma unroll
             for (int q = 0; q < kPairs; ++q) {
-                const f2_t t = fma2(s2, add2(x2[q], np), c2);
+                const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
                 sg[q] = fma2(I, ex2neg2(mul2(t, t)), sg[q]);
             }
         }
@@ -625,7 +651,7 @@ __device__ __forceinline__ void fwd_near(const Tab &tab, const Ranges &r, const 
 
 // Partial profile of one phase chunk: fpart[c][s][i] = sum over the chunk's
 // phases of h sum_m I_m [(1 - r) G + r L] (Neumaier-compensated over phases).
-template <bool kNaive, bool kWide>
+template <bool kNaive, bool kWide, bool kSec = false>
 __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
     extern __shared__ float4 s_raw[];
     int *s_off;
@@ -639,6 +665,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
         const int i0 = tile * kTile;
         f2_t x2[kPairs];
         item_points(a, i0, lane, x2);
+        PtScale<kSec> ps;
+        ps.load(a, i0, lane);
         float fs[kPts], fc[kPts];
 #pragma unroll
         for (int j = 0; j < kPts; ++j) fs[j] = fc[j] = 0.f;
@@ -652,9 +680,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
 #pragma unroll 1
             for (int side = 0; side < 2; ++side) {
                 fwdL_uniform(tab, side ? r.m2 : r.mb, side ? r.me : r.m1, side ? cp.sl : cp.sr,
-                             side ? cp.nslmu : cp.nsrmu, x2, sl);
+                             side ? cp.nslmu : cp.nsrmu, x2, ps, sl);
             }
-            if (near_work(r)) fwd_near(tab, r, cp, x2, sl, sg);  // warp-uniform
+            if (near_work(r)) fwd_near(tab, r, cp, x2, ps, sl, sg);  // warp-uniform
             const f2_t hl2 = bc2(cp.hl), hg2 = bc2(cp.hg);
 #pragma unroll
             for (int q = 0; q < kPairs; ++q) sl[q] = fma2(hl2, sl[q], mul2(hg2, sg[q]));
@@ -738,9 +766,9 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
 // range's sum q L^2 t^2 is S1 - C2 and needs no product of its own.  The
 // sums over the range's peaks are taken per point without the point's factor
 // g = y/f - 1, which multiplies them once at the end (q = g I).
-template <class Tab>
+template <class Tab, class Sc>
 __device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
-                                             const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs],
+                                             const f2_t (&x2)[kPairs], const Sc &ps, const f2_t (&g2)[kPairs],
                                              f2_t &S1, f2_t &A, f2_t &C2) {
     const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
     f2_t S1p[kPairs], Ap[kPairs], C2p[kPairs];
@@ -751,7 +779,7 @@ __device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, flo
         tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
             const f2_t L = rcp2(fma2(t, t, one2));
             const f2_t q1 = mul2(I, L);
             S1p[q] = add2(S1p[q], q1);
@@ -763,12 +791,12 @@ __device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, flo
 #pragma unroll
     for (int q = 0; q < kPairs; ++q) {
         S1 = fma2(g2[q], S1p[q], S1);
-        A = fma2(g2[q], Ap[q], A);
+        A = fma2(ps(g2[q], q), Ap[q], A);   // mu sums: g cos(x/2) in the angle-dependent variant
         C2 = fma2(g2[q], C2p[q], C2);
     }
 }
 
-template <bool kWide>
+template <bool kWide, bool kSec = false>
 __global__ void __launch_bounds__(kThreads, 4) k_bwd_uniform(ProfArgs a) {
     extern __shared__ float4 s_raw[];
     int *s_off;
@@ -782,6 +810,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_uniform(ProfArgs a) {
         const int i0 = tile * kTile;
         f2_t x2[kPairs], g2[kPairs];
         item_points(a, i0, lane, x2);
+        PtScale<kSec> ps;
+        ps.load(a, i0, lane);
         const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
@@ -794,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bwd_uniform(ProfArgs a) {
             for (int side = 0; side < 2; ++side) {
                 f2_t S1s = 0ull, As = 0ull, C2s = 0ull;
                 bwdL_uniform(tab, side ? r.m2 : r.mb, side ? r.me : r.m1, side ? cp.sl : cp.sr,
-                             side ? cp.nslmu : cp.nsrmu, x2, g2, S1s, As, C2s);
+                             side ? cp.nslmu : cp.nsrmu, x2, ps, g2, S1s, As, C2s);
                 S1 = add2(S1, S1s);
                 const f2_t Bs = sub2(S1s, C2s);
                 if (side) { A[1] = As; B[1] = Bs; } else { A[0] = As; B[0] = Bs; }
@@ -828,7 +858,7 @@ __device__ __forceinline__ f2_t fma_abs2(f2_t v, f2_t t, f2_t acc) {
 // the side-uniform ranges), added to the sums k_bwd_uniform wrote.  The
 // ranges of 32 phases are loaded at once, one per lane, and only the phases
 // with near work on this tile (a warp ballot) are visited.
-template <bool kWide>
+template <bool kWide, bool kSec = false>
 __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
     extern __shared__ float4 s_raw[];
     int *s_off;
@@ -841,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
         const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
         f2_t x2[kPairs], g2[kPairs];
+        PtScale<kSec> ps;
         bool loaded = false;
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
         const int kend = a.chunk[c + 1];
@@ -855,6 +886,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
             unsigned mask = __ballot_sync(0xffffffffu, work);
             if (mask && !loaded) {
                 item_points(a, i0, lane, x2);
+                ps.load(a, i0, lane);
                 const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
 #pragma unroll
                 for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
@@ -881,23 +913,24 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
                     tab.get(m, np, I);
 #pragma unroll
                     for (int q = 0; q < kPairs; ++q) {
-                        const f2_t t = t_mixed(x2[q], np, nmu2, cp.sl, cp.sr);
+                        const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
+                        const f2_t tA = ps(t, q);   // t for the mu sums (times cos(x/2) once more)
                         const f2_t u = mul2(t, t);
                         const f2_t L = rcp2(add2(u, one2));
                         const f2_t gI = mul2(g2[q], I);
                         const f2_t q1 = mul2(gI, L);
                         acc[1] = add2(acc[1], q1);
                         const f2_t q2 = mul2(q1, L);
-                        acc[3] = fma2(q2, t, acc[3]);
-                        acc[5] = fma_abs2(q2, t, acc[5]);
+                        acc[3] = fma2(q2, tA, acc[3]);
+                        acc[5] = fma_abs2(q2, tA, acc[5]);
                         const f2_t q3 = mul2(q2, t);
                         acc[7] = fma2(q3, t, acc[7]);
                         acc[9] = fma_abs2(q3, t, acc[9]);
                         if (any_gauss(u)) {
                             const f2_t qg = mul2(gI, ex2neg2(u));
                             acc[0] = add2(acc[0], qg);
-                            acc[2] = fma2(qg, t, acc[2]);
-                            acc[4] = fma_abs2(qg, t, acc[4]);
+                            acc[2] = fma2(qg, tA, acc[2]);
+                            acc[4] = fma_abs2(qg, tA, acc[4]);
                             const f2_t q3g = mul2(qg, t);
                             acc[6] = fma2(q3g, t, acc[6]);
                             acc[8] = fma_abs2(q3g, t, acc[8]);
@@ -914,12 +947,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
                         tab.get(m, np, I);
 #pragma unroll
                         for (int q = 0; q < kPairs; ++q) {
-                            const f2_t t = fma2(s2, add2(x2[q], np), c2);
+                            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
                             const f2_t u = mul2(t, t);
                             if (any_gauss(u)) {
                                 const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(u));
                                 S1 = add2(S1, qg);
-                                A = fma2(qg, t, A);
+                                A = fma2(qg, ps(t, q), A);
                                 B = fma2(mul2(qg, t), t, B);
                             }
                         }
@@ -1389,6 +1422,11 @@ void configure_grids(Problem &P, int sm_count) {
     set_smem_attr(k_bwd_uniform<true>, smax);
     set_smem_attr(k_bwd_near<false>, smax);
     set_smem_attr(k_bwd_near<true>, smax);
+    set_smem_attr(k_forward<false, false, true>, smax);
+    set_smem_attr(k_bwd_uniform<false, true>, smax);
+    set_smem_attr(k_bwd_uniform<true, true>, smax);
+    set_smem_attr(k_bwd_near<false, true>, smax);
+    set_smem_attr(k_bwd_near<true, true>, smax);
     int bf = 1, bb = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward<false, false>, kThreads, P.smem_fwd);
     if (P.wide)
@@ -1410,6 +1448,7 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     a.cst = W.cst; a.ranges = W.ranges; a.g = W.g; a.f_out = f_out; a.llpart = W.llpart; a.gpart = W.gpart;
     a.fpart = W.fpart; a.counter = W.counters;
     a.gauss = P.gauss ? 1 : 0;
+    a.csec = P.csec;
     return a;
 }
 
@@ -1456,6 +1495,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.tickets = W.tickets;
     a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
     a.shared = W.shared ? 1 : 0; a.H = W.H; a.Kpad = W.Kpad;
+    a.reach_scale = P.sec ? P.sec_max : 1.0f;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1477,7 +1517,9 @@ void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cu
     k_ranges<<<(nr + 255) / 256 < 4096 ? (nr + 255) / 256 : 4096, 256, 0, st>>>(a);
     // the forward reads the compact table (measured faster than the wide one)
     const int grid = grid_for(P.grid_fwd, W.S * P.T * W.C);
-    if (naive)
+    if (P.sec)   // angle-dependent width (compensated sums)
+        k_forward<false, false, true><<<grid, kThreads, P.smem_fwd, st>>>(a);
+    else if (naive)
         k_forward<true, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
     else
         k_forward<false, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
@@ -1488,6 +1530,18 @@ void launch_backward(const Problem &P, Workspace &W, cudaStream_t st) {
     ProfArgs a = prof_args(P, W, nullptr);
     const int grid = grid_for(P.grid_bwd, W.S * P.T * W.C);
     a.counter = W.counters + 2;
+    if (P.sec) {   // angle-dependent width
+        if (P.wide)
+            k_bwd_uniform<true, true><<<grid, kThreads, P.smem, st>>>(a);
+        else
+            k_bwd_uniform<false, true><<<grid, kThreads, P.smem, st>>>(a);
+        a.counter = W.counters + 3;
+        if (P.wide)
+            k_bwd_near<true, true><<<grid, kThreads, P.smem, st>>>(a);
+        else
+            k_bwd_near<false, true><<<grid, kThreads, P.smem, st>>>(a);
+        return;
+    }
     if (P.wide)
         k_bwd_uniform<true><<<grid, kThreads, P.smem, st>>>(a);
     else

@@ -253,6 +253,7 @@ struct ShapeArgs {
     int N, Npad, K, Kpad;
     const float *x, *pos, *inten;
     const int *off;
+    const float *csec;       // [N] cos(x/2) of the angle-dependent width (null: constant width)
     const PhaseConst *cst;   // sample 0's row [K]
     const float *theta;      // sample 0's row [K*5]
     float *D;                // [K*10*Npad]
@@ -269,9 +270,10 @@ __global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
     for (int j = 0; j < kGradSums; ++j) acc[j] = 0.f;
     if (i < a.N) {
         const float x = a.x[i];
+        const float cx = a.csec ? a.csec[i] : 1.f;   // t = s cos(x/2) d; mu sums take cos(x/2) once more
         for (int m = a.off[k]; m < a.off[k + 1]; ++m) {
             const float d = (x - __ldg(&a.pos[m])) - c.mu;
-            const float t = (d >= 0.f ? c.sr : c.sl) * d;
+            const float t = (d >= 0.f ? c.sr : c.sl) * d * cx;
             const float at = fabsf(t), u = t * t;
             float L;
             asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(L) : "f"(1.f + u));
@@ -294,6 +296,10 @@ __global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
             }
         }
     }
+    if (a.csec && i < a.N) {
+        const float cx = a.csec[i];
+        acc[2] *= cx; acc[3] *= cx; acc[4] *= cx; acc[5] *= cx;
+    }
 #pragma unroll
     for (int j = 0; j < kGradSums; ++j) a.D[(static_cast<size_t>(k) * kGradSums + j) * a.Npad + i] = acc[j];
     a.Ct[static_cast<size_t>(i) * a.Kpad + k] = fmaf(r, acc[1], (1.f - r) * acc[0]);
@@ -305,7 +311,7 @@ void launch_shared_forward(const Problem &P, Workspace &W, float *f_out, cudaStr
     ShapeArgs s;
     s.N = P.N; s.Npad = P.Npad; s.K = P.K; s.Kpad = W.Kpad;
     s.x = P.x; s.pos = P.pos; s.inten = P.inten; s.off = P.off;
-    s.cst = W.cst; s.theta = W.theta; s.D = W.D; s.Ct = W.Ct;
+    s.cst = W.cst; s.theta = W.theta; s.D = W.D; s.Ct = W.Ct; s.csec = P.csec;
     k_shapes<<<dim3(P.T, P.K), 256, 0, st>>>(s);
     // f_s - B = sum_k h_sk C_k: [S x N] = H [S x Kpad] . Ct [N x Kpad]^T, into the first chunk slot
     launch_gemm_nt_tf32x3(W.S, P.N, W.Kpad, W.H, W.Kpad, W.Ct, W.Kpad, W.fpart, P.Npad, 1, nullptr, W.gemm_err, st);

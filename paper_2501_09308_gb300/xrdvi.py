@@ -22,6 +22,7 @@ FLAG_NAIVE_SUM = 1 << 1
 FLAG_GAUSS_LIK = 1 << 2   # Gaussian likelihood, variance max(y, 1)
 FLAG_IW_ELBO = 1 << 3     # importance-weighted objective
 FLAG_SHARED_SHAPES = 1 << 4   # one shape draw per step, tensor-core contractions
+FLAG_SEC_WIDTH = 1 << 5       # side widths times sec(2theta / 2)
 
 
 class XrdviError(RuntimeError):

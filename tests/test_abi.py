@@ -113,3 +113,13 @@ def test_enumerate_rejects_bad_sizes_before_device_work():
     with pytest.raises(xrdvi.XrdviError) as e:
         xrdvi.xrdvi_enumerate(a["offsets"], a["pos"], a["inten"], a["x"], a["y"], a["bg"], cfg, 10, 1 << 30)
     assert e.value.status == 1
+
+
+def test_angle_dependent_width_needs_angles_below_174_degrees():
+    a = _base()
+    a["x"] = np.linspace(170.0, 178.0, len(a["x"])).astype(np.float32)
+    a["pos"][:] = 175.0
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.xrdvi_create(a["offsets"], a["pos"], a["inten"], a["x"], a["y"], a["bg"],
+                           xrdvi.xrdvi_config_default(flags=xrdvi.FLAG_SEC_WIDTH))
+    assert e.value.status == 1

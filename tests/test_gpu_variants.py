@@ -104,3 +104,33 @@ def test_gaussian_variant_recovers_planted_phases():
     post = c.posterior(512, 3, top_m=1)
     c.close()
     assert set(np.flatnonzero(post["combos"][0]).tolist()) == set(inst.planted.tolist())
+
+
+@pytest.mark.parametrize("K,M,N,S,seed,x_lo", [(3, 6, 300, 4, 7, 100.0), (8, 20, 1000, 8, 8, 60.0),
+                                               (2, 5, 700, 3, 9, 140.0)])
+def test_angle_dependent_width_parity(K, M, N, S, seed, x_lo):
+    """Side widths times sec(2theta / 2) at each point, at angles where the
+    factor reaches 1.1 - 2.9."""
+    inst = synth.small_problem(K=K, M=M, N=N, S=S, seed=seed, x_lo=x_lo, x_step=0.02)
+    g, o = _run(inst, S, xrdvi.FLAG_SEC_WIDTH, seed, width="sec")
+    _check(g, o)
+
+
+def test_angle_dependent_width_with_shared_shapes_parity():
+    inst = synth.small_problem(K=6, M=12, N=900, S=20, seed=10, x_lo=90.0, x_step=0.03)
+    g, o = _run(inst, 20, xrdvi.FLAG_SEC_WIDTH | xrdvi.FLAG_SHARED_SHAPES, 10, width="sec", shapes="shared")
+    _check(g, o)
+
+
+def test_angle_dependent_width_fit_steps_match_oracle():
+    inst = synth.small_problem(K=3, M=6, N=300, S=8, seed=15, x_lo=110.0)
+    ctx = xrdvi.Context.from_instance(inst, S=8, seed=4243, flags=xrdvi.FLAG_SEC_WIDTH)
+    loc0, raw0 = ctx.params()
+    trace = ctx.fit(3)
+    loc1, raw1 = ctx.params()
+    ctx.close()
+    ref = oracle.Problem.from_instance(inst, width="sec").fit(8, 3, 4243, loc=loc0.astype(np.float64),
+                                                               raw=raw0.astype(np.float64))
+    np.testing.assert_allclose(trace, ref["trace"], rtol=F_TOL)
+    np.testing.assert_allclose(loc1, ref["loc"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(raw1, ref["raw"], rtol=1e-5, atol=1e-5)

@@ -167,3 +167,39 @@ def test_shared_shape_estimator_is_unbiased():
     gse = np.sqrt(np.var(grads["plain"], axis=0) / R + np.var(grads["shared"], axis=0) / R)
     z = np.abs(grads["plain"].mean(axis=0) - grads["shared"].mean(axis=0)) / np.maximum(gse, 1e-300)
     assert np.mean(z <= 4) >= 0.97, np.sort(z.ravel())[-5:]
+
+
+def test_sec_width_factor_is_secant_of_half_two_theta():
+    """theta is half the diffraction angle 2-theta (given in degrees): at
+    2-theta = 120 deg the width doubles, at 90 deg it grows by sqrt(2)."""
+    lib = oracle.lib()
+    assert lib.orc_sec(120.0) == pytest.approx(2.0, rel=1e-14)
+    assert lib.orc_sec(90.0) == pytest.approx(math.sqrt(2.0), rel=1e-14)
+    assert lib.orc_sec(1e-6) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_sec_width_profile_against_library_densities():
+    """One asymmetric peak near 2-theta = 110 deg: at every point the profile
+    is scipy's normal and Cauchy densities (scaled to unit height) with the
+    side's FWHM times sec(x / 2) of that point."""
+    x = np.linspace(108.0, 112.0, 401)
+    P = oracle.Problem([0, 1], [110.0], [0.8], x, np.ones_like(x), np.zeros_like(x), width="sec")
+    h, mu, w, r, al = 3.0, 0.02, 0.3, 0.4, 1.7
+    f = P.profile(np.array([[[h, mu, w, r, al]]]))[0]
+    d = x - (110.0 + mu)
+    fwhm = np.where(d >= 0, al * w, w) / np.cos(np.radians(x / 2.0))
+    sd = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    G = stats.norm.pdf(d, scale=sd) / stats.norm.pdf(0.0, scale=sd)
+    L = stats.cauchy.pdf(d, scale=fwhm / 2.0) / stats.cauchy.pdf(0.0, scale=fwhm / 2.0)
+    np.testing.assert_allclose(f, h * 0.8 * ((1 - r) * G + r * L), rtol=1e-12, atol=1e-14)
+
+
+def test_sec_width_gradient_against_central_differences():
+    inst = synth.small_problem(K=3, M=6, N=240, seed=4, x_lo=70.0, x_step=0.1)
+    P = oracle.Problem.from_instance(inst, width="sec")
+    loc, raw = _perturbed(P, 8)
+    eps = synth.normals(12, 2, P.K).astype(np.float64)
+    g = P.elbo_grad(loc, raw, eps)["grad"]
+    num = _fd_grad(P, loc, raw, eps)
+    rel = np.max(np.abs(num - g), axis=0) / np.max(np.abs(g), axis=0)
+    assert np.all(rel < 1e-5), rel
