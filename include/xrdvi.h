@@ -104,6 +104,12 @@ typedef struct {
  * sec(theta) with theta = x/2 (x the 2-theta of the point in degrees), so the
  * peaks broaden towards high angles.  Needs every x below 174 degrees. */
 #define XRDVI_FLAG_SEC_WIDTH  (1u << 5)
+/* Background fitted in-model (model variant; the paper fixes B beforehand,
+ * App. A.2): B_i(beta) = B_i exp(sum_{j<3} beta_j T_j(z_i)) with Chebyshev T_j
+ * and z_i the grid mapped onto [-1, 1]; each beta_j has the prior
+ * N(0, bg_prior_sd^2) and is point-estimated (ln p(beta) joins every draw's
+ * log joint, beta takes the Adam step rule).  xrdvi_get_background reads it. */
+#define XRDVI_FLAG_FIT_BACKGROUND (1u << 6)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */
@@ -119,10 +125,12 @@ typedef struct {
     float init_h_frac;        /* initial h = init_h_frac * max(Y - B)              */
     float init_sigma;         /* initial sigma of every q factor                   */
     uint32_t flags;           /* XRDVI_FLAG_*                                      */
+    float bg_prior_sd;        /* prior sd of the fitted-background coefficients    */
 } xrdvi_config;
 
 /* Fills the defaults: S 256, Adam lr 0.01 betas (0.9, 0.999) eps 1e-8, seed 0,
- * priors of Appendix B.2, alpha_min 1e-3, init_h_frac 0.1, init_sigma 0.1. */
+ * priors of Appendix B.2, alpha_min 1e-3, init_h_frac 0.1, init_sigma 0.1,
+ * bg_prior_sd 0.1. */
 void xrdvi_config_default(xrdvi_config *cfg);
 
 /* Validates and uploads the problem (one host-to-device copy), computes
@@ -361,6 +369,11 @@ xrdvi_status xrdvi_enumerate(const xrdvi_peaks *peaks, const xrdvi_pattern *patt
 /* Device bytes of one enumeration batch of nsub sub-models (host arithmetic;
  * 0 on invalid sizes). */
 size_t xrdvi_enumerate_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t nsub);
+
+/* Fitted-background variant: beta [3], the background curve B(beta) [N] and
+ * the objective's gradient in beta from the last xrdvi_elbo_grad [3] (each
+ * may be NULL), HOST buffers.  EINVAL without the flag. */
+xrdvi_status xrdvi_get_background(xrdvi_ctx *ctx, float *beta, float *bg_curve, float *grad_beta);
 
 /* Tensor-core GEMM used by the shared-shape variant (XRDVI_FLAG_SHARED_SHAPES),
  * exported for testing: C[M x N] = A[M x K] . B[N x K]^T with A, B, C DEVICE

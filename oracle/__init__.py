@@ -49,8 +49,12 @@ class Prior(ctypes.Structure):
 
 
 class Variant(ctypes.Structure):
-    """orc_variant: likelihood, objective, shared shapes, angle-dependent width."""
-    _fields_ = [("lik", ctypes.c_int), ("iw", ctypes.c_int), ("shared", ctypes.c_int), ("sec", ctypes.c_int)]
+    """orc_variant: likelihood, objective, shared shapes, angle-dependent width,
+    fitted background (coefficients, their gradient and Adam moments)."""
+    _PD = ctypes.POINTER(ctypes.c_double)
+    _fields_ = [("lik", ctypes.c_int), ("iw", ctypes.c_int), ("shared", ctypes.c_int), ("sec", ctypes.c_int),
+                ("bgfit", ctypes.c_int), ("bg_sd", ctypes.c_double), ("beta", _PD), ("grad_beta", _PD),
+                ("m_beta", _PD), ("v_beta", _PD)]
 
 
 def build(force: bool = False) -> str:
@@ -107,6 +111,9 @@ def lib():
             L.orc_profile_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, i32, pd, d, i32, pd]
             L.orc_sec.restype = d
             L.orc_sec.argtypes = [d]
+            L.orc_background.argtypes = [i32, pd, pd, pd, pd, pd]
+            L.orc_background_prior.restype = d
+            L.orc_background_prior.argtypes = [pd, d]
             L.orc_tie_shapes.argtypes = [i32, i32, pd]
             L.orc_loglik_gauss.restype = d
             L.orc_loglik_gauss.argtypes = [i32, pd, pd]
@@ -138,18 +145,25 @@ class Problem:
     def __init__(self, offsets, pos, inten, x, y, bg, *, lam=None,
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
                  w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
-                 likelihood="poisson", objective="elbo", shapes="independent", width="constant"):
+                 likelihood="poisson", objective="elbo", shapes="independent", width="constant",
+                 background="fixed", bg_sd=0.1):
         # variants: likelihood "poisson" (the paper's) or "gauss" (variance
         # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound);
         # shapes "independent" or "shared" (one shape draw per step); width
         # "constant" or "sec" (side widths times sec(2theta / 2) at each point)
         assert likelihood in ("poisson", "gauss") and objective in ("elbo", "iw")
         assert shapes in ("independent", "shared") and width in ("constant", "sec")
+        assert background in ("fixed", "fitted")
         self.lik = 1 if likelihood == "gauss" else 0
         self.iw = 1 if objective == "iw" else 0
         self.shared = 1 if shapes == "shared" else 0
         self.sec = 1 if width == "sec" else 0
-        self.variant = Variant(self.lik, self.iw, self.shared, self.sec)
+        self.bgfit = 1 if background == "fitted" else 0
+        # fitted background: correction coefficients beta[3] (point estimate)
+        self.beta = np.zeros(3)
+        self._gb = np.zeros(3)
+        self.variant = Variant(self.lik, self.iw, self.shared, self.sec, self.bgfit, float(bg_sd),
+                               _pd(self.beta), _pd(self._gb), None, None)
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -222,6 +236,8 @@ class Problem:
                                _pd(f64(raw)), _pd(eps), ctypes.byref(elbo), _pd(ll), _pd(lpj),
                                _pd(grad), _pd(f) if want_f else None)
         out = {"elbo": elbo.value, "ll": ll, "lpj": lpj, "grad": grad}
+        if self.bgfit:
+            out["grad_beta"] = self._gb.copy()
         if want_f:
             out["f"] = f
         return out
@@ -238,17 +254,30 @@ class Problem:
         raw = np.full((self.K, 5), math.log(math.expm1(sigma0)))
         return loc, raw
 
+    def background(self, beta=None):
+        """B(beta) [N] of the fitted-background variant (the current beta by default)."""
+        b = self.beta if beta is None else f64(beta)
+        out = np.zeros(self.N)
+        lib().orc_background(self.N, _pd(self.x), _pd(self.bg), _pd(b), _pd(out), None)
+        return out
+
     def fit(self, S, iters, seed, loc=None, raw=None, m=None, v=None, t0=0,
-            lr=0.01, b1=0.9, b2=0.999, adam_eps=1e-8):
+            lr=0.01, b1=0.9, b2=0.999, adam_eps=1e-8, m_beta=None, v_beta=None):
         if loc is None:
             loc, raw = self.init_params()
         loc, raw = f64(loc).copy(), f64(raw).copy()
         m = np.zeros((self.K, 10)) if m is None else f64(m).copy()
         v = np.zeros((self.K, 10)) if v is None else f64(v).copy()
         trace = np.zeros(iters)
+        mb = np.zeros(3) if m_beta is None else f64(m_beta).copy()
+        vb = np.zeros(3) if v_beta is None else f64(v_beta).copy()
+        self.variant.m_beta, self.variant.v_beta = _pd(mb), _pd(vb)
         lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), ctypes.byref(self.variant), S, seed, t0, iters,
                          lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
-        return {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
+        out = {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
+        if self.bgfit:
+            out.update({"beta": self.beta.copy(), "m_beta": mb, "v_beta": vb})
+        return out
 
 
 def iw_weights(raw, eps, ll, lpj):

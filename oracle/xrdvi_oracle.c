@@ -191,6 +191,34 @@ void orc_profile(int K, const int *off, const double *pos, const double *inten,
     orc_profile_ex(K, off, pos, inten, N, x, bg, S, theta, alpha_min, 0, f);
 }
 
+/*
+ * Background variant (Reading: the paper fixes B beforehand, App. A.2; here a
+ * smooth multiplicative correction is fitted with the phases):
+ *   B_i(beta) = B_i exp(beta_0 T_0(z_i) + beta_1 T_1(z_i) + beta_2 T_2(z_i)),
+ * T_0 = 1, T_1 = z, T_2 = 2 z^2 - 1 (Chebyshev), z_i = 2 (x_i - x_0) /
+ * (x_{N-1} - x_0) - 1 in [-1, 1] (z = 0 when N = 1).  Each beta_j has the
+ * prior N(0, bg_sd^2) and is point-estimated (its q is a point mass): the
+ * objective adds ln p(beta) to every draw's log joint.
+ * Writes Bb[N] = B_i(beta) and T[3*N] = T_j(z_i).
+ */
+void orc_background(int N, const double *x, const double *bg, const double *beta, double *Bb, double *T)
+{
+    for (int i = 0; i < N; ++i) {
+        double z = N > 1 ? 2.0 * (x[i] - x[0]) / (x[N - 1] - x[0]) - 1.0 : 0.0;
+        double t0 = 1.0, t1 = z, t2 = 2.0 * z * z - 1.0;
+        if (T) { T[i] = t0; T[N + i] = t1; T[2 * N + i] = t2; }
+        Bb[i] = bg[i] * exp(beta[0] * t0 + beta[1] * t1 + beta[2] * t2);
+    }
+}
+
+/* ln p(beta) = sum_j ln N(beta_j; 0, bg_sd^2). */
+double orc_background_prior(const double *beta, double bg_sd)
+{
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) s += -0.5 * (beta[j] / bg_sd) * (beta[j] / bg_sd) - log(bg_sd) - 0.5 * log(2.0 * ORC_PI);
+    return s;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Poisson likelihood (Appendix A.2)                                         */
 /* ------------------------------------------------------------------------ */
@@ -264,9 +292,15 @@ typedef struct {
  *   shared  1: one shape draw per step for all samples       (orc_tie_shapes)
  *   sec     1: angle-dependent width, every side width at point x multiplied
  *           by sec(theta), theta = x / 2 (x = 2-theta in degrees)   (orc_sec)
+ *   bgfit   1: background fitted in-model                   (orc_background)
  */
 typedef struct {
     int lik, iw, shared, sec;
+    int bgfit;            /* 1: fitted background correction (orc_background)      */
+    double bg_sd;         /* prior standard deviation of each coefficient beta_j  */
+    double *beta;         /* [3] coefficients (in; orc_fit_ex updates them)        */
+    double *grad_beta;    /* [3] d objective / d beta (orc_elbo_grad_ex; may be NULL) */
+    double *m_beta, *v_beta;   /* [3] their Adam moments (orc_fit_ex)              */
 } orc_variant;
 
 /* ln p(theta) for one phase: Exp(lambda) on h, normal on mu and alpha,
@@ -378,6 +412,16 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                       double *grad, double *f_out)
 {
     const int lik = var ? var->lik : 0, iw = var ? var->iw : 0, sec = var ? var->sec : 0;
+    const int bgfit = var ? var->bgfit : 0;
+    double *Bb = NULL, *Tb = NULL, *gbs = NULL, lpb = 0.0;
+    if (bgfit) {   /* fitted background: B(beta), its Chebyshev terms, per-draw beta sums */
+        Bb = (double *)malloc((size_t)N * sizeof(double));
+        Tb = (double *)malloc((size_t)3 * N * sizeof(double));
+        gbs = (double *)calloc((size_t)S * 3, sizeof(double));
+        orc_background(N, x, bg, var->beta, Bb, Tb);
+        lpb = orc_background_prior(var->beta, var->bg_sd);
+        bg = Bb;
+    }
     size_t SK5 = (size_t)S * K * 5;
     double *u = (double *)malloc(SK5 * sizeof(double));
     double *th = (double *)malloc(SK5 * sizeof(double));
@@ -409,9 +453,12 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
         }
         if (f_out) memcpy(f_out + (size_t)s * N, f, (size_t)N * sizeof(double));
         lls[s] = lik ? orc_loglik_gauss(N, y, f) : orc_loglik_direct(N, y, f);
-        double lp = 0.0;
+        double lp = lpb;   /* ln p(beta) of the fitted background (0 otherwise) */
         for (int k = 0; k < K; ++k) lp += orc_log_prior(pr, ths + k * 5) + orc_log_jac(us + k * 5);
         lps[s] = lp;
+        if (bgfit)   /* d LL_s / d beta_j = sum_i g_i B_i(beta) T_j(z_i) */
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < N; ++i) gbs[(size_t)s * 3 + j] += gi[i] * Bb[i] * Tb[(size_t)j * N + i];
         /* backward: per-phase likelihood gradient in theta, chained to u */
         for (int k = 0; k < K; ++k) {
             const double *t = ths + k * 5;
@@ -483,7 +530,14 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 grad[k * 10 + 5 + j] = (ge + 1.0 / orc_softplus(rw)) * orc_sigmoid(rw);
             }
     }
+    if (bgfit && var->grad_beta)
+        for (int j = 0; j < 3; ++j) {
+            double gsum = 0.0;
+            for (int s = 0; s < S; ++s) gsum += wt[s] * gbs[(size_t)s * 3 + j];
+            var->grad_beta[j] = gsum - var->beta[j] / (var->bg_sd * var->bg_sd);
+        }
     free(u); free(th); free(G); free(lls); free(lps); free(wt);
+    free(Bb); free(Tb); free(gbs);
 }
 
 void orc_elbo_grad(int K, const int *off, const double *pos, const double *inten,
@@ -537,7 +591,8 @@ void orc_adam_step(int n, double *params, const double *grad, double *m, double 
  * t0 is the number of steps already taken.  trace[iters] receives the ELBO
  * estimate of each step (evaluated before that step's update).  orc_fit_ex
  * takes the variants as orc_elbo_grad_ex does (trace then holds that
- * objective; shared: the noise of orc_tie_shapes).
+ * objective; shared: the noise of orc_tie_shapes; bgfit: beta and its Adam
+ * moments m_beta, v_beta are updated in place by the same step rule).
  */
 void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
                 int N, const double *x, const double *y, const double *bg,
@@ -552,8 +607,14 @@ void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
         orc_normals(seed, 0u, (uint32_t)(t0 + t), S, K, eps);
         if (var && var->shared) orc_tie_shapes(S, K, eps);
         double elbo;
-        orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, var, S, loc, raw, eps, &elbo, NULL, NULL, grad, NULL);
+        double gb[3] = {0.0, 0.0, 0.0};
+        orc_variant v2;
+        if (var) { v2 = *var; v2.grad_beta = gb; }
+        orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, var ? &v2 : NULL, S, loc, raw, eps, &elbo, NULL, NULL,
+                         grad, NULL);
         if (trace) trace[t] = elbo;
+        if (var && var->bgfit)   /* the background coefficients take the same Adam step rule */
+            orc_adam_step(3, var->beta, gb, var->m_beta, var->v_beta, t0 + t + 1, lr, b1, b2, adam_eps);
         for (int k = 0; k < K; ++k)
             for (int j = 0; j < 5; ++j) {
                 par[k * 10 + j] = loc[k * 5 + j];

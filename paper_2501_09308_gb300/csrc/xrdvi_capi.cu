@@ -81,6 +81,7 @@ struct xrdvi_ctx {
     PostBuffers B;
     float *loc = nullptr, *raw = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     float *eps_in = nullptr;   // injected noise [S*K*5]
+    float *grad_beta = nullptr;   // [3] beta gradient of the last elbo_grad (fitted background)
     float *f_out = nullptr;    // profile output [S*N]
     double *ent = nullptr, *elbo = nullptr, *trace = nullptr;
     int *step = nullptr, *iter = nullptr;
@@ -159,6 +160,7 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
         XR_TRY(c->alloc(&W.tickets, static_cast<size_t>(W.B) * P.K, list));
         W.lq = nullptr;
         W.iw = nullptr;
+        if (P.bgfit) XR_TRY(c->alloc(&W.bgpart, static_cast<size_t>(S) * P.T * 3, list));
         if (c->cfg.flags & XRDVI_FLAG_IW_ELBO) {   // ln q(u_s) and the normalised weights
             XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
             XR_TRY(c->alloc(&W.iw, static_cast<size_t>(S), list));
@@ -190,6 +192,7 @@ AdamConst adam_const(const xrdvi_config &cfg) {
 // set: the dense profile kernels, or the tensor-core contractions of the
 // shared-shape variant.
 void fwd_pass(xrdvi_ctx *c, float *f_out, cudaStream_t st) {
+    if (c->P.bgfit) launch_bg_curve(c->P, st);
     if (c->W.shared)
         launch_shared_forward(c->P, c->W, f_out, st);
     else
@@ -210,6 +213,7 @@ void enqueue_step(xrdvi_ctx *c, cudaStream_t st) {
     bwd_pass(c, st);
     launch_grad(c->P, c->W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m,
                 c->v, c->iter, c->step, c->ent, c->elbo, c->trace, st);
+    if (c->P.bgfit) launch_bg_grad(c->P, c->W, true, adam_const(c->cfg), c->iter, nullptr, st);
 }
 
 // Captured on the context's private stream (capturable in every case); the
@@ -257,6 +261,8 @@ xrdvi_status validate(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdv
         if (!(std::isfinite(b) && b >= 0.f)) return fail(XRDVI_EINVAL, "background must be finite and >= 0");
     }
     if (cfg->S < 1 || cfg->S > kMaxS) return fail(XRDVI_EINVAL, "S must be in [1, 65536]");
+    if ((cfg->flags & XRDVI_FLAG_FIT_BACKGROUND) && !(std::isfinite(cfg->bg_prior_sd) && cfg->bg_prior_sd > 0.f))
+        return fail(XRDVI_EINVAL, "bg_prior_sd must be positive");
     const float pos_params[] = {cfg->prior_mu_sd, cfg->prior_alpha_sd, cfg->prior_w_shape, cfg->prior_w_rate,
                                 cfg->alpha_min, cfg->init_h_frac, cfg->init_sigma, cfg->lr};
     for (float q : pos_params)
@@ -314,6 +320,7 @@ void xrdvi_config_default(xrdvi_config *cfg) {
     cfg->init_h_frac = 0.1f;
     cfg->init_sigma = 0.1f;
     cfg->flags = 0;
+    cfg->bg_prior_sd = 0.1f;
 }
 
 xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
@@ -338,8 +345,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     const int K = pk->K, N = pt->N, M = pk->offsets[K];
     if (nsub < 1 || static_cast<int64_t>(nsub) * cfg->S > kMaxS)
         return fail(XRDVI_EINVAL, "sub-model batch: B * S must be in [1, 65536]");
-    if (masks && (cfg->flags & XRDVI_FLAG_SHARED_SHAPES))
-        return fail(XRDVI_EINVAL, "the shared-shape variant does not run in sub-model batches");
+    if (masks && (cfg->flags & (XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_FIT_BACKGROUND)))
+        return fail(XRDVI_EINVAL, "the shared-shape and fitted-background variants do not run in sub-model batches");
     if (masks) {
         if (K > 32) return fail(XRDVI_EINVAL, "sub-model batch: K must be <= 32");
         for (int b = 0; b < nsub; ++b)
@@ -450,6 +457,26 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     XR_C(c->alloc(&P.bg, N));
     XR_C(c->alloc(&P.isum, K));
     if (sec) XR_C(c->alloc(&P.csec, N));
+    std::vector<float> Tb;
+    if (cfg->flags & XRDVI_FLAG_FIT_BACKGROUND) {
+        // fitted background: Chebyshev terms of the grid mapped onto [-1, 1]
+        P.bgfit = true;
+        P.bg_sd = cfg->bg_prior_sd;
+        Tb.resize(static_cast<size_t>(3) * N);
+        const double x0 = pt->x_deg[0], x1 = pt->x_deg[N - 1];
+        for (int i = 0; i < N; ++i) {
+            const double z = N > 1 ? 2.0 * (pt->x_deg[i] - x0) / (x1 - x0) - 1.0 : 0.0;
+            Tb[i] = 1.f;
+            Tb[N + i] = static_cast<float>(z);
+            Tb[2 * N + i] = static_cast<float>(2.0 * z * z - 1.0);
+        }
+        XR_C(c->alloc(&P.Tb, static_cast<size_t>(3) * N));
+        XR_C(c->alloc(&P.Bb, N));
+        XR_C(c->alloc(&P.beta, 3));
+        XR_C(c->alloc(&P.m_beta, 3));
+        XR_C(c->alloc(&P.v_beta, 3));
+        XR_C(c->alloc(&c->grad_beta, 3));
+    }
     configure_grids(P, sms);
     c->host_off.assign(pk->offsets, pk->offsets + K + 1);
     c->W.B = nsub;
@@ -510,6 +537,9 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s) ||
         (d_mask && (up(d_mask, masks, static_cast<size_t>(nsub) * 4) ||
                     cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))) ||
+        (P.bgfit && (up(P.Tb, Tb.data(), Tb.size() * 4) || cudaMemsetAsync(P.beta, 0, 12, s) ||
+                     cudaMemsetAsync(P.m_beta, 0, 12, s) || cudaMemsetAsync(P.v_beta, 0, 12, s) ||
+                     cudaMemsetAsync(c->grad_beta, 0, 12, s))) ||
         (W.shared && (cudaMemsetAsync(W.H, 0, static_cast<size_t>(W.S) * W.Kpad * 4, s) ||
                       cudaMemsetAsync(W.Ct, 0, static_cast<size_t>(P.Npad) * W.Kpad * 4, s) ||
                       cudaMemsetAsync(W.gemm_err, 0, 4, s))))
@@ -589,6 +619,7 @@ xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float
     bwd_pass(c, st);
     launch_grad(P, c->W, c->loc, c->raw, nullptr, nullptr, c->grad, false, adam_const(c->cfg), nullptr, nullptr,
                 nullptr, nullptr, c->ent, c->elbo, nullptr, st);
+    if (P.bgfit) launch_bg_grad(P, c->W, false, adam_const(c->cfg), nullptr, c->grad_beta, st);
     XR_TRY(check_launch("elbo_grad"));
     double e = 0.0;
     XR_CUDA(cudaMemcpyAsync(&e, c->elbo, 8, cudaMemcpyDeviceToHost, st));
@@ -663,6 +694,7 @@ xrdvi_status xrdvi_posterior(xrdvi_ctx *c, int32_t S_post, uint64_t seed, int32_
     cudaStream_t st = c->stream;
     const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     launch_sample(P, c->Wp, c->loc, c->raw, nullptr, seed, 1u, nullptr, 0u, nullptr, nullptr, st);
+    if (P.bgfit) launch_bg_curve(P, st);
     launch_forward(P, c->Wp, nullptr, naive, st);
     launch_posterior(P, c->Wp, c->B, top_m, st);
     XR_TRY(check_launch("posterior"));
@@ -697,6 +729,7 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *c, int32_t steps, float *kernel_ms) 
         cudaEventRecord(ev[3], st);
         launch_grad(c->P, c->W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m, c->v,
                     c->iter, nullptr, c->ent, nullptr, nullptr, st);
+        if (c->P.bgfit) launch_bg_grad(c->P, c->W, true, adam_const(c->cfg), c->iter, nullptr, st);
         cudaEventRecord(ev[4], st);
         launch_grad(c->P, c->W, c->loc, c->raw, nullptr, nullptr, nullptr, false, adam_const(c->cfg), nullptr,
                     nullptr, c->iter, c->step, c->ent, c->elbo, c->trace, st);
@@ -747,13 +780,14 @@ struct StateHeader {
 xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
     if (!c || !len) return fail(XRDVI_EINVAL, "null argument");
     const int K = c->P.K;
-    const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * (5 + 5 + 10 + 10) * 4;
+    const int extra = c->P.bgfit ? 9 : 0;   // fitted background: beta, its Adam moments
+    const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * (5 + 5 + 10 + 10) * 4 + extra * 4;
     if (!buf) {
         *len = need;
         return XRDVI_OK;
     }
     if (*len < need) return fail(XRDVI_EINVAL, "state buffer too small");
-    StateHeader h{kStateMagic, 1u, K, 0, c->host_step, c->cfg.seed};
+    StateHeader h{kStateMagic, 1u, K, extra, c->host_step, c->cfg.seed};
     char *p = static_cast<char *>(buf);
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
@@ -761,6 +795,11 @@ xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
     XR_CUDA(cudaMemcpyAsync(p + K * 20, c->raw, K * 20, cudaMemcpyDeviceToHost, c->stream));
     XR_CUDA(cudaMemcpyAsync(p + K * 40, c->m, K * 40, cudaMemcpyDeviceToHost, c->stream));
     XR_CUDA(cudaMemcpyAsync(p + K * 80, c->v, K * 40, cudaMemcpyDeviceToHost, c->stream));
+    if (extra) {
+        XR_CUDA(cudaMemcpyAsync(p + K * 120, c->P.beta, 12, cudaMemcpyDeviceToHost, c->stream));
+        XR_CUDA(cudaMemcpyAsync(p + K * 120 + 12, c->P.m_beta, 12, cudaMemcpyDeviceToHost, c->stream));
+        XR_CUDA(cudaMemcpyAsync(p + K * 120 + 24, c->P.v_beta, 12, cudaMemcpyDeviceToHost, c->stream));
+    }
     XR_CUDA(cudaStreamSynchronize(c->stream));
     *len = need;
     return XRDVI_OK;
@@ -769,11 +808,13 @@ xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
 xrdvi_status xrdvi_set_state(xrdvi_ctx *c, const void *buf, size_t len) {
     if (!c || !buf) return fail(XRDVI_EINVAL, "null argument");
     const int K = c->P.K;
-    const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * 120;
+    const int extra = c->P.bgfit ? 9 : 0;
+    const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * 120 + extra * 4;
     if (len < need) return fail(XRDVI_EINVAL, "state buffer too small");
     StateHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (h.magic != kStateMagic || h.version != 1u || h.K != K) return fail(XRDVI_EINVAL, "state does not match this problem");
+    if (h.magic != kStateMagic || h.version != 1u || h.K != K || h.pad != extra)
+        return fail(XRDVI_EINVAL, "state does not match this problem");
     if (h.step < 0 || h.step > INT32_MAX) return fail(XRDVI_EINVAL, "bad step counter");
     const char *p = static_cast<const char *>(buf) + sizeof(h);
     const int step = static_cast<int>(h.step);
@@ -781,11 +822,28 @@ xrdvi_status xrdvi_set_state(xrdvi_ctx *c, const void *buf, size_t len) {
     XR_CUDA(cudaMemcpyAsync(c->raw, p + K * 20, K * 20, cudaMemcpyHostToDevice, c->stream));
     XR_CUDA(cudaMemcpyAsync(c->m, p + K * 40, K * 40, cudaMemcpyHostToDevice, c->stream));
     XR_CUDA(cudaMemcpyAsync(c->v, p + K * 80, K * 40, cudaMemcpyHostToDevice, c->stream));
+    if (extra) {
+        XR_CUDA(cudaMemcpyAsync(c->P.beta, p + K * 120, 12, cudaMemcpyHostToDevice, c->stream));
+        XR_CUDA(cudaMemcpyAsync(c->P.m_beta, p + K * 120 + 12, 12, cudaMemcpyHostToDevice, c->stream));
+        XR_CUDA(cudaMemcpyAsync(c->P.v_beta, p + K * 120 + 24, 12, cudaMemcpyHostToDevice, c->stream));
+    }
     XR_CUDA(cudaMemcpyAsync(c->step, &step, 4, cudaMemcpyHostToDevice, c->stream));
     XR_CUDA(cudaStreamSynchronize(c->stream));
     c->host_step = h.step;
     c->cfg.seed = h.seed;
     c->drop_graphs();  // the seed is a kernel argument of the captured step
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_get_background(xrdvi_ctx *c, float *beta, float *bg_curve, float *grad_beta) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    if (!c->P.bgfit) return fail(XRDVI_EINVAL, "the context does not fit the background");
+    if (bg_curve) launch_bg_curve(c->P, c->stream);
+    if (beta) XR_CUDA(cudaMemcpyAsync(beta, c->P.beta, 12, cudaMemcpyDeviceToHost, c->stream));
+    if (bg_curve) XR_CUDA(cudaMemcpyAsync(bg_curve, c->P.Bb, static_cast<size_t>(c->P.N) * 4, cudaMemcpyDeviceToHost,
+                                          c->stream));
+    if (grad_beta) XR_CUDA(cudaMemcpyAsync(grad_beta, c->grad_beta, 12, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
     return XRDVI_OK;
 }
 

@@ -90,6 +90,7 @@ struct Workspace {
     int B = 1, S_sub = 0;
     const uint32_t *mask = nullptr;   // [B] device
     double *tail_sum = nullptr;       // [B] sum of the ELBO estimates from step tail_start on
+    float *bgpart = nullptr;          // [S*T*3] per-(sample, tile) sums g B(beta) T_j (fitted background)
     double *iw = nullptr;             // [S] normalised importance weights (importance-weighted
                                       //     objective; null: the ELBO, weights 1/S)
     // Shared-shape variant (one shape draw per step for all samples): the
@@ -124,6 +125,12 @@ struct Problem {
     bool sec = false;            // angle-dependent width variant (side widths times sec(x/2))
     float *csec = nullptr;       // [N] cos(x_i / 2) for that variant
     float sec_max = 1.f;         // max_i sec(x_i / 2)
+    // fitted-background variant: B(beta) = B exp(sum_j beta_j T_j(z))
+    bool bgfit = false;
+    float bg_sd = 0.1f;
+    float *beta = nullptr, *m_beta = nullptr, *v_beta = nullptr;   // [3] coefficients, Adam moments
+    float *Tb = nullptr;         // [3*N] Chebyshev terms T_j(z_i)
+    float *Bb = nullptr;         // [N] B(beta) of the current step
     int grid_fwd = 0, grid_bwd = 0;
 };
 
@@ -191,6 +198,13 @@ xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, co
 // logp[c] = elbo[c] - logsumexp(elbo[0..n)) in FP64 with a fixed reduction
 // order (one block).
 void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st);
+
+// Fitted-background variant: B(beta) for the step (before the likelihood),
+// and after the gradient sums the beta gradient (weights 1/S or the
+// importance weights) with Adam on beta (adam) or written to grad_out [3].
+void launch_bg_curve(const Problem &P, cudaStream_t st);
+void launch_bg_grad(const Problem &P, Workspace &W, bool adam, AdamConst ac, const int *d_iter, float *grad_out,
+                    cudaStream_t st);
 
 // k_lik alone (f = B + chunk partials, deviance, g), over the first C chunks.
 void launch_lik(const Problem &P, Workspace &W, float *f_out, int C, cudaStream_t st);

@@ -147,6 +147,8 @@ struct SampleArgs {
     int B, S_sub;
     const uint32_t *mask;  // [B] phases kept by each sub-model (null: all)
     float reach_scale;     // Gaussian reach factor: max sec(x/2) of the pattern (angle-dependent width), else 1
+    const float *beta;     // [3] fitted-background coefficients (null: fixed background)
+    float bg_sd;
     int shared;            // shape noise of every sample = sample 0's (shared-shape variant)
     float *H;              // [S*Kpad] h_sk for the forward GEMM (shared-shape variant)
     int Kpad;
@@ -274,6 +276,12 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
     }
     if (s == 0 && a.tickets)
         for (int k = threadIdx.x; k < a.B * a.K; k += blockDim.x) a.tickets[k] = 0;
+    if (a.beta && threadIdx.x == 0) {   // ln p(beta) of the fitted background joins every draw's log joint
+        for (int j = 0; j < 3; ++j) {
+            const double z = static_cast<double>(a.beta[j]) / a.bg_sd;
+            acc += -0.5 * z * z - log(static_cast<double>(a.bg_sd)) - 0.5 * kLog2Pi;
+        }
+    }
     const double tot = block_sum(acc, sh);
     const double totq = a.lq ? block_sum(accq, sh) : 0.0;
     if (threadIdx.x == 0) {
@@ -334,6 +342,8 @@ struct ProfArgs {
     int *counter;      // work counter of this kernel (zeroed by k_sample)
     int gauss;         // Gaussian likelihood variant
     const float *csec; // [N] cos(x/2) of the angle-dependent width variant (null: constant width)
+    const float *Tb;   // [3*N] Chebyshev terms (fitted background; null: fixed background)
+    float *bgpart;     // [S*T*3] per-(sample, tile) sums of g B(beta) T_j
 };
 
 typedef unsigned long long f2_t;   // two packed floats
@@ -748,6 +758,29 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
         float t = threadIdx.x < kTile / 32 ? shf[threadIdx.x] : 0.f;
         t = warp_sumf(t);
         if (threadIdx.x == 0) a.llpart[static_cast<size_t>(s) * a.T + tile] = static_cast<double>(t);
+    }
+    if (a.Tb) {   // fitted background: d LL / d beta_j = sum_i g_i B_i(beta) T_j(z_i), per tile
+        __shared__ float shb[3][kTile / 32];
+        float v[3] = {0.f, 0.f, 0.f};
+        if (i < a.N) {
+            const float gb = gv * a.bg[i];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = gb * a.Tb[static_cast<size_t>(j) * a.N + i];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            v[j] = warp_sumf(v[j]);
+            if (l == 0) shb[j][w] = v[j];
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float t = threadIdx.x < kTile / 32 ? shb[j][threadIdx.x] : 0.f;
+                t = warp_sumf(t);
+                if (threadIdx.x == 0) a.bgpart[(static_cast<size_t>(s) * a.T + tile) * 3 + j] = t;
+            }
+        }
     }
 }
 
@@ -1449,6 +1482,9 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     a.fpart = W.fpart; a.counter = W.counters;
     a.gauss = P.gauss ? 1 : 0;
     a.csec = P.csec;
+    if (P.bgfit) a.bg = P.Bb;   // fitted background: the current curve B(beta)
+    a.bgpart = P.bgfit ? W.bgpart : nullptr;
+    a.Tb = a.bgpart ? P.Tb : nullptr;   // beta sums only where the sample set keeps them
     return a;
 }
 
@@ -1496,6 +1532,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.B = W.B; a.S_sub = W.B > 1 || W.mask ? W.S_sub : W.S; a.mask = W.mask;
     a.shared = W.shared ? 1 : 0; a.H = W.H; a.Kpad = W.Kpad;
     a.reach_scale = P.sec ? P.sec_max : 1.0f;
+    a.beta = P.bgfit ? P.beta : nullptr; a.bg_sd = P.bg_sd;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1618,6 +1655,57 @@ __global__ void __launch_bounds__(256) k_enum_lse(const double *elbo, int n, dou
 
 void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st) {
     k_enum_lse<<<1, 256, 0, st>>>(elbo, n, logp);
+}
+
+
+namespace {
+// Fitted background curve B_i(beta) = B_i exp(sum_j beta_j T_j(z_i)).
+__global__ void k_bg_curve(int N, const float *bg, const float *Tb, const float *beta, float *Bb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float e = beta[0] * Tb[i] + beta[1] * Tb[N + i] + beta[2] * Tb[2 * N + i];
+    Bb[i] = bg[i] * expf(e);
+}
+
+// beta gradient: sum over draws (weight 1/S, or the importance weights) of
+// the tile sums, in a fixed order, minus beta / sd^2; then Adam on beta (the
+// step rule of k_grad) or the gradient written out.  One block of 3 warps.
+__global__ void k_bg_grad(int S, int T, const float *bgpart, const double *iw, float *beta, float *m, float *v,
+                          float bg_sd, int adam, AdamConst ac, const int *d_iter, float *grad_out) {
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j >= 3) return;
+    double acc = 0.0;
+    for (int s = lane; s < S; s += 32) {
+        double t = 0.0;
+        for (int tile = 0; tile < T; ++tile) t += bgpart[(static_cast<size_t>(s) * T + tile) * 3 + j];
+        acc += iw ? iw[s] * t : t;
+    }
+    acc = warp_sumd(acc);
+    if (lane != 0) return;
+    const double b = beta[j];
+    const double grad = (iw ? acc : acc / S) - b / (static_cast<double>(bg_sd) * bg_sd);
+    if (grad_out) grad_out[j] = static_cast<float>(grad);
+    if (adam) {
+        const int t = *d_iter + 1;
+        const double gm = -grad;
+        const double mm = ac.b1 * static_cast<double>(m[j]) + (1.0 - ac.b1) * gm;
+        const double vv = ac.b2 * static_cast<double>(v[j]) + (1.0 - ac.b2) * gm * gm;
+        m[j] = static_cast<float>(mm);
+        v[j] = static_cast<float>(vv);
+        const double c1 = 1.0 - pow(static_cast<double>(ac.b1), t), c2 = 1.0 - pow(static_cast<double>(ac.b2), t);
+        beta[j] = static_cast<float>(b - ac.lr * (mm / c1) / (sqrt(vv / c2) + ac.eps));
+    }
+}
+}  // namespace
+
+void launch_bg_curve(const Problem &P, cudaStream_t st) {
+    k_bg_curve<<<(P.N + 255) / 256, 256, 0, st>>>(P.N, P.bg, P.Tb, P.beta, P.Bb);
+}
+
+void launch_bg_grad(const Problem &P, Workspace &W, bool adam, AdamConst ac, const int *d_iter, float *grad_out,
+                    cudaStream_t st) {
+    k_bg_grad<<<1, 96, 0, st>>>(W.S, P.T, W.bgpart, W.iw, P.beta, P.m_beta, P.v_beta, P.bg_sd, adam ? 1 : 0, ac,
+                                d_iter, grad_out);
 }
 
 }  // namespace xrdvi

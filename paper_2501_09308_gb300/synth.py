@@ -93,8 +93,11 @@ def _simulate_counts(rng, x, bg, phases, planted, hs, mus, ws):
 
 
 def make_problem(*, K, m_lo, m_hi, x_lo, x_step, N, n_planted, S, iters, seed,
-                 background="linear", overlap=False, name="custom"):
-    """Generic seeded instance.  M_k ~ U{m_lo..m_hi} (m_lo == m_hi: fixed)."""
+                 background="linear", overlap=False, name="custom", true_bg_factor=None):
+    """Generic seeded instance.  M_k ~ U{m_lo..m_hi} (m_lo == m_hi: fixed).
+    true_bg_factor: optional array [N] multiplying the background the counts
+    are simulated with (the instance still reports the unmultiplied one), for
+    problems whose background is mis-specified."""
     rng = np.random.default_rng(seed)
     x = x_lo + x_step * np.arange(N, dtype=np.float64)
     x_hi = float(x[-1])
@@ -134,7 +137,8 @@ def make_problem(*, K, m_lo, m_hi, x_lo, x_step, N, n_planted, S, iters, seed,
         bg = 50.0 + 1.0 * xr
     else:
         bg = 40.0 + 0.8 * xr + 0.01 * xr * xr
-    y = _simulate_counts(rng, x, bg, phases, planted, hs, mus, ws)
+    bg_true = bg if true_bg_factor is None else bg * np.asarray(true_bg_factor, dtype=np.float64)
+    y = _simulate_counts(rng, x, bg_true, phases, planted, hs, mus, ws)
     offsets = np.zeros(K + 1, dtype=np.int32)
     offsets[1:] = np.cumsum([len(p) for p, _ in phases])
     pos = np.concatenate([p for p, _ in phases]).astype(np.float32)

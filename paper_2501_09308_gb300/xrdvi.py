@@ -23,6 +23,7 @@ FLAG_GAUSS_LIK = 1 << 2   # Gaussian likelihood, variance max(y, 1)
 FLAG_IW_ELBO = 1 << 3     # importance-weighted objective
 FLAG_SHARED_SHAPES = 1 << 4   # one shape draw per step, tensor-core contractions
 FLAG_SEC_WIDTH = 1 << 5       # side widths times sec(2theta / 2)
+FLAG_FIT_BACKGROUND = 1 << 6  # background correction exp(sum beta_j T_j(z)) fitted in-model
 
 
 class XrdviError(RuntimeError):
@@ -48,7 +49,7 @@ class Config(ctypes.Structure):
                 ("prior_alpha_mean", ctypes.c_float), ("prior_alpha_sd", ctypes.c_float),
                 ("prior_w_shape", ctypes.c_float), ("prior_w_rate", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("init_h_frac", ctypes.c_float),
-                ("init_sigma", ctypes.c_float), ("flags", ctypes.c_uint32)]
+                ("init_sigma", ctypes.c_float), ("flags", ctypes.c_uint32), ("bg_prior_sd", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):
@@ -115,6 +116,7 @@ SIGNATURES = {
     "xrdvi_enumerate": (ctypes.c_int, [P(Peaks), P(Pattern), P(Config), _i32, ctypes.c_size_t, P(_d), P(_d)]),
     "xrdvi_enumerate_footprint_bytes": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _i32]),
     "xrdvi_gemm_nt_tf32x3": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp]),
+    "xrdvi_get_background": (ctypes.c_int, [_vp, P(_f), P(_f), P(_f)]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -354,6 +356,9 @@ class Context:
     def profile_steps(self, steps):
         return xrdvi_profile_steps(self.h, steps)
 
+    def background(self):
+        return xrdvi_get_background(self.h)
+
     def set_stream(self, stream_handle):
         xrdvi_set_stream(self.h, stream_handle)
 
@@ -450,3 +455,13 @@ def xrdvi_gemm_nt_tf32x3(M, N, K, d_A, lda, d_B, ldb, d_C, ldc, stream=None):
     """Device-pointer GEMM C = A . B^T on the tensor cores (3xTF32)."""
     _check(lib().xrdvi_gemm_nt_tf32x3(int(M), int(N), int(K), _vp(d_A), int(lda), _vp(d_B), int(ldb), _vp(d_C),
                                       int(ldc), _vp(stream or CUDA_STREAM_LEGACY)))
+
+
+def xrdvi_get_background(h):
+    """Fitted-background variant: {"beta": [3], "curve": [N], "grad_beta": [3]}."""
+    info = xrdvi_get_info(h)
+    beta = np.zeros(3, dtype=np.float32)
+    curve = np.zeros(info.N, dtype=np.float32)
+    gb = np.zeros(3, dtype=np.float32)
+    _check(lib().xrdvi_get_background(h, _ptr(beta, _f), _ptr(curve, _f), _ptr(gb, _f)))
+    return {"beta": beta, "curve": curve, "grad_beta": gb}

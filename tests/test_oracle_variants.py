@@ -203,3 +203,42 @@ def test_sec_width_gradient_against_central_differences():
     num = _fd_grad(P, loc, raw, eps)
     rel = np.max(np.abs(num - g), axis=0) / np.max(np.abs(g), axis=0)
     assert np.all(rel < 1e-5), rel
+
+
+def test_fitted_background_curve_is_a_chebyshev_exponential():
+    """B(beta) = B exp(sum_j beta_j T_j(z)) with numpy's Chebyshev series and z
+    the grid mapped onto [-1, 1]."""
+    inst, P = _problem(background="fitted")
+    beta = np.array([0.08, -0.05, 0.02])
+    z = 2.0 * (P.x - P.x[0]) / (P.x[-1] - P.x[0]) - 1.0
+    ref = P.bg * np.exp(np.polynomial.chebyshev.chebval(z, beta))
+    np.testing.assert_allclose(P.background(beta), ref, rtol=1e-13)
+
+
+def test_fitted_background_at_zero_is_the_fixed_model_plus_its_prior():
+    inst, P_fit = _problem(background="fitted", bg_sd=0.1)
+    P = oracle.Problem.from_instance(inst)
+    loc, raw = _perturbed(P, 9)
+    eps = synth.normals(13, 3, P.K).astype(np.float64)
+    a, b = P_fit.elbo_grad(loc, raw, eps), P.elbo_grad(loc, raw, eps)
+    lpb = 3 * stats.norm.logpdf(0.0, scale=0.1)
+    assert a["elbo"] == pytest.approx(b["elbo"] + lpb, rel=1e-13)
+    np.testing.assert_allclose(a["grad"], b["grad"], rtol=1e-12, atol=1e-12)
+
+
+def test_fitted_background_gradient_against_central_differences():
+    inst, P = _problem(background="fitted", bg_sd=0.1)
+    loc, raw = _perturbed(P, 10)
+    eps = synth.normals(14, 3, P.K).astype(np.float64)
+    P.beta[:] = [0.03, -0.02, 0.01]
+    g = P.elbo_grad(loc, raw, eps)["grad_beta"]
+    num = np.zeros(3)
+    for j in range(3):
+        b0 = P.beta[j]
+        P.beta[j] = b0 + 1e-6
+        ep = P.elbo_grad(loc, raw, eps)["elbo"]
+        P.beta[j] = b0 - 1e-6
+        em = P.elbo_grad(loc, raw, eps)["elbo"]
+        P.beta[j] = b0
+        num[j] = (ep - em) / 2e-6
+    np.testing.assert_allclose(g, num, rtol=1e-5, atol=1e-6 * np.max(np.abs(num)))
