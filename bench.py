@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=None, help="SVI steps per fit (default: workload's 2000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-enumeration", action="store_true", help="skip the K=8 exact-enumeration and estimator-variant legs")
+    ap.add_argument("--variants-only", action="store_true",
+                    help="run only the estimator/model-variant leg and print its JSON (profiling aid)")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
     return ap.parse_args()
@@ -331,6 +333,9 @@ def workload_config(inst, l2):
 
 def main():
     args = parse()
+    if args.variants_only:
+        print(json.dumps({"variants": variants_leg(measured_peaks()[0])}), flush=True)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -503,9 +503,10 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         W.Kpad = (K + 31) / 32 * 32;
         const int nk = K * kGradSums;
         W.gemm_splits = gemm_splits(W.S, nk, P.Npad, sms);
-        XR_C(c->alloc(&W.H, static_cast<size_t>(W.S) * W.Kpad));
-        XR_C(c->alloc(&W.Ct, static_cast<size_t>(P.Npad) * W.Kpad));
-        XR_C(c->alloc(&W.D, static_cast<size_t>(nk) * P.Npad));
+        XR_C(c->alloc(&W.H, static_cast<size_t>(2) * W.S * W.Kpad));      // TF32 hi + lo parts
+        XR_C(c->alloc(&W.Ct, static_cast<size_t>(2) * P.Npad * W.Kpad));
+        XR_C(c->alloc(&W.D, static_cast<size_t>(2) * nk * P.Npad));
+        XR_C(c->alloc(&W.ghl, static_cast<size_t>(2) * W.S * P.Npad));
         XR_C(c->alloc(&W.gemm_work, gemm_workspace_floats(W.S, nk, W.gemm_splits)));
         XR_C(c->alloc(&W.gemm_err, 1));
         if (gemm_configure() != cudaSuccess) return bail(fail(XRDVI_ECUDA, "tensor-core GEMM set-up failed"));
@@ -540,8 +541,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         (P.bgfit && (up(P.Tb, Tb.data(), Tb.size() * 4) || cudaMemsetAsync(P.beta, 0, 12, s) ||
                      cudaMemsetAsync(P.m_beta, 0, 12, s) || cudaMemsetAsync(P.v_beta, 0, 12, s) ||
                      cudaMemsetAsync(c->grad_beta, 0, 12, s))) ||
-        (W.shared && (cudaMemsetAsync(W.H, 0, static_cast<size_t>(W.S) * W.Kpad * 4, s) ||
-                      cudaMemsetAsync(W.Ct, 0, static_cast<size_t>(P.Npad) * W.Kpad * 4, s) ||
+        (W.shared && (cudaMemsetAsync(W.H, 0, static_cast<size_t>(2) * W.S * W.Kpad * 4, s) ||
+                      cudaMemsetAsync(W.Ct, 0, static_cast<size_t>(2) * P.Npad * W.Kpad * 4, s) ||
                       cudaMemsetAsync(W.gemm_err, 0, 4, s))))
         return bail(fail(XRDVI_ECUDA, "upload failed"));
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)

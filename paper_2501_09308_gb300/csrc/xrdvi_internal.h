@@ -96,10 +96,13 @@ struct Workspace {
     // Shared-shape variant (one shape draw per step for all samples): the
     // profile and the backward's sums become GEMMs over phase profiles.
     bool shared = false;
+    // GEMM operands are kept split for the 3xTF32 products: each array holds
+    // the TF32 hi parts followed by the lo parts (2x the size given)
     int Kpad = 0;                     // phases padded to a multiple of 32
     float *H = nullptr;               // [S*Kpad] intensities h_sk (GEMM A of the forward)
     float *Ct = nullptr;              // [Npad*Kpad] phase profiles C_k(x_i), point-major
     float *D = nullptr;               // [K*10*Npad] derivative profiles D_jk(x_i) (GEMM B of the backward)
+    float *ghl = nullptr;             // [S*Npad] y/f - 1 (GEMM A of the backward)
     float *gemm_work = nullptr;       // split-K partials of the backward GEMM
     int gemm_splits = 1;
     int *gemm_err = nullptr;          // set if a tensor-core pipeline wait gives up
@@ -215,16 +218,21 @@ void launch_shared_forward(const Problem &P, Workspace &W, float *f_out, cudaStr
 void launch_shared_backward(const Problem &P, Workspace &W, cudaStream_t st);
 
 // Tensor-core GEMM (xrdvi_tc.cu): out[M x N] = A[M x K] . B[N x K]^T, A and B
-// row-major with K contiguous (K, lda, ldb multiples of 4, 16-byte aligned),
-// 3xTF32 on tcgen05 with FP32 accumulation; split-K partials (work,
-// gemm_workspace_floats) are added in a fixed order.  err (device int) is set
-// if an mbarrier wait gives up.
+// given as TF32 hi / lo parts (launch_tf32_split), row-major with K contiguous
+// (K, lda, ldb multiples of 4, 16-byte aligned), 3xTF32 on tcgen05 with FP32
+// accumulation; split-K partials (work, gemm_workspace_floats) are added in a
+// fixed order.  err (device int) is set if an mbarrier wait gives up.
 size_t gemm_smem_bytes();
 cudaError_t gemm_configure();   // shared-memory attribute of the GEMM kernel (call before capture)
 int gemm_splits(int M, int N, int K, int sm_count);
 size_t gemm_workspace_floats(int M, int N, int splits);
-void launch_gemm_nt_tf32x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *out,
-                           int ldo, int splits, float *work, int *err, cudaStream_t st);
+void launch_gemm_nt_tf32x3(int M, int N, int K, const float *Ahi, const float *Alo, int lda, const float *Bhi,
+                           const float *Blo, int ldb, float *out, int ldo, int splits, float *work, int *err,
+                           cudaStream_t st);
+void launch_tf32_split(const float *a, size_t n, float *hi, float *lo, cudaStream_t st);
+
+// TF32 high part of a float (low 13 mantissa bits cleared); a - hi is exact.
+__device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
 
 // Occupancy-based persistent grid sizes.
 void configure_grids(Problem &P, int sm_count);

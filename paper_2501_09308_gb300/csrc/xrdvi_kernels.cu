@@ -233,7 +233,11 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
             a.eps[base + j] = e[j];
         }
         const float h = expf(u[0]);
-        if (a.H) a.H[static_cast<size_t>(s) * a.Kpad + k] = h;
+        if (a.H) {   // TF32 hi / lo parts for the forward GEMM
+            const float hh = tf32_hi(h);
+            a.H[static_cast<size_t>(s) * a.Kpad + k] = hh;
+            a.H[static_cast<size_t>(a.S) * a.Kpad + static_cast<size_t>(s) * a.Kpad + k] = h - hh;
+        }
         const float mu = u[1];
         const float w = expf(u[2]);
         const float r = sigmoidf(u[3]);
@@ -342,6 +346,7 @@ struct ProfArgs {
     int *counter;      // work counter of this kernel (zeroed by k_sample)
     int gauss;         // Gaussian likelihood variant
     const float *csec; // [N] cos(x/2) of the angle-dependent width variant (null: constant width)
+    float *ghl;        // [2*S*Npad] TF32 hi / lo parts of g (shared-shape variant; null otherwise)
     const float *Tb;   // [3*N] Chebyshev terms (fitted background; null: fixed background)
     float *bgpart;     // [S*T*3] per-(sample, tile) sums of g B(beta) T_j
 };
@@ -750,6 +755,11 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
         if (a.f_out) a.f_out[static_cast<size_t>(s) * a.N + i] = f;
     }
     a.g[static_cast<size_t>(s) * a.Npad + i] = gv;
+    if (a.ghl) {   // shared-shape variant: TF32 hi / lo parts for the backward GEMM
+        const float gh = tf32_hi(gv);
+        a.ghl[static_cast<size_t>(s) * a.Npad + i] = gh;
+        a.ghl[static_cast<size_t>(a.S) * a.Npad + static_cast<size_t>(s) * a.Npad + i] = gv - gh;
+    }
     dev = warp_sumf(dev);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) shf[w] = dev;
@@ -1040,6 +1050,8 @@ struct GradArgs {
     const double *lq;   // [S] ln q(u_s) (importance-weighted objective)
     double *iw;         // [S] normalised importance weights (null: the ELBO)
     int Tg;             // tiles per (sample, phase) record of gpart (T, or 1 for the shared-shape variant)
+    // FP32 prior constants of the per-sample gradient
+    float pr_lambda, pr_mu_isd2, pr_w_shape, pr_w_rate, pr_alpha_mean, pr_alpha_isd2;
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -1104,7 +1116,6 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
     const int s0 = sm * a.S_sub + static_cast<int>((static_cast<long long>(a.S_sub) * b) / a.NB);
     const int s1 = sm * a.S_sub + static_cast<int>((static_cast<long long>(a.S_sub) * (b + 1)) / a.NB);
     double accl[5] = {0, 0, 0, 0, 0}, acce[5] = {0, 0, 0, 0, 0};
-    const double ln2 = kLn2;
     for (int c0 = s0; c0 < s1; c0 += 32) {
         const int nc = s1 - c0 < 32 ? s1 - c0 : 32;
         for (int i = warp; i < nc; i += kWarps) {
@@ -1132,38 +1143,39 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         }
         __syncthreads();
         if (warp == 0 && lane < nc) {
-            double q[kGradSums];
+            // per-sample gradient in FP32 (its inputs are FP32 sums; FP64 keeps
+            // the accumulation over samples, where the terms cancel)
+            float q[kGradSums];
 #pragma unroll
             for (int j = 0; j < kGradSums; ++j) q[j] = qs[lane][j];
             const size_t sk = static_cast<size_t>(c0 + lane) * a.K + k;
             const float *th = a.theta + sk * 5;
             const float *ep = a.eps + sk * 5;
-            const double h = th[0], mu = th[1], w = th[2], r = th[3], al = th[4];
-            const bool clamped = !(th[4] > static_cast<float>(a.pr.alpha_min));
-            const double acl = clamped ? static_cast<double>(static_cast<float>(a.pr.alpha_min)) : al;
-            const double sl = 2.0 / w, sr = 2.0 / (acl * w);
+            const float h = th[0], mu = th[1], w = th[2], r = th[3], al = th[4];
+            const float amin = static_cast<float>(a.pr.alpha_min);
+            const bool clamped = !(al > amin);
+            const float acl = clamped ? amin : al;
+            const float sl = __fdiv_rn(2.f, w), sr = __fdiv_rn(2.f, acl * w);
+            const float ln2f = static_cast<float>(kLn2);
             // side splits: X+ = (X + Xs)/2 (d >= 0), X- = (X - Xs)/2 (d < 0)
-            const double AGp = 0.5 * (q[2] + q[4]), AGm = 0.5 * (q[2] - q[4]);
-            const double ALp = 0.5 * (q[3] + q[5]), ALm = 0.5 * (q[3] - q[5]);
-            const double BGp = 0.5 * (q[6] + q[8]), BLp = 0.5 * (q[7] + q[9]);
-            double G[5];
+            const float AGp = 0.5f * (q[2] + q[4]), AGm = 0.5f * (q[2] - q[4]);
+            const float ALp = 0.5f * (q[3] + q[5]), ALm = 0.5f * (q[3] - q[5]);
+            const float BGp = 0.5f * (q[6] + q[8]), BLp = 0.5f * (q[7] + q[9]);
+            float G[5];
             // likelihood part (chained to u) + prior/Jacobian part
-            G[0] = h * ((1.0 - r) * q[0] + r * q[1]) + (1.0 - a.pr.lambda * h);
-            G[1] = 2.0 * h * ((1.0 - r) * ln2 * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
-                   mu / (a.pr.mu_sd * a.pr.mu_sd);
-            G[2] = 2.0 * h * ((1.0 - r) * ln2 * q[6] + r * q[7]) + (a.pr.w_shape - a.pr.w_rate * w);
-            G[3] = r * (1.0 - r) * h * (q[1] - q[0]) + (1.0 - 2.0 * r);
-            const double gal = clamped ? 0.0 : (2.0 * h / acl) * ((1.0 - r) * ln2 * BGp + r * BLp);
-            G[4] = gal - (al - a.pr.alpha_mean) / (a.pr.alpha_sd * a.pr.alpha_sd);
-            if (a.iw) {   // importance-weighted objective: weight w_s / sum w
-                const double wt = __ldcg(&a.iw[c0 + lane]);
-#pragma unroll
-                for (int j = 0; j < 5; ++j) G[j] *= wt;
-            }
+            G[0] = h * ((1.f - r) * q[0] + r * q[1]) + (1.f - a.pr_lambda * h);
+            G[1] = 2.f * h * ((1.f - r) * ln2f * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
+                   mu * a.pr_mu_isd2;
+            G[2] = 2.f * h * ((1.f - r) * ln2f * q[6] + r * q[7]) + (a.pr_w_shape - a.pr_w_rate * w);
+            G[3] = r * (1.f - r) * h * (q[1] - q[0]) + (1.f - 2.f * r);
+            const float gal = clamped ? 0.f : __fdiv_rn(2.f * h, acl) * ((1.f - r) * ln2f * BGp + r * BLp);
+            G[4] = gal - (al - a.pr_alpha_mean) * a.pr_alpha_isd2;
+            const double wt = a.iw ? __ldcg(&a.iw[c0 + lane]) : 1.0;   // importance weight w_s / sum w
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
-                accl[j] += G[j];
-                acce[j] += G[j] * static_cast<double>(ep[j]);
+                const double gj = a.iw ? wt * static_cast<double>(G[j]) : static_cast<double>(G[j]);
+                accl[j] += gj;
+                acce[j] += gj * static_cast<double>(ep[j]);
             }
         }
         __syncthreads();
@@ -1215,8 +1227,9 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             const double vv = a.ac.b2 * static_cast<double>(a.v[idx]) + (1.0 - a.ac.b2) * gm * gm;
             a.m[idx] = static_cast<float>(mm);
             a.v[idx] = static_cast<float>(vv);
-            const double c1 = 1.0 - pow(static_cast<double>(a.ac.b1), t);
-            const double c2 = 1.0 - pow(static_cast<double>(a.ac.b2), t);
+            // bias corrections in FP32 (a few ulps; FP64 pow is slow on this part)
+            const double c1 = 1.0 - static_cast<double>(powf(a.ac.b1, static_cast<float>(t)));
+            const double c2 = 1.0 - static_cast<double>(powf(a.ac.b2, static_cast<float>(t)));
             const double step = a.ac.lr * (mm / c1) / (sqrt(vv / c2) + a.ac.eps);
             if (!is_raw) {
                 a.loc_out[bk * 5 + j] = static_cast<float>(a.loc_in[bk * 5 + j] - step);
@@ -1482,6 +1495,7 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     a.fpart = W.fpart; a.counter = W.counters;
     a.gauss = P.gauss ? 1 : 0;
     a.csec = P.csec;
+    a.ghl = W.ghl;
     if (P.bgfit) a.bg = P.Bb;   // fitted background: the current curve B(beta)
     a.bgpart = P.bgfit ? W.bgpart : nullptr;
     a.Tb = a.bgpart ? P.Tb : nullptr;   // beta sums only where the sample set keeps them
@@ -1606,6 +1620,12 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.tail_sum = W.tail_sum; a.tail_start = W.tail_start;
     a.lq = W.lq; a.iw = W.iw;
     a.Tg = W.shared ? 1 : P.T;
+    a.pr_lambda = static_cast<float>(P.prior.lambda);
+    a.pr_mu_isd2 = static_cast<float>(1.0 / (P.prior.mu_sd * P.prior.mu_sd));
+    a.pr_w_shape = static_cast<float>(P.prior.w_shape);
+    a.pr_w_rate = static_cast<float>(P.prior.w_rate);
+    a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
+    a.pr_alpha_isd2 = static_cast<float>(1.0 / (P.prior.alpha_sd * P.prior.alpha_sd));
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
     const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;
