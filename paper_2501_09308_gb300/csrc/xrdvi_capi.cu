@@ -510,6 +510,14 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         XR_C(c->alloc(&W.gemm_work, gemm_workspace_floats(W.S, nk, W.gemm_splits)));
         XR_C(c->alloc(&W.gemm_err, 1));
         if (gemm_configure() != cudaSuccess) return bail(fail(XRDVI_ECUDA, "tensor-core GEMM set-up failed"));
+        // the two contractions on fixed buffers: TMA descriptors built once
+        const size_t nh = static_cast<size_t>(W.S) * W.Kpad, nc = static_cast<size_t>(P.Npad) * W.Kpad;
+        const size_t ng = static_cast<size_t>(W.S) * P.Npad, nd = static_cast<size_t>(nk) * P.Npad;
+        if (!gemm_plan(W.plan_fwd, W.S, N, W.Kpad, W.H, W.H + nh, W.Kpad, W.Ct, W.Ct + nc, W.Kpad, W.fpart, P.Npad,
+                       1, nullptr, W.gemm_err) ||
+            !gemm_plan(W.plan_bwd, W.S, nk, P.Npad, W.ghl, W.ghl + ng, P.Npad, W.D, W.D + nd, P.Npad, W.gpart, nk,
+                       W.gemm_splits, W.gemm_work, W.gemm_err))
+            return bail(fail(XRDVI_ECUDA, "tensor-core GEMM: TMA descriptor encoding failed"));
     }
     XR_C(c->alloc(&c->trace, kTraceCap));
     XR_C(c->alloc(&c->step, 1));

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/xrdvi.h"
@@ -65,6 +66,15 @@ struct PriorConst {
     double lp_const;      // parameter-free part of ln p(theta) per phase
 };
 
+// A tensor-core GEMM out[M x N] = A[M x K] . B[N x K]^T with its TMA
+// descriptors (A, B as TF32 hi / lo parts), built once for fixed buffers.
+struct GemmPlan {
+    CUtensorMap tAh, tAl, tBh, tBl;
+    int M = 0, N = 0, K = 0, ldo = 0, tn = 64, nkb = 0, kb_per_split = 1, splits = 1;
+    float *out = nullptr, *work = nullptr;
+    int *err = nullptr;
+};
+
 // Buffers of one sample set (the fit's S, or the posterior's S_post).
 struct Workspace {
     int S = 0;
@@ -106,6 +116,7 @@ struct Workspace {
     float *gemm_work = nullptr;       // split-K partials of the backward GEMM
     int gemm_splits = 1;
     int *gemm_err = nullptr;          // set if a tensor-core pipeline wait gives up
+    GemmPlan plan_fwd, plan_bwd;      // the forward and backward contractions
     int tail_start = 0;
     int C = 1;                   // phase chunks
     int chunk[kMaxChunks + 1] = {0};
@@ -219,16 +230,18 @@ void launch_shared_backward(const Problem &P, Workspace &W, cudaStream_t st);
 
 // Tensor-core GEMM (xrdvi_tc.cu): out[M x N] = A[M x K] . B[N x K]^T, A and B
 // given as TF32 hi / lo parts (launch_tf32_split), row-major with K contiguous
-// (K, lda, ldb multiples of 4, 16-byte aligned), 3xTF32 on tcgen05 with FP32
-// accumulation; split-K partials (work, gemm_workspace_floats) are added in a
-// fixed order.  err (device int) is set if an mbarrier wait gives up.
+// (K, lda, ldb multiples of 4, 16-byte aligned), loaded by TMA and multiplied
+// 3xTF32 on tcgen05 with FP32 accumulation; split-K partials (work,
+// gemm_workspace_floats) are added in a fixed order.  gemm_plan encodes the
+// TMA descriptors (false if that fails); err (device int) is set if an
+// mbarrier wait gives up.
 size_t gemm_smem_bytes();
 cudaError_t gemm_configure();   // shared-memory attribute of the GEMM kernel (call before capture)
 int gemm_splits(int M, int N, int K, int sm_count);
 size_t gemm_workspace_floats(int M, int N, int splits);
-void launch_gemm_nt_tf32x3(int M, int N, int K, const float *Ahi, const float *Alo, int lda, const float *Bhi,
-                           const float *Blo, int ldb, float *out, int ldo, int splits, float *work, int *err,
-                           cudaStream_t st);
+bool gemm_plan(GemmPlan &p, int M, int N, int K, const float *Ahi, const float *Alo, int lda, const float *Bhi,
+               const float *Blo, int ldb, float *out, int ldo, int splits, float *work, int *err);
+void launch_gemm(const GemmPlan &p, cudaStream_t st);
 void launch_tf32_split(const float *a, size_t n, float *hi, float *lo, cudaStream_t st);
 
 // TF32 high part of a float (low 13 mantissa bits cleared); a - hi is exact.

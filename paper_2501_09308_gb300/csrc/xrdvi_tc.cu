@@ -10,7 +10,9 @@
 // with a 3xTF32 split for FP32-level accuracy: a = a_hi + a_lo with a_hi the
 // value truncated to TF32 and a_lo = a - a_hi, and
 //   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdint>
 #include <string>
@@ -22,12 +24,11 @@ namespace xrdvi {
 namespace {
 
 constexpr int kGM = 128;        // tile rows (MMA M)
-constexpr int kGKB = 16;        // reduction elements per stage (2 MMA steps of 8)
-constexpr int kGThreads = 128;  // 4 warps: warp w reads TMEM lanes 32w..32w+31
+constexpr int kGKB = 32;        // reduction elements per stage: one 128-byte row (4 MMA steps of 8)
+constexpr int kGThreads = 128;  // warp 0: TMA producer, warp 1: MMA issuer, warp 2: TMEM owner; all: epilogue
 constexpr int kStages = 3;      // stages in flight
-constexpr uint32_t kSBO = 512;  // bytes between 8-row groups (4 cores of 128 B along K)
-constexpr uint32_t kTileA = kGM * kGKB * 4;   // bytes of one A operand tile (8 KB)
-constexpr uint32_t kWaitLimit = 1u << 22;     // mbarrier polls before giving up
+constexpr uint32_t kTileA = kGM * kGKB * 4;   // bytes of one A operand tile (16 KB)
+constexpr uint32_t kWaitLimit = 1u << 24;     // mbarrier polls before giving up
 
 // Per tile width kGN (MMA N, TMEM columns): B operand tile and stage bytes.
 template <int kGN>
@@ -46,19 +47,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row r, reduction index e < kGKB) in a K-major tile
-// without swizzle built from core matrices of 8 rows x 16 bytes: the cores
-// along K of one 8-row group are 128 bytes apart (leading byte offset), the
-// 8-row groups kSBO bytes apart (stride byte offset).
-__device__ __forceinline__ uint32_t core_off(int r, int e) {
-    return static_cast<uint32_t>((r >> 3) * kSBO + (e >> 2) * 128 + (r & 7) * 16 + (e & 3) * 4);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (all >> 4), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(lbo >> 4) << 16) |
-           (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor (tcgen05) of a K-major operand in the
+// 128-byte swizzled layout that TMA writes: rows of 128 bytes, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1, layout type
+// SWIZZLE_128B; the leading byte offset is unused for this layout (encoded 1).
+// A k-step of 8 TF32 elements starts 32 bytes further along the row.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (static_cast<uint64_t>(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
@@ -79,6 +75,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
     return false;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// TMA: 2D tile (x = reduction index, y = row) into shared memory, completion
+// counted on the mbarrier in bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(y)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
@@ -95,18 +108,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16-byte asynchronous copy global -> shared (L2 only); src_bytes = 0 fills zeros.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int kN>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory"); }
-
 struct GemmArgs {
     int M, N, K;             // out[M x N] = A[M x K] . B[N x K]^T (row-major, K contiguous)
-    const float *Ahi, *Alo, *Bhi, *Blo;   // TF32 hi and lo parts (tf32_split)
-    int lda, ldb;
     float *out;              // split s writes out + s * split_stride (row stride ldo)
     int ldo;
     size_t split_stride;
@@ -114,116 +117,107 @@ struct GemmArgs {
     int *err;                // set to 1 if an mbarrier wait gives up
 };
 
-// Issues the copies of reduction block kb (kGKB elements) of A (kGM rows) and
-// B (kGN rows), hi and lo, into stage st in the core-matrix layout: one core
-// row (4 elements, 16 bytes) per copy; rows beyond M / N and elements beyond
-// K are zero-filled.
-template <int kGN>
-__device__ __forceinline__ void issue_stage(const GemmArgs &a, uint32_t st, int m0, int n0, int kb) {
-    constexpr uint32_t kTileB = TileCfg<kGN>::kTileB;
-    const int k0 = kb * kGKB;
-    for (int idx = threadIdx.x; idx < (kGM + kGN) * (kGKB / 4); idx += kGThreads) {
-        const bool isA = idx < kGM * (kGKB / 4);
-        const int j = isA ? idx : idx - kGM * (kGKB / 4);
-        const int r = j / (kGKB / 4), q = j % (kGKB / 4);
-        const int row = (isA ? m0 : n0) + r, k = k0 + 4 * q;
-        const bool ok = row < (isA ? a.M : a.N) && k < a.K;
-        const size_t off = ok ? static_cast<size_t>(row) * (isA ? a.lda : a.ldb) + k : 0;
-        const float *hi = (isA ? a.Ahi : a.Bhi) + off, *lo = (isA ? a.Alo : a.Blo) + off;
-        const uint32_t o = core_off(r, 4 * q);
-        const uint32_t base = isA ? st : st + 2 * kTileA;
-        const uint32_t tile = isA ? kTileA : kTileB;
-        cp_async16(base + o, hi, ok ? 16u : 0u);
-        cp_async16(base + tile + o, lo, ok ? 16u : 0u);
-    }
-}
-
 // One output tile of kGM x kGN per CTA over one split of the reduction.
-// kStages stages of copies in flight; one thread issues 2 k-steps x 3 MMAs
-// per stage (3xTF32) and commits them to the stage's mbarrier, which is
-// awaited before the stage is refilled.
+// Warp-specialised pipeline over kStages shared-memory stages: the producer
+// waits for a stage to be empty, arms its full barrier with the stage's bytes
+// and issues four TMA tile loads (A and B, TF32 hi and lo parts); the MMA
+// issuer waits for the full barrier, issues 4 k-steps x 3 MMAs (3xTF32) into
+// the TMEM accumulator and commits them to the stage's empty barrier; after
+// the last stage a commit to the done barrier releases the epilogue, in which
+// every warp reads its 32 TMEM lanes.  Every wait is bounded.
 template <int kGN>
-__global__ void __launch_bounds__(kGThreads) k_gemm_nt_tf32x3(GemmArgs a) {
+__global__ void __launch_bounds__(kGThreads) k_gemm_nt_tf32x3(const __grid_constant__ CUtensorMap tAh,
+                                                              const __grid_constant__ CUtensorMap tAl,
+                                                              const __grid_constant__ CUtensorMap tBh,
+                                                              const __grid_constant__ CUtensorMap tBl, GemmArgs a) {
     using Cfg = TileCfg<kGN>;
     constexpr uint32_t kTileB = Cfg::kTileB, kStage = Cfg::kStage;
     extern __shared__ uint8_t g_smem_raw[];
-    __shared__ __align__(8) uint64_t s_mbar[kStages];
+    __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    uint8_t *smem = g_smem_raw + ((1024u - (smem_addr(g_smem_raw) & 1023u)) & 1023u);   // 1 KB aligned
+    uint8_t *smem = g_smem_raw + ((1024u - (smem_addr(g_smem_raw) & 1023u)) & 1023u);   // 1 KB aligned (swizzle)
     const uint32_t sbase = smem_addr(smem);
     const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN, split = blockIdx.z;
     const int kb0 = split * a.kb_per_split;
-    const int kb1 = min(a.nkb, kb0 + a.kb_per_split);
-    const int nk = kb1 - kb0;
+    const int nk = min(a.nkb, kb0 + a.kb_per_split) - kb0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) mbar_init(smem_addr(&s_mbar[i]), 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(smem_addr(&s_full[i]), 1);
+            mbar_init(smem_addr(&s_empty[i]), 1);
+        }
+        mbar_init(smem_addr(&s_done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
-    if (warp == 0) {
+    if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
                      "r"(static_cast<uint32_t>(kGN)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    // prologue: the first kStages - 1 blocks in flight
-#pragma unroll
-    for (int i = 0; i < kStages - 1; ++i) {
-        if (i < nk) issue_stage<kGN>(a, sbase + i * kStage, m0, n0, kb0 + i);
-        cp_async_commit();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    for (int i = 0; i < nk; ++i) {
-        const int st = i % kStages;
-        cp_async_wait<kStages - 2>();   // this thread's copies of block i have landed
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA operand reads
-        __syncthreads();                // ... and every thread's
-        if (threadIdx.x == 0) {
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % kStages, n = i / kStages;
+            if (n > 0 && !mbar_wait(smem_addr(&s_empty[st]), static_cast<uint32_t>((n - 1) & 1))) {
+                s_abort = 1;
+                break;
+            }
+            if (*reinterpret_cast<volatile int *>(&s_abort)) break;
+            const uint32_t full = smem_addr(&s_full[st]);
+            const uint32_t base = sbase + st * kStage;
+            const int k0 = (kb0 + i) * kGKB;
+            mbar_expect_tx(full, kStage);
+            tma_load_2d(base, &tAh, k0, m0, full);
+            tma_load_2d(base + kTileA, &tAl, k0, m0, full);
+            tma_load_2d(base + 2 * kTileA, &tBh, k0, n0, full);
+            tma_load_2d(base + 2 * kTileA + kTileB, &tBl, k0, n0, full);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        bool ok = true;
+        for (int i = 0; i < nk && ok; ++i) {
+            const int st = i % kStages, n = i / kStages;
+            if (!mbar_wait(smem_addr(&s_full[st]), static_cast<uint32_t>(n & 1))) {
+                s_abort = 1;
+                ok = false;
+                break;
+            }
             tc_fence_after();
             const uint32_t base = sbase + st * kStage;
 #pragma unroll
             for (int t = 0; t < kGKB / 8; ++t) {
-                const uint32_t off = static_cast<uint32_t>(t) * 256u;   // two 128-byte cores per k-step
-                const uint64_t ahi = smem_desc(base + off, 128, kSBO), alo = smem_desc(base + kTileA + off, 128, kSBO);
-                const uint64_t bhi = smem_desc(base + 2 * kTileA + off, 128, kSBO);
-                const uint64_t blo = smem_desc(base + 2 * kTileA + kTileB + off, 128, kSBO);
+                const uint32_t off = static_cast<uint32_t>(t) * 32u;   // 8 TF32 = 32 bytes along the row
+                const uint64_t ahi = smem_desc_sw128(base + off), alo = smem_desc_sw128(base + kTileA + off);
+                const uint64_t bhi = smem_desc_sw128(base + 2 * kTileA + off);
+                const uint64_t blo = smem_desc_sw128(base + 2 * kTileA + kTileB + off);
                 mma_tf32(tmem, alo, bhi, Cfg::kIdesc, (i > 0 || t > 0) ? 1u : 0u);
                 mma_tf32(tmem, ahi, blo, Cfg::kIdesc, 1u);
                 mma_tf32(tmem, ahi, bhi, Cfg::kIdesc, 1u);
             }
-            mma_commit(smem_addr(&s_mbar[st]));
-            // the stage refilled next held block i - 1: its MMAs must be done
-            const int prev = i - 1;
-            if (prev >= 0 && prev + kStages < nk &&
-                !mbar_wait(smem_addr(&s_mbar[prev % kStages]), static_cast<uint32_t>((prev / kStages) & 1)))
-                s_abort = 1;
+            mma_commit(smem_addr(&s_empty[st]));
         }
-        __syncthreads();
-        if (s_abort) break;   // uniform: read after the barrier
-        const int nxt = i + kStages - 1;
-        if (nxt < nk) issue_stage<kGN>(a, sbase + (nxt % kStages) * kStage, m0, n0, kb0 + nxt);
-        cp_async_commit();
+        if (ok && nk > 0)
+            mma_commit(smem_addr(&s_done));
+        else
+            mbar_arrive(smem_addr(&s_done));   // nothing to wait for (no blocks, or aborted)
     }
-    cp_async_wait<0>();
-    // wait for the last block's MMAs (a commit tracks all earlier MMAs too);
-    // one thread waits, the barrier publishes the outcome to all
+    // epilogue: every thread waits for the accumulator
+    const bool done = mbar_wait(smem_addr(&s_done), 0u);
     __syncthreads();
-    if (threadIdx.x == 0 && !s_abort && nk > 0 &&
-        !mbar_wait(smem_addr(&s_mbar[(nk - 1) % kStages]), static_cast<uint32_t>(((nk - 1) / kStages) & 1)))
-        s_abort = 1;
-    __syncthreads();
-    const bool ok = !s_abort;
+    const bool ok = done && !*reinterpret_cast<volatile int *>(&s_abort);
     if (!ok && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
     tc_fence_after();
     if (ok) {
-        // epilogue: warp w owns rows 32w..32w+31 of the tile (TMEM lanes)
+        // warp w owns rows 32w..32w+31 of the tile (TMEM lanes)
         const int row = m0 + 32 * warp + lane;
         float *dst = a.out + static_cast<size_t>(split) * a.split_stride + static_cast<size_t>(row) * a.ldo;
-#pragma unroll
+#pragma unroll 1
         for (int c0 = 0; c0 < kGN; c0 += 16) {
             uint32_t v[16];
             const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0);
@@ -253,7 +247,7 @@ __global__ void __launch_bounds__(kGThreads) k_gemm_nt_tf32x3(GemmArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0)
+    if (warp == 2)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(static_cast<uint32_t>(kGN)));
 }
@@ -376,18 +370,14 @@ void launch_shared_forward(const Problem &P, Workspace &W, float *f_out, cudaStr
     s.Ct_lo = W.Ct + static_cast<size_t>(P.Npad) * W.Kpad;
     k_shapes<<<dim3(P.T, P.K), 256, 0, st>>>(s);
     // f_s - B = sum_k h_sk C_k: [S x N] = H [S x Kpad] . Ct [N x Kpad]^T, into the first chunk slot
-    const size_t nh = static_cast<size_t>(W.S) * W.Kpad;
-    launch_gemm_nt_tf32x3(W.S, P.N, W.Kpad, W.H, W.H + nh, W.Kpad, W.Ct, s.Ct_lo, W.Kpad, W.fpart, P.Npad, 1,
-                          nullptr, W.gemm_err, st);
+    launch_gemm(W.plan_fwd, st);
     launch_lik(P, W, f_out, 1, st);
 }
 
 void launch_shared_backward(const Problem &P, Workspace &W, cudaStream_t st) {
     // per (s, k) sums: [S x 10K] = g [S x Npad] . D [10K x Npad]^T  (g = 0 on padding)
-    const int nk = P.K * kGradSums;
-    const size_t ng = static_cast<size_t>(W.S) * P.Npad, nd = static_cast<size_t>(nk) * P.Npad;
-    launch_gemm_nt_tf32x3(W.S, nk, P.Npad, W.ghl, W.ghl + ng, P.Npad, W.D, W.D + nd, P.Npad, W.gpart, nk,
-                          W.gemm_splits, W.gemm_work, W.gemm_err, st);
+    (void)P;
+    launch_gemm(W.plan_bwd, st);
 }
 
 // Tile width: 128 columns where N is wide (fewer re-reads of A), 64 for
@@ -423,33 +413,60 @@ void launch_tf32_split(const float *a, size_t n, float *hi, float *lo, cudaStrea
     if (blocks > 0) k_tf32_split<<<blocks, 256, 0, st>>>(a, n, hi, lo);
 }
 
-void launch_gemm_nt_tf32x3(int M, int N, int K, const float *Ahi, const float *Alo, int lda, const float *Bhi,
-                           const float *Blo, int ldb, float *out, int ldo, int splits, float *work, int *err,
-                           cudaStream_t st) {
-    GemmArgs a;
-    a.M = M; a.N = N; a.K = K; a.Ahi = Ahi; a.Alo = Alo; a.Bhi = Bhi; a.Blo = Blo; a.lda = lda; a.ldb = ldb;
-    a.err = err;
-    a.nkb = (K + kGKB - 1) / kGKB;
-    if (splits < 1) splits = 1;
-    if (splits > a.nkb) splits = a.nkb > 0 ? a.nkb : 1;
-    a.kb_per_split = (a.nkb + splits - 1) / splits;
-    splits = a.nkb > 0 ? (a.nkb + a.kb_per_split - 1) / a.kb_per_split : 1;
-    if (splits == 1) {
-        a.out = out; a.ldo = ldo; a.split_stride = 0;
-    } else {
-        a.out = work; a.ldo = N; a.split_stride = static_cast<size_t>(M) * N;
+// TMA descriptor of a row-major FP32 matrix [rows x K] (row stride ld
+// elements) read in boxes of 32 reduction elements x box_rows rows with the
+// 128-byte swizzle; out-of-range elements read as zero.
+static bool encode_tmap(CUtensorMap *m, const float *ptr, int rows, int K, int ld, int box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f)
+            return false;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
     }
-    const int tn = tile_n(N);
-    dim3 grid((M + kGM - 1) / kGM, (N + tn - 1) / tn, splits);
-    if (tn == 128)
-        k_gemm_nt_tf32x3<128><<<grid, kGThreads, TileCfg<128>::kSmem, st>>>(a);
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(kGKB), static_cast<cuuint32_t>(box_rows)};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool gemm_plan(GemmPlan &p, int M, int N, int K, const float *Ahi, const float *Alo, int lda, const float *Bhi,
+               const float *Blo, int ldb, float *out, int ldo, int splits, float *work, int *err) {
+    p.M = M; p.N = N; p.K = K; p.out = out; p.ldo = ldo; p.work = work; p.err = err;
+    p.tn = tile_n(N);
+    p.nkb = (K + kGKB - 1) / kGKB;
+    if (splits < 1) splits = 1;
+    if (splits > p.nkb) splits = p.nkb > 0 ? p.nkb : 1;
+    p.kb_per_split = (p.nkb + splits - 1) / splits;
+    p.splits = p.nkb > 0 ? (p.nkb + p.kb_per_split - 1) / p.kb_per_split : 1;
+    return encode_tmap(&p.tAh, Ahi, M, K, lda, kGM) && encode_tmap(&p.tAl, Alo, M, K, lda, kGM) &&
+           encode_tmap(&p.tBh, Bhi, N, K, ldb, p.tn) && encode_tmap(&p.tBl, Blo, N, K, ldb, p.tn);
+}
+
+void launch_gemm(const GemmPlan &p, cudaStream_t st) {
+    GemmArgs a;
+    a.M = p.M; a.N = p.N; a.K = p.K; a.err = p.err; a.nkb = p.nkb; a.kb_per_split = p.kb_per_split;
+    if (p.splits == 1) {
+        a.out = p.out; a.ldo = p.ldo; a.split_stride = 0;
+    } else {
+        a.out = p.work; a.ldo = p.N; a.split_stride = static_cast<size_t>(p.M) * p.N;
+    }
+    dim3 grid((p.M + kGM - 1) / kGM, (p.N + p.tn - 1) / p.tn, p.splits);
+    if (p.tn == 128)
+        k_gemm_nt_tf32x3<128><<<grid, kGThreads, TileCfg<128>::kSmem, st>>>(p.tAh, p.tAl, p.tBh, p.tBl, a);
     else
-        k_gemm_nt_tf32x3<64><<<grid, kGThreads, TileCfg<64>::kSmem, st>>>(a);
-    if (splits > 1) {
-        const size_t total = static_cast<size_t>(M) * N;
+        k_gemm_nt_tf32x3<64><<<grid, kGThreads, TileCfg<64>::kSmem, st>>>(p.tAh, p.tAl, p.tBh, p.tBl, a);
+    if (p.splits > 1) {
+        const size_t total = static_cast<size_t>(p.M) * p.N;
         int blocks = static_cast<int>((total + 255) / 256);
         blocks = blocks < 4096 ? blocks : 4096;
-        k_splitk_reduce<<<blocks, 256, 0, st>>>(work, splits, a.split_stride, M, N, N, out, ldo);
+        k_splitk_reduce<<<blocks, 256, 0, st>>>(p.work, p.splits, a.split_stride, p.M, p.N, p.N, p.out, p.ldo);
     }
 }
 
@@ -482,9 +499,13 @@ extern "C" xrdvi_status xrdvi_gemm_nt_tf32x3(int32_t M, int32_t N, int32_t K, co
     if (e == cudaSuccess) {
         xrdvi::launch_tf32_split(d_A, na, ahl, ahl + na, st);
         xrdvi::launch_tf32_split(d_B, nb, bhl, bhl + nb, st);
-        xrdvi::launch_gemm_nt_tf32x3(M, N, K, ahl, ahl + na, lda, bhl, bhl + nb, ldb, d_C, ldc, splits, work, err,
-                                     st);
-        e = cudaGetLastError();
+        xrdvi::GemmPlan plan;
+        if (!xrdvi::gemm_plan(plan, M, N, K, ahl, ahl + na, lda, bhl, bhl + nb, ldb, d_C, ldc, splits, work, err)) {
+            e = cudaErrorInvalidValue;
+        } else {
+            xrdvi::launch_gemm(plan, st);
+            e = cudaGetLastError();
+        }
     }
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
