@@ -24,6 +24,7 @@ constexpr int kGradSums = 10;
 // Phases are split into up to kMaxChunks chunks of similar peak count so that
 // the profile kernels have enough equal-sized work items to fill the GPU.
 constexpr int kMaxChunks = 8;
+constexpr int kItemsPerWarp = 8;   // profile work items per resident warp the phase chunking aims for
 // Work counters of the profile kernels of one sample set.
 constexpr int kCounters = 4;
 // Sample blocks per phase in the gradient reduction.

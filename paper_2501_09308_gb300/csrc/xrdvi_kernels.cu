@@ -1510,7 +1510,7 @@ static int grid_for(int grid_max, int items) {
 void choose_chunks(const Problem &P, const int *offsets, int S, Workspace &W, int max_chunks) {
     const long long base = static_cast<long long>(S) * P.T;
     const long long resident = static_cast<long long>(P.grid_fwd) * kWarps;
-    int C = static_cast<int>((4 * resident + base - 1) / base);
+    int C = static_cast<int>((kItemsPerWarp * resident + base - 1) / base);
     C = C < 1 ? 1 : C;
     C = C > kMaxChunks ? kMaxChunks : C;
     C = C > max_chunks ? max_chunks : C;

@@ -95,7 +95,7 @@ extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, i
     // warps (up to 160 SMs x 4 blocks x 8 warps), so C is never underestimated
     auto chunks = [&](size_t s) {
         const size_t resident = 160 * 4 * kWarps, items = s * T;
-        size_t c = (4 * resident + items - 1) / items;
+        size_t c = (kItemsPerWarp * resident + items - 1) / items;
         c = std::min<size_t>(c, kMaxChunks);
         c = std::min<size_t>(c, static_cast<size_t>(K));
         return std::max<size_t>(c, 1);
