@@ -110,6 +110,13 @@ typedef struct {
  * N(0, bg_prior_sd^2) and is point-estimated (ln p(beta) joins every draw's
  * log joint, beta takes the Adam step rule).  xrdvi_get_background reads it. */
 #define XRDVI_FLAG_FIT_BACKGROUND (1u << 6)
+/* Shape parameters held fixed (model options): the Gauss-Lorentz ratio r at
+ * fix_r_value and / or the asymmetry alpha at fix_alpha_value, for every
+ * phase.  A fixed parameter is a constant of the model, not part of q: it has
+ * no prior, Jacobian, entropy or ln q term, its gradient is zero and its
+ * variational parameters are not updated. */
+#define XRDVI_FLAG_FIX_R      (1u << 7)
+#define XRDVI_FLAG_FIX_ALPHA  (1u << 8)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */
@@ -126,11 +133,13 @@ typedef struct {
     float init_sigma;         /* initial sigma of every q factor                   */
     uint32_t flags;           /* XRDVI_FLAG_*                                      */
     float bg_prior_sd;        /* prior sd of the fitted-background coefficients    */
+    float fix_r_value;        /* r with XRDVI_FLAG_FIX_R (in [0, 1])              */
+    float fix_alpha_value;    /* alpha with XRDVI_FLAG_FIX_ALPHA                  */
 } xrdvi_config;
 
 /* Fills the defaults: S 256, Adam lr 0.01 betas (0.9, 0.999) eps 1e-8, seed 0,
  * priors of Appendix B.2, alpha_min 1e-3, init_h_frac 0.1, init_sigma 0.1,
- * bg_prior_sd 0.1. */
+ * bg_prior_sd 0.1, fix_r_value 0.5, fix_alpha_value 1. */
 void xrdvi_config_default(xrdvi_config *cfg);
 
 /* Validates and uploads the problem (one host-to-device copy), computes

@@ -54,7 +54,8 @@ class Variant(ctypes.Structure):
     _PD = ctypes.POINTER(ctypes.c_double)
     _fields_ = [("lik", ctypes.c_int), ("iw", ctypes.c_int), ("shared", ctypes.c_int), ("sec", ctypes.c_int),
                 ("bgfit", ctypes.c_int), ("bg_sd", ctypes.c_double), ("beta", _PD), ("grad_beta", _PD),
-                ("m_beta", _PD), ("v_beta", _PD)]
+                ("m_beta", _PD), ("v_beta", _PD), ("fix_r", ctypes.c_int), ("fix_alpha", ctypes.c_int),
+                ("r_value", ctypes.c_double), ("alpha_value", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -118,7 +119,9 @@ def lib():
             L.orc_loglik_gauss.restype = d
             L.orc_loglik_gauss.argtypes = [i32, pd, pd]
             L.orc_iw_weights.restype = d
-            L.orc_iw_weights.argtypes = [i32, i32, pd, pd, pd, pd, pd]
+            L.orc_iw_weights.argtypes = [i32, i32, pd, pd, pd, pd, P(Variant), pd]
+            L.orc_fixed_lpj.restype = d
+            L.orc_fixed_lpj.argtypes = [P(Prior), P(Variant), pd, pd]
             L.orc_adam_step.argtypes = [i32, pd, pd, pd, pd, i32, d, d, d, d]
             L.orc_fit.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), i32, u64, i32, i32,
                                   d, d, d, d, pd, pd, pd, pd, pd]
@@ -146,7 +149,7 @@ class Problem:
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
                  w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
                  likelihood="poisson", objective="elbo", shapes="independent", width="constant",
-                 background="fixed", bg_sd=0.1):
+                 background="fixed", bg_sd=0.1, fix_r=None, fix_alpha=None):
         # variants: likelihood "poisson" (the paper's) or "gauss" (variance
         # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound);
         # shapes "independent" or "shared" (one shape draw per step); width
@@ -162,8 +165,12 @@ class Problem:
         # fitted background: correction coefficients beta[3] (point estimate)
         self.beta = np.zeros(3)
         self._gb = np.zeros(3)
+        # fix_r / fix_alpha: r / alpha held at that value (a model constant, not in q)
+        self.fix_r, self.fix_alpha = fix_r, fix_alpha
         self.variant = Variant(self.lik, self.iw, self.shared, self.sec, self.bgfit, float(bg_sd),
-                               _pd(self.beta), _pd(self._gb), None, None)
+                               _pd(self.beta), _pd(self._gb), None, None,
+                               0 if fix_r is None else 1, 0 if fix_alpha is None else 1,
+                               0.0 if fix_r is None else float(fix_r), 0.0 if fix_alpha is None else float(fix_alpha))
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -172,6 +179,10 @@ class Problem:
             # lambda = 1 / eta with eta = max(Y - B)  (Sec. 2.2)
             lam = 1.0 / float(np.max(self.y - self.bg))
         self.prior = Prior(lam, mu_sd, alpha_mean, alpha_sd, w_shape, w_rate, alpha_min)
+
+    def free(self, j):
+        """Is parameter j (h, mu, w, r, alpha) part of q?"""
+        return not ((j == 3 and self.fix_r is not None) or (j == 4 and self.fix_alpha is not None))
 
     @classmethod
     def from_instance(cls, inst, **kw):
@@ -215,10 +226,21 @@ class Problem:
         u = np.zeros((S, self.K, 5))
         th = np.zeros((S, self.K, 5))
         lib().orc_theta(S, self.K, _pd(f64(loc)), _pd(f64(raw)), _pd(eps), _pd(u), _pd(th))
+        if self.fix_r is not None:
+            th[:, :, 3] = self.fix_r
+        if self.fix_alpha is not None:
+            th[:, :, 4] = self.fix_alpha
         return u, th
 
     def log_prior(self, th_k):
         return lib().orc_log_prior(ctypes.byref(self.prior), _pd(f64(th_k)))
+
+    def log_prior_jac(self, u_k, th_k):
+        """ln p(theta) + ln|J| of one phase of one draw, without the terms of
+        parameters held fixed."""
+        u_k, th_k = f64(u_k), f64(th_k)
+        return (lib().orc_log_prior(ctypes.byref(self.prior), _pd(th_k)) + lib().orc_log_jac(_pd(u_k))
+                - lib().orc_fixed_lpj(ctypes.byref(self.prior), ctypes.byref(self.variant), _pd(u_k), _pd(th_k)))
 
     def elbo_grad(self, loc, raw, eps, want_f=False):
         """ELBO estimate + per-sample LL, log prior+Jacobian and the gradient
@@ -285,7 +307,7 @@ def iw_weights(raw, eps, ll, lpj):
     eps = f64(eps)
     S, K = eps.shape[0], eps.shape[1]
     wt = np.zeros(S)
-    L = lib().orc_iw_weights(K, S, _pd(f64(raw)), _pd(eps), _pd(f64(ll)), _pd(f64(lpj)), _pd(wt))
+    L = lib().orc_iw_weights(K, S, _pd(f64(raw)), _pd(eps), _pd(f64(ll)), _pd(f64(lpj)), None, _pd(wt))
     return L, wt
 
 

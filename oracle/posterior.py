@@ -127,11 +127,15 @@ def all_combination_logp(pi):
     return np.where(bits, np.log(pi)[None, :], np.log1p(-pi)[None, :]).sum(axis=1)
 
 
-def log_q(raw, eps):
-    """ln q(u) of the mean-field normal at u = loc + sigma * eps, per sample."""
+def log_q(raw, eps, free=None):
+    """ln q(u) of the mean-field normal at u = loc + sigma * eps, per sample
+    (free[5]: which parameters are part of q; default all)."""
     sig = np.vectorize(softplus)(f64(raw))
     e = f64(eps)
-    return np.sum(-0.5 * e * e - np.log(sig)[None] - 0.5 * math.log(2 * math.pi), axis=(1, 2))
+    terms = -0.5 * e * e - np.log(sig)[None] - 0.5 * math.log(2 * math.pi)
+    if free is not None:
+        terms = terms * np.asarray(free, dtype=np.float64)[None, None, :]
+    return np.sum(terms, axis=(1, 2))
 
 
 def posterior(prob: Problem, loc, raw, S_post, seed=None, eps=None, top_m=8, threshold=0.01):
@@ -146,8 +150,8 @@ def posterior(prob: Problem, loc, raw, S_post, seed=None, eps=None, top_m=8, thr
     lpj = np.zeros(S_post)
     for s in range(S_post):
         for k in range(prob.K):
-            lpj[s] += prob.log_prior(th[s, k]) + lib().orc_log_jac(_pd(f64(u[s, k])))
-    lq = log_q(raw, eps)
+            lpj[s] += prob.log_prior_jac(u[s, k], th[s, k])
+    lq = log_q(raw, eps, [prob.free(j) for j in range(5)])
     logw = ll + lpj - lq
     areas = phase_areas(prob, th)
     bits = inclusion_bits(areas, threshold)

@@ -293,6 +293,9 @@ typedef struct {
  *   sec     1: angle-dependent width, every side width at point x multiplied
  *           by sec(theta), theta = x / 2 (x = 2-theta in degrees)   (orc_sec)
  *   bgfit   1: background fitted in-model                   (orc_background)
+ *   fix_r, fix_alpha  1: r / alpha held at a given value: a constant of the
+ *           model, not a parameter of q (no prior, Jacobian, entropy, ln q
+ *           or gradient term; orc_fixed_terms)
  */
 typedef struct {
     int lik, iw, shared, sec;
@@ -301,6 +304,8 @@ typedef struct {
     double *beta;         /* [3] coefficients (in; orc_fit_ex updates them)        */
     double *grad_beta;    /* [3] d objective / d beta (orc_elbo_grad_ex; may be NULL) */
     double *m_beta, *v_beta;   /* [3] their Adam moments (orc_fit_ex)              */
+    int fix_r, fix_alpha;      /* 1: r / alpha held at r_value / alpha_value       */
+    double r_value, alpha_value;
 } orc_variant;
 
 /* ln p(theta) for one phase: Exp(lambda) on h, normal on mu and alpha,
@@ -340,6 +345,30 @@ double orc_entropy(int K, const double *raw)
     return H;
 }
 
+/*
+ * Parameters held fixed (orc_variant.fix_r / fix_alpha) leave q: per draw
+ * the ln p + ln|J| terms of a fixed r (its Jacobian ln r(1-r); the uniform
+ * prior adds nothing) and of a fixed alpha (its normal prior) are removed,
+ * and so are their entropy and ln q terms.  Returns the ln p + ln|J| part
+ * to subtract for one phase of one draw (u, theta of that phase).
+ */
+double orc_fixed_lpj(const orc_prior *pr, const orc_variant *var, const double *u, const double *th)
+{
+    double d = 0.0;
+    if (var && var->fix_r) d += -orc_softplus(-u[3]) - orc_softplus(u[3]);
+    if (var && var->fix_alpha) {
+        double za = (th[4] - pr->alpha_mean) / pr->alpha_sd;
+        d += -0.5 * za * za - log(pr->alpha_sd) - 0.5 * log(2.0 * ORC_PI);
+    }
+    return d;
+}
+
+/* Is parameter j of q free (not held fixed)? */
+int orc_free(const orc_variant *var, int j)
+{
+    return !(var && ((j == 3 && var->fix_r) || (j == 4 && var->fix_alpha)));
+}
+
 /* ------------------------------------------------------------------------ */
 /* Importance-weighted bound (estimator variant)                              */
 /* ------------------------------------------------------------------------ */
@@ -355,16 +384,18 @@ double orc_entropy(int K, const double *raw)
  *   dL_S/dloc = sum_s wt_s G_s,
  *   dL_S/draw = [ sum_s wt_s G_s eps_s + 1/sigma ] sigmoid(raw),
  * the 1/sigma being the derivative of -ln q(u_s) with u_s = loc + sigma eps_s.
- * Returns L_S and writes wt[S]; ll and lpj are the per-draw terms.
+ * Returns L_S and writes wt[S]; ll and lpj are the per-draw terms; parameters
+ * held fixed by var are not part of q.
  */
 double orc_iw_weights(int K, int S, const double *raw, const double *eps, const double *ll,
-                      const double *lpj, double *wt)
+                      const double *lpj, const orc_variant *var, double *wt)
 {
     double *lw = (double *)malloc((size_t)S * sizeof(double));
     double mx = -INFINITY;
     for (int s = 0; s < S; ++s) {
         double lq = 0.0;
         for (int i = 0; i < 5 * K; ++i) {
+            if (!orc_free(var, i % 5)) continue;   /* held fixed: not part of q */
             double e = eps[(size_t)s * K * 5 + i];
             lq += -0.5 * e * e - log(orc_softplus(raw[i])) - 0.5 * log(2.0 * ORC_PI);
         }
@@ -429,6 +460,11 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
     double *lls = (double *)malloc((size_t)S * sizeof(double));
     double *lps = (double *)malloc((size_t)S * sizeof(double));
     orc_theta(S, K, loc, raw, eps, u, th);
+    if (var && (var->fix_r || var->fix_alpha))   /* fixed r / alpha: model constants */
+        for (size_t i = 0; i < (size_t)S * K; ++i) {
+            if (var->fix_r) th[i * 5 + 3] = var->r_value;
+            if (var->fix_alpha) th[i * 5 + 4] = var->alpha_value;
+        }
 
 #pragma omp parallel for schedule(dynamic)
     for (int s = 0; s < S; ++s) {
@@ -454,7 +490,8 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
         if (f_out) memcpy(f_out + (size_t)s * N, f, (size_t)N * sizeof(double));
         lls[s] = lik ? orc_loglik_gauss(N, y, f) : orc_loglik_direct(N, y, f);
         double lp = lpb;   /* ln p(beta) of the fitted background (0 otherwise) */
-        for (int k = 0; k < K; ++k) lp += orc_log_prior(pr, ths + k * 5) + orc_log_jac(us + k * 5);
+        for (int k = 0; k < K; ++k)
+            lp += orc_log_prior(pr, ths + k * 5) + orc_log_jac(us + k * 5) - orc_fixed_lpj(pr, var, us + k * 5, ths + k * 5);
         lps[s] = lp;
         if (bgfit)   /* d LL_s / d beta_j = sum_i g_i B_i(beta) T_j(z_i) */
             for (int j = 0; j < 3; ++j)
@@ -496,8 +533,8 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
             Gs[0] = dh * h + pj[0];
             Gs[1] = dmu + pj[1];
             Gs[2] = dw * w + pj[2];
-            Gs[3] = dr * r * (1.0 - r) + pj[3];
-            Gs[4] = dal + pj[4];
+            Gs[3] = orc_free(var, 3) ? dr * r * (1.0 - r) + pj[3] : 0.0;
+            Gs[4] = orc_free(var, 4) ? dal + pj[4] : 0.0;
         }
         free(f);
         free(gi);
@@ -507,11 +544,15 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
        normalised weights w_s / sum w (Burda et al.), see orc_iw_weights */
     double *wt = (double *)malloc((size_t)S * sizeof(double));
     if (iw) {
-        *elbo = orc_iw_weights(K, S, raw, eps, lls, lps, wt);
+        *elbo = orc_iw_weights(K, S, raw, eps, lls, lps, var, wt);
     } else {
         double acc = 0.0;
         for (int s = 0; s < S; ++s) acc += lls[s] + lps[s];
-        *elbo = acc / S + orc_entropy(K, raw);
+        double H = orc_entropy(K, raw);
+        for (int k = 0; k < K; ++k)   /* fixed parameters carry no entropy */
+            for (int j = 3; j < 5; ++j)
+                if (!orc_free(var, j)) H -= log(orc_softplus(raw[k * 5 + j])) + 0.5 * (1.0 + log(2.0 * ORC_PI));
+        *elbo = acc / S + H;
         for (int s = 0; s < S; ++s) wt[s] = 1.0 / S;
     }
     if (ll) memcpy(ll, lls, (size_t)S * sizeof(double));
@@ -527,7 +568,7 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 }
                 double rw = raw[k * 5 + j];
                 grad[k * 10 + j] = gl;
-                grad[k * 10 + 5 + j] = (ge + 1.0 / orc_softplus(rw)) * orc_sigmoid(rw);
+                grad[k * 10 + 5 + j] = orc_free(var, j) ? (ge + 1.0 / orc_softplus(rw)) * orc_sigmoid(rw) : 0.0;
             }
     }
     if (bgfit && var->grad_beta)

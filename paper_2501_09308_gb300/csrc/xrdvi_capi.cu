@@ -263,6 +263,10 @@ xrdvi_status validate(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdv
     if (cfg->S < 1 || cfg->S > kMaxS) return fail(XRDVI_EINVAL, "S must be in [1, 65536]");
     if ((cfg->flags & XRDVI_FLAG_FIT_BACKGROUND) && !(std::isfinite(cfg->bg_prior_sd) && cfg->bg_prior_sd > 0.f))
         return fail(XRDVI_EINVAL, "bg_prior_sd must be positive");
+    if ((cfg->flags & XRDVI_FLAG_FIX_R) && !(cfg->fix_r_value >= 0.f && cfg->fix_r_value <= 1.f))
+        return fail(XRDVI_EINVAL, "fix_r_value must be in [0, 1]");
+    if ((cfg->flags & XRDVI_FLAG_FIX_ALPHA) && !std::isfinite(cfg->fix_alpha_value))
+        return fail(XRDVI_EINVAL, "fix_alpha_value must be finite");
     const float pos_params[] = {cfg->prior_mu_sd, cfg->prior_alpha_sd, cfg->prior_w_shape, cfg->prior_w_rate,
                                 cfg->alpha_min, cfg->init_h_frac, cfg->init_sigma, cfg->lr};
     for (float q : pos_params)
@@ -321,6 +325,8 @@ void xrdvi_config_default(xrdvi_config *cfg) {
     cfg->init_sigma = 0.1f;
     cfg->flags = 0;
     cfg->bg_prior_sd = 0.1f;
+    cfg->fix_r_value = 0.5f;
+    cfg->fix_alpha_value = 1.f;
 }
 
 xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
@@ -442,6 +448,12 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     P.prior.lgamma_w_shape = std::lgamma(static_cast<double>(cfg->prior_w_shape));
     P.prior.alpha_min = cfg->alpha_min;
     P.prior.lp_const = prior_constant(P.prior);
+    P.fix_r = (cfg->flags & XRDVI_FLAG_FIX_R) != 0;
+    P.fix_alpha = (cfg->flags & XRDVI_FLAG_FIX_ALPHA) != 0;
+    P.r_value = cfg->fix_r_value;
+    P.alpha_value = cfg->fix_alpha_value;
+    if (P.fix_alpha)   // a fixed alpha has no prior: drop its normal's constant
+        P.prior.lp_const += std::log(P.prior.alpha_sd) + 0.5 * std::log(2.0 * M_PI);
 
     xrdvi_status st;
 #define XR_C(expr)                         \

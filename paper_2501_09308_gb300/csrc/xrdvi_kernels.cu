@@ -149,6 +149,8 @@ struct SampleArgs {
     float reach_scale;     // Gaussian reach factor: max sec(x/2) of the pattern (angle-dependent width), else 1
     const float *beta;     // [3] fitted-background coefficients (null: fixed background)
     float bg_sd;
+    int fix_r, fix_a;      // r / alpha held fixed (model constants, not in q)
+    float r_value, a_value;
     int shared;            // shape noise of every sample = sample 0's (shared-shape variant)
     float *H;              // [S*Kpad] h_sk for the forward GEMM (shared-shape variant)
     int Kpad;
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
             u[j] = fmaf(sig[j], e[j], loc[k * 5 + j]);
             a.eps[base + j] = e[j];
         }
+        if (a.fix_r) u[3] = 0.f;   // fixed parameters: not drawn (their noise is unused)
+        if (a.fix_a) u[4] = a.a_value;
         const float h = expf(u[0]);
         if (a.H) {   // TF32 hi / lo parts for the forward GEMM
             const float hh = tf32_hi(h);
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         }
         const float mu = u[1];
         const float w = expf(u[2]);
-        const float r = sigmoidf(u[3]);
+        const float r = a.fix_r ? a.r_value : sigmoidf(u[3]);
         const float al = u[4];
         a.theta[base + 0] = h;
         a.theta[base + 1] = mu;
@@ -267,15 +271,20 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         // the parameter-free part is the host constant lp_const; the rest is
         // O(1) per phase and evaluated in FP32 (ln w = u_w exactly), summed in FP64.
         const float zm = mu * a.pr_mu_isd;
-        const float za = (al - a.pr_alpha_mean) * a.pr_alpha_isd;
+        const float za = a.fix_a ? 0.f : (al - a.pr_alpha_mean) * a.pr_alpha_isd;   // fixed: no prior
         const float lpf = -a.pr_lambda * h - 0.5f * zm * zm - 0.5f * za * za + a.pr_wsm1 * u[2] - a.pr_wrate * w;
-        const float ljf = u[0] + u[2] - softplusf(-u[3]) - softplusf(u[3]);
+        const float ljf = u[0] + u[2] - (a.fix_r ? 0.f : softplusf(-u[3]) + softplusf(u[3]));
         acc += a.pr.lp_const + static_cast<double>(lpf) + static_cast<double>(ljf);
         if (a.lq) {
             float q = 0.f;
+            int nfree = 0;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) q += -0.5f * e[j] * e[j] - logf(sig[j]);
-            accq += static_cast<double>(q) - 2.5 * kLog2Pi;
+            for (int j = 0; j < 5; ++j) {
+                if ((j == 3 && a.fix_r) || (j == 4 && a.fix_a)) continue;   // not part of q
+                q += -0.5f * e[j] * e[j] - logf(sig[j]);
+                ++nfree;
+            }
+            accq += static_cast<double>(q) - 0.5 * nfree * kLog2Pi;
         }
     }
     if (s == 0 && a.tickets)
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
     if (s_loc == 0 && a.ent) {
         double H = 0.0;
         for (int i = threadIdx.x; i < 5 * a.K; i += blockDim.x)
-            if (!a.mask || ((mk >> (i / 5)) & 1u))
+            if ((!a.mask || ((mk >> (i / 5)) & 1u)) && !((i % 5 == 3 && a.fix_r) || (i % 5 == 4 && a.fix_a)))
                 H += log(softplusd(static_cast<double>(raw[i]))) + 0.5 * (1.0 + kLog2Pi);
         H = block_sum(H, sh);
         if (threadIdx.x == 0) a.ent[b] = H;
@@ -1052,6 +1061,7 @@ struct GradArgs {
     int Tg;             // tiles per (sample, phase) record of gpart (T, or 1 for the shared-shape variant)
     // FP32 prior constants of the per-sample gradient
     float pr_lambda, pr_mu_isd2, pr_w_shape, pr_w_rate, pr_alpha_mean, pr_alpha_isd2;
+    int fix_r, fix_a;   // r / alpha held fixed: zero gradient, no update
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -1167,9 +1177,9 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             G[1] = 2.f * h * ((1.f - r) * ln2f * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
                    mu * a.pr_mu_isd2;
             G[2] = 2.f * h * ((1.f - r) * ln2f * q[6] + r * q[7]) + (a.pr_w_shape - a.pr_w_rate * w);
-            G[3] = r * (1.f - r) * h * (q[1] - q[0]) + (1.f - 2.f * r);
+            G[3] = a.fix_r ? 0.f : r * (1.f - r) * h * (q[1] - q[0]) + (1.f - 2.f * r);
             const float gal = clamped ? 0.f : __fdiv_rn(2.f * h, acl) * ((1.f - r) * ln2f * BGp + r * BLp);
-            G[4] = gal - (al - a.pr_alpha_mean) * a.pr_alpha_isd2;
+            G[4] = a.fix_a ? 0.f : gal - (al - a.pr_alpha_mean) * a.pr_alpha_isd2;
             const double wt = a.iw ? __ldcg(&a.iw[c0 + lane]) : 1.0;   // importance weight w_s / sum w
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
@@ -1218,8 +1228,10 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         } else {
             grad = ((a.iw ? red[5 + j] : red[5 + j] / a.S_sub) + 1.0 / softplusd(rw)) * sigmoidd(rw);
         }
+        const bool fixed = (j == 3 && a.fix_r) || (j == 4 && a.fix_a);   // not part of q: no gradient
+        if (fixed) grad = 0.0;
         if (a.grad_out) a.grad_out[bk * 10 + threadIdx.x] = static_cast<float>(grad);
-        if (a.adam) {
+        if (a.adam && !fixed) {
             const int t = *a.d_iter + 1;
             const int idx = bk * 10 + threadIdx.x;
             const double gm = -grad;  // minimise -ELBO
@@ -1547,6 +1559,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.shared = W.shared ? 1 : 0; a.H = W.H; a.Kpad = W.Kpad;
     a.reach_scale = P.sec ? P.sec_max : 1.0f;
     a.beta = P.bgfit ? P.beta : nullptr; a.bg_sd = P.bg_sd;
+    a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0; a.r_value = P.r_value; a.a_value = P.alpha_value;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1626,6 +1639,7 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.pr_w_rate = static_cast<float>(P.prior.w_rate);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
     a.pr_alpha_isd2 = static_cast<float>(1.0 / (P.prior.alpha_sd * P.prior.alpha_sd));
+    a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
     const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;

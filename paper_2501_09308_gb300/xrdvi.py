@@ -24,6 +24,8 @@ FLAG_IW_ELBO = 1 << 3     # importance-weighted objective
 FLAG_SHARED_SHAPES = 1 << 4   # one shape draw per step, tensor-core contractions
 FLAG_SEC_WIDTH = 1 << 5       # side widths times sec(2theta / 2)
 FLAG_FIT_BACKGROUND = 1 << 6  # background correction exp(sum beta_j T_j(z)) fitted in-model
+FLAG_FIX_R = 1 << 7           # r held at fix_r_value
+FLAG_FIX_ALPHA = 1 << 8       # alpha held at fix_alpha_value
 
 
 class XrdviError(RuntimeError):
@@ -49,7 +51,8 @@ class Config(ctypes.Structure):
                 ("prior_alpha_mean", ctypes.c_float), ("prior_alpha_sd", ctypes.c_float),
                 ("prior_w_shape", ctypes.c_float), ("prior_w_rate", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("init_h_frac", ctypes.c_float),
-                ("init_sigma", ctypes.c_float), ("flags", ctypes.c_uint32), ("bg_prior_sd", ctypes.c_float)]
+                ("init_sigma", ctypes.c_float), ("flags", ctypes.c_uint32), ("bg_prior_sd", ctypes.c_float),
+                ("fix_r_value", ctypes.c_float), ("fix_alpha_value", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):

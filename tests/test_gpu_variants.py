@@ -215,3 +215,50 @@ def test_fitted_background_checkpoint_resume_is_bit_identical():
     b.close()
     np.testing.assert_array_equal(ta, tb)
     np.testing.assert_array_equal(ba, bb)
+
+
+@pytest.mark.parametrize("flags,okw", [
+    (xrdvi.FLAG_FIX_R | xrdvi.FLAG_FIX_ALPHA, {"fix_r": 0.5, "fix_alpha": 1.0}),
+    (xrdvi.FLAG_FIX_R, {"fix_r": 0.3}),
+    (xrdvi.FLAG_FIX_ALPHA, {"fix_alpha": 1.4}),
+])
+def test_fixed_shape_parameters_parity(flags, okw):
+    inst = synth.small_problem(K=5, M=10, N=700, S=6, seed=22, x_step=0.03)
+    cfg = {"fix_r_value": okw.get("fix_r", 0.5), "fix_alpha_value": okw.get("fix_alpha", 1.0)}
+    ctx = xrdvi.Context.from_instance(inst, S=6, flags=flags, **cfg)
+    loc, raw = ctx.params()
+    rng = np.random.default_rng(22)
+    loc = loc + rng.normal(0, 0.05, loc.shape).astype(np.float32)
+    raw = raw + rng.normal(0, 0.1, raw.shape).astype(np.float32)
+    ctx.set_params(loc, raw)
+    eps = synth.normals(5022, 6, inst.K)
+    g = ctx.elbo_grad(eps, want_f=True)
+    ctx.close()
+    o = oracle.Problem.from_instance(inst, **okw).elbo_grad(loc.astype(np.float64), raw.astype(np.float64),
+                                                            eps.astype(np.float64), want_f=True)
+    assert np.max(np.abs(g["f"] - o["f"]) / np.abs(o["f"])) <= F_TOL
+    np.testing.assert_allclose(g["ll"], o["ll"], rtol=F_TOL)
+    assert abs(g["elbo"] - o["elbo"]) <= F_TOL * abs(o["elbo"])
+    for b in range(10):
+        ref = np.max(np.abs(o["grad"][:, b]))
+        if ref == 0.0:
+            np.testing.assert_array_equal(g["grad"][:, b], 0.0)
+        else:
+            assert np.max(np.abs(g["grad"][:, b] - o["grad"][:, b])) <= G_TOL * ref, b
+
+
+def test_fixed_shape_fit_recovers_planted_phases_and_keeps_fixed_parameters():
+    """The tiny workload is simulated with r = 0.5 and alpha = 1; fitting with
+    both held there recovers the planted phases and leaves their variational
+    parameters untouched."""
+    inst = synth.config(0)
+    c = xrdvi.Context.from_instance(inst, S=inst.S, flags=xrdvi.FLAG_FIX_R | xrdvi.FLAG_FIX_ALPHA,
+                                    fix_r_value=0.5, fix_alpha_value=1.0)
+    loc0, raw0 = c.params()
+    c.fit(1000)
+    loc1, raw1 = c.params()
+    post = c.posterior(512, 3, top_m=1)
+    c.close()
+    np.testing.assert_array_equal(loc1[:, 3:], loc0[:, 3:])
+    np.testing.assert_array_equal(raw1[:, 3:], raw0[:, 3:])
+    assert set(np.flatnonzero(post["combos"][0]).tolist()) == set(inst.planted.tolist())

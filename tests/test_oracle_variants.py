@@ -242,3 +242,37 @@ def test_fitted_background_gradient_against_central_differences():
         P.beta[j] = b0
         num[j] = (ep - em) / 2e-6
     np.testing.assert_allclose(g, num, rtol=1e-5, atol=1e-6 * np.max(np.abs(num)))
+
+
+def test_fixed_r_and_alpha_equal_the_free_model_at_zero_width_minus_their_terms():
+    """Holding r = 0.5 and alpha = 1.2 fixed equals the free model with those
+    parameters' sigma -> 0 at the same values, minus exactly the removed terms
+    per phase and draw: the Jacobian ln r(1 - r) of r, the normal prior of
+    alpha, and their two entropy terms ln sigma + (1 + ln 2 pi)/2."""
+    inst, P = _problem()
+    Pf = oracle.Problem.from_instance(inst, fix_r=0.5, fix_alpha=1.2)
+    loc, raw = _perturbed(P, 11)
+    loc[:, 3], loc[:, 4] = 0.0, 1.2          # logit(0.5) = 0
+    raw[:, 3] = raw[:, 4] = -60.0             # sigma = softplus(-60) ~ 8.8e-27
+    eps = synth.normals(15, 3, P.K).astype(np.float64)
+    a, b = Pf.elbo_grad(loc, raw, eps), P.elbo_grad(loc, raw, eps)
+    sig0 = math.log1p(math.exp(-60.0))
+    per_phase = (math.log(0.25) + stats.norm.logpdf(1.2, 1.0, 0.2)
+                 + 2 * (math.log(sig0) + 0.5 * (1 + math.log(2 * math.pi))))
+    assert a["elbo"] == pytest.approx(b["elbo"] - P.K * per_phase, rel=1e-12, abs=1e-9)
+    np.testing.assert_array_equal(a["grad"][:, [3, 4, 8, 9]], 0.0)
+    np.testing.assert_allclose(a["grad"][:, [0, 1, 2, 5, 6, 7]], b["grad"][:, [0, 1, 2, 5, 6, 7]], rtol=1e-9,
+                               atol=1e-9 * np.max(np.abs(b["grad"])))
+
+
+def test_fixed_r_and_alpha_gradient_against_central_differences():
+    inst, _ = _problem()
+    P = oracle.Problem.from_instance(inst, fix_r=0.3, fix_alpha=0.9)
+    loc, raw = _perturbed(P, 12)
+    eps = synth.normals(16, 2, P.K).astype(np.float64)
+    g = P.elbo_grad(loc, raw, eps)["grad"]
+    num = _fd_grad(P, loc, raw, eps)
+    np.testing.assert_array_equal(num[:, [3, 4, 8, 9]], 0.0)   # the objective does not depend on them
+    free = [0, 1, 2, 5, 6, 7]
+    rel = np.max(np.abs(num[:, free] - g[:, free]), axis=0) / np.max(np.abs(g[:, free]), axis=0)
+    assert np.all(rel < 1e-5), rel
