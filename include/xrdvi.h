@@ -117,6 +117,18 @@ typedef struct {
  * variational parameters are not updated. */
 #define XRDVI_FLAG_FIX_R      (1u << 7)
 #define XRDVI_FLAG_FIX_ALPHA  (1u << 8)
+/* xrdvi_create: the peak and pattern arrays (offsets, pos_deg, rel_int,
+ * x_deg, y_counts, bg) are DEVICE pointers; they are read back once for
+ * validation and preparation (sorting, the data constants), then handled as
+ * host input.  K and N stay host values. */
+#define XRDVI_FLAG_DEVICE_PTRS (1u << 9)
+/* Area-normalised profiles (the alternative to the height normalisation the
+ * paper's lambda = 1 / max(Y - B) suggests): each phase's profile is divided
+ * by the area of its unit-height shape, a(w, alpha, r) = ((1 + alpha) w / 2)
+ * [(1 - r) sqrt(pi / ln 2) / 2 + r pi / 2], so h is an integrated intensity
+ * (per unit relative intensity), the posterior's area of phase k is
+ * h_k sum_m I_m, and the initial h is scaled by the initial shape's area. */
+#define XRDVI_FLAG_AREA_NORM  (1u << 10)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */

@@ -55,7 +55,7 @@ class Variant(ctypes.Structure):
     _fields_ = [("lik", ctypes.c_int), ("iw", ctypes.c_int), ("shared", ctypes.c_int), ("sec", ctypes.c_int),
                 ("bgfit", ctypes.c_int), ("bg_sd", ctypes.c_double), ("beta", _PD), ("grad_beta", _PD),
                 ("m_beta", _PD), ("v_beta", _PD), ("fix_r", ctypes.c_int), ("fix_alpha", ctypes.c_int),
-                ("r_value", ctypes.c_double), ("alpha_value", ctypes.c_double)]
+                ("r_value", ctypes.c_double), ("alpha_value", ctypes.c_double), ("area_norm", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -109,7 +109,9 @@ def lib():
                                            pd, pd, pd, pd, pd, pd, pd, pd]
             L.orc_fit_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, pd, P(Prior), P(Variant), i32, u64, i32, i32,
                                      d, d, d, d, pd, pd, pd, pd, pd]
-            L.orc_profile_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, i32, pd, d, i32, pd]
+            L.orc_profile_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, i32, pd, d, i32, i32, pd]
+            L.orc_area_factor.restype = d
+            L.orc_area_factor.argtypes = [d, d, d]
             L.orc_sec.restype = d
             L.orc_sec.argtypes = [d]
             L.orc_background.argtypes = [i32, pd, pd, pd, pd, pd]
@@ -149,7 +151,7 @@ class Problem:
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
                  w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
                  likelihood="poisson", objective="elbo", shapes="independent", width="constant",
-                 background="fixed", bg_sd=0.1, fix_r=None, fix_alpha=None):
+                 background="fixed", bg_sd=0.1, fix_r=None, fix_alpha=None, normalisation="height"):
         # variants: likelihood "poisson" (the paper's) or "gauss" (variance
         # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound);
         # shapes "independent" or "shared" (one shape draw per step); width
@@ -170,7 +172,11 @@ class Problem:
         self.variant = Variant(self.lik, self.iw, self.shared, self.sec, self.bgfit, float(bg_sd),
                                _pd(self.beta), _pd(self._gb), None, None,
                                0 if fix_r is None else 1, 0 if fix_alpha is None else 1,
-                               0.0 if fix_r is None else float(fix_r), 0.0 if fix_alpha is None else float(fix_alpha))
+                               0.0 if fix_r is None else float(fix_r), 0.0 if fix_alpha is None else float(fix_alpha),
+                               1 if normalisation == "area" else 0)
+        # normalisation "height" (peak height h) or "area" (h = integrated intensity)
+        assert normalisation in ("height", "area")
+        self.area_norm = normalisation == "area"
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -203,7 +209,8 @@ class Problem:
         S = theta.shape[0]
         f = np.zeros((S, self.N))
         lib().orc_profile_ex(self.K, _pi(self.off), _pd(self.pos), _pd(self.inten), self.N,
-                             _pd(self.x), _pd(self.bg), S, _pd(theta), self.prior.alpha_min, self.sec, _pd(f))
+                             _pd(self.x), _pd(self.bg), S, _pd(theta), self.prior.alpha_min, self.sec,
+                             1 if self.area_norm else 0, _pd(f))
         return f
 
     def loglik(self, f, form="direct"):
@@ -269,6 +276,9 @@ class Problem:
         w = prior mean shape/rate, r = 1/2, alpha = prior mean; every sigma = sigma0."""
         loc = np.zeros((self.K, 5))
         loc[:, 0] = math.log(h_frac * self.eta)
+        if self.area_norm:   # same starting curve: the height times the area of the initial shape
+            loc[:, 0] += math.log(lib().orc_area_factor(self.prior.w_shape / self.prior.w_rate,
+                                                        max(self.prior.alpha_mean, self.prior.alpha_min), 0.5))
         loc[:, 1] = 0.0
         loc[:, 2] = math.log(self.prior.w_shape / self.prior.w_rate)
         loc[:, 3] = 0.0

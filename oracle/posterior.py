@@ -56,6 +56,8 @@ def phase_areas(prob: Problem, theta):
     Isum = np.add.reduceat(prob.inten, prob.off[:-1]) if prob.K > 0 else np.zeros(0)
     # empty phases are rejected at create time, so reduceat is safe
     h, w, r, al = theta[..., 0], theta[..., 2], theta[..., 3], theta[..., 4]
+    if getattr(prob, "area_norm", False):   # h is already the area per unit intensity
+        return h * Isum[None, :]
     ac = np.maximum(al, prob.prior.alpha_min)
     return h * Isum[None, :] * peak_area(w, r, ac)
 

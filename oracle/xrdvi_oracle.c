@@ -145,6 +145,18 @@ void orc_components(double d, double w, double alpha_c, double *G, double *L)
  * sec(theta) with theta = x / 2, i.e. 1 / cos(x pi / 360). */
 double orc_sec(double x) { return 1.0 / cos(x * ORC_PI / 360.0); }
 
+/*
+ * Area of the height-normalised split pseudo-Voigt of unit height (the
+ * closed form of the area-ratio reading, Sec. 4): the Gaussian and Lorentzian
+ * halves of FWHM w on the left and alpha w on the right integrate to
+ *   a(w, alpha, r) = ((1 + alpha) w / 2) [(1 - r) sqrt(pi / ln 2) / 2 + r pi / 2].
+ * The area-normalised variant divides each phase's profile by it.
+ */
+double orc_area_factor(double w, double alpha_c, double r)
+{
+    return 0.5 * (1.0 + alpha_c) * w * ((1.0 - r) * 0.5 * sqrt(ORC_PI / ORC_LN2) + r * 0.5 * ORC_PI);
+}
+
 /* Pseudo-Voigt V = (1 - r) G + r L (Appendix A.2, profile of one peak). */
 double orc_pvoigt(double d, double w, double r, double alpha_c)
 {
@@ -162,7 +174,7 @@ double orc_pvoigt(double d, double w, double r, double alpha_c)
  */
 void orc_profile_ex(int K, const int *off, const double *pos, const double *inten,
                     int N, const double *x, const double *bg,
-                    int S, const double *theta, double alpha_min, int sec, double *f)
+                    int S, const double *theta, double alpha_min, int sec, int area_norm, double *f)
 {
 #pragma omp parallel for schedule(dynamic)
     for (int s = 0; s < S; ++s) {
@@ -177,6 +189,7 @@ void orc_profile_ex(int K, const int *off, const double *pos, const double *inte
                     double d = x[i] - (pos[m] + mu);
                     C += inten[m] * orc_pvoigt(d, wx, r, ac);
                 }
+                if (area_norm) C /= orc_area_factor(w, ac, r);
                 acc += h * C;
             }
             f[(size_t)s * N + i] = acc;
@@ -188,7 +201,7 @@ void orc_profile(int K, const int *off, const double *pos, const double *inten,
                  int N, const double *x, const double *bg,
                  int S, const double *theta, double alpha_min, double *f)
 {
-    orc_profile_ex(K, off, pos, inten, N, x, bg, S, theta, alpha_min, 0, f);
+    orc_profile_ex(K, off, pos, inten, N, x, bg, S, theta, alpha_min, 0, 0, f);
 }
 
 /*
@@ -293,6 +306,8 @@ typedef struct {
  *   sec     1: angle-dependent width, every side width at point x multiplied
  *           by sec(theta), theta = x / 2 (x = 2-theta in degrees)   (orc_sec)
  *   bgfit   1: background fitted in-model                   (orc_background)
+ *   area_norm 1: each phase's profile divided by its area per unit height
+ *           (orc_area_factor), so h is an integrated intensity
  *   fix_r, fix_alpha  1: r / alpha held at a given value: a constant of the
  *           model, not a parameter of q (no prior, Jacobian, entropy, ln q
  *           or gradient term; orc_fixed_terms)
@@ -306,6 +321,7 @@ typedef struct {
     double *m_beta, *v_beta;   /* [3] their Adam moments (orc_fit_ex)              */
     int fix_r, fix_alpha;      /* 1: r / alpha held at r_value / alpha_value       */
     double r_value, alpha_value;
+    int area_norm;             /* 1: area-normalised profiles (orc_area_factor)    */
 } orc_variant;
 
 /* ln p(theta) for one phase: Exp(lambda) on h, normal on mu and alpha,
@@ -482,6 +498,7 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 double wx = sec ? t[2] * orc_sec(x[i]) : t[2];   /* width at this point */
                 for (int m = off[k]; m < off[k + 1]; ++m)
                     C += inten[m] * orc_pvoigt(x[i] - (pos[m] + t[1]), wx, t[3], ac);
+                if (var && var->area_norm) C /= orc_area_factor(t[2], ac, t[3]);
                 acc += t[0] * C;
             }
             f[i] = acc;
@@ -520,6 +537,19 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                     Cw += I * dVdt * (-tt / w);               /* d t / d w  = -t / w      */
                     Cr += I * (Lc - Gc);                      /* d V / d r  = L - G        */
                     if (d >= 0.0 && !clamped) Cal += I * dVdt * (-tt / ac); /* d t / d alpha */
+                }
+                if (var && var->area_norm) {
+                    /* f = h C / a(w, alpha, r): product rule with d ln a / dw = 1/w,
+                       d ln a / d alpha = 1/(1 + alpha), d ln a / dr as below */
+                    double a = orc_area_factor(w, ac, r);
+                    double A = (1.0 - r) * 0.5 * sqrt(ORC_PI / ORC_LN2) + r * 0.5 * ORC_PI;
+                    double dlna_dr = (0.5 * ORC_PI - 0.5 * sqrt(ORC_PI / ORC_LN2)) / A;
+                    dh += gi[i] * C / a;
+                    dmu += gi[i] * h * Cmu / a;
+                    dw += gi[i] * h * (Cw - C / w) / a;
+                    dr += gi[i] * h * (Cr - C * dlna_dr) / a;
+                    if (!clamped) dal += gi[i] * h * (Cal - C / (1.0 + ac)) / a;
+                    continue;
                 }
                 dh += gi[i] * C;
                 dmu += gi[i] * h * Cmu;

@@ -331,6 +331,25 @@ void xrdvi_config_default(xrdvi_config *cfg) {
 
 xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
                           xrdvi_ctx **out) {
+    if (cfg && cfg->size == sizeof(xrdvi_config) && (cfg->flags & XRDVI_FLAG_DEVICE_PTRS) && pk && pt) {
+        // device inputs: one read-back, then the host path
+        if (pk->K < 1 || pk->K > kMaxK || pt->N < 1 || pt->N > kMaxN || !pk->offsets || !pk->pos_deg ||
+            !pk->rel_int || !pt->x_deg || !pt->y_counts || !pt->bg)
+            return fail(XRDVI_EINVAL, "bad sizes or null device arrays");
+        std::vector<int32_t> off(pk->K + 1);
+        XR_CUDA(cudaMemcpy(off.data(), pk->offsets, off.size() * 4, cudaMemcpyDeviceToHost));
+        if (off[0] != 0 || off[pk->K] < 1 || off[pk->K] > kMaxPeaks) return fail(XRDVI_EINVAL, "bad offsets");
+        const int M = off[pk->K], N = pt->N;
+        std::vector<float> pos(M), inten(M), x(N), y(N), bg(N);
+        XR_CUDA(cudaMemcpy(pos.data(), pk->pos_deg, M * 4, cudaMemcpyDeviceToHost));
+        XR_CUDA(cudaMemcpy(inten.data(), pk->rel_int, M * 4, cudaMemcpyDeviceToHost));
+        XR_CUDA(cudaMemcpy(x.data(), pt->x_deg, N * 4, cudaMemcpyDeviceToHost));
+        XR_CUDA(cudaMemcpy(y.data(), pt->y_counts, N * 4, cudaMemcpyDeviceToHost));
+        XR_CUDA(cudaMemcpy(bg.data(), pt->bg, N * 4, cudaMemcpyDeviceToHost));
+        const xrdvi_peaks hpk{pk->K, off.data(), pos.data(), inten.data()};
+        const xrdvi_pattern hpt{N, x.data(), y.data(), bg.data()};
+        return xrdvi::create_context(&hpk, &hpt, cfg, nullptr, nullptr, out);
+    }
     return xrdvi::create_context(pk, pt, cfg, nullptr, nullptr, out);
 }
 
@@ -448,6 +467,7 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     P.prior.lgamma_w_shape = std::lgamma(static_cast<double>(cfg->prior_w_shape));
     P.prior.alpha_min = cfg->alpha_min;
     P.prior.lp_const = prior_constant(P.prior);
+    P.area_norm = (cfg->flags & XRDVI_FLAG_AREA_NORM) != 0;
     P.fix_r = (cfg->flags & XRDVI_FLAG_FIX_R) != 0;
     P.fix_alpha = (cfg->flags & XRDVI_FLAG_FIX_ALPHA) != 0;
     P.r_value = cfg->fix_r_value;
@@ -540,7 +560,12 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     std::vector<float> loc(KB * 5), raw(KB * 5);
     const double raw0 = std::log(std::expm1(static_cast<double>(cfg->init_sigma)));
     for (size_t k = 0; k < KB; ++k) {
-        loc[k * 5 + 0] = static_cast<float>(std::log(cfg->init_h_frac * eta));
+        // area-normalised profiles start from the same curve: height times the initial shape's area
+        const double a0 = 0.5 * (1.0 + std::max(static_cast<double>(cfg->prior_alpha_mean),
+                                                 static_cast<double>(cfg->alpha_min))) *
+                          (static_cast<double>(cfg->prior_w_shape) / cfg->prior_w_rate) *
+                          (0.5 * 0.5 * std::sqrt(M_PI / std::log(2.0)) + 0.5 * 0.5 * M_PI);
+        loc[k * 5 + 0] = static_cast<float>(std::log(cfg->init_h_frac * eta * ((cfg->flags & XRDVI_FLAG_AREA_NORM) ? a0 : 1.0)));
         loc[k * 5 + 1] = 0.f;
         loc[k * 5 + 2] = static_cast<float>(std::log(static_cast<double>(cfg->prior_w_shape) / cfg->prior_w_rate));
         loc[k * 5 + 3] = 0.f;

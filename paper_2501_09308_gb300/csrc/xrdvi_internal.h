@@ -138,6 +138,7 @@ struct Problem {
     bool wide = false;           // backward peak table stored as (-p, -p, I, I) float4
     bool gauss = false;          // Gaussian likelihood variant (variance max(y, 1))
     bool fix_r = false, fix_alpha = false;   // r / alpha held at r_value / alpha_value
+    bool area_norm = false;      // area-normalised profiles (h = integrated intensity)
     float r_value = 0.5f, alpha_value = 1.f;
     bool sec = false;            // angle-dependent width variant (side widths times sec(x/2))
     float *csec = nullptr;       // [N] cos(x_i / 2) for that variant

@@ -82,6 +82,14 @@ __device__ __forceinline__ double sigmoidd(double x) {
     return e / (1.0 + e);
 }
 
+// Area of the unit-height split pseudo-Voigt of FWHM w (left) and alpha w
+// (right): ((1 + alpha) w / 2) [(1 - r) sqrt(pi / ln 2) / 2 + r pi / 2].
+__device__ __forceinline__ float area_factorf(float w, float alpha_c, float r) {
+    constexpr float kAG = 1.0644670194312262f;   // sqrt(pi / ln 2) / 2
+    constexpr float kAL = 1.5707963267948966f;   // pi / 2
+    return 0.5f * (1.f + alpha_c) * w * fmaf(r, kAL - kAG, kAG);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -151,6 +159,7 @@ struct SampleArgs {
     float bg_sd;
     int fix_r, fix_a;      // r / alpha held fixed (model constants, not in q)
     float r_value, a_value;
+    int area_norm;         // area-normalised profiles: h / a(w, alpha, r) scales the profile
     int shared;            // shape noise of every sample = sample 0's (shared-shape variant)
     float *H;              // [S*Kpad] h_sk for the forward GEMM (shared-shape variant)
     int Kpad;
@@ -237,11 +246,6 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         if (a.fix_r) u[3] = 0.f;   // fixed parameters: not drawn (their noise is unused)
         if (a.fix_a) u[4] = a.a_value;
         const float h = expf(u[0]);
-        if (a.H) {   // TF32 hi / lo parts for the forward GEMM
-            const float hh = tf32_hi(h);
-            a.H[static_cast<size_t>(s) * a.Kpad + k] = hh;
-            a.H[static_cast<size_t>(a.S) * a.Kpad + static_cast<size_t>(s) * a.Kpad + k] = h - hh;
-        }
         const float mu = u[1];
         const float w = expf(u[2]);
         const float r = a.fix_r ? a.r_value : sigmoidf(u[3]);
@@ -254,10 +258,18 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         const float ac = al > static_cast<float>(a.pr.alpha_min) ? al : static_cast<float>(a.pr.alpha_min);
         const float wl = w, wr = ac * w;
         const float sl = 2.0f / wl, sr = 2.0f / wr;
+        // area-normalised profiles divide by the area of the unit-height shape
+        // a(w, alpha, r) = ((1 + alpha) w / 2) [(1 - r) sqrt(pi/ln2)/2 + r pi/2]
+        const float he = a.area_norm ? __fdiv_rn(h, area_factorf(w, ac, r)) : h;
+        if (a.H) {   // TF32 hi / lo parts of the profile scale for the forward GEMM
+            const float hh = tf32_hi(he);
+            a.H[static_cast<size_t>(s) * a.Kpad + k] = hh;
+            a.H[static_cast<size_t>(a.S) * a.Kpad + static_cast<size_t>(s) * a.Kpad + k] = he - hh;
+        }
         PhaseConst pc;
         pc.mu = mu;
-        pc.hl = h * r;
-        pc.hg = h * (1.0f - r);
+        pc.hl = he * r;
+        pc.hg = he * (1.0f - r);
         pc.rl = 0.5f * sq * wl * a.reach_scale;
         pc.rr = 0.5f * sq * wr * a.reach_scale;
         pc.sl = sl;
@@ -1062,6 +1074,7 @@ struct GradArgs {
     // FP32 prior constants of the per-sample gradient
     float pr_lambda, pr_mu_isd2, pr_w_shape, pr_w_rate, pr_alpha_mean, pr_alpha_isd2;
     int fix_r, fix_a;   // r / alpha held fixed: zero gradient, no update
+    int area_norm;      // area-normalised profiles
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -1172,13 +1185,23 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             const float ALp = 0.5f * (q[3] + q[5]), ALm = 0.5f * (q[3] - q[5]);
             const float BGp = 0.5f * (q[6] + q[8]), BLp = 0.5f * (q[7] + q[9]);
             float G[5];
+            // the profile scale he: h, or h / a(w, alpha, r) for area-normalised
+            // profiles, whose derivatives add -he * dLL/dhe * d ln a / d(u_w, r, alpha)
+            const float aw = a.area_norm ? area_factorf(w, acl, r) : 1.f;
+            const float he = a.area_norm ? __fdiv_rn(h, aw) : h;
+            const float LLh = (1.f - r) * q[0] + r * q[1];   // d LL / d he
+            constexpr float kAG = 1.0644670194312262f, kAL = 1.5707963267948966f;
+            const float dlna_dr = a.area_norm ? __fdiv_rn(kAL - kAG, fmaf(r, kAL - kAG, kAG)) : 0.f;
             // likelihood part (chained to u) + prior/Jacobian part
-            G[0] = h * ((1.f - r) * q[0] + r * q[1]) + (1.f - a.pr_lambda * h);
-            G[1] = 2.f * h * ((1.f - r) * ln2f * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
+            G[0] = he * LLh + (1.f - a.pr_lambda * h);
+            G[1] = 2.f * he * ((1.f - r) * ln2f * (sl * AGm + sr * AGp) + r * (sl * ALm + sr * ALp)) -
                    mu * a.pr_mu_isd2;
-            G[2] = 2.f * h * ((1.f - r) * ln2f * q[6] + r * q[7]) + (a.pr_w_shape - a.pr_w_rate * w);
-            G[3] = a.fix_r ? 0.f : r * (1.f - r) * h * (q[1] - q[0]) + (1.f - 2.f * r);
-            const float gal = clamped ? 0.f : __fdiv_rn(2.f * h, acl) * ((1.f - r) * ln2f * BGp + r * BLp);
+            G[2] = 2.f * he * ((1.f - r) * ln2f * q[6] + r * q[7]) - (a.area_norm ? he * LLh : 0.f) +
+                   (a.pr_w_shape - a.pr_w_rate * w);
+            G[3] = a.fix_r ? 0.f : r * (1.f - r) * he * (q[1] - q[0] - dlna_dr * LLh) + (1.f - 2.f * r);
+            const float gal = clamped ? 0.f
+                                      : __fdiv_rn(2.f * he, acl) * ((1.f - r) * ln2f * BGp + r * BLp) -
+                                            (a.area_norm ? __fdiv_rn(he * LLh, 1.f + acl) : 0.f);
             G[4] = a.fix_a ? 0.f : gal - (al - a.pr_alpha_mean) * a.pr_alpha_isd2;
             const double wt = a.iw ? __ldcg(&a.iw[c0 + lane]) : 1.0;   // importance weight w_s / sum w
 #pragma unroll
@@ -1258,6 +1281,7 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
 struct PostArgs {
     int S, K, T, W, top_m;
     double csum, alpha_min;
+    int area_norm;   // area-normalised profiles: the area of phase k is h_k sum_m I_m
     const double *llpart, *lpj, *lq, *isum;
     const float *theta;
     double *logw, *pi, *scalars, *combo_logp, *cost;
@@ -1279,16 +1303,20 @@ __global__ void __launch_bounds__(128) k_post_sample(PostArgs a) {
     for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
         const float *th = a.theta + (static_cast<size_t>(s) * a.K + k) * 5;
         const double ac = th[4] > static_cast<float>(a.alpha_min) ? static_cast<double>(th[4]) : a.alpha_min;
-        const double area = static_cast<double>(th[0]) * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
-                            ((1.0 - th[3]) * AG + static_cast<double>(th[3]) * AL);
+        // area-normalised profiles: h is already the area per unit intensity
+        const double area = a.area_norm ? static_cast<double>(th[0]) * a.isum[k]
+                                        : static_cast<double>(th[0]) * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
+                                              ((1.0 - th[3]) * AG + static_cast<double>(th[3]) * AL);
         tot += area;
     }
     tot = block_sum(tot, sh);
     for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
         const float *th = a.theta + (static_cast<size_t>(s) * a.K + k) * 5;
         const double ac = th[4] > static_cast<float>(a.alpha_min) ? static_cast<double>(th[4]) : a.alpha_min;
-        const double area = static_cast<double>(th[0]) * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
-                            ((1.0 - th[3]) * AG + static_cast<double>(th[3]) * AL);
+        // area-normalised profiles: h is already the area per unit intensity
+        const double area = a.area_norm ? static_cast<double>(th[0]) * a.isum[k]
+                                        : static_cast<double>(th[0]) * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
+                                              ((1.0 - th[3]) * AG + static_cast<double>(th[3]) * AL);
         a.bits[static_cast<size_t>(s) * a.K + k] = (area / tot >= 0.01) ? 1 : 0;
     }
     if (threadIdx.x == 0) {
@@ -1560,6 +1588,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.reach_scale = P.sec ? P.sec_max : 1.0f;
     a.beta = P.bgfit ? P.beta : nullptr; a.bg_sd = P.bg_sd;
     a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0; a.r_value = P.r_value; a.a_value = P.alpha_value;
+    a.area_norm = P.area_norm ? 1 : 0;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1640,6 +1669,7 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
     a.pr_alpha_isd2 = static_cast<float>(1.0 / (P.prior.alpha_sd * P.prior.alpha_sd));
     a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0;
+    a.area_norm = P.area_norm ? 1 : 0;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
     const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;
@@ -1657,6 +1687,7 @@ void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m,
     PostArgs a;
     a.S = W.S; a.K = P.K; a.T = P.T; a.W = (P.K + 63) / 64; a.top_m = top_m;
     a.csum = P.csum; a.alpha_min = static_cast<double>(static_cast<float>(P.prior.alpha_min));
+    a.area_norm = P.area_norm ? 1 : 0;
     a.llpart = W.llpart; a.lpj = W.lpj; a.lq = W.lq; a.isum = P.isum; a.theta = W.theta;
     a.logw = B.logw; a.pi = B.pi; a.scalars = B.scalars; a.combo_logp = B.combo_logp;
     a.cost = B.cost; a.bits = B.bits; a.combos = B.combos; a.order = B.order;

@@ -54,9 +54,10 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
         return report_error(XRDVI_EINVAL, "elbo_grad_static: lambda_ must be positive, data_const finite");
     if (cfg->flags &
         (XRDVI_FLAG_IW_ELBO | XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_SEC_WIDTH | XRDVI_FLAG_FIT_BACKGROUND |
-         XRDVI_FLAG_FIX_R | XRDVI_FLAG_FIX_ALPHA))
+         XRDVI_FLAG_FIX_R | XRDVI_FLAG_FIX_ALPHA | XRDVI_FLAG_AREA_NORM))
         return report_error(XRDVI_EINVAL, "elbo_grad_static: the importance-weighted, shared-shape, angle-dependent "
-                                          "width, fitted-background and fixed-shape variants are not supported");
+                                          "width, fitted-background, fixed-shape and area-normalised variants are not "
+                                          "supported");
 
     // Layout of the scratch array for this call.
     const size_t T = (static_cast<size_t>(N) + kTile - 1) / kTile;

@@ -26,6 +26,8 @@ FLAG_SEC_WIDTH = 1 << 5       # side widths times sec(2theta / 2)
 FLAG_FIT_BACKGROUND = 1 << 6  # background correction exp(sum beta_j T_j(z)) fitted in-model
 FLAG_FIX_R = 1 << 7           # r held at fix_r_value
 FLAG_FIX_ALPHA = 1 << 8       # alpha held at fix_alpha_value
+FLAG_DEVICE_PTRS = 1 << 9     # xrdvi_create reads device arrays
+FLAG_AREA_NORM = 1 << 10      # area-normalised profiles (h = integrated intensity)
 
 
 class XrdviError(RuntimeError):
@@ -174,6 +176,19 @@ def xrdvi_create(offsets, pos, inten, x, y, bg, cfg: Config):
     return h
 
 
+def xrdvi_create_device(K, N, d_offsets, d_pos, d_inten, d_x, d_y, d_bg, cfg: Config):
+    """xrdvi_create from DEVICE arrays (integer addresses, e.g. tensor.data_ptr());
+    sets XRDVI_FLAG_DEVICE_PTRS."""
+    cfg.flags |= FLAG_DEVICE_PTRS
+    pk = Peaks(int(K), ctypes.cast(_vp(d_offsets), ctypes.POINTER(ctypes.c_int32)),
+               ctypes.cast(_vp(d_pos), ctypes.POINTER(_f)), ctypes.cast(_vp(d_inten), ctypes.POINTER(_f)))
+    pt = Pattern(int(N), ctypes.cast(_vp(d_x), ctypes.POINTER(_f)), ctypes.cast(_vp(d_y), ctypes.POINTER(_f)),
+                 ctypes.cast(_vp(d_bg), ctypes.POINTER(_f)))
+    h = _vp()
+    _check(lib().xrdvi_create(ctypes.byref(pk), ctypes.byref(pt), ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
 def xrdvi_destroy(h):
     if h:
         lib().xrdvi_destroy(h)
@@ -313,6 +328,14 @@ class Context:
     def from_instance(cls, inst, **cfg_overrides):
         cfg_overrides.setdefault("S", inst.S)
         return cls(inst.offsets, inst.pos, inst.inten, inst.x, inst.y, inst.bg, **cfg_overrides)
+
+    @classmethod
+    def from_device(cls, K, N, d_offsets, d_pos, d_inten, d_x, d_y, d_bg, **cfg_overrides):
+        """Context from DEVICE arrays (integer addresses)."""
+        self = cls.__new__(cls)
+        self.cfg = xrdvi_config_default(**cfg_overrides)
+        self.h = xrdvi_create_device(K, N, d_offsets, d_pos, d_inten, d_x, d_y, d_bg, self.cfg)
+        return self
 
     def close(self):
         if getattr(self, "h", None):

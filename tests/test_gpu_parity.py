@@ -265,3 +265,35 @@ def test_contexts_with_different_table_sizes_coexist():
     cb.close()
     cs.close()
     assert e1 == e2
+
+
+def test_create_from_device_arrays_equals_host_create():
+    import torch
+    inst = synth.small_problem(K=4, M=8, N=600, S=4, seed=23, x_step=0.03)
+    eps = synth.normals(23, 4, inst.K)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+         (inst.offsets.astype(np.int32), inst.pos, inst.inten, inst.x, inst.y, inst.bg)]
+    torch.cuda.synchronize()
+    cd = xrdvi.Context.from_device(inst.K, inst.N, *[t.data_ptr() for t in d], S=4)
+    ch = xrdvi.Context.from_instance(inst, S=4)
+    a, b = cd.elbo_grad(eps, want_f=True), ch.elbo_grad(eps, want_f=True)
+    cd.close()
+    ch.close()
+    assert a["elbo"] == b["elbo"]
+    np.testing.assert_array_equal(a["grad"], b["grad"])
+    np.testing.assert_array_equal(a["f"], b["f"])
+
+
+def test_posterior_parity_area_normalised():
+    """Posterior of the area-normalised model against the oracle's (area of a
+    phase = h sum I) on the same fitted q and draws."""
+    inst = synth.small_problem(K=5, M=10, N=600, S=8, seed=26, x_step=0.04)
+    c = xrdvi.Context.from_instance(inst, S=8, seed=3, flags=xrdvi.FLAG_AREA_NORM)
+    c.fit(200)
+    loc, raw = c.params()
+    post = c.posterior(256, 11, top_m=4)
+    c.close()
+    P = oracle.Problem.from_instance(inst, normalisation="area")
+    ref = opost.posterior(P, loc.astype(np.float64), raw.astype(np.float64), 256, seed=11, top_m=4)
+    assert np.max(np.abs(post["pi"] - ref["pi"])) <= 2.0 / 257
+    assert abs(post["log_evidence"] - ref["log_evidence"]) <= F_TOL * abs(ref["log_evidence"])

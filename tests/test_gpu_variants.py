@@ -262,3 +262,32 @@ def test_fixed_shape_fit_recovers_planted_phases_and_keeps_fixed_parameters():
     np.testing.assert_array_equal(loc1[:, 3:], loc0[:, 3:])
     np.testing.assert_array_equal(raw1[:, 3:], raw0[:, 3:])
     assert set(np.flatnonzero(post["combos"][0]).tolist()) == set(inst.planted.tolist())
+
+
+@pytest.mark.parametrize("extra,okw", [(0, {}), (xrdvi.FLAG_SHARED_SHAPES, {"shapes": "shared"})])
+def test_area_normalised_parity(extra, okw):
+    inst = synth.small_problem(K=5, M=10, N=700, S=6, seed=24, x_step=0.03)
+    g, o = _run(inst, 6, xrdvi.FLAG_AREA_NORM | extra, 24, normalisation="area", **okw)
+    _check(g, o)
+
+
+def test_area_normalised_start_is_the_height_normalised_start():
+    """The initial h is scaled by the initial shape's area, so both
+    normalisations start from the same profile."""
+    inst = synth.small_problem(K=4, M=8, N=500, S=4, seed=25)
+    eps = np.zeros((4, inst.K, 5), dtype=np.float32)
+    f = []
+    for flags in (0, xrdvi.FLAG_AREA_NORM):
+        c = xrdvi.Context.from_instance(inst, S=4, flags=flags)
+        f.append(c.elbo_grad(eps, want_f=True)["f"])
+        c.close()
+    np.testing.assert_allclose(f[1], f[0], rtol=1e-5)
+
+
+def test_area_normalised_fit_recovers_planted_phases():
+    inst = synth.config(0)
+    c = xrdvi.Context.from_instance(inst, S=inst.S, flags=xrdvi.FLAG_AREA_NORM)
+    c.fit(1000)
+    post = c.posterior(512, 3, top_m=1)
+    c.close()
+    assert set(np.flatnonzero(post["combos"][0]).tolist()) == set(inst.planted.tolist())

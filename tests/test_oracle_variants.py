@@ -276,3 +276,42 @@ def test_fixed_r_and_alpha_gradient_against_central_differences():
     free = [0, 1, 2, 5, 6, 7]
     rel = np.max(np.abs(num[:, free] - g[:, free]), axis=0) / np.max(np.abs(g[:, free]), axis=0)
     assert np.all(rel < 1e-5), rel
+
+
+@pytest.mark.parametrize("w,alpha,r", [(0.1, 1.0, 0.5), (0.05, 2.5, 0.2), (0.3, 0.4, 0.9)])
+def test_area_factor_against_quadrature(w, alpha, r):
+    """orc_area_factor equals the integral of the unit-height split
+    pseudo-Voigt (FWHM w left of the peak, alpha w right of it)."""
+    from scipy import integrate
+    lib = oracle.lib()
+
+    def v(d):
+        side = alpha * w if d >= 0 else w
+        t = d / side
+        return (1 - r) * math.exp(-4 * math.log(2) * t * t) + r / (1 + 4 * t * t)
+
+    left = integrate.quad(v, -np.inf, 0.0, epsabs=0, epsrel=1e-11, limit=500)[0]
+    right = integrate.quad(v, 0.0, np.inf, epsabs=0, epsrel=1e-11, limit=500)[0]
+    assert lib.orc_area_factor(w, alpha, r) == pytest.approx(left + right, rel=1e-8)
+
+
+def test_area_normalised_peak_integrates_to_its_intensity():
+    """One area-normalised peak (Gaussian-leaning, so the truncated tails are
+    small) integrates over a wide grid to h I."""
+    x = np.linspace(20.0, 80.0, 300001)
+    P = oracle.Problem([0, 1], [50.0], [0.7], x, np.ones_like(x), np.zeros_like(x), normalisation="area")
+    h = 123.0
+    f = P.profile(np.array([[[h, 0.01, 0.08, 0.05, 1.6]]]))[0]
+    area = np.trapezoid(f, x) if hasattr(np, "trapezoid") else np.trapz(f, x)
+    assert area == pytest.approx(h * 0.7, rel=2e-4)
+
+
+def test_area_normalised_gradient_against_central_differences():
+    inst, _ = _problem()
+    P = oracle.Problem.from_instance(inst, normalisation="area")
+    loc, raw = _perturbed(P, 13)
+    eps = synth.normals(17, 2, P.K).astype(np.float64)
+    g = P.elbo_grad(loc, raw, eps)["grad"]
+    num = _fd_grad(P, loc, raw, eps)
+    rel = np.max(np.abs(num - g), axis=0) / np.max(np.abs(g), axis=0)
+    assert np.all(rel < 1e-5), rel
