@@ -129,6 +129,16 @@ typedef struct {
  * (per unit relative intensity), the posterior's area of phase k is
  * h_k sum_m I_m, and the initial h is scaled by the initial shape's area. */
 #define XRDVI_FLAG_AREA_NORM  (1u << 10)
+/* Explicit phase gates (model variant, not in the paper, whose sparsity
+ * comes from the exponential prior on h): each phase's profile is scaled by a
+ * binary-Concrete gate z = sigmoid((a_k + L)/tau) (Maddison, Mnih & Teh,
+ * ICLR 2017) with logistic noise L and a learned logit a_k (starting at 0);
+ * the prior is the same family with logit ln(gate_prior / (1 - gate_prior)),
+ * and each draw's log joint gains ln p(y) - ln q(y) of the logit y.  The
+ * logits take the Adam step rule; xrdvi_get_gates reads them.  With injected
+ * noise (xrdvi_elbo_grad) eps holds [S*K*5] normals followed by [S*K]
+ * logistic gate noise values.  The posterior's areas use z h. */
+#define XRDVI_FLAG_GATES      (1u << 11)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */
@@ -147,11 +157,14 @@ typedef struct {
     float bg_prior_sd;        /* prior sd of the fitted-background coefficients    */
     float fix_r_value;        /* r with XRDVI_FLAG_FIX_R (in [0, 1])              */
     float fix_alpha_value;    /* alpha with XRDVI_FLAG_FIX_ALPHA                  */
+    float gate_tau;           /* gate temperature (XRDVI_FLAG_GATES)              */
+    float gate_prior;         /* prior inclusion probability of a gate, (0, 1)     */
 } xrdvi_config;
 
 /* Fills the defaults: S 256, Adam lr 0.01 betas (0.9, 0.999) eps 1e-8, seed 0,
  * priors of Appendix B.2, alpha_min 1e-3, init_h_frac 0.1, init_sigma 0.1,
- * bg_prior_sd 0.1, fix_r_value 0.5, fix_alpha_value 1. */
+ * bg_prior_sd 0.1, fix_r_value 0.5, fix_alpha_value 1, gate_tau 2/3,
+ * gate_prior 0.5. */
 void xrdvi_config_default(xrdvi_config *cfg);
 
 /* Validates and uploads the problem (one host-to-device copy), computes
@@ -181,7 +194,8 @@ xrdvi_status xrdvi_fit(xrdvi_ctx *ctx, int32_t iters, double *elbo_trace);
 
 /* One ELBO + gradient evaluation at the current q, without an update.
  * eps: NULL (noise from the fit stream at the current step) or injected
- * standard normals [S*K*5].  Outputs (each may be NULL): elbo [1],
+ * standard normals [S*K*5] (with XRDVI_FLAG_GATES [S*K*6]: the normals, then
+ * [S*K] logistic gate noise).  Outputs (each may be NULL): elbo [1],
  * grad [K*10], f_out profile [S*N], ll_out [S] log-likelihood per sample,
  * lpj_out [S] log prior + log Jacobian per sample. */
 xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *ctx, const float *eps, double *elbo, float *grad,
@@ -228,7 +242,8 @@ typedef struct {
 xrdvi_status xrdvi_get_info(xrdvi_ctx *ctx, xrdvi_info *info);
 
 /* Device-pointer entry points used by the torch.autograd.Function wrapper.
- * d_loc, d_raw: float [K*5]; d_eps: float [S*K*5] standard normals.
+ * d_loc, d_raw: float [K*5]; d_eps: float [S*K*5] standard normals (with
+ * XRDVI_FLAG_GATES [S*K*6]: the normals, then [S*K] logistic gate noise).
  * xrdvi_forward_dev writes the ELBO estimate (double) to d_elbo.
  * xrdvi_backward_dev recomputes the profiles (nothing of size S*K*N is kept)
  * and writes dELBO/d(loc, raw) to d_grad (float [K*10]).
@@ -390,6 +405,11 @@ xrdvi_status xrdvi_enumerate(const xrdvi_peaks *peaks, const xrdvi_pattern *patt
 /* Device bytes of one enumeration batch of nsub sub-models (host arithmetic;
  * 0 on invalid sizes). */
 size_t xrdvi_enumerate_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t nsub);
+
+/* Gate variant: the logits a [K] and the objective's gradient in them from
+ * the last xrdvi_elbo_grad [K] (each may be NULL), HOST buffers.  EINVAL
+ * without the flag. */
+xrdvi_status xrdvi_get_gates(xrdvi_ctx *ctx, float *logits, float *grad);
 
 /* Fitted-background variant: beta [3], the background curve B(beta) [N] and
  * the objective's gradient in beta from the last xrdvi_elbo_grad [3] (each

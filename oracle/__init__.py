@@ -55,7 +55,9 @@ class Variant(ctypes.Structure):
     _fields_ = [("lik", ctypes.c_int), ("iw", ctypes.c_int), ("shared", ctypes.c_int), ("sec", ctypes.c_int),
                 ("bgfit", ctypes.c_int), ("bg_sd", ctypes.c_double), ("beta", _PD), ("grad_beta", _PD),
                 ("m_beta", _PD), ("v_beta", _PD), ("fix_r", ctypes.c_int), ("fix_alpha", ctypes.c_int),
-                ("r_value", ctypes.c_double), ("alpha_value", ctypes.c_double), ("area_norm", ctypes.c_int)]
+                ("r_value", ctypes.c_double), ("alpha_value", ctypes.c_double), ("area_norm", ctypes.c_int),
+                ("gates", ctypes.c_int), ("gate_tau", ctypes.c_double), ("gate_prior_logit", ctypes.c_double),
+                ("gate_a", _PD), ("grad_gate", _PD), ("m_gate", _PD), ("v_gate", _PD), ("gate_noise", _PD)]
 
 
 def build(force: bool = False) -> str:
@@ -112,6 +114,9 @@ def lib():
             L.orc_profile_ex.argtypes = [i32, pi, pd, pd, i32, pd, pd, i32, pd, d, i32, i32, pd]
             L.orc_area_factor.restype = d
             L.orc_area_factor.argtypes = [d, d, d]
+            L.orc_gate_noise.argtypes = [u64, ctypes.c_uint32, ctypes.c_uint32, i32, i32, pd]
+            L.orc_gate_terms.restype = d
+            L.orc_gate_terms.argtypes = [d, d, d, d, pd, pd]
             L.orc_sec.restype = d
             L.orc_sec.argtypes = [d]
             L.orc_background.argtypes = [i32, pd, pd, pd, pd, pd]
@@ -151,7 +156,8 @@ class Problem:
                  mu_sd=PRIOR_MU_SD, alpha_mean=PRIOR_ALPHA_MEAN, alpha_sd=PRIOR_ALPHA_SD,
                  w_shape=PRIOR_W_SHAPE, w_rate=PRIOR_W_RATE, alpha_min=ALPHA_MIN,
                  likelihood="poisson", objective="elbo", shapes="independent", width="constant",
-                 background="fixed", bg_sd=0.1, fix_r=None, fix_alpha=None, normalisation="height"):
+                 background="fixed", bg_sd=0.1, fix_r=None, fix_alpha=None, normalisation="height",
+                 gates=False, gate_tau=2.0 / 3.0, gate_prior=0.5):
         # variants: likelihood "poisson" (the paper's) or "gauss" (variance
         # max(y, 1)); objective "elbo" or "iw" (importance-weighted bound);
         # shapes "independent" or "shared" (one shape draw per step); width
@@ -177,6 +183,15 @@ class Problem:
         # normalisation "height" (peak height h) or "area" (h = integrated intensity)
         assert normalisation in ("height", "area")
         self.area_norm = normalisation == "area"
+        # gates: binary-Concrete phase gates with temperature gate_tau and prior
+        # inclusion probability gate_prior; gate logits a[K] start at 0
+        self.gates = bool(gates)
+        self.gate_tau = float(gate_tau)
+        self.gate_a = None
+        self._ggate = None
+        self.variant.gates = 1 if gates else 0
+        self.variant.gate_tau = float(gate_tau)
+        self.variant.gate_prior_logit = math.log(gate_prior / (1.0 - gate_prior))
         self.off = np.ascontiguousarray(offsets, dtype=np.int32)
         self.pos, self.inten = f64(pos), f64(inten)
         self.x, self.y, self.bg = f64(x), f64(y), f64(bg)
@@ -185,6 +200,10 @@ class Problem:
             # lambda = 1 / eta with eta = max(Y - B)  (Sec. 2.2)
             lam = 1.0 / float(np.max(self.y - self.bg))
         self.prior = Prior(lam, mu_sd, alpha_mean, alpha_sd, w_shape, w_rate, alpha_min)
+        if self.gates:
+            self.gate_a = np.zeros(self.K)
+            self._ggate = np.zeros(self.K)
+            self.variant.gate_a, self.variant.grad_gate = _pd(self.gate_a), _pd(self._ggate)
 
     def free(self, j):
         """Is parameter j (h, mu, w, r, alpha) part of q?"""
@@ -249,13 +268,16 @@ class Problem:
         return (lib().orc_log_prior(ctypes.byref(self.prior), _pd(th_k)) + lib().orc_log_jac(_pd(u_k))
                 - lib().orc_fixed_lpj(ctypes.byref(self.prior), ctypes.byref(self.variant), _pd(u_k), _pd(th_k)))
 
-    def elbo_grad(self, loc, raw, eps, want_f=False):
+    def elbo_grad(self, loc, raw, eps, want_f=False, gate_noise=None):
         """ELBO estimate + per-sample LL, log prior+Jacobian and the gradient
         [K, 10] (loc grads then raw grads) for injected noise eps[S, K, 5]."""
         eps = f64(eps).copy()
         S = eps.shape[0]
         if self.shared:
             lib().orc_tie_shapes(S, self.K, _pd(eps))
+        if self.gates:   # logistic gate noise [S, K] (zeros: the gate at its location)
+            gn = np.zeros((S, self.K)) if gate_noise is None else f64(gate_noise).copy()
+            self.variant.gate_noise = _pd(gn)
         elbo = ctypes.c_double(0.0)
         ll = np.zeros(S)
         lpj = np.zeros(S)
@@ -267,6 +289,8 @@ class Problem:
         out = {"elbo": elbo.value, "ll": ll, "lpj": lpj, "grad": grad}
         if self.bgfit:
             out["grad_beta"] = self._gb.copy()
+        if self.gates:
+            out["grad_gate"] = self._ggate.copy()
         if want_f:
             out["f"] = f
         return out
@@ -304,11 +328,17 @@ class Problem:
         mb = np.zeros(3) if m_beta is None else f64(m_beta).copy()
         vb = np.zeros(3) if v_beta is None else f64(v_beta).copy()
         self.variant.m_beta, self.variant.v_beta = _pd(mb), _pd(vb)
+        mg = np.zeros(self.K)
+        vg = np.zeros(self.K)
+        if self.gates:
+            self.variant.m_gate, self.variant.v_gate = _pd(mg), _pd(vg)
         lib().orc_fit_ex(*self._args(), ctypes.byref(self.prior), ctypes.byref(self.variant), S, seed, t0, iters,
                          lr, b1, b2, adam_eps, _pd(loc), _pd(raw), _pd(m), _pd(v), _pd(trace))
         out = {"loc": loc, "raw": raw, "m": m, "v": v, "trace": trace}
         if self.bgfit:
             out.update({"beta": self.beta.copy(), "m_beta": mb, "v_beta": vb})
+        if self.gates:
+            out.update({"gate_a": self.gate_a.copy(), "m_gate": mg, "v_gate": vg})
         return out
 
 
@@ -319,6 +349,20 @@ def iw_weights(raw, eps, ll, lpj):
     wt = np.zeros(S)
     L = lib().orc_iw_weights(K, S, _pd(f64(raw)), _pd(eps), _pd(f64(ll)), _pd(f64(lpj)), None, _pd(wt))
     return L, wt
+
+
+def gate_noise(seed, tag, it, S, K):
+    """Logistic gate noise [S, K] of the oracle's stream."""
+    L = np.zeros((S, K))
+    lib().orc_gate_noise(seed, tag, it, S, K, _pd(L))
+    return L
+
+
+def gate_terms(a, L, tau, a0):
+    """(z, ln p(y) - ln q(y), d ln p / dy) of one binary-Concrete gate."""
+    z, dp = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    v = lib().orc_gate_terms(float(a), float(L), float(tau), float(a0), ctypes.byref(z), ctypes.byref(dp))
+    return z.value, v, dp.value
 
 
 def philox(ctr, key):

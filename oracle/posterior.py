@@ -140,22 +140,35 @@ def log_q(raw, eps, free=None):
     return np.sum(terms, axis=(1, 2))
 
 
-def posterior(prob: Problem, loc, raw, S_post, seed=None, eps=None, top_m=8, threshold=0.01):
+def posterior(prob: Problem, loc, raw, S_post, seed=None, eps=None, top_m=8, threshold=0.01, gate_noise=None):
     """Posterior summary of a fitted q.  Noise: eps[S_post, K, 5] if given,
-    else the oracle's Philox stream with tag 1 (posterior) at step 0."""
+    else the oracle's Philox stream with tag 1 (posterior) at step 0 (gates:
+    gate_noise[S_post, K], else the gate stream with tag 1)."""
     if eps is None:
         eps = normals(seed, 1, 0, S_post, prob.K)
     eps = f64(eps)
     u, th = prob.theta(loc, raw, eps)
-    f = prob.profile(th)
+    glp = np.zeros(S_post)
+    th_eff = th
+    if getattr(prob, "gates", False):   # the gate z scales the phase's profile and its area
+        from . import gate_noise as _gn, gate_terms
+        L = _gn(seed, 1, 0, S_post, prob.K) if gate_noise is None else f64(gate_noise)
+        th_eff = th.copy()
+        for s in range(S_post):
+            for k in range(prob.K):
+                z, v, _ = gate_terms(prob.gate_a[k], L[s, k], prob.gate_tau, prob.variant.gate_prior_logit)
+                th_eff[s, k, 0] *= z
+                glp[s] += v
+    f = prob.profile(th_eff)
     ll = np.array([prob.loglik(f[s]) for s in range(S_post)])
     lpj = np.zeros(S_post)
     for s in range(S_post):
         for k in range(prob.K):
             lpj[s] += prob.log_prior_jac(u[s, k], th[s, k])
+    lpj += glp
     lq = log_q(raw, eps, [prob.free(j) for j in range(5)])
     logw = ll + lpj - lq
-    areas = phase_areas(prob, th)
+    areas = phase_areas(prob, th_eff)
     bits = inclusion_bits(areas, threshold)
     pi = marginal_pi(bits)
     combos, clp = top_combinations(pi, top_m)

@@ -94,6 +94,50 @@ void orc_normals(uint64_t seed, uint32_t tag, uint32_t iter, int S, int K, doubl
     }
 }
 
+double orc_softplus(double x);
+double orc_sigmoid(double x);
+
+/*
+ * Logistic noise of the gate variant: for sample s, phase k, step iter and
+ * stream tag, the first output of Philox4x32-10 at counter
+ * (s, k, iter, tag*256 + 2) gives u in (0, 1) and L = ln u - ln(1 - u).
+ */
+void orc_gate_noise(uint64_t seed, uint32_t tag, uint32_t iter, int S, int K, double *L)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int s = 0; s < S; ++s)
+        for (int k = 0; k < K; ++k) {
+            uint32_t c[4] = {(uint32_t)s, (uint32_t)k, iter, tag * 256u + 2u}, o[4];
+            orc_philox4x32_10(c, key, o);
+            double u = orc_u01(o[0]);
+            L[(size_t)s * K + k] = log(u) - log1p(-u);
+        }
+}
+
+/*
+ * Binary-Concrete gate (Maddison, Mnih & Teh, "The Concrete Distribution",
+ * ICLR 2017; Reading: a model variant, not in the paper, whose sparsity comes
+ * from the exponential prior on h).  With location a (a logit), temperature
+ * tau and logistic noise L, y = (a + L) / tau and the gate is z = sigmoid(y).
+ * The density of y is
+ *   ln q(y) = ln tau + a - tau y - 2 softplus(a - tau y),
+ * and the prior is the same family with location a0 = ln(pi0/(1 - pi0)) and
+ * the same temperature.  Per draw and phase the objective gains
+ * ln p(y) - ln q(y); its reparameterisation gradient in a is
+ * (1/tau) [dLL/dy + d ln p/dy] (the ln q terms cancel for a location family),
+ * with d ln p/dy = tau (2 sigmoid(a0 - tau y) - 1) and dLL/dy = dLL/dz z(1-z).
+ * Writes z and returns ln p(y) - ln q(y); *dlnp_dy receives d ln p/dy.
+ */
+double orc_gate_terms(double a, double L, double tau, double a0, double *z, double *dlnp_dy)
+{
+    double y = (a + L) / tau;
+    *z = orc_sigmoid(y);
+    double lq = log(tau) + a - tau * y - 2.0 * orc_softplus(a - tau * y);
+    double lp = log(tau) + a0 - tau * y - 2.0 * orc_softplus(a0 - tau * y);
+    *dlnp_dy = tau * (2.0 * orc_sigmoid(a0 - tau * y) - 1.0);
+    return lp - lq;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Variational transform                                                    */
 /* ------------------------------------------------------------------------ */
@@ -306,6 +350,8 @@ typedef struct {
  *   sec     1: angle-dependent width, every side width at point x multiplied
  *           by sec(theta), theta = x / 2 (x = 2-theta in degrees)   (orc_sec)
  *   bgfit   1: background fitted in-model                   (orc_background)
+ *   gates   1: explicit phase gates z = sigmoid((a + L)/tau) scale each
+ *           phase's profile (not in the paper; orc_gate_terms)
  *   area_norm 1: each phase's profile divided by its area per unit height
  *           (orc_area_factor), so h is an integrated intensity
  *   fix_r, fix_alpha  1: r / alpha held at a given value: a constant of the
@@ -322,6 +368,12 @@ typedef struct {
     int fix_r, fix_alpha;      /* 1: r / alpha held at r_value / alpha_value       */
     double r_value, alpha_value;
     int area_norm;             /* 1: area-normalised profiles (orc_area_factor)    */
+    int gates;                 /* 1: binary-Concrete phase gates (orc_gate_terms)   */
+    double gate_tau, gate_prior_logit;   /* temperature; prior logit ln(pi0 / (1 - pi0)) */
+    double *gate_a;            /* [K] gate logits (in; orc_fit_ex updates them)     */
+    double *grad_gate;         /* [K] d objective / d gate_a (may be NULL)          */
+    double *m_gate, *v_gate;   /* [K] their Adam moments (orc_fit_ex)               */
+    const double *gate_noise;  /* [S*K] logistic noise L (orc_gate_noise)           */
 } orc_variant;
 
 /* ln p(theta) for one phase: Exp(lambda) on h, normal on mu and alpha,
@@ -460,6 +512,8 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
 {
     const int lik = var ? var->lik : 0, iw = var ? var->iw : 0, sec = var ? var->sec : 0;
     const int bgfit = var ? var->bgfit : 0;
+    const int gates = var ? var->gates : 0;
+    double *gg = gates ? (double *)calloc((size_t)S * K, sizeof(double)) : NULL;   /* per-draw gate gradients */
     double *Bb = NULL, *Tb = NULL, *gbs = NULL, lpb = 0.0;
     if (bgfit) {   /* fitted background: B(beta), its Chebyshev terms, per-draw beta sums */
         Bb = (double *)malloc((size_t)N * sizeof(double));
@@ -488,6 +542,15 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
         double *gi = (double *)malloc((size_t)N * sizeof(double));
         const double *ths = th + (size_t)s * K * 5;
         const double *us = u + (size_t)s * K * 5;
+        /* gates: z_k of this draw, its ln p - ln q and d ln p / dy */
+        double *zg = NULL, *dpg = NULL, glp = 0.0;
+        if (gates) {
+            zg = (double *)malloc((size_t)K * sizeof(double));
+            dpg = (double *)malloc((size_t)K * sizeof(double));
+            for (int k = 0; k < K; ++k)
+                glp += orc_gate_terms(var->gate_a[k], var->gate_noise[(size_t)s * K + k], var->gate_tau,
+                                      var->gate_prior_logit, &zg[k], &dpg[k]);
+        }
         /* forward: profile, likelihood */
         for (int i = 0; i < N; ++i) {
             double acc = bg[i];
@@ -499,14 +562,14 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 for (int m = off[k]; m < off[k + 1]; ++m)
                     C += inten[m] * orc_pvoigt(x[i] - (pos[m] + t[1]), wx, t[3], ac);
                 if (var && var->area_norm) C /= orc_area_factor(t[2], ac, t[3]);
-                acc += t[0] * C;
+                acc += t[0] * C * (gates ? zg[k] : 1.0);
             }
             f[i] = acc;
             gi[i] = lik ? (y[i] - acc) / orc_gauss_var(y[i]) : y[i] / acc - 1.0;
         }
         if (f_out) memcpy(f_out + (size_t)s * N, f, (size_t)N * sizeof(double));
         lls[s] = lik ? orc_loglik_gauss(N, y, f) : orc_loglik_direct(N, y, f);
-        double lp = lpb;   /* ln p(beta) of the fitted background (0 otherwise) */
+        double lp = lpb + glp;   /* ln p(beta) of the fitted background, gate terms (0 otherwise) */
         for (int k = 0; k < K; ++k)
             lp += orc_log_prior(pr, ths + k * 5) + orc_log_jac(us + k * 5) - orc_fixed_lpj(pr, var, us + k * 5, ths + k * 5);
         lps[s] = lp;
@@ -516,7 +579,8 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
         /* backward: per-phase likelihood gradient in theta, chained to u */
         for (int k = 0; k < K; ++k) {
             const double *t = ths + k * 5;
-            double h = t[0], mu = t[1], w = t[2], r = t[3], al = t[4];
+            double h0 = t[0], mu = t[1], w = t[2], r = t[3], al = t[4];
+            double h = gates ? h0 * zg[k] : h0;   /* the phase's profile scale */
             int clamped = !(al > pr->alpha_min);
             double ac = clamped ? pr->alpha_min : al;
             double dh = 0, dmu = 0, dw = 0, dr = 0, dal = 0;
@@ -561,6 +625,8 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
             orc_prior_jac_grad(pr, t, pj);
             double *Gs = G + ((size_t)s * K + k) * 5;
             Gs[0] = dh * h + pj[0];
+            if (gates)   /* dLL/dz = h0 dh; dy: times z(1 - z); then (1/tau)(dLL/dy + d ln p/dy) */
+                gg[(size_t)s * K + k] = (h0 * dh * zg[k] * (1.0 - zg[k]) + dpg[k]) / var->gate_tau;
             Gs[1] = dmu + pj[1];
             Gs[2] = dw * w + pj[2];
             Gs[3] = orc_free(var, 3) ? dr * r * (1.0 - r) + pj[3] : 0.0;
@@ -568,6 +634,8 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
         }
         free(f);
         free(gi);
+        free(zg);
+        free(dpg);
     }
 
     /* sample weights: 1/S for the ELBO; for the importance-weighted bound the
@@ -601,6 +669,13 @@ void orc_elbo_grad_ex(int K, const int *off, const double *pos, const double *in
                 grad[k * 10 + 5 + j] = orc_free(var, j) ? (ge + 1.0 / orc_softplus(rw)) * orc_sigmoid(rw) : 0.0;
             }
     }
+    if (gates && var->grad_gate)
+        for (int k = 0; k < K; ++k) {
+            double gsum = 0.0;
+            for (int s = 0; s < S; ++s) gsum += wt[s] * gg[(size_t)s * K + k];
+            var->grad_gate[k] = gsum;
+        }
+    free(gg);
     if (bgfit && var->grad_beta)
         for (int j = 0; j < 3; ++j) {
             double gsum = 0.0;
@@ -674,18 +749,23 @@ void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
     double *eps = (double *)malloc((size_t)S * K * 5 * sizeof(double));
     double *grad = (double *)malloc((size_t)K * 10 * sizeof(double));
     double *par = (double *)malloc((size_t)K * 10 * sizeof(double));
+    double *gnoise = (double *)malloc((size_t)S * K * sizeof(double));
+    double *ggate = (double *)malloc((size_t)K * sizeof(double));
     for (int t = 0; t < iters; ++t) {
         orc_normals(seed, 0u, (uint32_t)(t0 + t), S, K, eps);
         if (var && var->shared) orc_tie_shapes(S, K, eps);
+        if (var && var->gates) orc_gate_noise(seed, 0u, (uint32_t)(t0 + t), S, K, gnoise);
         double elbo;
         double gb[3] = {0.0, 0.0, 0.0};
         orc_variant v2;
-        if (var) { v2 = *var; v2.grad_beta = gb; }
+        if (var) { v2 = *var; v2.grad_beta = gb; v2.grad_gate = ggate; v2.gate_noise = gnoise; }
         orc_elbo_grad_ex(K, off, pos, inten, N, x, y, bg, pr, var ? &v2 : NULL, S, loc, raw, eps, &elbo, NULL, NULL,
                          grad, NULL);
         if (trace) trace[t] = elbo;
         if (var && var->bgfit)   /* the background coefficients take the same Adam step rule */
             orc_adam_step(3, var->beta, gb, var->m_beta, var->v_beta, t0 + t + 1, lr, b1, b2, adam_eps);
+        if (var && var->gates)   /* and so do the gate logits */
+            orc_adam_step(K, var->gate_a, ggate, var->m_gate, var->v_gate, t0 + t + 1, lr, b1, b2, adam_eps);
         for (int k = 0; k < K; ++k)
             for (int j = 0; j < 5; ++j) {
                 par[k * 10 + j] = loc[k * 5 + j];
@@ -698,7 +778,7 @@ void orc_fit_ex(int K, const int *off, const double *pos, const double *inten,
                 raw[k * 5 + j] = par[k * 10 + 5 + j];
             }
     }
-    free(eps); free(grad); free(par);
+    free(eps); free(grad); free(par); free(gnoise); free(ggate);
 }
 
 void orc_fit(int K, const int *off, const double *pos, const double *inten,

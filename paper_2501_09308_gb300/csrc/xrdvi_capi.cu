@@ -156,7 +156,7 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
     XR_TRY(c->alloc(&W.llpart, static_cast<size_t>(S) * P.T, list));
     if (fit) {
         XR_TRY(c->alloc(&W.gpart, SK * P.T * kGradSums, list));
-        XR_TRY(c->alloc(&W.gred, static_cast<size_t>(W.B) * P.K * kGradBlocks * 10, list));
+        XR_TRY(c->alloc(&W.gred, static_cast<size_t>(W.B) * P.K * kGradBlocks * kGredVals, list));
         XR_TRY(c->alloc(&W.tickets, static_cast<size_t>(W.B) * P.K, list));
         W.lq = nullptr;
         W.iw = nullptr;
@@ -169,6 +169,7 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
         XR_TRY(c->alloc(&W.lq, static_cast<size_t>(S), list));
         W.gpart = nullptr;
     }
+    if (P.gates) XR_TRY(c->alloc(&W.gzy, SK * 2, list));
     choose_chunks(P, c->host_off.data(), S, W);
     W.fpart_cap = static_cast<size_t>(W.C) * S * P.Npad;
     XR_TRY(c->alloc(&W.fpart, W.fpart_cap, list));
@@ -267,6 +268,9 @@ xrdvi_status validate(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdv
         return fail(XRDVI_EINVAL, "fix_r_value must be in [0, 1]");
     if ((cfg->flags & XRDVI_FLAG_FIX_ALPHA) && !std::isfinite(cfg->fix_alpha_value))
         return fail(XRDVI_EINVAL, "fix_alpha_value must be finite");
+    if ((cfg->flags & XRDVI_FLAG_GATES) &&
+        !(cfg->gate_tau > 0.f && cfg->gate_tau < 100.f && cfg->gate_prior > 0.f && cfg->gate_prior < 1.f))
+        return fail(XRDVI_EINVAL, "gates need gate_tau in (0, 100) and gate_prior in (0, 1)");
     const float pos_params[] = {cfg->prior_mu_sd, cfg->prior_alpha_sd, cfg->prior_w_shape, cfg->prior_w_rate,
                                 cfg->alpha_min, cfg->init_h_frac, cfg->init_sigma, cfg->lr};
     for (float q : pos_params)
@@ -327,6 +331,8 @@ void xrdvi_config_default(xrdvi_config *cfg) {
     cfg->bg_prior_sd = 0.1f;
     cfg->fix_r_value = 0.5f;
     cfg->fix_alpha_value = 1.f;
+    cfg->gate_tau = 2.f / 3.f;
+    cfg->gate_prior = 0.5f;
 }
 
 xrdvi_status xrdvi_create(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
@@ -370,8 +376,9 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     const int K = pk->K, N = pt->N, M = pk->offsets[K];
     if (nsub < 1 || static_cast<int64_t>(nsub) * cfg->S > kMaxS)
         return fail(XRDVI_EINVAL, "sub-model batch: B * S must be in [1, 65536]");
-    if (masks && (cfg->flags & (XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_FIT_BACKGROUND)))
-        return fail(XRDVI_EINVAL, "the shared-shape and fitted-background variants do not run in sub-model batches");
+    if (masks && (cfg->flags & (XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_FIT_BACKGROUND | XRDVI_FLAG_GATES)))
+        return fail(XRDVI_EINVAL,
+                    "the shared-shape, fitted-background and gate variants do not run in sub-model batches");
     if (masks) {
         if (K > 32) return fail(XRDVI_EINVAL, "sub-model batch: K must be <= 32");
         for (int b = 0; b < nsub; ++b)
@@ -468,6 +475,9 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     P.prior.alpha_min = cfg->alpha_min;
     P.prior.lp_const = prior_constant(P.prior);
     P.area_norm = (cfg->flags & XRDVI_FLAG_AREA_NORM) != 0;
+    P.gates = (cfg->flags & XRDVI_FLAG_GATES) != 0;
+    P.gate_tau = cfg->gate_tau;
+    P.gate_a0 = static_cast<float>(std::log(cfg->gate_prior / (1.0 - cfg->gate_prior)));
     P.fix_r = (cfg->flags & XRDVI_FLAG_FIX_R) != 0;
     P.fix_alpha = (cfg->flags & XRDVI_FLAG_FIX_ALPHA) != 0;
     P.r_value = cfg->fix_r_value;
@@ -489,6 +499,12 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     XR_C(c->alloc(&P.bg, N));
     XR_C(c->alloc(&P.isum, K));
     if (sec) XR_C(c->alloc(&P.csec, N));
+    if (P.gates) {   // gate logits start at 0 (z = sigmoid(L / tau))
+        XR_C(c->alloc(&P.gate_a, K));
+        XR_C(c->alloc(&P.m_gate, K));
+        XR_C(c->alloc(&P.v_gate, K));
+        XR_C(c->alloc(&P.grad_gate, K));
+    }
     std::vector<float> Tb;
     if (cfg->flags & XRDVI_FLAG_FIT_BACKGROUND) {
         // fitted background: Chebyshev terms of the grid mapped onto [-1, 1]
@@ -583,6 +599,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s) ||
         (d_mask && (up(d_mask, masks, static_cast<size_t>(nsub) * 4) ||
                     cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))) ||
+        (P.gates && (cudaMemsetAsync(P.gate_a, 0, K * 4, s) || cudaMemsetAsync(P.m_gate, 0, K * 4, s) ||
+                     cudaMemsetAsync(P.v_gate, 0, K * 4, s) || cudaMemsetAsync(P.grad_gate, 0, K * 4, s))) ||
         (P.bgfit && (up(P.Tb, Tb.data(), Tb.size() * 4) || cudaMemsetAsync(P.beta, 0, 12, s) ||
                      cudaMemsetAsync(P.m_beta, 0, 12, s) || cudaMemsetAsync(P.v_beta, 0, 12, s) ||
                      cudaMemsetAsync(c->grad_beta, 0, 12, s))) ||
@@ -651,7 +669,8 @@ xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float
     if (!c) return fail(XRDVI_EINVAL, "null context");
     const Problem &P = c->P;
     const int S = c->W.S;
-    const size_t SK5 = static_cast<size_t>(S) * P.K * 5;
+    // injected noise: [S*K*5] normals, followed with gates by [S*K] logistic gate noise
+    const size_t SK5 = static_cast<size_t>(S) * P.K * (P.gates ? 6 : 5);
     cudaStream_t st = c->stream;
     if (eps) {
         if (!finite_all(eps, SK5)) return fail(XRDVI_EINVAL, "eps must be finite");
@@ -826,7 +845,8 @@ struct StateHeader {
 xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
     if (!c || !len) return fail(XRDVI_EINVAL, "null argument");
     const int K = c->P.K;
-    const int extra = c->P.bgfit ? 9 : 0;   // fitted background: beta, its Adam moments
+    // fitted background: beta and its Adam moments; gates: logits and their moments
+    const int extra = (c->P.bgfit ? 9 : 0) + (c->P.gates ? 3 * K : 0);
     const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * (5 + 5 + 10 + 10) * 4 + extra * 4;
     if (!buf) {
         *len = need;
@@ -841,10 +861,17 @@ xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
     XR_CUDA(cudaMemcpyAsync(p + K * 20, c->raw, K * 20, cudaMemcpyDeviceToHost, c->stream));
     XR_CUDA(cudaMemcpyAsync(p + K * 40, c->m, K * 40, cudaMemcpyDeviceToHost, c->stream));
     XR_CUDA(cudaMemcpyAsync(p + K * 80, c->v, K * 40, cudaMemcpyDeviceToHost, c->stream));
-    if (extra) {
-        XR_CUDA(cudaMemcpyAsync(p + K * 120, c->P.beta, 12, cudaMemcpyDeviceToHost, c->stream));
-        XR_CUDA(cudaMemcpyAsync(p + K * 120 + 12, c->P.m_beta, 12, cudaMemcpyDeviceToHost, c->stream));
-        XR_CUDA(cudaMemcpyAsync(p + K * 120 + 24, c->P.v_beta, 12, cudaMemcpyDeviceToHost, c->stream));
+    char *q = p + K * 120;
+    if (c->P.bgfit) {
+        XR_CUDA(cudaMemcpyAsync(q, c->P.beta, 12, cudaMemcpyDeviceToHost, c->stream));
+        XR_CUDA(cudaMemcpyAsync(q + 12, c->P.m_beta, 12, cudaMemcpyDeviceToHost, c->stream));
+        XR_CUDA(cudaMemcpyAsync(q + 24, c->P.v_beta, 12, cudaMemcpyDeviceToHost, c->stream));
+        q += 36;
+    }
+    if (c->P.gates) {
+        XR_CUDA(cudaMemcpyAsync(q, c->P.gate_a, K * 4, cudaMemcpyDeviceToHost, c->stream));
+        XR_CUDA(cudaMemcpyAsync(q + K * 4, c->P.m_gate, K * 4, cudaMemcpyDeviceToHost, c->stream));
+        XR_CUDA(cudaMemcpyAsync(q + K * 8, c->P.v_gate, K * 4, cudaMemcpyDeviceToHost, c->stream));
     }
     XR_CUDA(cudaStreamSynchronize(c->stream));
     *len = need;
@@ -854,7 +881,7 @@ xrdvi_status xrdvi_get_state(xrdvi_ctx *c, void *buf, size_t *len) {
 xrdvi_status xrdvi_set_state(xrdvi_ctx *c, const void *buf, size_t len) {
     if (!c || !buf) return fail(XRDVI_EINVAL, "null argument");
     const int K = c->P.K;
-    const int extra = c->P.bgfit ? 9 : 0;
+    const int extra = (c->P.bgfit ? 9 : 0) + (c->P.gates ? 3 * K : 0);
     const size_t need = sizeof(StateHeader) + static_cast<size_t>(K) * 120 + extra * 4;
     if (len < need) return fail(XRDVI_EINVAL, "state buffer too small");
     StateHeader h;
@@ -868,16 +895,33 @@ xrdvi_status xrdvi_set_state(xrdvi_ctx *c, const void *buf, size_t len) {
     XR_CUDA(cudaMemcpyAsync(c->raw, p + K * 20, K * 20, cudaMemcpyHostToDevice, c->stream));
     XR_CUDA(cudaMemcpyAsync(c->m, p + K * 40, K * 40, cudaMemcpyHostToDevice, c->stream));
     XR_CUDA(cudaMemcpyAsync(c->v, p + K * 80, K * 40, cudaMemcpyHostToDevice, c->stream));
-    if (extra) {
-        XR_CUDA(cudaMemcpyAsync(c->P.beta, p + K * 120, 12, cudaMemcpyHostToDevice, c->stream));
-        XR_CUDA(cudaMemcpyAsync(c->P.m_beta, p + K * 120 + 12, 12, cudaMemcpyHostToDevice, c->stream));
-        XR_CUDA(cudaMemcpyAsync(c->P.v_beta, p + K * 120 + 24, 12, cudaMemcpyHostToDevice, c->stream));
+    const char *q = p + K * 120;
+    if (c->P.bgfit) {
+        XR_CUDA(cudaMemcpyAsync(c->P.beta, q, 12, cudaMemcpyHostToDevice, c->stream));
+        XR_CUDA(cudaMemcpyAsync(c->P.m_beta, q + 12, 12, cudaMemcpyHostToDevice, c->stream));
+        XR_CUDA(cudaMemcpyAsync(c->P.v_beta, q + 24, 12, cudaMemcpyHostToDevice, c->stream));
+        q += 36;
+    }
+    if (c->P.gates) {
+        XR_CUDA(cudaMemcpyAsync(c->P.gate_a, q, K * 4, cudaMemcpyHostToDevice, c->stream));
+        XR_CUDA(cudaMemcpyAsync(c->P.m_gate, q + K * 4, K * 4, cudaMemcpyHostToDevice, c->stream));
+        XR_CUDA(cudaMemcpyAsync(c->P.v_gate, q + K * 8, K * 4, cudaMemcpyHostToDevice, c->stream));
     }
     XR_CUDA(cudaMemcpyAsync(c->step, &step, 4, cudaMemcpyHostToDevice, c->stream));
     XR_CUDA(cudaStreamSynchronize(c->stream));
     c->host_step = h.step;
     c->cfg.seed = h.seed;
     c->drop_graphs();  // the seed is a kernel argument of the captured step
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_get_gates(xrdvi_ctx *c, float *logits, float *grad) {
+    if (!c) return fail(XRDVI_EINVAL, "null context");
+    if (!c->P.gates) return fail(XRDVI_EINVAL, "the context has no gates");
+    const size_t n = static_cast<size_t>(c->P.K) * 4;
+    if (logits) XR_CUDA(cudaMemcpyAsync(logits, c->P.gate_a, n, cudaMemcpyDeviceToHost, c->stream));
+    if (grad) XR_CUDA(cudaMemcpyAsync(grad, c->P.grad_gate, n, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
     return XRDVI_OK;
 }
 

@@ -24,7 +24,8 @@ constexpr int kGradSums = 10;
 // Phases are split into up to kMaxChunks chunks of similar peak count so that
 // the profile kernels have enough equal-sized work items to fill the GPU.
 constexpr int kMaxChunks = 8;
-constexpr int kItemsPerWarp = 8;   // profile work items per resident warp the phase chunking aims for
+constexpr int kItemsPerWarp = 8;
+constexpr int kGredVals = 11;      // per-(phase, sample block) gradient partials: loc 5, raw 5, gate 1   // profile work items per resident warp the phase chunking aims for
 // Work counters of the profile kernels of one sample set.
 constexpr int kCounters = 4;
 // Sample blocks per phase in the gradient reduction.
@@ -102,6 +103,7 @@ struct Workspace {
     const uint32_t *mask = nullptr;   // [B] device
     double *tail_sum = nullptr;       // [B] sum of the ELBO estimates from step tail_start on
     float *bgpart = nullptr;          // [S*T*3] per-(sample, tile) sums g B(beta) T_j (fitted background)
+    float *gzy = nullptr;             // [S*K*2] gate z and y of every draw and phase (gates)
     double *iw = nullptr;             // [S] normalised importance weights (importance-weighted
                                       //     objective; null: the ELBO, weights 1/S)
     // Shared-shape variant (one shape draw per step for all samples): the
@@ -139,6 +141,10 @@ struct Problem {
     bool gauss = false;          // Gaussian likelihood variant (variance max(y, 1))
     bool fix_r = false, fix_alpha = false;   // r / alpha held at r_value / alpha_value
     bool area_norm = false;      // area-normalised profiles (h = integrated intensity)
+    // binary-Concrete phase gates: logits a[K], temperature, prior logit
+    bool gates = false;
+    float gate_tau = 2.f / 3.f, gate_a0 = 0.f;
+    float *gate_a = nullptr, *m_gate = nullptr, *v_gate = nullptr, *grad_gate = nullptr;   // [K]
     float r_value = 0.5f, alpha_value = 1.f;
     bool sec = false;            // angle-dependent width variant (side widths times sec(x/2))
     float *csec = nullptr;       // [N] cos(x_i / 2) for that variant

@@ -160,6 +160,9 @@ struct SampleArgs {
     int fix_r, fix_a;      // r / alpha held fixed (model constants, not in q)
     float r_value, a_value;
     int area_norm;         // area-normalised profiles: h / a(w, alpha, r) scales the profile
+    const float *gate_a;   // [K] gate logits (null: no gates)
+    float gate_tau, gate_a0;   // temperature, prior logit
+    float *gzy;            // [S*K*2] gate z and y per draw and phase
     int shared;            // shape noise of every sample = sample 0's (shared-shape variant)
     float *H;              // [S*Kpad] h_sk for the forward GEMM (shared-shape variant)
     int Kpad;
@@ -260,7 +263,32 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         const float sl = 2.0f / wl, sr = 2.0f / wr;
         // area-normalised profiles divide by the area of the unit-height shape
         // a(w, alpha, r) = ((1 + alpha) w / 2) [(1 - r) sqrt(pi/ln2)/2 + r pi/2]
-        const float he = a.area_norm ? __fdiv_rn(h, area_factorf(w, ac, r)) : h;
+        float he = a.area_norm ? __fdiv_rn(h, area_factorf(w, ac, r)) : h;
+        float glp = 0.f;
+        if (a.gate_a) {
+            // binary-Concrete gate: y = (a + L)/tau with logistic noise L, z = sigmoid(y)
+            // scales the profile; the draw's log joint gains ln p(y) - ln q(y)
+            float L;
+            if (a.eps_in) {
+                L = a.eps_in[static_cast<size_t>(5) * a.S * a.K + static_cast<size_t>(s) * a.K + k];
+            } else {
+                uint32_t c[4] = {static_cast<uint32_t>(s_loc), kl, step, a.tag * 256u + 2u};
+                philox4x32_10(c, a.key0, a.key1);
+                // ln u - ln(1 - u) with 1 - u taken from the complemented counter
+                // word (exactly 1 - u in real arithmetic), so that the rounding
+                // of u to 1.0f near the top never gives an infinite L
+                L = logf(u01(c[0])) - logf(u01(~c[0]));
+            }
+            const float ga = a.gate_a[k], tau = a.gate_tau;
+            const float y = __fdiv_rn(ga + L, tau);
+            const float z = sigmoidf(y);
+            const float lq = logf(tau) + ga - tau * y - 2.f * softplusf(ga - tau * y);
+            const float lp = logf(tau) + a.gate_a0 - tau * y - 2.f * softplusf(a.gate_a0 - tau * y);
+            glp = lp - lq;
+            he *= z;
+            a.gzy[(static_cast<size_t>(s) * a.K + k) * 2] = z;
+            a.gzy[(static_cast<size_t>(s) * a.K + k) * 2 + 1] = y;
+        }
         if (a.H) {   // TF32 hi / lo parts of the profile scale for the forward GEMM
             const float hh = tf32_hi(he);
             a.H[static_cast<size_t>(s) * a.Kpad + k] = hh;
@@ -286,7 +314,7 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         const float za = a.fix_a ? 0.f : (al - a.pr_alpha_mean) * a.pr_alpha_isd;   // fixed: no prior
         const float lpf = -a.pr_lambda * h - 0.5f * zm * zm - 0.5f * za * za + a.pr_wsm1 * u[2] - a.pr_wrate * w;
         const float ljf = u[0] + u[2] - (a.fix_r ? 0.f : softplusf(-u[3]) + softplusf(u[3]));
-        acc += a.pr.lp_const + static_cast<double>(lpf) + static_cast<double>(ljf);
+        acc += a.pr.lp_const + static_cast<double>(lpf) + static_cast<double>(ljf) + static_cast<double>(glp);
         if (a.lq) {
             float q = 0.f;
             int nfree = 0;
@@ -1075,6 +1103,10 @@ struct GradArgs {
     float pr_lambda, pr_mu_isd2, pr_w_shape, pr_w_rate, pr_alpha_mean, pr_alpha_isd2;
     int fix_r, fix_a;   // r / alpha held fixed: zero gradient, no update
     int area_norm;      // area-normalised profiles
+    const float *gzy;   // [S*K*2] gate z, y (null: no gates)
+    float gate_tau, gate_a0;
+    float *gate_a, *m_gate, *v_gate;   // [K] gate logits and their Adam moments
+    float *grad_gate;   // [K] gate gradient out (may be null)
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -1130,7 +1162,7 @@ __global__ void __launch_bounds__(256) k_elbo(GradArgs a) {
 // Adam.
 __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
     __shared__ float qs[32][kGradSums + 1];
-    __shared__ double red[10];
+    __shared__ double red[kGredVals];
     __shared__ int is_last;
     const int bk = blockIdx.x, b = blockIdx.y;   // (sub-model, phase), sample block
     const int sm = bk / a.K, k = bk - sm * a.K;
@@ -1138,7 +1170,7 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s0 = sm * a.S_sub + static_cast<int>((static_cast<long long>(a.S_sub) * b) / a.NB);
     const int s1 = sm * a.S_sub + static_cast<int>((static_cast<long long>(a.S_sub) * (b + 1)) / a.NB);
-    double accl[5] = {0, 0, 0, 0, 0}, acce[5] = {0, 0, 0, 0, 0};
+    double accl[5] = {0, 0, 0, 0, 0}, acce[5] = {0, 0, 0, 0, 0}, accg = 0.0;
     for (int c0 = s0; c0 < s1; c0 += 32) {
         const int nc = s1 - c0 < 32 ? s1 - c0 : 32;
         for (int i = warp; i < nc; i += kWarps) {
@@ -1188,7 +1220,8 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             // the profile scale he: h, or h / a(w, alpha, r) for area-normalised
             // profiles, whose derivatives add -he * dLL/dhe * d ln a / d(u_w, r, alpha)
             const float aw = a.area_norm ? area_factorf(w, acl, r) : 1.f;
-            const float he = a.area_norm ? __fdiv_rn(h, aw) : h;
+            const float zg = a.gzy ? a.gzy[sk * 2] : 1.f;   // gate of this draw and phase
+            const float he = (a.area_norm ? __fdiv_rn(h, aw) : h) * zg;
             const float LLh = (1.f - r) * q[0] + r * q[1];   // d LL / d he
             constexpr float kAG = 1.0644670194312262f, kAL = 1.5707963267948966f;
             const float dlna_dr = a.area_norm ? __fdiv_rn(kAL - kAG, fmaf(r, kAL - kAG, kAG)) : 0.f;
@@ -1204,6 +1237,12 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
                                             (a.area_norm ? __fdiv_rn(he * LLh, 1.f + acl) : 0.f);
             G[4] = a.fix_a ? 0.f : gal - (al - a.pr_alpha_mean) * a.pr_alpha_isd2;
             const double wt = a.iw ? __ldcg(&a.iw[c0 + lane]) : 1.0;   // importance weight w_s / sum w
+            if (a.gzy) {   // gate logit: (1/tau) [dLL/dy + d ln p/dy], dLL/dy = he dLL/dhe (1 - z)
+                const float yg = a.gzy[sk * 2 + 1];
+                const float dlnp = a.gate_tau * (2.f * sigmoidf(a.gate_a0 - a.gate_tau * yg) - 1.f);
+                const float gg = __fdiv_rn(he * LLh * (1.f - zg) + dlnp, a.gate_tau);
+                accg += a.iw ? wt * static_cast<double>(gg) : static_cast<double>(gg);
+            }
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
                 const double gj = a.iw ? wt * static_cast<double>(G[j]) : static_cast<double>(G[j]);
@@ -1219,12 +1258,14 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
             accl[j] = warp_sumd(accl[j]);
             acce[j] = warp_sumd(acce[j]);
         }
+        accg = warp_sumd(accg);
         if (lane == 0) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
-                a.gred[(static_cast<size_t>(bk) * a.NB + b) * 10 + j] = accl[j];
-                a.gred[(static_cast<size_t>(bk) * a.NB + b) * 10 + 5 + j] = acce[j];
+                a.gred[(static_cast<size_t>(bk) * a.NB + b) * kGredVals + j] = accl[j];
+                a.gred[(static_cast<size_t>(bk) * a.NB + b) * kGredVals + 5 + j] = acce[j];
             }
+            a.gred[(static_cast<size_t>(bk) * a.NB + b) * kGredVals + 10] = accg;
         }
     }
     __threadfence();
@@ -1233,13 +1274,29 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (threadIdx.x < 10) {
+    if (threadIdx.x < kGredVals) {
         double tot = 0.0;
-        for (int bb = 0; bb < a.NB; ++bb) tot += __ldcg(&a.gred[(static_cast<size_t>(bk) * a.NB + bb) * 10 + threadIdx.x]);
+        for (int bb = 0; bb < a.NB; ++bb)
+            tot += __ldcg(&a.gred[(static_cast<size_t>(bk) * a.NB + bb) * kGredVals + threadIdx.x]);
         red[threadIdx.x] = tot;
     }
     __syncthreads();
     if (threadIdx.x == 0) a.tickets[bk] = 0;
+    if (threadIdx.x == 10 && a.gzy) {   // gate logit of phase bk (one model: bk = k)
+        const double grad = a.iw ? red[10] : red[10] / a.S_sub;
+        if (a.grad_gate) a.grad_gate[bk] = static_cast<float>(grad);
+        if (a.adam) {
+            const int t = *a.d_iter + 1;
+            const double gm = -grad;
+            const double mm = a.ac.b1 * static_cast<double>(a.m_gate[bk]) + (1.0 - a.ac.b1) * gm;
+            const double vv = a.ac.b2 * static_cast<double>(a.v_gate[bk]) + (1.0 - a.ac.b2) * gm * gm;
+            a.m_gate[bk] = static_cast<float>(mm);
+            a.v_gate[bk] = static_cast<float>(vv);
+            const double c1 = 1.0 - static_cast<double>(powf(a.ac.b1, static_cast<float>(t)));
+            const double c2 = 1.0 - static_cast<double>(powf(a.ac.b2, static_cast<float>(t)));
+            a.gate_a[bk] = static_cast<float>(a.gate_a[bk] - a.ac.lr * (mm / c1) / (sqrt(vv / c2) + a.ac.eps));
+        }
+    }
     if (threadIdx.x < 10) {
         const int j = threadIdx.x % 5;
         const bool is_raw = threadIdx.x >= 5;
@@ -1282,6 +1339,7 @@ struct PostArgs {
     int S, K, T, W, top_m;
     double csum, alpha_min;
     int area_norm;   // area-normalised profiles: the area of phase k is h_k sum_m I_m
+    const float *gzy;   // [S*K*2] gate z of each draw (null: no gates)
     const double *llpart, *lpj, *lq, *isum;
     const float *theta;
     double *logw, *pi, *scalars, *combo_logp, *cost;
@@ -1304,8 +1362,9 @@ __global__ void __launch_bounds__(128) k_post_sample(PostArgs a) {
         const float *th = a.theta + (static_cast<size_t>(s) * a.K + k) * 5;
         const double ac = th[4] > static_cast<float>(a.alpha_min) ? static_cast<double>(th[4]) : a.alpha_min;
         // area-normalised profiles: h is already the area per unit intensity
-        const double area = a.area_norm ? static_cast<double>(th[0]) * a.isum[k]
-                                        : static_cast<double>(th[0]) * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
+        const double hz = static_cast<double>(th[0]) * (a.gzy ? a.gzy[(static_cast<size_t>(s) * a.K + k) * 2] : 1.f);
+        const double area = a.area_norm ? hz * a.isum[k]
+                                        : hz * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
                                               ((1.0 - th[3]) * AG + static_cast<double>(th[3]) * AL);
         tot += area;
     }
@@ -1314,8 +1373,9 @@ __global__ void __launch_bounds__(128) k_post_sample(PostArgs a) {
         const float *th = a.theta + (static_cast<size_t>(s) * a.K + k) * 5;
         const double ac = th[4] > static_cast<float>(a.alpha_min) ? static_cast<double>(th[4]) : a.alpha_min;
         // area-normalised profiles: h is already the area per unit intensity
-        const double area = a.area_norm ? static_cast<double>(th[0]) * a.isum[k]
-                                        : static_cast<double>(th[0]) * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
+        const double hz = static_cast<double>(th[0]) * (a.gzy ? a.gzy[(static_cast<size_t>(s) * a.K + k) * 2] : 1.f);
+        const double area = a.area_norm ? hz * a.isum[k]
+                                        : hz * a.isum[k] * ((1.0 + ac) * th[2] * 0.5) *
                                               ((1.0 - th[3]) * AG + static_cast<double>(th[3]) * AL);
         a.bits[static_cast<size_t>(s) * a.K + k] = (area / tot >= 0.01) ? 1 : 0;
     }
@@ -1589,6 +1649,7 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.beta = P.bgfit ? P.beta : nullptr; a.bg_sd = P.bg_sd;
     a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0; a.r_value = P.r_value; a.a_value = P.alpha_value;
     a.area_norm = P.area_norm ? 1 : 0;
+    a.gate_a = P.gates ? P.gate_a : nullptr; a.gate_tau = P.gate_tau; a.gate_a0 = P.gate_a0; a.gzy = W.gzy;
     a.pr_lambda = static_cast<float>(P.prior.lambda);
     a.pr_mu_isd = static_cast<float>(1.0 / P.prior.mu_sd);
     a.pr_alpha_mean = static_cast<float>(P.prior.alpha_mean);
@@ -1670,6 +1731,8 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.pr_alpha_isd2 = static_cast<float>(1.0 / (P.prior.alpha_sd * P.prior.alpha_sd));
     a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0;
     a.area_norm = P.area_norm ? 1 : 0;
+    a.gzy = P.gates ? W.gzy : nullptr; a.gate_tau = P.gate_tau; a.gate_a0 = P.gate_a0;
+    a.gate_a = P.gate_a; a.m_gate = P.m_gate; a.v_gate = P.v_gate; a.grad_gate = grad_out ? P.grad_gate : nullptr;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
     const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;
@@ -1688,6 +1751,7 @@ void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m,
     a.S = W.S; a.K = P.K; a.T = P.T; a.W = (P.K + 63) / 64; a.top_m = top_m;
     a.csum = P.csum; a.alpha_min = static_cast<double>(static_cast<float>(P.prior.alpha_min));
     a.area_norm = P.area_norm ? 1 : 0;
+    a.gzy = P.gates ? W.gzy : nullptr;
     a.llpart = W.llpart; a.lpj = W.lpj; a.lq = W.lq; a.isum = P.isum; a.theta = W.theta;
     a.logw = B.logw; a.pi = B.pi; a.scalars = B.scalars; a.combo_logp = B.combo_logp;
     a.cost = B.cost; a.bits = B.bits; a.combos = B.combos; a.order = B.order;

@@ -105,7 +105,7 @@ extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, i
         size_t b = 0;
         b += a256(sk * 5 * 4) * 2 + a256(sk * sizeof(PhaseConst)) + a256(s * 8) * 2 + a256(s * Npad * 4) +
              a256(s * T * 8) + a256(C * s * Npad * 4) + a256(sk * T * 8) + a256(kCounters * 4);
-        b += fit ? a256(sk * T * kGradSums * 4) + a256(static_cast<size_t>(K) * kGradBlocks * 80) +
+        b += fit ? a256(sk * T * kGradSums * 4) + a256(static_cast<size_t>(K) * kGradBlocks * kGredVals * 8) +
                        a256(static_cast<size_t>(K) * 4)
                  : a256(s * 8);
         return b;
@@ -361,7 +361,8 @@ size_t xrdvi_enumerate_footprint_bytes(int32_t K, int32_t N, int32_t M_total, in
     const size_t base = xrdvi_footprint_bytes(K, N, M_total, S * nsub, 0, 0);
     if (base == 0) return 0;
     const size_t kb = static_cast<size_t>(K) * nsub;
-    return base + a256(kb * 20) * 2 + a256(kb * 40) * 3 + a256(kb * xrdvi::kGradBlocks * 80) + a256(kb * 4) +
+    return base + a256(kb * 20) * 2 + a256(kb * 40) * 3 + a256(kb * xrdvi::kGradBlocks * xrdvi::kGredVals * 8) +
+           a256(kb * 4) +
            a256(static_cast<size_t>(nsub) * 8) * 3 + a256(static_cast<size_t>(nsub) * 4);
 }
 

@@ -54,10 +54,10 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
         return report_error(XRDVI_EINVAL, "elbo_grad_static: lambda_ must be positive, data_const finite");
     if (cfg->flags &
         (XRDVI_FLAG_IW_ELBO | XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_SEC_WIDTH | XRDVI_FLAG_FIT_BACKGROUND |
-         XRDVI_FLAG_FIX_R | XRDVI_FLAG_FIX_ALPHA | XRDVI_FLAG_AREA_NORM))
+         XRDVI_FLAG_FIX_R | XRDVI_FLAG_FIX_ALPHA | XRDVI_FLAG_AREA_NORM | XRDVI_FLAG_GATES))
         return report_error(XRDVI_EINVAL, "elbo_grad_static: the importance-weighted, shared-shape, angle-dependent "
-                                          "width, fitted-background, fixed-shape and area-normalised variants are not "
-                                          "supported");
+                                          "width, fitted-background, fixed-shape, area-normalised and gated variants "
+                                          "are not supported");
 
     // Layout of the scratch array for this call.
     const size_t T = (static_cast<size_t>(N) + kTile - 1) / kTile;
@@ -76,7 +76,7 @@ extern "C" xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const
     const size_t o_fp = off;     off += align256(static_cast<size_t>(S) * Npad * sizeof(float));
     const size_t o_rg = off;     off += align256(SK * T * sizeof(ushort4));
     const size_t o_cnt = off;    off += align256(kCounters * sizeof(int));
-    const size_t o_gred = off;   off += align256(static_cast<size_t>(K) * kGradBlocks * 10 * sizeof(double));
+    const size_t o_gred = off;   off += align256(static_cast<size_t>(K) * kGradBlocks * kGredVals * sizeof(double));
     const size_t o_tk = off;     off += align256(static_cast<size_t>(K) * sizeof(int));
     if (off > XRDVI_STATIC_SCRATCH_BYTES)
         return report_error(XRDVI_EINVAL, "elbo_grad_static: this problem needs " + std::to_string(off) +

@@ -28,6 +28,7 @@ FLAG_FIX_R = 1 << 7           # r held at fix_r_value
 FLAG_FIX_ALPHA = 1 << 8       # alpha held at fix_alpha_value
 FLAG_DEVICE_PTRS = 1 << 9     # xrdvi_create reads device arrays
 FLAG_AREA_NORM = 1 << 10      # area-normalised profiles (h = integrated intensity)
+FLAG_GATES = 1 << 11          # binary-Concrete phase gates
 
 
 class XrdviError(RuntimeError):
@@ -54,7 +55,8 @@ class Config(ctypes.Structure):
                 ("prior_w_shape", ctypes.c_float), ("prior_w_rate", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("init_h_frac", ctypes.c_float),
                 ("init_sigma", ctypes.c_float), ("flags", ctypes.c_uint32), ("bg_prior_sd", ctypes.c_float),
-                ("fix_r_value", ctypes.c_float), ("fix_alpha_value", ctypes.c_float)]
+                ("fix_r_value", ctypes.c_float), ("fix_alpha_value", ctypes.c_float),
+                ("gate_tau", ctypes.c_float), ("gate_prior", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):
@@ -122,6 +124,7 @@ SIGNATURES = {
     "xrdvi_enumerate_footprint_bytes": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _i32]),
     "xrdvi_gemm_nt_tf32x3": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp]),
     "xrdvi_get_background": (ctypes.c_int, [_vp, P(_f), P(_f), P(_f)]),
+    "xrdvi_get_gates": (ctypes.c_int, [_vp, P(_f), P(_f)]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -219,10 +222,15 @@ def xrdvi_get_info(h) -> Info:
     return info
 
 
-def xrdvi_elbo_grad(h, eps=None, want_f=False, want_grad=True):
+def xrdvi_elbo_grad(h, eps=None, want_f=False, want_grad=True, gate_noise=None):
+    """One step without an update.  eps [S, K, 5] injected normals (None: the
+    step's own draws); with the gate variant gate_noise [S, K] holds the
+    logistic gate noise and is passed after eps."""
     info = xrdvi_get_info(h)
     S, K, N = info.S, info.K, info.N
-    e = None if eps is None else _f32(eps).reshape(S, K, 5)
+    e = None if eps is None else _f32(eps).reshape(S * K * 5)
+    if e is not None and gate_noise is not None:
+        e = np.ascontiguousarray(np.concatenate([e, _f32(gate_noise).reshape(S * K)]))
     elbo = ctypes.c_double(0.0)
     grad = np.zeros((K, 10), dtype=np.float32)
     f = np.zeros((S, N), dtype=np.float32) if want_f else None
@@ -361,8 +369,8 @@ class Context:
     def fit(self, iters, trace=True):
         return xrdvi_fit(self.h, iters, trace)
 
-    def elbo_grad(self, eps=None, want_f=False):
-        return xrdvi_elbo_grad(self.h, eps, want_f)
+    def elbo_grad(self, eps=None, want_f=False, gate_noise=None):
+        return xrdvi_elbo_grad(self.h, eps, want_f, gate_noise=gate_noise)
 
     def posterior(self, S_post, seed, top_m=8):
         return xrdvi_posterior(self.h, S_post, seed, top_m)
@@ -384,6 +392,9 @@ class Context:
 
     def background(self):
         return xrdvi_get_background(self.h)
+
+    def gates(self):
+        return xrdvi_get_gates(self.h)
 
     def set_stream(self, stream_handle):
         xrdvi_set_stream(self.h, stream_handle)
@@ -491,3 +502,12 @@ def xrdvi_get_background(h):
     gb = np.zeros(3, dtype=np.float32)
     _check(lib().xrdvi_get_background(h, _ptr(beta, _f), _ptr(curve, _f), _ptr(gb, _f)))
     return {"beta": beta, "curve": curve, "grad_beta": gb}
+
+
+def xrdvi_get_gates(h):
+    """Gate variant: {"logits": [K], "grad": [K]}."""
+    K = xrdvi_get_info(h).K
+    a = np.zeros(K, dtype=np.float32)
+    g = np.zeros(K, dtype=np.float32)
+    _check(lib().xrdvi_get_gates(h, _ptr(a, _f), _ptr(g, _f)))
+    return {"logits": a, "grad": g}

@@ -315,3 +315,70 @@ def test_area_normalised_gradient_against_central_differences():
     num = _fd_grad(P, loc, raw, eps)
     rel = np.max(np.abs(num - g), axis=0) / np.max(np.abs(g), axis=0)
     assert np.all(rel < 1e-5), rel
+
+
+@pytest.mark.parametrize("a,L,tau,a0", [(0.3, -1.2, 2 / 3, 0.0), (-2.0, 0.7, 0.5, math.log(0.1 / 0.9)),
+                                        (4.0, 3.0, 1.0, 1.0)])
+def test_gate_terms_against_logistic_densities(a, L, tau, a0):
+    """y = (a + L)/tau with L standard logistic is logistic with location a/tau
+    and scale 1/tau: ln q(y) and ln p(y) are scipy's logistic log-densities."""
+    z, v, dp = oracle.gate_terms(a, L, tau, a0)
+    y = (a + L) / tau
+    assert z == pytest.approx(special.expit(y), rel=1e-14)
+    ref = stats.logistic.logpdf(y, loc=a0 / tau, scale=1 / tau) - stats.logistic.logpdf(y, loc=a / tau, scale=1 / tau)
+    assert v == pytest.approx(ref, rel=1e-12, abs=1e-12)
+    h = 1e-6
+    num = (stats.logistic.logpdf(y + h, loc=a0 / tau, scale=1 / tau)
+           - stats.logistic.logpdf(y - h, loc=a0 / tau, scale=1 / tau)) / (2 * h)
+    assert dp == pytest.approx(num, rel=1e-6, abs=1e-8)
+
+
+def test_gate_noise_is_logistic_and_counter_keyed():
+    L = oracle.gate_noise(7, 0, 3, 400, 25).ravel()
+    assert stats.kstest(L, "logistic").pvalue > 1e-3
+    assert not np.array_equal(oracle.gate_noise(7, 0, 4, 4, 3), oracle.gate_noise(7, 0, 3, 4, 3))
+
+
+def test_gated_gradient_against_central_differences():
+    inst, _ = _problem()
+    P = oracle.Problem.from_instance(inst, gates=True, gate_prior=0.3)
+    loc, raw = _perturbed(P, 14)
+    P.gate_a[:] = [0.5, -0.3, 1.1]
+    eps = synth.normals(18, 3, P.K).astype(np.float64)
+    L = oracle.gate_noise(9, 0, 0, 3, P.K)
+    r = P.elbo_grad(loc, raw, eps, gate_noise=L)
+    num = np.zeros((P.K, 10))
+    for k in range(P.K):
+        for j in range(5):
+            for which in (0, 1):
+                Lc, R = loc.copy(), raw.copy()
+                A = Lc if which == 0 else R
+                A[k, j] += 1e-6
+                ep = P.elbo_grad(Lc, R, eps, gate_noise=L)["elbo"]
+                A[k, j] -= 2e-6
+                em = P.elbo_grad(Lc, R, eps, gate_noise=L)["elbo"]
+                num[k, j + 5 * which] = (ep - em) / 2e-6
+    rel = np.max(np.abs(num - r["grad"]), axis=0) / np.max(np.abs(r["grad"]), axis=0)
+    assert np.all(rel < 1e-5), rel
+    ga = np.zeros(P.K)
+    for k in range(P.K):
+        a0 = P.gate_a[k]
+        P.gate_a[k] = a0 + 1e-6
+        ep = P.elbo_grad(loc, raw, eps, gate_noise=L)["elbo"]
+        P.gate_a[k] = a0 - 1e-6
+        em = P.elbo_grad(loc, raw, eps, gate_noise=L)["elbo"]
+        P.gate_a[k] = a0
+        ga[k] = (ep - em) / 2e-6
+    np.testing.assert_allclose(r["grad_gate"], ga, rtol=1e-5, atol=1e-6 * np.max(np.abs(ga)))
+
+
+def test_open_gates_give_the_ungated_profile():
+    inst, P = _problem()
+    Pg = oracle.Problem.from_instance(inst, gates=True)
+    Pg.gate_a[:] = 60.0                      # z = sigmoid(90 + L/tau) = 1 to double precision
+    loc, raw = _perturbed(P, 15)
+    eps = synth.normals(19, 2, P.K).astype(np.float64)
+    a = Pg.elbo_grad(loc, raw, eps, want_f=True, gate_noise=np.zeros((2, P.K)))
+    b = P.elbo_grad(loc, raw, eps, want_f=True)
+    np.testing.assert_allclose(a["f"], b["f"], rtol=1e-14)
+    np.testing.assert_allclose(a["ll"], b["ll"], rtol=1e-14)
