@@ -9,8 +9,13 @@ One bench step = one complete fit on the resident problem: 2000 SVI steps
 (sample -> profile/likelihood -> backward -> Adam -> ELBO) followed by the
 posterior over phase combinations (4096 posterior draws).  The headline value
 is ELBO evaluations per second, counted densely as S * sum_k M_k * N per SVI
-step (every step evaluates the profile and its gradient at every
-(sample, peak, point) triple), and the step time is the time-to-posterior.
+step: every step computes the profile and its gradient as the full sum over
+every (sample, peak, point) triple.  Peaks far from a 256-point tile reach it
+only through a smooth Lorentzian tail, which is evaluated at 32 Chebyshev
+nodes of the tile and interpolated (the same sums to below FP32 rounding), so
+fewer evaluations are executed than counted; "executed_evals_per_step" gives
+their number, and the roofline is taken on the executed work.  The step time
+is the time-to-posterior.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,16 +44,31 @@ TOP_M = 16
 PROFILE_STEPS = 64          # of the 2000 SVI steps, launched kernel by kernel between events
 CPU_SAMPLE_STEPS = 4        # oracle cpu-baseline sample: 4 of the fit's 2000 SVI steps (S = 256)
 REF_STEP_ITERS = 1          # reference-arm step: one oracle SVI step (S = 256)
-# Algorithmic FP32-pipe operations (lane operations; an FMA counts once) per dense
-# evaluation, on the side-uniform peak ranges that hold almost all evaluations:
-#   forward : x - p, t = fma(s, ., -s mu), 1 + t^2 for two peaks, I0 d1 + I1 d0 (2),
-#             d0 d1, accumulate (num * rcp)  -> 10 per two evaluations = 5, and 0.5 MUFU (rcp)
-#   backward: x - p, t, 1 + t^2, I L, sum I L, I L^2, sum I L^2 t, sum I L^2
-#             -> 8 (sum I L^2 t^2 follows from sum I L - sum I L^2; the point's factor
-#             g = y/f - 1 multiplies the per-point sums once per range), and 1 MUFU (rcp)
-# Both kernels are bound by the FP32 pipe (128 lanes/clk/SM; MUFU 16/clk/SM).
-FP32_OPS_PER_EVAL = {"forward": 5, "backward": 8}
-MUFU_PER_EVAL = {"forward": 0.5, "backward": 1.0}
+# Algorithmic work of each profile kernel: FP32-pipe lane operations (an FMA
+# counts once) and MUFU operations per evaluation of each kind, times the
+# evaluations the step executed (counted from its peak ranges):
+#   direct side-uniform, forward: t = fma(s, x - x0, b), 1 + t^2, I0 d1 + I1 d0 (2 for
+#       two peaks), d0 d1, accumulate          -> 4 FP32 + 0.5 MUFU (rcp per two peaks)
+#   direct side-uniform, backward: t, 1 + t^2, I L, sum I L, I L^2, sum I L^2 t,
+#       sum I L^2                               -> 7 FP32 + 1 MUFU
+#   mixed range, forward: x - p - mu (2), s t, t^2, 1 + t^2, two accumulations
+#                                               -> 7 FP32 + 2 MUFU (rcp, ex2)
+#   mixed range, backward: t (3), t^2, 1 + t^2, g I, q L, q L^2, q L^2 t, q L^2 t^2
+#       and their five sums (Lorentzian part)   -> 14 FP32 + 1 MUFU
+#   Gaussian reach beyond the mixed range: t (2), t^2, accumulate (forward: 4 FP32,
+#       backward: g I G, three sums: 9 FP32), 1 MUFU (ex2)
+#   far field, per (peak, node): x_p - p, t, 1 + t^2, accumulate -> 4 FP32 + 1 MUFU
+#       forward; backward t (2), 1 + t^2, I L, I L^2 and three sums -> 8 FP32 + 1 MUFU
+#   likelihood: the far-field interpolation and node weights, 32 FMAs each per point
+# FP32 pipe 128 lanes/clk/SM; MUFU 32 lanes/clk/SM (ex2.approx measured at 30).
+OPS = {
+    "direct": {"uniform": (4, 0.5), "mixed": (7, 2), "gauss_reach": (4, 1)},
+    "far_fwd": {"far_nodes": (4, 1)},
+    "bwd_uniform": {"uniform": (7, 1)},
+    "bwd_near": {"mixed": (14, 1), "gauss_reach": (9, 1)},
+    "far_bwd": {"far_nodes": (8, 1)},
+}
+MUFU_LANES = 32
 
 
 def parse():
@@ -362,7 +382,7 @@ def main():
 
     def one_step(prof):
         ctx.fit(iters - (n_prof if prof else 0), trace=False)
-        k = ctx.profile_steps(n_prof) if prof else None
+        k = ctx.profile_kernels(n_prof) if prof else None
         post = ctx.posterior(S_POST, 77, TOP_M)
         return k, post
 
@@ -373,7 +393,8 @@ def main():
 
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     times = []
-    kern = {k: 0.0 for k in xrdvi.KERNELS}
+    kern = {k: 0.0 for k in xrdvi.PROFILE_KERNELS}
+    work = None
     post = None
     barrier(world)
     torch.cuda.synchronize()
@@ -383,7 +404,7 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        km, post = one_step(prof=True)
+        (km, work), post = one_step(prof=True)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -428,15 +449,31 @@ def main():
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * 128 * clock_mhz * 1e6 / 1e12   # FP32 lane operations per second (Top/s)
-    dom = "backward" if kern["backward"] >= kern["forward"] else "forward"
-    evals_launch = inst.evals_per_iter
-    achieved = {k: evals_launch * FP32_OPS_PER_EVAL[k] / (kern[k] * 1e-3) / 1e12 for k in ("forward", "backward")}
-    mufu_frac = {k: evals_launch * MUFU_PER_EVAL[k] / (kern[k] * 1e-3) / (sms * 16 * clock_mhz * 1e6)
-                 for k in ("forward", "backward")}
-    # per SVI step: sample, ranges, forward, lik, bwd_uniform, bwd_near, grad, elbo;
-    # posterior: sample, ranges, forward, lik, post_sample, post_reduce, post_sort, post_topm
-    launches_per_step = 8 * iters + 8
+    mufu_peak = sms * MUFU_LANES * clock_mhz * 1e6 / 1e12
+    ops_table = dict(OPS)
+    if work["far_nodes"] > 0:   # far field on: one direct backward kernel (timed as bwd_uniform)
+        ops_table["bwd_uniform"] = {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1)}
+        del ops_table["bwd_near"]
+    per_kernel = {}
+    for name, kinds in ops_table.items():
+        if kern[name] <= 1e-4:
+            continue
+        ops = sum(work[kd] * o[0] for kd, o in kinds.items())
+        mufu = sum(work[kd] * o[1] for kd, o in kinds.items())
+        ach = ops / (kern[name] * 1e-3) / 1e12
+        per_kernel[name] = {"ms": kern[name], "fp32_tops": ach, "frac": ach / fp32_peak,
+                            "mufu_frac": mufu / (kern[name] * 1e-3) / 1e12 / mufu_peak}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    executed = work["uniform"] + work["mixed"] + work["gauss_reach"] + work["far_nodes"]
+    far_on = work["far_nodes"] > 0
+    # per SVI step: sample, ranges, direct profile, [far field], lik, bwd_uniform, bwd_near,
+    # [far-field backward], grad, elbo; posterior: sample, ranges, direct, [far], lik,
+    # post_sample, post_reduce, post_sort, post_topm
+    launches_per_step = (10 if far_on else 8) * iters + (9 if far_on else 8)
     share = {k: kern[k] / sum(kern.values()) for k in kern}
+    kernel_names = {"direct": "k_forward", "far_fwd": "k_far_fwd",
+                    "bwd_uniform": "k_bwd_direct" if far_on else "k_bwd_uniform",
+                    "bwd_near": "k_bwd_near", "far_bwd": "k_far_bwd"}
     out = {
         "metric": METRIC,
         "value": value,
@@ -455,21 +492,20 @@ def main():
         "svi_step_ms": ms_step / iters,
         "kernel_ms_per_launch": kern,
         "kernel_share": share,
+        "executed_evals_per_step": executed,
+        "work_counts_per_step": work,
         "roofline": {
             "bound": "alu",
-            "kernel": {"backward": "k_bwd_uniform + k_bwd_near",
-                       "forward": "k_ranges + k_forward + k_lik"}[dom],
-            "achieved": achieved[dom],
+            "kernel": kernel_names[dom],
+            "achieved": per_kernel[dom]["fp32_tops"],
             "peak": fp32_peak,
             "unit": "Top/s (FP32 lane ops)",
-            "frac": achieved[dom] / fp32_peak,
+            "frac": per_kernel[dom]["frac"],
             "traffic": None,
             "peak_source": f"FP32 pipe: {sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({peak_src} sm_max_mhz); "
-                           f"{FP32_OPS_PER_EVAL[dom]} algorithmic FP32 ops per evaluation",
-            "forward_frac": achieved["forward"] / fp32_peak,
-            "backward_frac": achieved["backward"] / fp32_peak,
-            "forward_mufu_frac": mufu_frac["forward"],
-            "backward_mufu_frac": mufu_frac["backward"],
+                           "algorithmic FP32 ops per executed evaluation of each kind x the step's counts",
+            "mufu_frac": per_kernel[dom]["mufu_frac"],
+            "kernels": per_kernel,
         },
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "seconds": e2e_s},

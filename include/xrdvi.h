@@ -139,6 +139,12 @@ typedef struct {
  * noise (xrdvi_elbo_grad) eps holds [S*K*5] normals followed by [S*K]
  * logistic gate noise values.  The posterior's areas use z h. */
 #define XRDVI_FLAG_GATES      (1u << 11)
+/* Every peak evaluated directly at every point.  By default the Lorentzian
+ * tails of peaks more than half a tile width (of 256 points) beyond a tile,
+ * and beyond their Gaussian reach, are summed at 32 Chebyshev nodes of the
+ * tile and interpolated (error below 1e-8 of those tails, under FP32
+ * rounding); the shared-shape variant always runs dense. */
+#define XRDVI_FLAG_DENSE      (1u << 12)
 
 typedef struct {
     uint32_t size;            /* sizeof(xrdvi_config): set by xrdvi_config_default */
@@ -260,6 +266,22 @@ xrdvi_status xrdvi_backward_dev(xrdvi_ctx *ctx, const float *d_loc, const float 
  * finalisation.  Blocks until done.  For measurement only; xrdvi_fit is the
  * fast path. */
 xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms);
+
+/* Per-kernel form of xrdvi_profile_steps (the same fit steps): kernel_ms
+ * [XRDVI_PROFILE_KERNELS] receives the mean duration per step (ms) of
+ *   0 sampling, 1 peak ranges, 2 direct profile, 3 far field at the nodes,
+ *   4 likelihood (with the far-field interpolation), 5 backward direct sums
+ *   (the side-uniform ranges only with XRDVI_FLAG_DENSE), 6 backward near
+ *   sums (XRDVI_FLAG_DENSE; else ~0), 7 backward far-field sums, 8 gradient
+ *   reduction + Adam, 9 ELBO
+ * (a kernel the configuration does not launch reads ~0; the shared-shape
+ * variant's contractions count as 2 and 5).  work (NULL or [4], HOST)
+ * receives the last step's evaluation counts, (peak, point) pairs over all
+ * samples: 0 direct on side-uniform ranges, 1 on mixed ranges, 2 Gaussian
+ * terms beyond the mixed range, 3 far-field (peak, node) pairs (zeros for the
+ * shared-shape variant).  Blocks until done.  For measurement only. */
+#define XRDVI_PROFILE_KERNELS 10
+xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms, int64_t *work);
 
 /* Allocation-free variant of xrdvi_elbo_grad, for callers that may not
  * allocate device memory themselves: code whose device memory is owned by

@@ -141,6 +141,63 @@ struct xrdvi_ctx {
 
 namespace {
 
+// Far-field tables of each 2-theta tile: kFarNodes Chebyshev nodes of the
+// first kind on the tile's span [x_lo, x_hi] (rounded to FP32, the positions
+// the kernels evaluate at) and the Lagrange weights lam_p(x_i) of the tile's
+// points for those nodes, by the barycentric formula (Berrut & Trefethen,
+// "Barycentric Lagrange interpolation", SIAM Review 2004) in FP64.  Layout
+// lam[(tile * kFarNodes + p) * kTile + j] for point tile * kTile + j (points
+// past N repeat the last one).  A one-point tile gets equal weights 1/n
+// (all its nodes are that point).
+void far_tables(const float *x, int N, int T, bool sec, std::vector<float> &nx, std::vector<float> &nc,
+                std::vector<float> &lam) {
+    const int n = kFarNodes;
+    nx.assign(static_cast<size_t>(T) * n, 0.f);
+    if (sec) nc.assign(static_cast<size_t>(T) * n, 0.f);
+    lam.assign(static_cast<size_t>(T) * n * kTile, 0.f);
+    std::vector<double> z(n), bw(n), term(n);
+    for (int t = 0; t < T; ++t) {
+        const int i0 = t * kTile, i1 = std::min(i0 + kTile, N) - 1;
+        const double lo = x[i0], hi = x[i1], c = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+        for (int p = 0; p < n; ++p) {
+            const float xp = static_cast<float>(c + h * std::cos(M_PI * (2 * p + 1) / (2.0 * n)));
+            nx[static_cast<size_t>(t) * n + p] = xp;
+            if (sec)
+                nc[static_cast<size_t>(t) * n + p] = static_cast<float>(std::cos(static_cast<double>(xp) * M_PI / 360.0));
+            z[p] = h > 0.0 ? (static_cast<double>(xp) - c) / h : 0.0;
+        }
+        float *L = lam.data() + static_cast<size_t>(t) * n * kTile;
+        if (!(h > 0.0)) {
+            for (int p = 0; p < n; ++p)
+                for (int j = 0; j < kTile; ++j) L[p * kTile + j] = 1.f / n;
+            continue;
+        }
+        // barycentric weights of the (rounded) nodes, scaled to max 1
+        double wmax = 0.0;
+        for (int p = 0; p < n; ++p) {
+            double prod = 1.0;
+            for (int q = 0; q < n; ++q)
+                if (q != p) prod *= z[p] - z[q];
+            bw[p] = 1.0 / prod;
+            wmax = std::max(wmax, std::fabs(bw[p]));
+        }
+        for (int p = 0; p < n; ++p) bw[p] /= wmax;
+        for (int j = 0; j < kTile; ++j) {
+            const int i = std::min(i0 + j, N - 1);
+            const double zi = (static_cast<double>(x[i]) - c) / h;
+            int hit = -1;
+            double den = 0.0;
+            for (int p = 0; p < n && hit < 0; ++p) {
+                const double d = zi - z[p];
+                if (d == 0.0) hit = p;
+                else den += (term[p] = bw[p] / d);
+            }
+            for (int p = 0; p < n; ++p)
+                L[p * kTile + j] = hit >= 0 ? (p == hit ? 1.f : 0.f) : static_cast<float>(term[p] / den);
+        }
+    }
+}
+
 xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
                              std::vector<void *> *list) {
     const Problem &P = c->P;
@@ -170,6 +227,11 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
         W.gpart = nullptr;
     }
     if (P.gates) XR_TRY(c->alloc(&W.gzy, SK * 2, list));
+    if (P.far) {   // far field: range ends, node sums, node weights of g
+        XR_TRY(c->alloc(&W.franges, SK * P.T, list));
+        XR_TRY(c->alloc(&W.fnode, static_cast<size_t>(S) * P.T * kFarNodes, list));
+        if (fit) XR_TRY(c->alloc(&W.wfar, static_cast<size_t>(S) * P.T * kFarNodes, list));
+    }
     choose_chunks(P, c->host_off.data(), S, W);
     W.fpart_cap = static_cast<size_t>(W.C) * S * P.Npad;
     XR_TRY(c->alloc(&W.fpart, W.fpart_cap, list));
@@ -525,6 +587,23 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         XR_C(c->alloc(&P.v_beta, 3));
         XR_C(c->alloc(&c->grad_beta, 3));
     }
+    // far field (off with the dense flag, the shared-shape variant and very
+    // long patterns): Chebyshev nodes and Lagrange weights of every tile
+    std::vector<float> nodex, nodec, lamh;
+    P.far = !(cfg->flags & (XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_DENSE)) &&
+            static_cast<size_t>(P.T) * kFarNodes * kTile * sizeof(float) <= kFarMaxLamBytes;
+    std::vector<int> far_order(K);
+    if (P.far) {
+        far_tables(pt->x_deg, N, P.T, sec, nodex, nodec, lamh);
+        XR_C(c->alloc(&P.node_x, nodex.size()));
+        XR_C(c->alloc(&P.lam, lamh.size()));
+        if (sec) XR_C(c->alloc(&P.node_c, nodec.size()));
+        std::iota(far_order.begin(), far_order.end(), 0);
+        std::stable_sort(far_order.begin(), far_order.end(), [&](int i, int j) {
+            return pk->offsets[i + 1] - pk->offsets[i] > pk->offsets[j + 1] - pk->offsets[j];
+        });
+        XR_C(c->alloc(&P.far_order, static_cast<size_t>(K)));
+    }
     configure_grids(P, sms);
     c->host_off.assign(pk->offsets, pk->offsets + K + 1);
     c->W.B = nsub;
@@ -601,6 +680,9 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
                     cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))) ||
         (P.gates && (cudaMemsetAsync(P.gate_a, 0, K * 4, s) || cudaMemsetAsync(P.m_gate, 0, K * 4, s) ||
                      cudaMemsetAsync(P.v_gate, 0, K * 4, s) || cudaMemsetAsync(P.grad_gate, 0, K * 4, s))) ||
+        (P.far && (up(P.node_x, nodex.data(), nodex.size() * 4) || up(P.lam, lamh.data(), lamh.size() * 4) ||
+                   up(P.far_order, far_order.data(), static_cast<size_t>(K) * 4) ||
+                   (sec && up(P.node_c, nodec.data(), nodec.size() * 4)))) ||
         (P.bgfit && (up(P.Tb, Tb.data(), Tb.size() * 4) || cudaMemsetAsync(P.beta, 0, 12, s) ||
                      cudaMemsetAsync(P.m_beta, 0, 12, s) || cudaMemsetAsync(P.v_beta, 0, 12, s) ||
                      cudaMemsetAsync(c->grad_beta, 0, 12, s))) ||
@@ -813,6 +895,88 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *c, int32_t steps, float *kernel_ms) 
     if (rc != XRDVI_OK) return rc;
     c->host_step += steps;
     for (int k = 0; k < 5; ++k) kernel_ms[k] = static_cast<float>(acc[k] / steps);
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms, int64_t *work) {
+    if (!c || !kernel_ms) return fail(XRDVI_EINVAL, "null argument");
+    if (steps < 1) return fail(XRDVI_EINVAL, "steps must be >= 1");
+    if (c->host_step + steps > INT32_MAX) return fail(XRDVI_EINVAL, "step counter would overflow");
+    constexpr int nk = XRDVI_PROFILE_KERNELS;
+    cudaEvent_t ev[nk + 1];
+    for (auto &e : ev) XR_CUDA(cudaEventCreate(&e));
+    double acc[nk] = {};
+    cudaStream_t st = c->stream;
+    const Problem &P = c->P;
+    Workspace &W = c->W;
+    const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
+    xrdvi_status rc = XRDVI_OK;
+    for (int i = 0; i < steps && rc == XRDVI_OK; ++i) {
+        cudaEventRecord(ev[0], st);
+        launch_sample(P, W, c->loc, c->raw, nullptr, c->cfg.seed, 0u, c->step, 0u, c->iter, c->ent, st);
+        cudaEventRecord(ev[1], st);
+        if (P.bgfit) launch_bg_curve(P, st);
+        if (W.shared) {   // one contraction: its time counts as the direct profile
+            cudaEventRecord(ev[2], st);
+            launch_shared_forward(P, W, nullptr, st);
+            cudaEventRecord(ev[3], st);
+            cudaEventRecord(ev[4], st);
+        } else {
+            launch_forward(P, W, nullptr, naive, st, &ev[2]);
+        }
+        cudaEventRecord(ev[5], st);
+        if (W.shared) {
+            launch_shared_backward(P, W, st);
+            cudaEventRecord(ev[6], st);
+            cudaEventRecord(ev[7], st);
+        } else {
+            launch_backward(P, W, st, &ev[6]);
+        }
+        cudaEventRecord(ev[8], st);
+        launch_grad(P, W, c->loc, c->raw, c->loc, c->raw, nullptr, true, adam_const(c->cfg), c->m, c->v, c->iter,
+                    nullptr, c->ent, nullptr, nullptr, st);
+        if (P.bgfit) launch_bg_grad(P, W, true, adam_const(c->cfg), c->iter, nullptr, st);
+        cudaEventRecord(ev[9], st);
+        launch_grad(P, W, c->loc, c->raw, nullptr, nullptr, nullptr, false, adam_const(c->cfg), nullptr, nullptr,
+                    c->iter, c->step, c->ent, c->elbo, c->trace, st);
+        cudaEventRecord(ev[10], st);
+        if (cudaEventSynchronize(ev[nk]) != cudaSuccess) {
+            rc = fail(XRDVI_ECUDA, std::string("profile_kernels: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        for (int k = 0; k < nk; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            acc[k] += ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc != XRDVI_OK) return rc;
+    c->host_step += steps;
+    for (int k = 0; k < nk; ++k) kernel_ms[k] = static_cast<float>(acc[k] / steps);
+    if (work) {   // evaluation counts of the last step, from its peak ranges
+        for (int j = 0; j < 4; ++j) work[j] = 0;
+        if (!W.shared) {
+            const size_t nr = static_cast<size_t>(W.S) * P.K * P.T;
+            std::vector<ushort4> rg(nr);
+            std::vector<ushort2> fr(P.far ? nr : 0);
+            XR_CUDA(cudaMemcpyAsync(rg.data(), W.ranges, nr * sizeof(ushort4), cudaMemcpyDeviceToHost, st));
+            if (P.far) XR_CUDA(cudaMemcpyAsync(fr.data(), W.franges, nr * sizeof(ushort2), cudaMemcpyDeviceToHost, st));
+            XR_CUDA(cudaStreamSynchronize(st));
+            for (size_t id = 0; id < nr; ++id) {
+                const ushort4 r = rg[id];
+                if (r.x == 0xffffu) continue;   // phase absent from this sample's sub-model
+                const int k = static_cast<int>((id / P.T) % P.K);
+                const int64_t me = c->host_off[k + 1] - c->host_off[k];
+                const int64_t m1 = r.x, m2 = r.y, nb = r.z, ne = r.w;
+                const int64_t fb = P.far ? fr[id].x : 0, fe = P.far ? fr[id].y : me;
+                work[0] += ((m1 - fb) + (fe - m2)) * kTile;
+                work[1] += (m2 - m1) * kTile;
+                work[2] += ((m1 - std::min(nb, m1)) + (std::max(ne, m2) - m2)) * kTile;
+                work[3] += (fb + (me - fe)) * kFarNodes;
+            }
+        }
+    }
     return XRDVI_OK;
 }
 

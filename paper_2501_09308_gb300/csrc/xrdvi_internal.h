@@ -26,6 +26,13 @@ constexpr int kGradSums = 10;
 constexpr int kMaxChunks = 8;
 constexpr int kItemsPerWarp = 8;
 constexpr int kGredVals = 11;      // per-(phase, sample block) gradient partials: loc 5, raw 5, gate 1   // profile work items per resident warp the phase chunking aims for
+// Far field: the Lorentzian tails of peaks more than kFarGap tile half-widths
+// beyond a 2-theta tile (and beyond their Gaussian reach) are summed at
+// kFarNodes Chebyshev nodes of the tile's span and interpolated at its points.
+constexpr int kFarNodes = 32;
+constexpr float kFarGap = 0.5f;
+// Largest interpolation table (kFarNodes weights per point) the far field uses.
+constexpr size_t kFarMaxLamBytes = static_cast<size_t>(64) << 20;
 // Work counters of the profile kernels of one sample set.
 constexpr int kCounters = 4;
 // Sample blocks per phase in the gradient reduction.
@@ -91,6 +98,9 @@ struct Workspace {
     float *gpart = nullptr;      // [S*K*T*kGradSums] gradient partial sums (fit only)
     float *fpart = nullptr;      // [C*S*Npad] partial profiles per phase chunk
     ushort4 *ranges = nullptr;   // [S*K*T] peak index ranges per (sample, phase, tile)
+    ushort2 *franges = nullptr;  // [S*K*T] end of the far peaks below / start of those above (far field)
+    float *fnode = nullptr;      // [S*T*kFarNodes] far-field profile at the tile's nodes
+    float *wfar = nullptr;       // [S*T*kFarNodes] sum_i g_i lam_p(x_i) per tile (fit only)
     int *counters = nullptr;     // [kCounters] work counters of the profile kernels
     double *gred = nullptr;      // [K*kGradBlocks*10] gradient partials per sample block (fit only)
     int *tickets = nullptr;      // [K] arrival tickets of the gradient reduction (fit only)
@@ -138,6 +148,12 @@ struct Problem {
     size_t smem = 0;             // dynamic shared memory of the backward profile kernels
     size_t smem_fwd = 0;         // ... of the forward kernel (compact table)
     bool wide = false;           // backward peak table stored as (-p, -p, I, I) float4
+    // Far field (off: every peak evaluated at every point)
+    bool far = false;
+    float *node_x = nullptr;     // [T*kFarNodes] Chebyshev nodes of each tile's span
+    float *node_c = nullptr;     // [T*kFarNodes] cos(x/2) at the nodes (angle-dependent width)
+    float *lam = nullptr;        // [T*kFarNodes*kTile] Lagrange weights lam_p(x_i) of the tile's points
+    int *far_order = nullptr;    // [K] phases by decreasing peak count (far-field work balance)
     bool gauss = false;          // Gaussian likelihood variant (variance max(y, 1))
     bool fix_r = false, fix_alpha = false;   // r / alpha held at r_value / alpha_value
     bool area_norm = false;      // area-normalised profiles (h = integrated intensity)
@@ -155,7 +171,7 @@ struct Problem {
     float *beta = nullptr, *m_beta = nullptr, *v_beta = nullptr;   // [3] coefficients, Adam moments
     float *Tb = nullptr;         // [3*N] Chebyshev terms T_j(z_i)
     float *Bb = nullptr;         // [N] B(beta) of the current step
-    int grid_fwd = 0, grid_bwd = 0;
+    int grid_fwd = 0, grid_bwd = 0, grid_far = 0, grid_bwd_direct = 0;
 };
 
 // --- kernel launchers (xrdvi_kernels.cu) ------------------------------------
@@ -165,8 +181,12 @@ struct Problem {
 void launch_sample(const Problem &P, Workspace &W, const float *loc, const float *raw,
                    const float *eps_in, uint64_t seed, uint32_t tag, const int *d_step,
                    uint32_t step, int *d_iter, double *ent, cudaStream_t st);
-void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st);
-void launch_backward(const Problem &P, Workspace &W, cudaStream_t st);
+// marks (may be null): events recorded between the kernels, for per-kernel
+// timing: forward after k_ranges, the direct profile and the far field [3];
+// backward after the side-uniform and the near sums [2].
+void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st,
+                    cudaEvent_t *marks = nullptr);
+void launch_backward(const Problem &P, Workspace &W, cudaStream_t st, cudaEvent_t *marks = nullptr);
 // Reduces gradient partials per phase and optionally applies Adam (when
 // grad_out or adam), then finalises the ELBO (when elbo_out or trace: writes
 // ll[S], *elbo_out, trace[step] and advances *d_step).

@@ -398,6 +398,12 @@ struct ProfArgs {
     float *ghl;        // [2*S*Npad] TF32 hi / lo parts of g (shared-shape variant; null otherwise)
     const float *Tb;   // [3*N] Chebyshev terms (fitted background; null: fixed background)
     float *bgpart;     // [S*T*3] per-(sample, tile) sums of g B(beta) T_j
+    // far field (null: every peak evaluated at every point)
+    ushort2 *franges;  // [S*K*T] (fb, fe) relative to the phase's first peak
+    float *fnode;      // [S*T*kFarNodes] far-field profile at the nodes
+    float *wfar;       // [S*T*kFarNodes] node weights of g (null: not needed)
+    const float *node_x, *node_c, *lam;
+    const int *far_order;   // [K] phases by decreasing peak count
 };
 
 typedef unsigned long long f2_t;   // two packed floats
@@ -501,6 +507,14 @@ __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
         const int ne = first_beyond<true>(a.pos, nb, me, xhi - c.mu + c.rl);
         a.ranges[idx] = make_ushort4(static_cast<unsigned short>(m1 - mb), static_cast<unsigned short>(m2 - mb),
                                      static_cast<unsigned short>(nb - mb), static_cast<unsigned short>(ne - mb));
+        if (a.franges) {
+            // far peaks: more than kFarGap half-widths of the tile beyond it and
+            // beyond their Gaussian reach, so only their Lorentzian reaches it
+            const float gap = fmaxf(kFarGap * 0.5f * (xhi - xlo), kSideMargin);
+            const int fb = min(min(first_beyond<true>(a.pos, mb, m1, xlo - c.mu - gap), nb), m1);
+            const int fe = max(max(first_beyond<false>(a.pos, m2, me, xhi - c.mu + gap), ne), m2);
+            a.franges[idx] = make_ushort2(static_cast<unsigned short>(fb - mb), static_cast<unsigned short>(fe - mb));
+        }
     }
 }
 
@@ -518,6 +532,11 @@ struct PeakTable<false> {
         np = bc2(v.x);
         I = bc2(v.y);
     }
+    __device__ __forceinline__ void scalar(int m, float &np, float &I) const {
+        const float2 v = p[m];
+        np = v.x;
+        I = v.y;
+    }
 };
 template <>
 struct PeakTable<true> {
@@ -526,6 +545,11 @@ struct PeakTable<true> {
         const float4 v = p[m];
         np = pk2(v.x, v.y);
         I = pk2(v.z, v.w);
+    }
+    __device__ __forceinline__ void scalar(int m, float &np, float &I) const {
+        const float4 v = p[m];
+        np = v.x;
+        I = v.z;
     }
 };
 
@@ -551,16 +575,21 @@ __device__ __forceinline__ PeakTable<kWide> load_table(const ProfArgs &a, float4
     return t;
 }
 
+// Peak ranges of one (sample, phase, tile): [mb, fb) far below, [fb, m1)
+// near below, [m1, m2) mixed, [m2, fe) near above, [fe, me) far above, and
+// the Gaussian reach [nb, ne) (inside [fb, fe)).  Without the far field
+// fb = mb and fe = me.
 struct Ranges {
-    int mb, m1, m2, me, nb, ne;
+    int mb, m1, m2, me, nb, ne, fb, fe;
 };
 
 __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_off, int s, int k, int tile) {
-    const ushort4 r = a.ranges[(static_cast<size_t>(s) * a.K + k) * a.T + tile];
+    const size_t id = (static_cast<size_t>(s) * a.K + k) * a.T + tile;
+    const ushort4 r = a.ranges[id];
     Ranges o;
     o.mb = s_off[k];
     if (r.x == kAbsentRange) {  // phase not in this sample's sub-model: every range empty
-        o.me = o.m1 = o.m2 = o.nb = o.ne = o.mb;
+        o.me = o.m1 = o.m2 = o.nb = o.ne = o.fb = o.fe = o.mb;
         return o;
     }
     o.me = s_off[k + 1];
@@ -568,6 +597,74 @@ __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_of
     o.m2 = o.mb + r.y;
     o.nb = o.mb + r.z;
     o.ne = o.mb + r.w;
+    if (a.franges) {
+        const ushort2 f = a.franges[id];
+        o.fb = o.mb + f.x;
+        o.fe = o.mb + f.y;
+    } else {
+        o.fb = o.mb;
+        o.fe = o.me;
+    }
+    return o;
+}
+
+// A warp's copy of the per-phase data of up to 32 phases.  The far-field
+// kernels visit a sample's phases one after another; staging them
+// lane-parallel in shared memory takes the dependent global loads (ranges,
+// constants) off that loop.
+struct __align__(16) Staged {
+    float mu, hl, hg, sl, sr, nslmu, nsrmu;
+    int k;
+    ushort4 r;
+    ushort2 f;
+    int pad;
+};
+
+// Stages phases order[j] (order null: j) for j in [j0, min(j0 + 32, j1)).
+__device__ __forceinline__ void stage_phases(const ProfArgs &a, Staged *buf, int s, int tile, const int *order,
+                                             int j0, int j1, int lane) {
+    __syncwarp();   // the previous batch's reads are done
+    const int j = j0 + lane;
+    if (j < j1) {
+        const int k = order ? order[j] : j;
+        const size_t id = (static_cast<size_t>(s) * a.K + k) * a.T + tile;
+        const PhaseConst *c = a.cst + static_cast<size_t>(s) * a.K + k;
+        Staged st;
+        st.mu = c->mu;
+        st.hl = c->hl;
+        st.hg = c->hg;
+        st.sl = c->sl;
+        st.sr = c->sr;
+        st.nslmu = c->nslmu;
+        st.nsrmu = c->nsrmu;
+        st.k = k;
+        st.r = a.ranges[id];
+        st.f = a.franges ? a.franges[id] : make_ushort2(0, 0);
+        st.pad = 0;
+        buf[lane] = st;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ Ranges staged_ranges(const ProfArgs &a, const int *s_off, const Staged &st) {
+    Ranges o;
+    o.mb = s_off[st.k];
+    if (st.r.x == kAbsentRange) {
+        o.me = o.m1 = o.m2 = o.nb = o.ne = o.fb = o.fe = o.mb;
+        return o;
+    }
+    o.me = s_off[st.k + 1];
+    o.m1 = o.mb + st.r.x;
+    o.m2 = o.mb + st.r.y;
+    o.nb = o.mb + st.r.z;
+    o.ne = o.mb + st.r.w;
+    if (a.franges) {
+        o.fb = o.mb + st.f.x;
+        o.fe = o.mb + st.f.y;
+    } else {
+        o.fb = o.mb;
+        o.fe = o.me;
+    }
     return o;
 }
 
@@ -646,34 +743,72 @@ __device__ __forceinline__ void acc_points(float (&fs)[kPts], float (&fc)[kPts],
 }
 
 // --- forward ------------------------------------------------------------------
+// Side-uniform ranges take the points relative to the tile's edge on the
+// range's side, x0 (the first point for peaks below the tile, the last for
+// peaks above it): t = s (x - x0) + b with b = s (x0 - p) - s mu.  Over such a
+// range both terms have the sign of t, so t keeps full relative accuracy and
+// costs one FMA per evaluation.  The b of up to 32 peaks are formed at once,
+// one per lane, into the warp's buffer as (b, b, I, I).
+template <class Tab>
+__device__ __forceinline__ void fill_offsets(const Tab &tab, float4 *wb, int lane, int mb, int n, float sc,
+                                             float cmu, float x0) {
+    __syncwarp();   // the previous batch's reads are done
+    if (lane < n) {
+        float np, I;
+        tab.scalar(mb + lane, np, I);
+        const float b = fmaf(sc, x0 + np, cmu);
+        wb[lane] = make_float4(b, b, I, I);
+    }
+    __syncwarp();
+}
+
+// The lane's points relative to x0, x - x0 (exact for points of one tile away
+// from x = 0), loaded again for each range so that no point coordinates stay
+// in registers across the phase loop.
+__device__ __forceinline__ void rel_points(const ProfArgs &a, int i0, int lane, float x0, f2_t (&dx2)[kPairs]) {
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        const int i_a = min(i0 + (2 * q) * 32 + lane, a.N - 1);
+        const int i_b = min(i0 + (2 * q + 1) * 32 + lane, a.N - 1);
+        dx2[q] = pk2(a.x[i_a] - x0, a.x[i_b] - x0);
+    }
+}
+
 // Lorentzian sums on a side-uniform range, one reciprocal per two peaks:
 // I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1)  (d = 1 + t^2; d0 d1 stays finite
 // while s |d| < 1e9).
 template <class Tab, class Sc>
-__device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
-                                             const f2_t (&x2)[kPairs], const Sc &ps, f2_t (&sl)[kPairs]) {
-    const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
-    int m = m0;
-    for (; m + 1 < m1; m += 2) {
-        f2_t np0, I0, np1, I1;
-        tab.get(m, np0, I0);
-        tab.get(m + 1, np1, I1);
+__device__ __forceinline__ void fwdL_uniform(const ProfArgs &a, const Tab &tab, float4 *wb, int i0, int lane, int m0,
+                                             int m1, float sc, float cmu, float x0, const Sc &ps, f2_t (&sl)[kPairs]) {
+    if (m0 >= m1) return;
+    const f2_t s2 = bc2(sc), one2 = bc2(1.f);
+    f2_t dx2[kPairs];
+    rel_points(a, i0, lane, x0, dx2);
+    for (int mb = m0; mb < m1; mb += 32) {
+        const int n = min(32, m1 - mb);
+        fill_offsets(tab, wb, lane, mb, n, sc, cmu, x0);
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+            const float4 v0 = wb[j], v1 = wb[j + 1];
+            const f2_t b0 = pk2(v0.x, v0.y), I0 = pk2(v0.z, v0.w);
+            const f2_t b1 = pk2(v1.x, v1.y), I1 = pk2(v1.z, v1.w);
 #pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const f2_t t0 = ps(fma2(s2, add2(x2[q], np0), c2), q);
-            const f2_t t1 = ps(fma2(s2, add2(x2[q], np1), c2), q);
-            const f2_t d0 = fma2(t0, t0, one2), d1 = fma2(t1, t1, one2);
-            const f2_t num = fma2(I0, d1, mul2(I1, d0));
-            sl[q] = fma2(num, rcp2(mul2(d0, d1)), sl[q]);
+            for (int q = 0; q < kPairs; ++q) {
+                const f2_t t0 = ps(fma2(s2, dx2[q], b0), q);
+                const f2_t t1 = ps(fma2(s2, dx2[q], b1), q);
+                const f2_t d0 = fma2(t0, t0, one2), d1 = fma2(t1, t1, one2);
+                const f2_t num = fma2(I0, d1, mul2(I1, d0));
+                sl[q] = fma2(num, rcp2(mul2(d0, d1)), sl[q]);
+            }
         }
-    }
-    if (m < m1) {
-        f2_t np, I;
-        tab.get(m, np, I);
+        if (j < n) {
+            const float4 v = wb[j];
+            const f2_t b = pk2(v.x, v.y), I = pk2(v.z, v.w);
 #pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
-            sl[q] = fma2(I, rcp2(fma2(t, t, one2)), sl[q]);
+            for (int q = 0; q < kPairs; ++q) {
+                const f2_t t = ps(fma2(s2, dx2[q], b), q);
+                sl[q] = fma2(I, rcp2(fma2(t, t, one2)), sl[q]);
+            }
         }
     }
 }
@@ -681,10 +816,11 @@ __device__ __forceinline__ void fwdL_uniform(const Tab &tab, int m0, int m1, flo
 // Near part of one phase's profile on the tile: the mixed range (both
 // components, side chosen per point) and the Gaussian on the side-uniform
 // ranges within its reach.
-template <class Tab, class Sc>
-__device__ __forceinline__ void fwd_near(const Tab &tab, const Ranges &r, const PhaseConst &cp,
-                                         const f2_t (&x2)[kPairs], const Sc &ps, f2_t (&sl)[kPairs],
-                                         f2_t (&sg)[kPairs]) {
+template <class Tab, class Sc, class PC>
+__device__ __forceinline__ void fwd_near(const ProfArgs &a, const Tab &tab, const Ranges &r, const PC &cp,
+                                         int i0, int lane, const Sc &ps, f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
+    f2_t x2[kPairs];
+    item_points(a, i0, lane, x2);
     const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
     for (int m = r.m1; m < r.m2; ++m) {
         f2_t np, I;
@@ -718,17 +854,18 @@ __device__ __forceinline__ void fwd_near(const Tab &tab, const Ranges &r, const 
 template <bool kNaive, bool kWide, bool kSec = false>
 __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
     extern __shared__ float4 s_raw[];
+    __shared__ float4 s_wb[kWarps][32];
     int *s_off;
     const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
     const int lane = threadIdx.x & 31;
+    float4 *wb = s_wb[threadIdx.x >> 5];
     const int items = a.S * a.T * a.C;
     for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
         const int c = item % a.C;
         const int st = item / a.C;
         const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
-        f2_t x2[kPairs];
-        item_points(a, i0, lane, x2);
+        const float xlo = a.x[i0], xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
         PtScale<kSec> ps;
         ps.load(a, i0, lane);
         float fs[kPts], fc[kPts];
@@ -743,10 +880,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
             for (int q = 0; q < kPairs; ++q) sl[q] = sg[q] = 0ull;
 #pragma unroll 1
             for (int side = 0; side < 2; ++side) {
-                fwdL_uniform(tab, side ? r.m2 : r.mb, side ? r.me : r.m1, side ? cp.sl : cp.sr,
-                             side ? cp.nslmu : cp.nsrmu, x2, ps, sl);
+                fwdL_uniform(a, tab, wb, i0, lane, side ? r.m2 : r.fb, side ? r.fe : r.m1, side ? cp.sl : cp.sr,
+                             side ? cp.nslmu : cp.nsrmu, side ? xhi : xlo, ps, sl);
             }
-            if (near_work(r)) fwd_near(tab, r, cp, x2, ps, sl, sg);  // warp-uniform
+            if (near_work(r)) fwd_near(a, tab, r, cp, i0, lane, ps, sl, sg);  // warp-uniform
             const f2_t hl2 = bc2(cp.hl), hg2 = bc2(cp.hg);
 #pragma unroll
             for (int q = 0; q < kPairs; ++q) sl[q] = fma2(hl2, sl[q], mul2(hg2, sg[q]));
@@ -755,6 +892,210 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
         float *dst = a.fpart + (static_cast<size_t>(c) * a.S + s) * a.Npad + i0 + lane;
 #pragma unroll
         for (int j = 0; j < kPts; ++j) dst[j * 32] = fs[j] + fc[j];
+    }
+}
+
+// --- far field -------------------------------------------------------------------
+// The Lorentzian tails that reach a tile from peaks beyond kFarGap half-widths
+// of it are analytic on the tile's span, with poles x = rho +- i/s at least
+// 1.5 half-widths from its centre.  Their sums are therefore evaluated at
+// kFarNodes Chebyshev nodes of the first kind of the span (Trefethen,
+// "Approximation Theory and Approximation Practice", ch. 8 bounds the
+// interpolation error by a power of the Bernstein-ellipse parameter; for
+// these poles it is below 1e-8 of the tail, under FP32 rounding) and
+// interpolated at the tile's points with Lagrange weights lam_p(x_i):
+//   forward   f_far(x_i) = sum_p lam_p(x_i) F_p          (in k_lik)
+//   backward  sum_i g_i phi(x_i) = sum_p W_p phi(x_p),  W_p = sum_i g_i lam_p(x_i).
+// Work item: one warp per (sample, tile).  Lane group q = lane / 8 takes the
+// peaks m = q (mod 4) of each range; lane l % 8 owns nodes 4 (l % 8) .. + 3.
+
+// Far-field profile at the nodes: F_p = sum_k h_k r_k sum_{far m} I_m L(t_mkp),
+// one reciprocal per two peaks (I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1)).
+template <bool kWide, bool kSec>
+__global__ void __launch_bounds__(kThreads) k_far_fwd(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    __shared__ Staged s_st[kWarps][32];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    const int lane = threadIdx.x & 31, grp = lane >> 3, nl = lane & 7;
+    Staged *sb = s_st[threadIdx.x >> 5];
+    const int nwarps = gridDim.x * kWarps;
+    const f2_t one2 = bc2(1.f);
+    for (int item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < a.S * a.T; item += nwarps) {
+        const int s = item / a.T, tile = item - s * a.T;
+        const float4 xv = reinterpret_cast<const float4 *>(a.node_x + static_cast<size_t>(tile) * kFarNodes)[nl];
+        const f2_t xn[2] = {pk2(xv.x, xv.y), pk2(xv.z, xv.w)};
+        f2_t cn[2] = {one2, one2};
+        if (kSec) {
+            const float4 cv = reinterpret_cast<const float4 *>(a.node_c + static_cast<size_t>(tile) * kFarNodes)[nl];
+            cn[0] = pk2(cv.x, cv.y);
+            cn[1] = pk2(cv.z, cv.w);
+        }
+        float F[4] = {0.f, 0.f, 0.f, 0.f}, Fc[4] = {0.f, 0.f, 0.f, 0.f};
+        // lane group q takes the phases order[q], order[q + 4], ... of each
+        // staged batch of 32 (sorted by peak count, so the four groups' loops
+        // have similar lengths)
+        for (int jb = 0; jb < a.K; jb += 32) {
+            stage_phases(a, sb, s, tile, a.far_order, jb, a.K, lane);
+            const int nb = min(32, a.K - jb);
+            for (int jj = grp; jj < nb; jj += 4) {
+            const Staged &ph = sb[jj];
+            const Ranges r = staged_ranges(a, s_off, ph);
+            const int mb = r.mb, fb = r.fb, fe = r.fe, me = r.me;
+            if (fb > mb || me > fe) {
+                f2_t acc[2] = {0ull, 0ull};
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const int m0 = side ? fe : mb, m1 = side ? me : fb;
+                    const f2_t s2 = bc2(side ? ph.sl : ph.sr), c2 = bc2(side ? ph.nslmu : ph.nsrmu);
+                    int m = m0;
+                    for (; m + 1 < m1; m += 2) {
+                        f2_t np0, I0, np1, I1;
+                        tab.get(m, np0, I0);
+                        tab.get(m + 1, np1, I1);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            f2_t t0 = fma2(s2, add2(xn[q], np0), c2), t1 = fma2(s2, add2(xn[q], np1), c2);
+                            if (kSec) {
+                                t0 = mul2(t0, cn[q]);
+                                t1 = mul2(t1, cn[q]);
+                            }
+                            const f2_t d0 = fma2(t0, t0, one2), d1 = fma2(t1, t1, one2);
+                            const f2_t num = fma2(I0, d1, mul2(I1, d0));
+                            acc[q] = fma2(num, rcp2(mul2(d0, d1)), acc[q]);
+                        }
+                    }
+                    if (m < m1) {
+                        f2_t np, I;
+                        tab.get(m, np, I);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            f2_t t = fma2(s2, add2(xn[q], np), c2);
+                            if (kSec) t = mul2(t, cn[q]);
+                            acc[q] = fma2(I, rcp2(fma2(t, t, one2)), acc[q]);
+                        }
+                    }
+                }
+                // F += h r acc, Neumaier-compensated over the phases
+                const f2_t hl2 = bc2(ph.hl);
+                float v[4];
+                up2(mul2(hl2, acc[0]), v[0], v[1]);
+                up2(mul2(hl2, acc[1]), v[2], v[3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float t = F[q] + v[q];
+                    Fc[q] += (fabsf(F[q]) >= fabsf(v[q])) ? ((F[q] - t) + v[q]) : ((v[q] - t) + F[q]);
+                    F[q] = t;
+                }
+            }
+            }
+        }
+        __syncwarp();
+        // the four lane groups' partial sums of each node
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float t = F[q] + Fc[q];
+            t += __shfl_xor_sync(0xffffffffu, t, 8);
+            t += __shfl_xor_sync(0xffffffffu, t, 16);
+            F[q] = t;
+        }
+        if (grp == 0)
+            reinterpret_cast<float4 *>(a.fnode + static_cast<size_t>(item) * kFarNodes)[nl] =
+                make_float4(F[0], F[1], F[2], F[3]);
+    }
+}
+
+// Far-field part of the gradient sums, added to the Lorentzian entries the
+// direct kernel wrote: with the node weights W_p of g,
+//   S1 = sum_p W_p sum_m I L,  A = sum_p W_p c_p sum_m I L^2 t,  B = S1 - sum_p W_p sum_m I L^2
+// per side (c_p = cos(x_p/2) with the angle-dependent width, else 1).  Lane
+// group q takes phases order[q], order[q + 4], ...; the group's 8 lanes hold
+// the 32 nodes and reduce among themselves.
+template <bool kWide, bool kSec>
+__global__ void __launch_bounds__(kThreads) k_far_bwd(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    __shared__ Staged s_st[kWarps][32];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    const int lane = threadIdx.x & 31, grp = lane >> 3, nl = lane & 7;
+    Staged *sb = s_st[threadIdx.x >> 5];
+    const int nwarps = gridDim.x * kWarps;
+    const f2_t one2 = bc2(1.f);
+    for (int item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < a.S * a.T; item += nwarps) {
+        const int s = item / a.T, tile = item - s * a.T;
+        const float4 xv = reinterpret_cast<const float4 *>(a.node_x + static_cast<size_t>(tile) * kFarNodes)[nl];
+        const f2_t xn[2] = {pk2(xv.x, xv.y), pk2(xv.z, xv.w)};
+        const float4 wv = reinterpret_cast<const float4 *>(a.wfar + static_cast<size_t>(item) * kFarNodes)[nl];
+        const f2_t W[2] = {pk2(wv.x, wv.y), pk2(wv.z, wv.w)};
+        f2_t cn[2] = {one2, one2}, WA[2] = {W[0], W[1]};
+        if (kSec) {
+            const float4 cv = reinterpret_cast<const float4 *>(a.node_c + static_cast<size_t>(tile) * kFarNodes)[nl];
+            cn[0] = pk2(cv.x, cv.y);
+            cn[1] = pk2(cv.z, cv.w);
+            WA[0] = mul2(W[0], cn[0]);
+            WA[1] = mul2(W[1], cn[1]);
+        }
+        // staged batches of 32 phases (by decreasing peak count), rounds of
+        // four; every lane runs every round (the reduction below shuffles
+        // within the group)
+        for (int jb = 0; jb < a.K; jb += 32) {
+          stage_phases(a, sb, s, tile, a.far_order, jb, a.K, lane);
+          const int nb = min(32, a.K - jb);
+          for (int j0 = 0; j0 < nb; j0 += 4) {
+            const int jj = j0 + grp;
+            const Staged &ph = sb[jj < nb ? jj : 0];
+            const int k = ph.k;
+            const Ranges r = staged_ranges(a, s_off, ph);
+            int mb = r.mb, fb = r.fb, fe = r.fe, me = r.me;
+            if (jj >= nb) fb = mb, fe = me;                // no phase for this group in the last round
+            const bool any = fb > mb || me > fe;
+            float S1 = 0.f, A[2] = {0.f, 0.f}, B[2] = {0.f, 0.f};
+            if (any) {
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const int m0 = side ? fe : mb, m1 = side ? me : fb;
+                    const f2_t s2 = bc2(side ? ph.sl : ph.sr), c2 = bc2(side ? ph.nslmu : ph.nsrmu);
+                    f2_t S1n[2] = {0ull, 0ull}, An[2] = {0ull, 0ull}, C2n[2] = {0ull, 0ull};
+                    for (int m = m0; m < m1; ++m) {
+                        f2_t np, I;
+                        tab.get(m, np, I);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            f2_t t = fma2(s2, add2(xn[q], np), c2);
+                            if (kSec) t = mul2(t, cn[q]);
+                            const f2_t L = rcp2(fma2(t, t, one2));
+                            const f2_t q1 = mul2(I, L);
+                            S1n[q] = add2(S1n[q], q1);
+                            const f2_t q2 = mul2(q1, L);
+                            An[q] = fma2(q2, t, An[q]);
+                            C2n[q] = add2(C2n[q], q2);
+                        }
+                    }
+                    const float s1 = sum2(fma2(W[0], S1n[0], mul2(W[1], S1n[1])));
+                    const float as = sum2(fma2(WA[0], An[0], mul2(WA[1], An[1])));
+                    const float c2s = sum2(fma2(W[0], C2n[0], mul2(W[1], C2n[1])));
+                    S1 += s1;
+                    A[side] = as;
+                    B[side] = s1 - c2s;
+                }
+            }
+            __syncwarp();
+            // side 0: all d > 0 (|t| = t); side 1: all d < 0 (|t| = -t)
+            float v[5] = {S1, A[0] + A[1], A[0] - A[1], B[0] + B[1], B[0] - B[1]};
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
+                v[q] += __shfl_xor_sync(0xffffffffu, v[q], 2);
+                v[q] += __shfl_xor_sync(0xffffffffu, v[q], 4);
+            }
+            if (any && nl == 0) {
+                float2 *dst = reinterpret_cast<float2 *>(
+                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) dst[q].y += v[q];
+            }
+          }
+        }
     }
 }
 
@@ -788,9 +1129,17 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
     const int i = tile * kTile + threadIdx.x;
     float dev = 0.f;
     float gv = 0.f;
+    const float *lam = a.fnode ? a.lam + static_cast<size_t>(tile) * kFarNodes * kTile + threadIdx.x : nullptr;
     if (i < a.N) {
         float f = a.bg[i];
         for (int c = 0; c < a.C; ++c) f += a.fpart[(static_cast<size_t>(c) * a.S + s) * a.Npad + i];
+        if (lam) {   // far field: interpolated from the tile's nodes
+            const float *fn = a.fnode + static_cast<size_t>(blockIdx.x) * kFarNodes;
+            float ff = 0.f;
+#pragma unroll 8
+            for (int p = 0; p < kFarNodes; ++p) ff = fmaf(lam[p * kTile], fn[p], ff);
+            f += ff;
+        }
         const float yv = a.y[i];
         if (a.gauss) {
             // Gaussian variant: -(y - f)^2 / (2 v), d/df = (y - f) / v, v = max(y, 1)
@@ -812,6 +1161,32 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
     dev = warp_sumf(dev);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) shf[w] = dev;
+    if (a.wfar) {
+        // node weights of g: W_p = sum_i g_i lam_p(x_i).  A reduce-scatter
+        // leaves lane p of each warp with its warp's sum for node p.
+        __shared__ float shw[kTile / 32][kFarNodes];
+        float v[kFarNodes];
+#pragma unroll
+        for (int p = 0; p < kFarNodes; ++p) v[p] = gv * lam[p * kTile];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const bool up = (l & o) != 0;
+#pragma unroll
+            for (int j = 0; j < o; ++j) {
+                const float send = up ? v[j] : v[j + o];
+                const float keep = up ? v[j + o] : v[j];
+                v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        shw[w][l] = v[0];
+        __syncthreads();
+        if (threadIdx.x < kFarNodes) {
+            float t = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < kTile / 32; ++ww) t += shw[ww][threadIdx.x];
+            a.wfar[static_cast<size_t>(blockIdx.x) * kFarNodes + threadIdx.x] = t;
+        }
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
         float t = threadIdx.x < kTile / 32 ? shf[threadIdx.x] : 0.f;
@@ -859,71 +1234,78 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
 // sums over the range's peaks are taken per point without the point's factor
 // g = y/f - 1, which multiplies them once at the end (q = g I).
 template <class Tab, class Sc>
-__device__ __forceinline__ void bwdL_uniform(const Tab &tab, int m0, int m1, float sc, float cmu,
-                                             const f2_t (&x2)[kPairs], const Sc &ps, const f2_t (&g2)[kPairs],
-                                             f2_t &S1, f2_t &A, f2_t &C2) {
-    const f2_t s2 = bc2(sc), c2 = bc2(cmu), one2 = bc2(1.f);
+__device__ __forceinline__ void bwdL_uniform(const ProfArgs &a, const Tab &tab, float4 *wb, int i0, int lane,
+                                             const float *gs, int m0, int m1, float sc, float cmu, float x0,
+                                             const Sc &ps, f2_t &S1, f2_t &A, f2_t &C2) {
+    if (m0 >= m1) return;
+    const f2_t s2 = bc2(sc), one2 = bc2(1.f);
+    f2_t dx2[kPairs];
+    rel_points(a, i0, lane, x0, dx2);
     f2_t S1p[kPairs], Ap[kPairs], C2p[kPairs];
 #pragma unroll
     for (int q = 0; q < kPairs; ++q) S1p[q] = Ap[q] = C2p[q] = 0ull;
-    for (int m = m0; m < m1; ++m) {
-        f2_t np, I;
-        tab.get(m, np, I);
+    for (int mb = m0; mb < m1; mb += 32) {
+        const int n = min(32, m1 - mb);
+        fill_offsets(tab, wb, lane, mb, n, sc, cmu, x0);
+        for (int j = 0; j < n; ++j) {
+            const float4 v = wb[j];
+            const f2_t b = pk2(v.x, v.y), I = pk2(v.z, v.w);
 #pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
-            const f2_t L = rcp2(fma2(t, t, one2));
-            const f2_t q1 = mul2(I, L);
-            S1p[q] = add2(S1p[q], q1);
-            const f2_t q2 = mul2(q1, L);
-            Ap[q] = fma2(q2, t, Ap[q]);
-            C2p[q] = add2(C2p[q], q2);
+            for (int q = 0; q < kPairs; ++q) {
+                const f2_t t = ps(fma2(s2, dx2[q], b), q);
+                const f2_t L = rcp2(fma2(t, t, one2));
+                const f2_t q1 = mul2(I, L);
+                S1p[q] = add2(S1p[q], q1);
+                const f2_t q2 = mul2(q1, L);
+                Ap[q] = fma2(q2, t, Ap[q]);
+                C2p[q] = add2(C2p[q], q2);
+            }
         }
     }
 #pragma unroll
     for (int q = 0; q < kPairs; ++q) {
-        S1 = fma2(g2[q], S1p[q], S1);
-        A = fma2(ps(g2[q], q), Ap[q], A);   // mu sums: g cos(x/2) in the angle-dependent variant
-        C2 = fma2(g2[q], C2p[q], C2);
+        const f2_t g2 = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);   // g = y/f - 1 (0 on padding)
+        S1 = fma2(g2, S1p[q], S1);
+        A = fma2(ps(g2, q), Ap[q], A);   // mu sums: g cos(x/2) in the angle-dependent variant
+        C2 = fma2(g2, C2p[q], C2);
     }
 }
 
 template <bool kWide, bool kSec = false>
 __global__ void __launch_bounds__(kThreads, 4) k_bwd_uniform(ProfArgs a) {
     extern __shared__ float4 s_raw[];
+    __shared__ float4 s_wb[kWarps][32];
     int *s_off;
     const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
     const int lane = threadIdx.x & 31;
+    float4 *wb = s_wb[threadIdx.x >> 5];
     const int items = a.S * a.T * a.C;
     for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
         const int c = item % a.C;
         const int st = item / a.C;
         const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
-        f2_t x2[kPairs], g2[kPairs];
-        item_points(a, i0, lane, x2);
+        const float xlo = a.x[i0], xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
         PtScale<kSec> ps;
         ps.load(a, i0, lane);
         const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
-#pragma unroll
-        for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
         for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
             const PhaseConst cp = cs[k];
             const Ranges r = load_ranges(a, s_off, s, k, tile);
-            f2_t S1 = 0ull, A[2] = {0ull, 0ull}, B[2] = {0ull, 0ull};
+            // the lane's sums over its points, per side
+            float S1 = 0.f, A[2] = {0.f, 0.f}, B[2] = {0.f, 0.f};
 #pragma unroll 1
             for (int side = 0; side < 2; ++side) {
                 f2_t S1s = 0ull, As = 0ull, C2s = 0ull;
-                bwdL_uniform(tab, side ? r.m2 : r.mb, side ? r.me : r.m1, side ? cp.sl : cp.sr,
-                             side ? cp.nslmu : cp.nsrmu, x2, ps, g2, S1s, As, C2s);
-                S1 = add2(S1, S1s);
-                const f2_t Bs = sub2(S1s, C2s);
-                if (side) { A[1] = As; B[1] = Bs; } else { A[0] = As; B[0] = Bs; }
+                bwdL_uniform(a, tab, wb, i0, lane, gs, side ? r.m2 : r.fb, side ? r.fe : r.m1, side ? cp.sl : cp.sr,
+                             side ? cp.nslmu : cp.nsrmu, side ? xhi : xlo, ps, S1s, As, C2s);
+                S1 += sum2(S1s);
+                const float as = sum2(As), bs = sum2(sub2(S1s, C2s));
+                if (side) { A[1] = as; B[1] = bs; } else { A[0] = as; B[0] = bs; }
             }
             // side 0: all d > 0 (|t| = t); side 1: all d < 0 (|t| = -t)
-            float v[5] = {sum2(S1), sum2(add2(A[0], A[1])), sum2(sub2(A[0], A[1])), sum2(add2(B[0], B[1])),
-                          sum2(sub2(B[0], B[1]))};
+            float v[5] = {S1, A[0] + A[1], A[0] - A[1], B[0] + B[1], B[0] - B[1]};
 #pragma unroll
             for (int j = 0; j < 5; ++j) v[j] = warp_sumf(v[j]);
             if (lane == 0) {
@@ -944,6 +1326,72 @@ __device__ __forceinline__ f2_t fma_abs2(f2_t v, f2_t t, f2_t acc) {
     up2(v, v0, v1);
     up2(acc, a0, a1);
     return pk2(fmaf(v0, fabsf(t0), a0), fmaf(v1, fabsf(t1), a1));
+}
+
+// Near part of one phase's gradient sums on a tile (mixed range: both
+// components with the side chosen per point; Gaussian terms on the
+// side-uniform ranges within its reach), accumulated into acc[kGradSums]
+// (even entries Gaussian, odd Lorentzian: S1, A, A|t|, B, B|t|).
+template <class Tab, class Sc, class PC>
+__device__ __forceinline__ void bwd_near_sums(const Tab &tab, const Ranges &r, const PC &cp,
+                                              const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs], const Sc &ps,
+                                              f2_t (&acc)[kGradSums]) {
+    const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
+    for (int m = r.m1; m < r.m2; ++m) {
+        f2_t np, I;
+        tab.get(m, np, I);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
+            const f2_t tA = ps(t, q);   // t for the mu sums (times cos(x/2) once more)
+            const f2_t u = mul2(t, t);
+            const f2_t L = rcp2(add2(u, one2));
+            const f2_t gI = mul2(g2[q], I);
+            const f2_t q1 = mul2(gI, L);
+            acc[1] = add2(acc[1], q1);
+            const f2_t q2 = mul2(q1, L);
+            acc[3] = fma2(q2, tA, acc[3]);
+            acc[5] = fma_abs2(q2, tA, acc[5]);
+            const f2_t q3 = mul2(q2, t);
+            acc[7] = fma2(q3, t, acc[7]);
+            acc[9] = fma_abs2(q3, t, acc[9]);
+            if (any_gauss(u)) {
+                const f2_t qg = mul2(gI, ex2neg2(u));
+                acc[0] = add2(acc[0], qg);
+                acc[2] = fma2(qg, tA, acc[2]);
+                acc[4] = fma_abs2(qg, tA, acc[4]);
+                const f2_t q3g = mul2(qg, t);
+                acc[6] = fma2(q3g, t, acc[6]);
+                acc[8] = fma_abs2(q3g, t, acc[8]);
+            }
+        }
+    }
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
+        const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
+        f2_t S1 = 0ull, A = 0ull, B = 0ull;
+        for (int m = m0; m < m1; ++m) {
+            f2_t np, I;
+            tab.get(m, np, I);
+#pragma unroll
+            for (int q = 0; q < kPairs; ++q) {
+                const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
+                const f2_t u = mul2(t, t);
+                if (any_gauss(u)) {
+                    const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(u));
+                    S1 = add2(S1, qg);
+                    A = fma2(qg, ps(t, q), A);
+                    B = fma2(mul2(qg, t), t, B);
+                }
+            }
+        }
+        acc[0] = add2(acc[0], S1);
+        acc[2] = add2(acc[2], A);
+        acc[6] = add2(acc[6], B);
+        acc[4] = side ? sub2(acc[4], A) : add2(acc[4], A);
+        acc[8] = side ? sub2(acc[8], B) : add2(acc[8], B);
+    }
 }
 
 // Near part of the gradient sums (mixed range: both components; Gaussian on
@@ -999,62 +1447,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
                 f2_t acc[kGradSums];
 #pragma unroll
                 for (int j = 0; j < kGradSums; ++j) acc[j] = 0ull;
-                const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
-                for (int m = r.m1; m < r.m2; ++m) {
-                    f2_t np, I;
-                    tab.get(m, np, I);
-#pragma unroll
-                    for (int q = 0; q < kPairs; ++q) {
-                        const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
-                        const f2_t tA = ps(t, q);   // t for the mu sums (times cos(x/2) once more)
-                        const f2_t u = mul2(t, t);
-                        const f2_t L = rcp2(add2(u, one2));
-                        const f2_t gI = mul2(g2[q], I);
-                        const f2_t q1 = mul2(gI, L);
-                        acc[1] = add2(acc[1], q1);
-                        const f2_t q2 = mul2(q1, L);
-                        acc[3] = fma2(q2, tA, acc[3]);
-                        acc[5] = fma_abs2(q2, tA, acc[5]);
-                        const f2_t q3 = mul2(q2, t);
-                        acc[7] = fma2(q3, t, acc[7]);
-                        acc[9] = fma_abs2(q3, t, acc[9]);
-                        if (any_gauss(u)) {
-                            const f2_t qg = mul2(gI, ex2neg2(u));
-                            acc[0] = add2(acc[0], qg);
-                            acc[2] = fma2(qg, tA, acc[2]);
-                            acc[4] = fma_abs2(qg, tA, acc[4]);
-                            const f2_t q3g = mul2(qg, t);
-                            acc[6] = fma2(q3g, t, acc[6]);
-                            acc[8] = fma_abs2(q3g, t, acc[8]);
-                        }
-                    }
-                }
-#pragma unroll 1
-                for (int side = 0; side < 2; ++side) {
-                    const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
-                    const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
-                    f2_t S1 = 0ull, A = 0ull, B = 0ull;
-                    for (int m = m0; m < m1; ++m) {
-                        f2_t np, I;
-                        tab.get(m, np, I);
-#pragma unroll
-                        for (int q = 0; q < kPairs; ++q) {
-                            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
-                            const f2_t u = mul2(t, t);
-                            if (any_gauss(u)) {
-                                const f2_t qg = mul2(mul2(g2[q], I), ex2neg2(u));
-                                S1 = add2(S1, qg);
-                                A = fma2(qg, ps(t, q), A);
-                                B = fma2(mul2(qg, t), t, B);
-                            }
-                        }
-                    }
-                    acc[0] = add2(acc[0], S1);
-                    acc[2] = add2(acc[2], A);
-                    acc[6] = add2(acc[6], B);
-                    acc[4] = side ? sub2(acc[4], A) : add2(acc[4], A);
-                    acc[8] = side ? sub2(acc[8], B) : add2(acc[8], B);
-                }
+                bwd_near_sums(tab, r, cp, x2, g2, ps, acc);
                 float v[kGradSums];
 #pragma unroll
                 for (int j = 0; j < kGradSums; ++j) v[j] = warp_sumf(sum2(acc[j]));
@@ -1067,6 +1460,110 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
                         dst[j / 2] = make_float2(o.x + v[j], o.y + v[j + 1]);
                     }
                 }
+            }
+        }
+    }
+}
+
+// Direct backward sums with the far field on: per (sample, tile, phase chunk)
+// and phase, the Lorentzian sums of the side-uniform band [fb, m1), [m2, fe)
+// and the near part (bwd_near_sums), reduced once and written to gpart (the
+// far-field kernel adds its part afterwards).  The band holds a few peaks per
+// phase, so one kernel with the point coordinates and g in registers replaces
+// the dense path's side-uniform + near pair.
+template <bool kWide, bool kSec>
+__global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    __shared__ float4 s_wb[kWarps][32];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    const int lane = threadIdx.x & 31;
+    float4 *wb = s_wb[threadIdx.x >> 5];
+    const f2_t one2 = bc2(1.f);
+    const int items = a.S * a.T * a.C;
+    for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
+        const int c = item % a.C;
+        const int st = item / a.C;
+        const int s = st / a.T, tile = st - s * a.T;
+        const int i0 = tile * kTile;
+        const float xlo = a.x[i0], xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
+        f2_t x2[kPairs], g2[kPairs];
+        item_points(a, i0, lane, x2);
+        PtScale<kSec> ps;
+        ps.load(a, i0, lane);
+        const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
+        const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
+        for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
+            const PhaseConst cp = cs[k];
+            const Ranges r = load_ranges(a, s_off, s, k, tile);
+            float v[kGradSums];
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) v[j] = 0.f;
+            // band: lane-local Lorentzian sums per side (g applied per point at the end)
+            float A[2] = {0.f, 0.f}, B[2] = {0.f, 0.f};
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                const int m0 = side ? r.m2 : r.fb, m1 = side ? r.fe : r.m1;
+                if (m0 >= m1) continue;
+                const float sc = side ? cp.sl : cp.sr, cmu = side ? cp.nslmu : cp.nsrmu, x0 = side ? xhi : xlo;
+                const f2_t s2 = bc2(sc), n0 = bc2(-x0);
+                f2_t dx2[kPairs], S1p[kPairs], Ap[kPairs], C2p[kPairs];
+#pragma unroll
+                for (int q = 0; q < kPairs; ++q) {
+                    dx2[q] = add2(x2[q], n0);
+                    S1p[q] = Ap[q] = C2p[q] = 0ull;
+                }
+                for (int mb = m0; mb < m1; mb += 32) {
+                    const int n = min(32, m1 - mb);
+                    fill_offsets(tab, wb, lane, mb, n, sc, cmu, x0);
+                    for (int j = 0; j < n; ++j) {
+                        const float4 w = wb[j];
+                        const f2_t b = pk2(w.x, w.y), I = pk2(w.z, w.w);
+#pragma unroll
+                        for (int q = 0; q < kPairs; ++q) {
+                            const f2_t t = ps(fma2(s2, dx2[q], b), q);
+                            const f2_t L = rcp2(fma2(t, t, one2));
+                            const f2_t q1 = mul2(I, L);
+                            S1p[q] = add2(S1p[q], q1);
+                            const f2_t q2 = mul2(q1, L);
+                            Ap[q] = fma2(q2, t, Ap[q]);
+                            C2p[q] = add2(C2p[q], q2);
+                        }
+                    }
+                }
+                f2_t S1s = 0ull, As = 0ull, C2s = 0ull;
+#pragma unroll
+                for (int q = 0; q < kPairs; ++q) {
+                    S1s = fma2(g2[q], S1p[q], S1s);
+                    As = fma2(ps(g2[q], q), Ap[q], As);
+                    C2s = fma2(g2[q], C2p[q], C2s);
+                }
+                v[1] += sum2(S1s);
+                A[side] = sum2(As);
+                B[side] = sum2(sub2(S1s, C2s));
+            }
+            // side 0: all d > 0 (|t| = t); side 1: all d < 0 (|t| = -t)
+            v[3] = A[0] + A[1];
+            v[5] = A[0] - A[1];
+            v[7] = B[0] + B[1];
+            v[9] = B[0] - B[1];
+            if (near_work(r)) {   // warp-uniform
+                f2_t acc[kGradSums];
+#pragma unroll
+                for (int j = 0; j < kGradSums; ++j) acc[j] = 0ull;
+                bwd_near_sums(tab, r, cp, x2, g2, ps, acc);
+#pragma unroll
+                for (int j = 0; j < kGradSums; ++j) v[j] += sum2(acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kGradSums; ++j) v[j] = warp_sumf(v[j]);
+            if (lane == 0) {
+                float2 *dst = reinterpret_cast<float2 *>(
+                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
+#pragma unroll
+                for (int j = 0; j < kGradSums; j += 2) dst[j / 2] = make_float2(v[j], v[j + 1]);
             }
         }
     }
@@ -1573,7 +2070,32 @@ void configure_grids(Problem &P, int sm_count) {
     set_smem_attr(k_bwd_uniform<true, true>, smax);
     set_smem_attr(k_bwd_near<false, true>, smax);
     set_smem_attr(k_bwd_near<true, true>, smax);
-    int bf = 1, bb = 1;
+    set_smem_attr(k_bwd_direct<false, false>, smax);
+    set_smem_attr(k_bwd_direct<true, false>, smax);
+    set_smem_attr(k_bwd_direct<false, true>, smax);
+    set_smem_attr(k_bwd_direct<true, true>, smax);
+    set_smem_attr(k_far_fwd<false, false>, smax);
+    set_smem_attr(k_far_fwd<true, false>, smax);
+    set_smem_attr(k_far_fwd<false, true>, smax);
+    set_smem_attr(k_far_fwd<true, true>, smax);
+    set_smem_attr(k_far_bwd<false, false>, smax);
+    set_smem_attr(k_far_bwd<true, false>, smax);
+    set_smem_attr(k_far_bwd<false, true>, smax);
+    set_smem_attr(k_far_bwd<true, true>, smax);
+    int bf = 1, bb = 1, bfar = 1;
+    if (P.wide)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfar, k_far_bwd<true, false>, kThreads, P.smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfar, k_far_bwd<false, false>, kThreads, P.smem);
+    if (bfar < 1) bfar = 1;
+    P.grid_far = bfar * sm_count;
+    int bd = 1;
+    if (P.wide)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_bwd_direct<true, false>, kThreads, P.smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_bwd_direct<false, false>, kThreads, P.smem);
+    if (bd < 1) bd = 1;
+    P.grid_bwd_direct = bd * sm_count;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward<false, false>, kThreads, P.smem_fwd);
     if (P.wide)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_bwd_uniform<true>, kThreads, P.smem);
@@ -1599,6 +2121,11 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     if (P.bgfit) a.bg = P.Bb;   // fitted background: the current curve B(beta)
     a.bgpart = P.bgfit ? W.bgpart : nullptr;
     a.Tb = a.bgpart ? P.Tb : nullptr;   // beta sums only where the sample set keeps them
+    const bool far = P.far && W.franges;
+    a.franges = far ? W.franges : nullptr;
+    a.fnode = far ? W.fnode : nullptr;
+    a.wfar = far ? W.wfar : nullptr;
+    a.node_x = P.node_x; a.node_c = P.node_c; a.lam = P.lam; a.far_order = P.far_order;
     return a;
 }
 
@@ -1665,10 +2192,11 @@ void launch_lik(const Problem &P, Workspace &W, float *f_out, int C, cudaStream_
     k_lik<<<W.S * P.T, kTile, 0, st>>>(a);
 }
 
-void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st) {
+void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cudaStream_t st, cudaEvent_t *marks) {
     ProfArgs a = prof_args(P, W, f_out);
     const int nr = W.S * P.K * P.T;
     k_ranges<<<(nr + 255) / 256 < 4096 ? (nr + 255) / 256 : 4096, 256, 0, st>>>(a);
+    if (marks) cudaEventRecord(marks[0], st);
     // the forward reads the compact table (measured faster than the wide one)
     const int grid = grid_for(P.grid_fwd, W.S * P.T * W.C);
     if (P.sec)   // angle-dependent width (compensated sums)
@@ -1677,34 +2205,69 @@ void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cu
         k_forward<true, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
     else
         k_forward<false, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
+    if (marks) cudaEventRecord(marks[1], st);
+    if (a.fnode) {   // far field at the nodes (k_lik interpolates it)
+        const int gf = grid_for(P.grid_far, W.S * P.T);
+        if (P.sec) {
+            if (P.wide) k_far_fwd<true, true><<<gf, kThreads, P.smem, st>>>(a);
+            else k_far_fwd<false, true><<<gf, kThreads, P.smem, st>>>(a);
+        } else {
+            if (P.wide) k_far_fwd<true, false><<<gf, kThreads, P.smem, st>>>(a);
+            else k_far_fwd<false, false><<<gf, kThreads, P.smem, st>>>(a);
+        }
+    }
+    if (marks) cudaEventRecord(marks[2], st);
     k_lik<<<W.S * P.T, kTile, 0, st>>>(a);
 }
 
-void launch_backward(const Problem &P, Workspace &W, cudaStream_t st) {
+void launch_backward(const Problem &P, Workspace &W, cudaStream_t st, cudaEvent_t *marks) {
     ProfArgs a = prof_args(P, W, nullptr);
     const int grid = grid_for(P.grid_bwd, W.S * P.T * W.C);
     a.counter = W.counters + 2;
-    if (P.sec) {   // angle-dependent width
+    if (a.wfar) {   // far field on: one direct kernel, then the far-field sums
+        const int grid = grid_for(P.grid_bwd_direct, W.S * P.T * W.C);
+        if (P.sec) {
+            if (P.wide) k_bwd_direct<true, true><<<grid, kThreads, P.smem, st>>>(a);
+            else k_bwd_direct<false, true><<<grid, kThreads, P.smem, st>>>(a);
+        } else {
+            if (P.wide) k_bwd_direct<true, false><<<grid, kThreads, P.smem, st>>>(a);
+            else k_bwd_direct<false, false><<<grid, kThreads, P.smem, st>>>(a);
+        }
+        if (marks) cudaEventRecord(marks[0], st);
+    } else if (P.sec) {   // angle-dependent width
         if (P.wide)
             k_bwd_uniform<true, true><<<grid, kThreads, P.smem, st>>>(a);
         else
             k_bwd_uniform<false, true><<<grid, kThreads, P.smem, st>>>(a);
+        if (marks) cudaEventRecord(marks[0], st);
         a.counter = W.counters + 3;
         if (P.wide)
             k_bwd_near<true, true><<<grid, kThreads, P.smem, st>>>(a);
         else
             k_bwd_near<false, true><<<grid, kThreads, P.smem, st>>>(a);
-        return;
+    } else {
+        if (P.wide)
+            k_bwd_uniform<true><<<grid, kThreads, P.smem, st>>>(a);
+        else
+            k_bwd_uniform<false><<<grid, kThreads, P.smem, st>>>(a);
+        if (marks) cudaEventRecord(marks[0], st);
+        a.counter = W.counters + 3;
+        if (P.wide)
+            k_bwd_near<true><<<grid, kThreads, P.smem, st>>>(a);
+        else
+            k_bwd_near<false><<<grid, kThreads, P.smem, st>>>(a);
     }
-    if (P.wide)
-        k_bwd_uniform<true><<<grid, kThreads, P.smem, st>>>(a);
-    else
-        k_bwd_uniform<false><<<grid, kThreads, P.smem, st>>>(a);
-    a.counter = W.counters + 3;
-    if (P.wide)
-        k_bwd_near<true><<<grid, kThreads, P.smem, st>>>(a);
-    else
-        k_bwd_near<false><<<grid, kThreads, P.smem, st>>>(a);
+    if (marks) cudaEventRecord(marks[1], st);
+    if (a.wfar) {   // far-field sums, added after the direct kernels (fixed order)
+        const int gf = grid_for(P.grid_far, W.S * P.T);
+        if (P.sec) {
+            if (P.wide) k_far_bwd<true, true><<<gf, kThreads, P.smem, st>>>(a);
+            else k_far_bwd<false, true><<<gf, kThreads, P.smem, st>>>(a);
+        } else {
+            if (P.wide) k_far_bwd<true, false><<<gf, kThreads, P.smem, st>>>(a);
+            else k_far_bwd<false, false><<<gf, kThreads, P.smem, st>>>(a);
+        }
+    }
 }
 
 void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,

@@ -29,6 +29,7 @@ FLAG_FIX_ALPHA = 1 << 8       # alpha held at fix_alpha_value
 FLAG_DEVICE_PTRS = 1 << 9     # xrdvi_create reads device arrays
 FLAG_AREA_NORM = 1 << 10      # area-normalised profiles (h = integrated intensity)
 FLAG_GATES = 1 << 11          # binary-Concrete phase gates
+FLAG_DENSE = 1 << 12          # every peak evaluated directly (no far-field interpolation)
 
 
 class XrdviError(RuntimeError):
@@ -111,6 +112,7 @@ SIGNATURES = {
     "xrdvi_forward_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "xrdvi_backward_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "xrdvi_profile_steps": (ctypes.c_int, [_vp, _i32, P(_f)]),
+    "xrdvi_profile_kernels": (ctypes.c_int, [_vp, _i32, P(_f), P(ctypes.c_int64)]),
     "xrdvi_elbo_grad_static": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _d, _d,
                                               P(Config), _vp, _vp, _vp, _vp, _vp, _vp]),
     "xrdvi_footprint_bytes": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _i32, _i32]),
@@ -390,6 +392,9 @@ class Context:
     def profile_steps(self, steps):
         return xrdvi_profile_steps(self.h, steps)
 
+    def profile_kernels(self, steps):
+        return xrdvi_profile_kernels(self.h, steps)
+
     def background(self):
         return xrdvi_get_background(self.h)
 
@@ -511,3 +516,17 @@ def xrdvi_get_gates(h):
     g = np.zeros(K, dtype=np.float32)
     _check(lib().xrdvi_get_gates(h, _ptr(a, _f), _ptr(g, _f)))
     return {"logits": a, "grad": g}
+
+
+PROFILE_KERNELS = ("sample", "ranges", "direct", "far_fwd", "lik", "bwd_uniform", "bwd_near", "far_bwd",
+                   "grad_adam", "elbo")
+WORK_COUNTS = ("uniform", "mixed", "gauss_reach", "far_nodes")
+
+
+def xrdvi_profile_kernels(h, steps):
+    """Per-kernel mean ms per step over `steps` fit steps, and the last step's
+    evaluation counts: ({name: ms}, {name: count})."""
+    ms = np.zeros(len(PROFILE_KERNELS), dtype=np.float32)
+    work = np.zeros(len(WORK_COUNTS), dtype=np.int64)
+    _check(lib().xrdvi_profile_kernels(h, steps, _ptr(ms, _f), _ptr(work, ctypes.c_int64)))
+    return ({k: float(v) for k, v in zip(PROFILE_KERNELS, ms)}, {k: int(v) for k, v in zip(WORK_COUNTS, work)})
