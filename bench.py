@@ -466,10 +466,10 @@ def main():
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     executed = work["uniform"] + work["mixed"] + work["gauss_reach"] + work["far_nodes"]
     far_on = work["far_nodes"] > 0
-    # per SVI step: sample, ranges, direct profile, [far field], lik, bwd_uniform, bwd_near,
-    # [far-field backward], grad, elbo; posterior: sample, ranges, direct, [far], lik,
-    # post_sample, post_reduce, post_sort, post_topm
-    launches_per_step = (10 if far_on else 8) * iters + (9 if far_on else 8)
+    # per SVI step: sample, ranges, forward, lik, grad, elbo and either bwd_uniform + bwd_near
+    # (dense) or far_fwd + bwd_direct + far_bwd (far field); posterior: sample, ranges, forward,
+    # [far_fwd], lik, post_sample, post_reduce, post_sort, post_topm
+    launches_per_step = (9 if far_on else 8) * iters + (9 if far_on else 8)
     share = {k: kern[k] / sum(kern.values()) for k in kern}
     kernel_names = {"direct": "k_forward", "far_fwd": "k_far_fwd",
                     "bwd_uniform": "k_bwd_direct" if far_on else "k_bwd_uniform",
