@@ -171,7 +171,7 @@ struct Problem {
     float *beta = nullptr, *m_beta = nullptr, *v_beta = nullptr;   // [3] coefficients, Adam moments
     float *Tb = nullptr;         // [3*N] Chebyshev terms T_j(z_i)
     float *Bb = nullptr;         // [N] B(beta) of the current step
-    int grid_fwd = 0, grid_bwd = 0, grid_far = 0, grid_bwd_direct = 0;
+    int grid_fwd = 0, grid_bwd = 0, grid_far = 0, grid_bwd_direct = 0, grid_fwd_direct = 0;
 };
 
 // --- kernel launchers (xrdvi_kernels.cu) ------------------------------------

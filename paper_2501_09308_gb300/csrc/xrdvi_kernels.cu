@@ -895,6 +895,108 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
     }
 }
 
+// Direct profile with the far field on: per (sample, tile, phase chunk), each
+// phase's near band [fb, m1), [m2, fe) (a few peaks: t = s (x - p) - s mu per
+// evaluation, no staging), its mixed range and its Gaussian reach; the
+// Gaussian of a pair block is skipped when no point of it is within reach.
+// Phase contributions are summed with packed Kahan compensation (all terms
+// are non-negative).
+template <bool kNaive, bool kWide, bool kSec>
+__global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    const int lane = threadIdx.x & 31;
+    const f2_t one2 = bc2(1.f);
+    const int items = a.S * a.T * a.C;
+    for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
+        const int c = item % a.C;
+        const int st = item / a.C;
+        const int s = st / a.T, tile = st - s * a.T;
+        const int i0 = tile * kTile;
+        f2_t x2[kPairs];
+        item_points(a, i0, lane, x2);
+        PtScale<kSec> ps;
+        ps.load(a, i0, lane);
+        f2_t fs[kPairs], fc[kPairs];
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) fs[q] = fc[q] = 0ull;
+        const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
+        for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
+            const PhaseConst cp = cs[k];
+            const Ranges r = load_ranges(a, s_off, s, k, tile);
+            f2_t sl[kPairs], sg[kPairs];
+#pragma unroll
+            for (int q = 0; q < kPairs; ++q) sl[q] = sg[q] = 0ull;
+            // near band, Lorentzian (its Gaussian part is in the reach loops below)
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                const int m0 = side ? r.m2 : r.fb, m1 = side ? r.fe : r.m1;
+                const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
+                for (int m = m0; m < m1; ++m) {
+                    f2_t np, I;
+                    tab.get(m, np, I);
+#pragma unroll
+                    for (int q = 0; q < kPairs; ++q) {
+                        const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
+                        sl[q] = fma2(I, rcp2(fma2(t, t, one2)), sl[q]);
+                    }
+                }
+            }
+            if (near_work(r)) {   // warp-uniform
+                const f2_t nmu2 = bc2(-cp.mu);
+                for (int m = r.m1; m < r.m2; ++m) {
+                    f2_t np, I;
+                    tab.get(m, np, I);
+#pragma unroll
+                    for (int q = 0; q < kPairs; ++q) {
+                        const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
+                        const f2_t u = mul2(t, t);
+                        sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
+                        if (any_gauss(u)) sg[q] = fma2(I, ex2neg2(u), sg[q]);
+                    }
+                }
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const int m0 = side ? r.m2 : min(r.nb, r.m1), m1 = side ? max(r.ne, r.m2) : r.m1;
+                    const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
+                    for (int m = m0; m < m1; ++m) {
+                        f2_t np, I;
+                        tab.get(m, np, I);
+#pragma unroll
+                        for (int q = 0; q < kPairs; ++q) {
+                            const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
+                            const f2_t u = mul2(t, t);
+                            if (any_gauss(u)) sg[q] = fma2(I, ex2neg2(u), sg[q]);
+                        }
+                    }
+                }
+            }
+            const f2_t hl2 = bc2(cp.hl), hg2 = bc2(cp.hg);
+#pragma unroll
+            for (int q = 0; q < kPairs; ++q) {
+                const f2_t v = fma2(hl2, sl[q], mul2(hg2, sg[q]));
+                if (kNaive) {
+                    fs[q] = add2(fs[q], v);
+                } else {   // Kahan: fc holds the rounding error of fs (subtracted at the end)
+                    const f2_t y = sub2(v, fc[q]);
+                    const f2_t t = add2(fs[q], y);
+                    fc[q] = sub2(sub2(t, fs[q]), y);
+                    fs[q] = t;
+                }
+            }
+        }
+        float *dst = a.fpart + (static_cast<size_t>(c) * a.S + s) * a.Npad + i0 + lane;
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            float lo, hi;
+            up2(kNaive ? fs[q] : sub2(fs[q], fc[q]), lo, hi);
+            dst[(2 * q) * 32] = lo;
+            dst[(2 * q + 1) * 32] = hi;
+        }
+    }
+}
+
 // --- far field -------------------------------------------------------------------
 // The Lorentzian tails that reach a tile from peaks beyond kFarGap half-widths
 // of it are analytic on the tile's span, with poles x = rho +- i/s at least
@@ -1471,14 +1573,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_near(ProfArgs a) {
 // far-field kernel adds its part afterwards).  The band holds a few peaks per
 // phase, so one kernel with the point coordinates and g in registers replaces
 // the dense path's side-uniform + near pair.
+// Warp sum of 16 values by recursive halving (8 + 4 + 2 + 1 + 1 shuffles):
+// lane l ends with the total of value (l >> 1) & 15 in v[0].
+__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+    for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+            const float send = up ? v[j] : v[j + n];
+            const float keep = up ? v[j + n] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <bool kWide, bool kSec>
 __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
     extern __shared__ float4 s_raw[];
-    __shared__ float4 s_wb[kWarps][32];
     int *s_off;
     const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
     const int lane = threadIdx.x & 31;
-    float4 *wb = s_wb[threadIdx.x >> 5];
     const f2_t one2 = bc2(1.f);
     const int items = a.S * a.T * a.C;
     for (int item = next_item(a.counter, lane); item < items; item = next_item(a.counter, lane)) {
@@ -1486,7 +1602,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
         const int st = item / a.C;
         const int s = st / a.T, tile = st - s * a.T;
         const int i0 = tile * kTile;
-        const float xlo = a.x[i0], xhi = a.x[min(i0 + kTile - 1, a.N - 1)];
         f2_t x2[kPairs], g2[kPairs];
         item_points(a, i0, lane, x2);
         PtScale<kSec> ps;
@@ -1498,39 +1613,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
         for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
             const PhaseConst cp = cs[k];
             const Ranges r = load_ranges(a, s_off, s, k, tile);
-            float v[kGradSums];
+            float v[16];
 #pragma unroll
-            for (int j = 0; j < kGradSums; ++j) v[j] = 0.f;
-            // band: lane-local Lorentzian sums per side (g applied per point at the end)
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+            // near band: lane-local Lorentzian sums per side (a few peaks; g applied per point at the end)
             float A[2] = {0.f, 0.f}, B[2] = {0.f, 0.f};
 #pragma unroll 1
             for (int side = 0; side < 2; ++side) {
                 const int m0 = side ? r.m2 : r.fb, m1 = side ? r.fe : r.m1;
                 if (m0 >= m1) continue;
-                const float sc = side ? cp.sl : cp.sr, cmu = side ? cp.nslmu : cp.nsrmu, x0 = side ? xhi : xlo;
-                const f2_t s2 = bc2(sc), n0 = bc2(-x0);
-                f2_t dx2[kPairs], S1p[kPairs], Ap[kPairs], C2p[kPairs];
+                const f2_t s2 = bc2(side ? cp.sl : cp.sr), c2 = bc2(side ? cp.nslmu : cp.nsrmu);
+                f2_t S1p[kPairs], Ap[kPairs], C2p[kPairs];
 #pragma unroll
-                for (int q = 0; q < kPairs; ++q) {
-                    dx2[q] = add2(x2[q], n0);
-                    S1p[q] = Ap[q] = C2p[q] = 0ull;
-                }
-                for (int mb = m0; mb < m1; mb += 32) {
-                    const int n = min(32, m1 - mb);
-                    fill_offsets(tab, wb, lane, mb, n, sc, cmu, x0);
-                    for (int j = 0; j < n; ++j) {
-                        const float4 w = wb[j];
-                        const f2_t b = pk2(w.x, w.y), I = pk2(w.z, w.w);
+                for (int q = 0; q < kPairs; ++q) S1p[q] = Ap[q] = C2p[q] = 0ull;
+                for (int m = m0; m < m1; ++m) {
+                    f2_t np, I;
+                    tab.get(m, np, I);
 #pragma unroll
-                        for (int q = 0; q < kPairs; ++q) {
-                            const f2_t t = ps(fma2(s2, dx2[q], b), q);
-                            const f2_t L = rcp2(fma2(t, t, one2));
-                            const f2_t q1 = mul2(I, L);
-                            S1p[q] = add2(S1p[q], q1);
-                            const f2_t q2 = mul2(q1, L);
-                            Ap[q] = fma2(q2, t, Ap[q]);
-                            C2p[q] = add2(C2p[q], q2);
-                        }
+                    for (int q = 0; q < kPairs; ++q) {
+                        const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
+                        const f2_t L = rcp2(fma2(t, t, one2));
+                        const f2_t q1 = mul2(I, L);
+                        S1p[q] = add2(S1p[q], q1);
+                        const f2_t q2 = mul2(q1, L);
+                        Ap[q] = fma2(q2, t, Ap[q]);
+                        C2p[q] = add2(C2p[q], q2);
                     }
                 }
                 f2_t S1s = 0ull, As = 0ull, C2s = 0ull;
@@ -1557,14 +1664,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
 #pragma unroll
                 for (int j = 0; j < kGradSums; ++j) v[j] += sum2(acc[j]);
             }
-#pragma unroll
-            for (int j = 0; j < kGradSums; ++j) v[j] = warp_sumf(v[j]);
-            if (lane == 0) {
-                float2 *dst = reinterpret_cast<float2 *>(
-                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
-#pragma unroll
-                for (int j = 0; j < kGradSums; j += 2) dst[j / 2] = make_float2(v[j], v[j + 1]);
-            }
+            warp_reduce_scatter16(v, lane);
+            const int j = (lane >> 1) & 15;
+            if ((lane & 1) == 0 && j < kGradSums)
+                a.gpart[((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums + j] = v[0];
         }
     }
 }
@@ -2070,6 +2173,12 @@ void configure_grids(Problem &P, int sm_count) {
     set_smem_attr(k_bwd_uniform<true, true>, smax);
     set_smem_attr(k_bwd_near<false, true>, smax);
     set_smem_attr(k_bwd_near<true, true>, smax);
+    set_smem_attr(k_fwd_direct<false, false, false>, smax);
+    set_smem_attr(k_fwd_direct<false, true, false>, smax);
+    set_smem_attr(k_fwd_direct<true, false, false>, smax);
+    set_smem_attr(k_fwd_direct<true, true, false>, smax);
+    set_smem_attr(k_fwd_direct<false, false, true>, smax);
+    set_smem_attr(k_fwd_direct<false, true, true>, smax);
     set_smem_attr(k_bwd_direct<false, false>, smax);
     set_smem_attr(k_bwd_direct<true, false>, smax);
     set_smem_attr(k_bwd_direct<false, true>, smax);
@@ -2096,6 +2205,13 @@ void configure_grids(Problem &P, int sm_count) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_bwd_direct<false, false>, kThreads, P.smem);
     if (bd < 1) bd = 1;
     P.grid_bwd_direct = bd * sm_count;
+    int bfd = 1;
+    if (P.wide)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfd, k_fwd_direct<false, true, false>, kThreads, P.smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfd, k_fwd_direct<false, false, false>, kThreads, P.smem);
+    if (bfd < 1) bfd = 1;
+    P.grid_fwd_direct = bfd * sm_count;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward<false, false>, kThreads, P.smem_fwd);
     if (P.wide)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_bwd_uniform<true>, kThreads, P.smem);
@@ -2199,12 +2315,25 @@ void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cu
     if (marks) cudaEventRecord(marks[0], st);
     // the forward reads the compact table (measured faster than the wide one)
     const int grid = grid_for(P.grid_fwd, W.S * P.T * W.C);
-    if (P.sec)   // angle-dependent width (compensated sums)
+    if (a.fnode) {   // far field on: the direct part only (peak table as the backward's)
+        const int gd = grid_for(P.grid_fwd_direct, W.S * P.T * W.C);
+        if (P.sec) {
+            if (P.wide) k_fwd_direct<false, true, true><<<gd, kThreads, P.smem, st>>>(a);
+            else k_fwd_direct<false, false, true><<<gd, kThreads, P.smem, st>>>(a);
+        } else if (naive) {
+            if (P.wide) k_fwd_direct<true, true, false><<<gd, kThreads, P.smem, st>>>(a);
+            else k_fwd_direct<true, false, false><<<gd, kThreads, P.smem, st>>>(a);
+        } else {
+            if (P.wide) k_fwd_direct<false, true, false><<<gd, kThreads, P.smem, st>>>(a);
+            else k_fwd_direct<false, false, false><<<gd, kThreads, P.smem, st>>>(a);
+        }
+    } else if (P.sec) {   // angle-dependent width (compensated sums)
         k_forward<false, false, true><<<grid, kThreads, P.smem_fwd, st>>>(a);
-    else if (naive)
+    } else if (naive) {
         k_forward<true, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
-    else
+    } else {
         k_forward<false, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
+    }
     if (marks) cudaEventRecord(marks[1], st);
     if (a.fnode) {   // far field at the nodes (k_lik interpolates it)
         const int gf = grid_for(P.grid_far, W.S * P.T);
