@@ -451,9 +451,10 @@ def main():
     fp32_peak = sms * 128 * clock_mhz * 1e6 / 1e12   # FP32 lane operations per second (Top/s)
     mufu_peak = sms * MUFU_LANES * clock_mhz * 1e6 / 1e12
     ops_table = dict(OPS)
-    if work["far_nodes"] > 0:   # far field on: one direct backward kernel (timed as bwd_uniform)
-        ops_table["bwd_uniform"] = {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1)}
-        del ops_table["bwd_near"]
+    if work["far_nodes"] > 0:   # far field on: node evaluations inside the two direct kernels
+        ops_table = {"direct": dict(OPS["direct"], far_nodes=OPS["far_fwd"]["far_nodes"]),
+                     "bwd_uniform": {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1),
+                                     "far_nodes": OPS["far_bwd"]["far_nodes"]}}
     per_kernel = {}
     for name, kinds in ops_table.items():
         if kern[name] <= 1e-4:
@@ -467,13 +468,13 @@ def main():
     executed = work["uniform"] + work["mixed"] + work["gauss_reach"] + work["far_nodes"]
     far_on = work["far_nodes"] > 0
     # per SVI step: sample, ranges, forward, lik, grad, elbo and either bwd_uniform + bwd_near
-    # (dense) or far_fwd + bwd_direct + far_bwd (far field); posterior: sample, ranges, forward,
-    # [far_fwd], lik, post_sample, post_reduce, post_sort, post_topm
-    launches_per_step = (9 if far_on else 8) * iters + (9 if far_on else 8)
+    # (dense) or bwd_direct (far field); posterior: sample, ranges, forward, lik, post_sample,
+    # post_reduce, post_sort, post_topm
+    launches_per_step = (7 if far_on else 8) * iters + 8
     share = {k: kern[k] / sum(kern.values()) for k in kern}
-    kernel_names = {"direct": "k_forward", "far_fwd": "k_far_fwd",
+    kernel_names = {"direct": "k_fwd_direct" if far_on else "k_forward",
                     "bwd_uniform": "k_bwd_direct" if far_on else "k_bwd_uniform",
-                    "bwd_near": "k_bwd_near", "far_bwd": "k_far_bwd"}
+                    "bwd_near": "k_bwd_near"}
     out = {
         "metric": METRIC,
         "value": value,

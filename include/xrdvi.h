@@ -269,11 +269,12 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms
 
 /* Per-kernel form of xrdvi_profile_steps (the same fit steps): kernel_ms
  * [XRDVI_PROFILE_KERNELS] receives the mean duration per step (ms) of
- *   0 sampling, 1 peak ranges, 2 direct profile, 3 far field at the nodes,
- *   4 likelihood (with the far-field interpolation), 5 backward direct sums
- *   (the side-uniform ranges only with XRDVI_FLAG_DENSE), 6 backward near
- *   sums (XRDVI_FLAG_DENSE; else ~0), 7 backward far-field sums, 8 gradient
- *   reduction + Adam, 9 ELBO
+ *   0 sampling, 1 peak ranges, 2 profile (with the far-field node sums),
+ *   3 reserved (~0), 4 likelihood (with the far-field interpolation),
+ *   5 backward sums (with the far field at the nodes; the side-uniform
+ *   ranges only with XRDVI_FLAG_DENSE), 6 backward near sums
+ *   (XRDVI_FLAG_DENSE; else ~0), 7 reserved (~0), 8 gradient reduction +
+ *   Adam, 9 ELBO
  * (a kernel the configuration does not launch reads ~0; the shared-shape
  * variant's contractions count as 2 and 5).  work (NULL or [4], HOST)
  * receives the last step's evaluation counts, (peak, point) pairs over all

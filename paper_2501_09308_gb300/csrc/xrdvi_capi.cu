@@ -198,6 +198,70 @@ void far_tables(const float *x, int N, int T, bool sec, std::vector<float> &nx, 
     }
 }
 
+// Second far-field level: kFarNodes Chebyshev nodes on each super-tile's span
+// (kSuperTiles tiles), the distance beyond it from which a peak is super-far
+// (above every member tile's far gap, with a margin against rounding), and
+// the super-level Lagrange weights at every tile's (FP32) nodes, as
+// Mf[(t, P, p)] and Mb[(t, p, P)].
+void far_tables2(const float *x, int N, int T, bool sec, const std::vector<float> &nx, std::vector<float> &nx2,
+                 std::vector<float> &nc2, std::vector<float> &sgap, std::vector<float> &Mf, std::vector<float> &Mb) {
+    const int n = kFarNodes, Tg = (T + kSuperTiles - 1) / kSuperTiles;
+    nx2.assign(static_cast<size_t>(Tg) * n, 0.f);
+    if (sec) nc2.assign(static_cast<size_t>(Tg) * n, 0.f);
+    sgap.assign(Tg, 0.f);
+    Mf.assign(static_cast<size_t>(T) * n * n, 0.f);
+    Mb.assign(static_cast<size_t>(T) * n * n, 0.f);
+    std::vector<double> z(n), bw(n), term(n);
+    for (int g = 0; g < Tg; ++g) {
+        const int i0 = g * kSuperTiles * kTile, i1 = std::min(i0 + kSuperTiles * kTile, N) - 1;
+        const double lo = x[i0], hi = x[i1], c = 0.5 * (lo + hi), H = 0.5 * (hi - lo);
+        double hmax = 0.0;
+        for (int t = g * kSuperTiles; t < std::min((g + 1) * kSuperTiles, T); ++t) {
+            const double tl = x[t * kTile], th = x[std::min(t * kTile + kTile, N) - 1];
+            hmax = std::max(hmax, 0.5 * (th - tl));
+        }
+        sgap[g] = static_cast<float>(1.02 * std::max(0.5 * H, static_cast<double>(kFarGap) * hmax) + 2e-4);
+        for (int p = 0; p < n; ++p) {
+            const float xp = static_cast<float>(c + H * std::cos(M_PI * (2 * p + 1) / (2.0 * n)));
+            nx2[static_cast<size_t>(g) * n + p] = xp;
+            if (sec)
+                nc2[static_cast<size_t>(g) * n + p] = static_cast<float>(std::cos(static_cast<double>(xp) * M_PI / 360.0));
+            z[p] = H > 0.0 ? (static_cast<double>(xp) - c) / H : 0.0;
+        }
+        double wmax = 0.0;
+        for (int p = 0; p < n; ++p) {
+            double prod = 1.0;
+            for (int q = 0; q < n; ++q)
+                if (q != p) prod *= z[p] - z[q];
+            bw[p] = 1.0 / prod;
+            wmax = std::max(wmax, std::fabs(bw[p]));
+        }
+        for (int p = 0; p < n; ++p) bw[p] /= wmax;
+        for (int t = g * kSuperTiles; t < std::min((g + 1) * kSuperTiles, T); ++t) {
+            for (int q = 0; q < n; ++q) {   // tile node q
+                double w[kFarNodes];
+                if (!(H > 0.0)) {
+                    for (int P = 0; P < n; ++P) w[P] = 1.0 / n;
+                } else {
+                    const double zi = (static_cast<double>(nx[static_cast<size_t>(t) * n + q]) - c) / H;
+                    int hit = -1;
+                    double den = 0.0;
+                    for (int P = 0; P < n && hit < 0; ++P) {
+                        const double d = zi - z[P];
+                        if (d == 0.0) hit = P;
+                        else den += (term[P] = bw[P] / d);
+                    }
+                    for (int P = 0; P < n; ++P) w[P] = hit >= 0 ? (P == hit ? 1.0 : 0.0) : term[P] / den;
+                }
+                for (int P = 0; P < n; ++P) {
+                    Mf[(static_cast<size_t>(t) * n + P) * n + q] = static_cast<float>(w[P]);
+                    Mb[(static_cast<size_t>(t) * n + q) * n + P] = static_cast<float>(w[P]);
+                }
+            }
+        }
+    }
+}
+
 xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
                              std::vector<void *> *list) {
     const Problem &P = c->P;
@@ -227,14 +291,18 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
         W.gpart = nullptr;
     }
     if (P.gates) XR_TRY(c->alloc(&W.gzy, SK * 2, list));
-    if (P.far) {   // far field: range ends, node sums, node weights of g
+    if (P.far) {   // far field: range ends, node weights of g (node sums below, sized with fpart)
         XR_TRY(c->alloc(&W.franges, SK * P.T, list));
-        XR_TRY(c->alloc(&W.fnode, static_cast<size_t>(S) * P.T * kFarNodes, list));
+        if (P.Tg) XR_TRY(c->alloc(&W.sranges, SK * P.Tg, list));
         if (fit) XR_TRY(c->alloc(&W.wfar, static_cast<size_t>(S) * P.T * kFarNodes, list));
     }
     choose_chunks(P, c->host_off.data(), S, W);
     W.fpart_cap = static_cast<size_t>(W.C) * S * P.Npad;
     XR_TRY(c->alloc(&W.fpart, W.fpart_cap, list));
+    if (P.far) {   // per-chunk node sums: kFarNodes per kTile points, so any chunk count fpart holds fits
+        XR_TRY(c->alloc(&W.fnode, W.fpart_cap / kTile * kFarNodes, list));
+        if (P.Tg) XR_TRY(c->alloc(&W.fnode2, W.fpart_cap / kTile * kFarNodes, list));
+    }
     XR_TRY(c->alloc(&W.ranges, SK * P.T, list));
     XR_TRY(c->alloc(&W.counters, kCounters, list));
     W.bytes = c->bytes - before;
@@ -593,8 +661,18 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     P.far = !(cfg->flags & (XRDVI_FLAG_SHARED_SHAPES | XRDVI_FLAG_DENSE)) &&
             static_cast<size_t>(P.T) * kFarNodes * kTile * sizeof(float) <= kFarMaxLamBytes;
     std::vector<int> far_order(K);
+    std::vector<float> nodex2, nodec2, sgaph, Mfh, Mbh;
     if (P.far) {
         far_tables(pt->x_deg, N, P.T, sec, nodex, nodec, lamh);
+        if (P.T > kSuperTiles) {   // second level (with up to kSuperTiles tiles it would add nothing)
+            far_tables2(pt->x_deg, N, P.T, sec, nodex, nodex2, nodec2, sgaph, Mfh, Mbh);
+            P.Tg = (P.T + kSuperTiles - 1) / kSuperTiles;
+            XR_C(c->alloc(&P.node_x2, nodex2.size()));
+            if (sec) XR_C(c->alloc(&P.node_c2, nodec2.size()));
+            XR_C(c->alloc(&P.sgap, sgaph.size()));
+            XR_C(c->alloc(&P.Mf, Mfh.size()));
+            XR_C(c->alloc(&P.Mb, Mbh.size()));
+        }
         XR_C(c->alloc(&P.node_x, nodex.size()));
         XR_C(c->alloc(&P.lam, lamh.size()));
         if (sec) XR_C(c->alloc(&P.node_c, nodec.size()));
@@ -682,6 +760,9 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
                      cudaMemsetAsync(P.v_gate, 0, K * 4, s) || cudaMemsetAsync(P.grad_gate, 0, K * 4, s))) ||
         (P.far && (up(P.node_x, nodex.data(), nodex.size() * 4) || up(P.lam, lamh.data(), lamh.size() * 4) ||
                    up(P.far_order, far_order.data(), static_cast<size_t>(K) * 4) ||
+                   (P.Tg && (up(P.node_x2, nodex2.data(), nodex2.size() * 4) || up(P.sgap, sgaph.data(), sgaph.size() * 4) ||
+                             up(P.Mf, Mfh.data(), Mfh.size() * 4) || up(P.Mb, Mbh.data(), Mbh.size() * 4) ||
+                             (sec && up(P.node_c2, nodec2.data(), nodec2.size() * 4)))) ||
                    (sec && up(P.node_c, nodec.data(), nodec.size() * 4)))) ||
         (P.bgfit && (up(P.Tb, Tb.data(), Tb.size() * 4) || cudaMemsetAsync(P.beta, 0, 12, s) ||
                      cudaMemsetAsync(P.m_beta, 0, 12, s) || cudaMemsetAsync(P.v_beta, 0, 12, s) ||
@@ -960,8 +1041,11 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms
             const size_t nr = static_cast<size_t>(W.S) * P.K * P.T;
             std::vector<ushort4> rg(nr);
             std::vector<ushort2> fr(P.far ? nr : 0);
+            const size_t ng = static_cast<size_t>(W.S) * P.K * P.Tg;
+            std::vector<ushort2> sr(ng);
             XR_CUDA(cudaMemcpyAsync(rg.data(), W.ranges, nr * sizeof(ushort4), cudaMemcpyDeviceToHost, st));
             if (P.far) XR_CUDA(cudaMemcpyAsync(fr.data(), W.franges, nr * sizeof(ushort2), cudaMemcpyDeviceToHost, st));
+            if (ng) XR_CUDA(cudaMemcpyAsync(sr.data(), W.sranges, ng * sizeof(ushort2), cudaMemcpyDeviceToHost, st));
             XR_CUDA(cudaStreamSynchronize(st));
             for (size_t id = 0; id < nr; ++id) {
                 const ushort4 r = rg[id];
@@ -973,7 +1057,12 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms
                 work[0] += ((m1 - fb) + (fe - m2)) * kTile;
                 work[1] += (m2 - m1) * kTile;
                 work[2] += ((m1 - std::min(nb, m1)) + (std::max(ne, m2) - m2)) * kTile;
-                work[3] += (fb + (me - fe)) * kFarNodes;
+                // far (peak, node) pairs: level 1 at the tile's nodes, level 2 once per super-tile
+                const int tile = static_cast<int>(id % P.T);
+                const size_t gid = (id / P.T) * P.Tg + tile / kSuperTiles;
+                const int64_t sfb = ng ? sr[gid].x : 0, sfe = ng ? sr[gid].y : me;
+                work[3] += ((fb - sfb) + (sfe - fe)) * kFarNodes;
+                if (ng && tile % kSuperTiles == 0) work[3] += (sfb + (me - sfe)) * kFarNodes;
             }
         }
     }

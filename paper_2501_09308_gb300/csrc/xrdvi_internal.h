@@ -31,6 +31,10 @@ constexpr int kGredVals = 11;      // per-(phase, sample block) gradient partial
 // kFarNodes Chebyshev nodes of the tile's span and interpolated at its points.
 constexpr int kFarNodes = 32;
 constexpr float kFarGap = 0.5f;
+// Second far-field level: super-tiles of kSuperTiles tiles with their own
+// kFarNodes nodes take the peaks far beyond the super-tile; their node sums
+// are translated to (forward) and from (backward) the tiles' nodes.
+constexpr int kSuperTiles = 4;
 // Largest interpolation table (kFarNodes weights per point) the far field uses.
 constexpr size_t kFarMaxLamBytes = static_cast<size_t>(64) << 20;
 // Work counters of the profile kernels of one sample set.
@@ -99,7 +103,9 @@ struct Workspace {
     float *fpart = nullptr;      // [C*S*Npad] partial profiles per phase chunk
     ushort4 *ranges = nullptr;   // [S*K*T] peak index ranges per (sample, phase, tile)
     ushort2 *franges = nullptr;  // [S*K*T] end of the far peaks below / start of those above (far field)
-    float *fnode = nullptr;      // [S*T*kFarNodes] far-field profile at the tile's nodes
+    ushort2 *sranges = nullptr;  // [S*K*Tg] the same for the super-tiles' far peaks
+    float *fnode = nullptr;      // [kMaxChunks*S*T*kFarNodes] far-field node sums of each phase chunk
+    float *fnode2 = nullptr;     // [kMaxChunks*S*Tg*kFarNodes] the same at the super-tiles' nodes
     float *wfar = nullptr;       // [S*T*kFarNodes] sum_i g_i lam_p(x_i) per tile (fit only)
     int *counters = nullptr;     // [kCounters] work counters of the profile kernels
     double *gred = nullptr;      // [K*kGradBlocks*10] gradient partials per sample block (fit only)
@@ -154,6 +160,12 @@ struct Problem {
     float *node_c = nullptr;     // [T*kFarNodes] cos(x/2) at the nodes (angle-dependent width)
     float *lam = nullptr;        // [T*kFarNodes*kTile] Lagrange weights lam_p(x_i) of the tile's points
     int *far_order = nullptr;    // [K] phases by decreasing peak count (far-field work balance)
+    int Tg = 0;                  // super-tiles (second far-field level; 0: one level)
+    float *node_x2 = nullptr;    // [Tg*kFarNodes] nodes of each super-tile's span
+    float *node_c2 = nullptr;    // [Tg*kFarNodes] cos(x/2) there (angle-dependent width)
+    float *sgap = nullptr;       // [Tg] distance beyond a super-tile from which a peak is super-far
+    float *Mf = nullptr;         // [T*kFarNodes*kFarNodes] Mf[(t, P, p)] = super-level weight of node P at tile node p
+    float *Mb = nullptr;         // [T*kFarNodes*kFarNodes] the same as Mb[(t, p, P)]
     bool gauss = false;          // Gaussian likelihood variant (variance max(y, 1))
     bool fix_r = false, fix_alpha = false;   // r / alpha held at r_value / alpha_value
     bool area_norm = false;      // area-normalised profiles (h = integrated intensity)
@@ -171,7 +183,7 @@ struct Problem {
     float *beta = nullptr, *m_beta = nullptr, *v_beta = nullptr;   // [3] coefficients, Adam moments
     float *Tb = nullptr;         // [3*N] Chebyshev terms T_j(z_i)
     float *Bb = nullptr;         // [N] B(beta) of the current step
-    int grid_fwd = 0, grid_bwd = 0, grid_far = 0, grid_bwd_direct = 0, grid_fwd_direct = 0;
+    int grid_fwd = 0, grid_bwd = 0, grid_bwd_direct = 0, grid_fwd_direct = 0;
 };
 
 // --- kernel launchers (xrdvi_kernels.cu) ------------------------------------

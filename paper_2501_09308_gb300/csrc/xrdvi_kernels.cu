@@ -400,10 +400,15 @@ struct ProfArgs {
     float *bgpart;     // [S*T*3] per-(sample, tile) sums of g B(beta) T_j
     // far field (null: every peak evaluated at every point)
     ushort2 *franges;  // [S*K*T] (fb, fe) relative to the phase's first peak
-    float *fnode;      // [S*T*kFarNodes] far-field profile at the nodes
+    float *fnode;      // [C*S*T*kFarNodes] far-field profile at the tile nodes per phase chunk
     float *wfar;       // [S*T*kFarNodes] node weights of g (null: not needed)
     const float *node_x, *node_c, *lam;
     const int *far_order;   // [K] phases by decreasing peak count
+    // second far-field level (Tg = 0: none)
+    int Tg;
+    ushort2 *sranges;  // [S*K*Tg] super-far ends relative to the phase's first peak
+    float *fnode2;     // [C*S*Tg*kFarNodes] super-level node sums per phase chunk
+    const float *node_x2, *node_c2, *sgap, *Mf, *Mb;
 };
 
 typedef unsigned long long f2_t;   // two packed floats
@@ -514,6 +519,19 @@ __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
             const int fb = min(min(first_beyond<true>(a.pos, mb, m1, xlo - c.mu - gap), nb), m1);
             const int fe = max(max(first_beyond<false>(a.pos, m2, me, xhi - c.mu + gap), ne), m2);
             a.franges[idx] = make_ushort2(static_cast<unsigned short>(fb - mb), static_cast<unsigned short>(fe - mb));
+            if (a.sranges && tile % kSuperTiles == 0) {
+                // super-far peaks: beyond the super-tile by sgap (which exceeds
+                // every member tile's far gap) and beyond the Gaussian reach, so
+                // they are far for every tile of it
+                const int g = tile / kSuperTiles;
+                const float slo = a.x[g * kSuperTiles * kTile];
+                const float shi = a.x[min((g + 1) * kSuperTiles * kTile - 1, a.N - 1)];
+                const float sg = a.sgap[g];
+                const int sfb = first_beyond<true>(a.pos, mb, fb, slo - c.mu - fmaxf(sg, c.rr));
+                const int sfe = first_beyond<false>(a.pos, fe, me, shi - c.mu + fmaxf(sg, c.rl));
+                a.sranges[(idx / a.T) * a.Tg + g] =
+                    make_ushort2(static_cast<unsigned short>(sfb - mb), static_cast<unsigned short>(sfe - mb));
+            }
         }
     }
 }
@@ -601,66 +619,6 @@ __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_of
         const ushort2 f = a.franges[id];
         o.fb = o.mb + f.x;
         o.fe = o.mb + f.y;
-    } else {
-        o.fb = o.mb;
-        o.fe = o.me;
-    }
-    return o;
-}
-
-// A warp's copy of the per-phase data of up to 32 phases.  The far-field
-// kernels visit a sample's phases one after another; staging them
-// lane-parallel in shared memory takes the dependent global loads (ranges,
-// constants) off that loop.
-struct __align__(16) Staged {
-    float mu, hl, hg, sl, sr, nslmu, nsrmu;
-    int k;
-    ushort4 r;
-    ushort2 f;
-    int pad;
-};
-
-// Stages phases order[j] (order null: j) for j in [j0, min(j0 + 32, j1)).
-__device__ __forceinline__ void stage_phases(const ProfArgs &a, Staged *buf, int s, int tile, const int *order,
-                                             int j0, int j1, int lane) {
-    __syncwarp();   // the previous batch's reads are done
-    const int j = j0 + lane;
-    if (j < j1) {
-        const int k = order ? order[j] : j;
-        const size_t id = (static_cast<size_t>(s) * a.K + k) * a.T + tile;
-        const PhaseConst *c = a.cst + static_cast<size_t>(s) * a.K + k;
-        Staged st;
-        st.mu = c->mu;
-        st.hl = c->hl;
-        st.hg = c->hg;
-        st.sl = c->sl;
-        st.sr = c->sr;
-        st.nslmu = c->nslmu;
-        st.nsrmu = c->nsrmu;
-        st.k = k;
-        st.r = a.ranges[id];
-        st.f = a.franges ? a.franges[id] : make_ushort2(0, 0);
-        st.pad = 0;
-        buf[lane] = st;
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ Ranges staged_ranges(const ProfArgs &a, const int *s_off, const Staged &st) {
-    Ranges o;
-    o.mb = s_off[st.k];
-    if (st.r.x == kAbsentRange) {
-        o.me = o.m1 = o.m2 = o.nb = o.ne = o.fb = o.fe = o.mb;
-        return o;
-    }
-    o.me = s_off[st.k + 1];
-    o.m1 = o.mb + st.r.x;
-    o.m2 = o.mb + st.r.y;
-    o.nb = o.mb + st.r.z;
-    o.ne = o.mb + st.r.w;
-    if (a.franges) {
-        o.fb = o.mb + st.f.x;
-        o.fe = o.mb + st.f.y;
     } else {
         o.fb = o.mb;
         o.fe = o.me;
@@ -895,12 +853,106 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
     }
 }
 
-// Direct profile with the far field on: per (sample, tile, phase chunk), each
+// --- far field -------------------------------------------------------------------
+// The Lorentzian tails that reach a tile from peaks beyond kFarGap half-widths
+// of it are analytic on the tile's span, with poles x = rho +- i/s at least
+// 1.5 half-widths from its centre.  Their sums are therefore evaluated at
+// kFarNodes Chebyshev nodes of the first kind of the span (Trefethen,
+// "Approximation Theory and Approximation Practice", ch. 8 bounds the
+// interpolation error by a power of the Bernstein-ellipse parameter; for
+// these poles it is below 1e-8 of the tail, under FP32 rounding) and
+// interpolated at the tile's points with Lagrange weights lam_p(x_i):
+//   forward   f_far(x_i) = sum_p lam_p(x_i) F_p          (in k_lik)
+//   backward  sum_i g_i phi(x_i) = sum_p W_p phi(x_p),  W_p = sum_i g_i lam_p(x_i).
+// A second level does the same on super-tiles of kSuperTiles tiles for the
+// peaks far beyond the super-tile.  The node evaluations run inside the
+// direct kernels, lane p taking node p, in the same loop over phases.
+
+// One phase's far Lorentzian sum at this lane's node x: sum_m I_m L(t_m(x))
+// over [lo0, hi0) (peaks below, scale sr) and [lo1, hi1) (peaks above, sl).
+template <class Tab, class PC, bool kSec>
+__device__ __forceinline__ float far_node_sum(const Tab &tab, const PC &cp, float x, float cx, int lo0, int hi0,
+                                              int lo1, int hi1) {
+    float acc = 0.f;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int m0 = side ? lo1 : lo0, m1 = side ? hi1 : hi0;
+        const float sc = side ? cp.sl : cp.sr, cm = side ? cp.nslmu : cp.nsrmu;
+        for (int m = m0; m < m1; ++m) {
+            float np, I;
+            tab.scalar(m, np, I);
+            float t = fmaf(sc, x + np, cm);
+            if (kSec) t *= cx;
+            acc = fmaf(I, rcp_approx(fmaf(t, t, 1.f)), acc);
+        }
+    }
+    return acc;
+}
+
+// One phase's far gradient sums at this lane's node (weight w, w cos(x/2) for
+// the mu sums): adds w sum I L to S1 and, per side, w c sum I L^2 t to A and
+// w (sum I L - sum I L^2) to B.
+template <class Tab, class PC, bool kSec>
+__device__ __forceinline__ void far_node_grad(const Tab &tab, const PC &cp, float x, float cx, float w, float wa,
+                                              int lo0, int hi0, int lo1, int hi1, float &S1, float (&A)[2],
+                                              float (&B)[2]) {
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int m0 = side ? lo1 : lo0, m1 = side ? hi1 : hi0;
+        if (m0 >= m1) continue;
+        const float sc = side ? cp.sl : cp.sr, cm = side ? cp.nslmu : cp.nsrmu;
+        float s1 = 0.f, an = 0.f, c2 = 0.f;
+        for (int m = m0; m < m1; ++m) {
+            float np, I;
+            tab.scalar(m, np, I);
+            float t = fmaf(sc, x + np, cm);
+            if (kSec) t *= cx;
+            const float L = rcp_approx(fmaf(t, t, 1.f));
+            const float q1 = I * L;
+            s1 += q1;
+            const float q2 = q1 * L;
+            an = fmaf(q2, t, an);
+            c2 += q2;
+        }
+        S1 = fmaf(w, s1, S1);
+        if (side) {
+            A[1] = fmaf(wa, an, A[1]);
+            B[1] = fmaf(w, s1 - c2, B[1]);
+        } else {
+            A[0] = fmaf(wa, an, A[0]);
+            B[0] = fmaf(w, s1 - c2, B[0]);
+        }
+    }
+}
+
+// Far peaks of one (sample, phase, tile): level 1 (the tile's nodes) [lo0,
+// hi0) below and [lo1, hi1) above the tile without the super-far ones; level
+// 2 (the super-tile's nodes) the super-far ones.
+struct FarRanges {
+    int l1[4], l2[4];
+};
+__device__ __forceinline__ FarRanges far_ranges(const ProfArgs &a, const Ranges &r, int s, int k, int tile) {
+    FarRanges f;
+    int sfb = r.mb, sfe = r.me;
+    if (a.sranges && r.me > r.mb) {
+        const ushort2 sr = a.sranges[(static_cast<size_t>(s) * a.K + k) * a.Tg + tile / kSuperTiles];
+        sfb = r.mb + sr.x;
+        sfe = r.mb + sr.y;
+    }
+    f.l1[0] = sfb; f.l1[1] = r.fb; f.l1[2] = r.fe; f.l1[3] = sfe;
+    f.l2[0] = r.mb; f.l2[1] = sfb; f.l2[2] = sfe; f.l2[3] = r.me;
+    return f;
+}
+
+// Profile with the far field on: per (sample, tile, phase chunk), each
 // phase's near band [fb, m1), [m2, fe) (a few peaks: t = s (x - p) - s mu per
-// evaluation, no staging), its mixed range and its Gaussian reach; the
-// Gaussian of a pair block is skipped when no point of it is within reach.
-// Phase contributions are summed with packed Kahan compensation (all terms
-// are non-negative).
+// evaluation), its mixed range and its Gaussian reach at the tile's points;
+// the Gaussian of a pair block is skipped when no point of it is within
+// reach.  Phase contributions are summed with packed Kahan compensation (all
+// terms are non-negative).  Lane p also sums the phase's far peaks at node p
+// of the tile (and, for a super-tile's first tile, its super-far peaks at node
+// p of the super-tile), Kahan-compensated over the phases, into the chunk's
+// node partials fnode (fnode2), which k_lik combines and interpolates.
 template <bool kNaive, bool kWide, bool kSec>
 __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
     extern __shared__ float4 s_raw[];
@@ -921,10 +973,33 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
         f2_t fs[kPairs], fc[kPairs];
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) fs[q] = fc[q] = 0ull;
+        // far field: this lane's node of the tile (and of the super-tile)
+        const bool lvl2 = a.Tg && tile % kSuperTiles == 0;
+        const int g = tile / kSuperTiles;
+        const float xn = a.node_x[tile * kFarNodes + lane];
+        const float xn2 = lvl2 ? a.node_x2[g * kFarNodes + lane] : 0.f;
+        const float cn = kSec ? a.node_c[tile * kFarNodes + lane] : 1.f;
+        const float cn2 = kSec && lvl2 ? a.node_c2[g * kFarNodes + lane] : 1.f;
+        float F = 0.f, Fc = 0.f, F2 = 0.f, F2c = 0.f;
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
         for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
             const PhaseConst cp = cs[k];
             const Ranges r = load_ranges(a, s_off, s, k, tile);
+            {   // far peaks at the nodes
+                const FarRanges fr = far_ranges(a, r, s, k, tile);
+                const float v = cp.hl * far_node_sum<PeakTable<kWide>, PhaseConst, kSec>(
+                                            tab, cp, xn, cn, fr.l1[0], fr.l1[1], fr.l1[2], fr.l1[3]);
+                const float y = v - Fc, t = F + y;   // Kahan (non-negative terms)
+                Fc = (t - F) - y;
+                F = t;
+                if (lvl2) {
+                    const float v2 = cp.hl * far_node_sum<PeakTable<kWide>, PhaseConst, kSec>(
+                                                 tab, cp, xn2, cn2, fr.l2[0], fr.l2[1], fr.l2[2], fr.l2[3]);
+                    const float y2 = v2 - F2c, t2 = F2 + y2;
+                    F2c = (t2 - F2) - y2;
+                    F2 = t2;
+                }
+            }
             f2_t sl[kPairs], sg[kPairs];
 #pragma unroll
             for (int q = 0; q < kPairs; ++q) sl[q] = sg[q] = 0ull;
@@ -994,210 +1069,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
             dst[(2 * q) * 32] = lo;
             dst[(2 * q + 1) * 32] = hi;
         }
-    }
-}
-
-// --- far field -------------------------------------------------------------------
-// The Lorentzian tails that reach a tile from peaks beyond kFarGap half-widths
-// of it are analytic on the tile's span, with poles x = rho +- i/s at least
-// 1.5 half-widths from its centre.  Their sums are therefore evaluated at
-// kFarNodes Chebyshev nodes of the first kind of the span (Trefethen,
-// "Approximation Theory and Approximation Practice", ch. 8 bounds the
-// interpolation error by a power of the Bernstein-ellipse parameter; for
-// these poles it is below 1e-8 of the tail, under FP32 rounding) and
-// interpolated at the tile's points with Lagrange weights lam_p(x_i):
-//   forward   f_far(x_i) = sum_p lam_p(x_i) F_p          (in k_lik)
-//   backward  sum_i g_i phi(x_i) = sum_p W_p phi(x_p),  W_p = sum_i g_i lam_p(x_i).
-// Work item: one warp per (sample, tile).  Lane group q = lane / 8 takes the
-// peaks m = q (mod 4) of each range; lane l % 8 owns nodes 4 (l % 8) .. + 3.
-
-// Far-field profile at the nodes: F_p = sum_k h_k r_k sum_{far m} I_m L(t_mkp),
-// one reciprocal per two peaks (I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1)).
-template <bool kWide, bool kSec>
-__global__ void __launch_bounds__(kThreads) k_far_fwd(ProfArgs a) {
-    extern __shared__ float4 s_raw[];
-    __shared__ Staged s_st[kWarps][32];
-    int *s_off;
-    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
-    const int lane = threadIdx.x & 31, grp = lane >> 3, nl = lane & 7;
-    Staged *sb = s_st[threadIdx.x >> 5];
-    const int nwarps = gridDim.x * kWarps;
-    const f2_t one2 = bc2(1.f);
-    for (int item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < a.S * a.T; item += nwarps) {
-        const int s = item / a.T, tile = item - s * a.T;
-        const float4 xv = reinterpret_cast<const float4 *>(a.node_x + static_cast<size_t>(tile) * kFarNodes)[nl];
-        const f2_t xn[2] = {pk2(xv.x, xv.y), pk2(xv.z, xv.w)};
-        f2_t cn[2] = {one2, one2};
-        if (kSec) {
-            const float4 cv = reinterpret_cast<const float4 *>(a.node_c + static_cast<size_t>(tile) * kFarNodes)[nl];
-            cn[0] = pk2(cv.x, cv.y);
-            cn[1] = pk2(cv.z, cv.w);
-        }
-        float F[4] = {0.f, 0.f, 0.f, 0.f}, Fc[4] = {0.f, 0.f, 0.f, 0.f};
-        // lane group q takes the phases order[q], order[q + 4], ... of each
-        // staged batch of 32 (sorted by peak count, so the four groups' loops
-        // have similar lengths)
-        for (int jb = 0; jb < a.K; jb += 32) {
-            stage_phases(a, sb, s, tile, a.far_order, jb, a.K, lane);
-            const int nb = min(32, a.K - jb);
-            for (int jj = grp; jj < nb; jj += 4) {
-            const Staged &ph = sb[jj];
-            const Ranges r = staged_ranges(a, s_off, ph);
-            const int mb = r.mb, fb = r.fb, fe = r.fe, me = r.me;
-            if (fb > mb || me > fe) {
-                f2_t acc[2] = {0ull, 0ull};
-#pragma unroll 1
-                for (int side = 0; side < 2; ++side) {
-                    const int m0 = side ? fe : mb, m1 = side ? me : fb;
-                    const f2_t s2 = bc2(side ? ph.sl : ph.sr), c2 = bc2(side ? ph.nslmu : ph.nsrmu);
-                    int m = m0;
-                    for (; m + 1 < m1; m += 2) {
-                        f2_t np0, I0, np1, I1;
-                        tab.get(m, np0, I0);
-                        tab.get(m + 1, np1, I1);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            f2_t t0 = fma2(s2, add2(xn[q], np0), c2), t1 = fma2(s2, add2(xn[q], np1), c2);
-                            if (kSec) {
-                                t0 = mul2(t0, cn[q]);
-                                t1 = mul2(t1, cn[q]);
-                            }
-                            const f2_t d0 = fma2(t0, t0, one2), d1 = fma2(t1, t1, one2);
-                            const f2_t num = fma2(I0, d1, mul2(I1, d0));
-                            acc[q] = fma2(num, rcp2(mul2(d0, d1)), acc[q]);
-                        }
-                    }
-                    if (m < m1) {
-                        f2_t np, I;
-                        tab.get(m, np, I);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            f2_t t = fma2(s2, add2(xn[q], np), c2);
-                            if (kSec) t = mul2(t, cn[q]);
-                            acc[q] = fma2(I, rcp2(fma2(t, t, one2)), acc[q]);
-                        }
-                    }
-                }
-                // F += h r acc, Neumaier-compensated over the phases
-                const f2_t hl2 = bc2(ph.hl);
-                float v[4];
-                up2(mul2(hl2, acc[0]), v[0], v[1]);
-                up2(mul2(hl2, acc[1]), v[2], v[3]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float t = F[q] + v[q];
-                    Fc[q] += (fabsf(F[q]) >= fabsf(v[q])) ? ((F[q] - t) + v[q]) : ((v[q] - t) + F[q]);
-                    F[q] = t;
-                }
-            }
-            }
-        }
-        __syncwarp();
-        // the four lane groups' partial sums of each node
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float t = F[q] + Fc[q];
-            t += __shfl_xor_sync(0xffffffffu, t, 8);
-            t += __shfl_xor_sync(0xffffffffu, t, 16);
-            F[q] = t;
-        }
-        if (grp == 0)
-            reinterpret_cast<float4 *>(a.fnode + static_cast<size_t>(item) * kFarNodes)[nl] =
-                make_float4(F[0], F[1], F[2], F[3]);
-    }
-}
-
-// Far-field part of the gradient sums, added to the Lorentzian entries the
-// direct kernel wrote: with the node weights W_p of g,
-//   S1 = sum_p W_p sum_m I L,  A = sum_p W_p c_p sum_m I L^2 t,  B = S1 - sum_p W_p sum_m I L^2
-// per side (c_p = cos(x_p/2) with the angle-dependent width, else 1).  Lane
-// group q takes phases order[q], order[q + 4], ...; the group's 8 lanes hold
-// the 32 nodes and reduce among themselves.
-template <bool kWide, bool kSec>
-__global__ void __launch_bounds__(kThreads) k_far_bwd(ProfArgs a) {
-    extern __shared__ float4 s_raw[];
-    __shared__ Staged s_st[kWarps][32];
-    int *s_off;
-    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
-    const int lane = threadIdx.x & 31, grp = lane >> 3, nl = lane & 7;
-    Staged *sb = s_st[threadIdx.x >> 5];
-    const int nwarps = gridDim.x * kWarps;
-    const f2_t one2 = bc2(1.f);
-    for (int item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < a.S * a.T; item += nwarps) {
-        const int s = item / a.T, tile = item - s * a.T;
-        const float4 xv = reinterpret_cast<const float4 *>(a.node_x + static_cast<size_t>(tile) * kFarNodes)[nl];
-        const f2_t xn[2] = {pk2(xv.x, xv.y), pk2(xv.z, xv.w)};
-        const float4 wv = reinterpret_cast<const float4 *>(a.wfar + static_cast<size_t>(item) * kFarNodes)[nl];
-        const f2_t W[2] = {pk2(wv.x, wv.y), pk2(wv.z, wv.w)};
-        f2_t cn[2] = {one2, one2}, WA[2] = {W[0], W[1]};
-        if (kSec) {
-            const float4 cv = reinterpret_cast<const float4 *>(a.node_c + static_cast<size_t>(tile) * kFarNodes)[nl];
-            cn[0] = pk2(cv.x, cv.y);
-            cn[1] = pk2(cv.z, cv.w);
-            WA[0] = mul2(W[0], cn[0]);
-            WA[1] = mul2(W[1], cn[1]);
-        }
-        // staged batches of 32 phases (by decreasing peak count), rounds of
-        // four; every lane runs every round (the reduction below shuffles
-        // within the group)
-        for (int jb = 0; jb < a.K; jb += 32) {
-          stage_phases(a, sb, s, tile, a.far_order, jb, a.K, lane);
-          const int nb = min(32, a.K - jb);
-          for (int j0 = 0; j0 < nb; j0 += 4) {
-            const int jj = j0 + grp;
-            const Staged &ph = sb[jj < nb ? jj : 0];
-            const int k = ph.k;
-            const Ranges r = staged_ranges(a, s_off, ph);
-            int mb = r.mb, fb = r.fb, fe = r.fe, me = r.me;
-            if (jj >= nb) fb = mb, fe = me;                // no phase for this group in the last round
-            const bool any = fb > mb || me > fe;
-            float S1 = 0.f, A[2] = {0.f, 0.f}, B[2] = {0.f, 0.f};
-            if (any) {
-#pragma unroll 1
-                for (int side = 0; side < 2; ++side) {
-                    const int m0 = side ? fe : mb, m1 = side ? me : fb;
-                    const f2_t s2 = bc2(side ? ph.sl : ph.sr), c2 = bc2(side ? ph.nslmu : ph.nsrmu);
-                    f2_t S1n[2] = {0ull, 0ull}, An[2] = {0ull, 0ull}, C2n[2] = {0ull, 0ull};
-                    for (int m = m0; m < m1; ++m) {
-                        f2_t np, I;
-                        tab.get(m, np, I);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            f2_t t = fma2(s2, add2(xn[q], np), c2);
-                            if (kSec) t = mul2(t, cn[q]);
-                            const f2_t L = rcp2(fma2(t, t, one2));
-                            const f2_t q1 = mul2(I, L);
-                            S1n[q] = add2(S1n[q], q1);
-                            const f2_t q2 = mul2(q1, L);
-                            An[q] = fma2(q2, t, An[q]);
-                            C2n[q] = add2(C2n[q], q2);
-                        }
-                    }
-                    const float s1 = sum2(fma2(W[0], S1n[0], mul2(W[1], S1n[1])));
-                    const float as = sum2(fma2(WA[0], An[0], mul2(WA[1], An[1])));
-                    const float c2s = sum2(fma2(W[0], C2n[0], mul2(W[1], C2n[1])));
-                    S1 += s1;
-                    A[side] = as;
-                    B[side] = s1 - c2s;
-                }
-            }
-            __syncwarp();
-            // side 0: all d > 0 (|t| = t); side 1: all d < 0 (|t| = -t)
-            float v[5] = {S1, A[0] + A[1], A[0] - A[1], B[0] + B[1], B[0] - B[1]};
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
-                v[q] += __shfl_xor_sync(0xffffffffu, v[q], 2);
-                v[q] += __shfl_xor_sync(0xffffffffu, v[q], 4);
-            }
-            if (any && nl == 0) {
-                float2 *dst = reinterpret_cast<float2 *>(
-                    a.gpart + ((static_cast<size_t>(s) * a.K + k) * a.T + tile) * kGradSums);
-#pragma unroll
-                for (int q = 0; q < 5; ++q) dst[q].y += v[q];
-            }
-          }
-        }
+        a.fnode[((static_cast<size_t>(c) * a.S + s) * a.T + tile) * kFarNodes + lane] = F - Fc;
+        if (lvl2) a.fnode2[((static_cast<size_t>(c) * a.S + s) * a.Tg + g) * kFarNodes + lane] = F2 - F2c;
     }
 }
 
@@ -1227,19 +1100,42 @@ __device__ __forceinline__ float deviance_term(float y, float f) {
 // kTile == blockDim.x.
 __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
     __shared__ float shf[kTile / 32];
+    __shared__ float sFn[kFarNodes], sF2[kFarNodes];
     const int s = blockIdx.x / a.T, tile = blockIdx.x - s * a.T;
     const int i = tile * kTile + threadIdx.x;
     float dev = 0.f;
     float gv = 0.f;
     const float *lam = a.fnode ? a.lam + static_cast<size_t>(tile) * kFarNodes * kTile + threadIdx.x : nullptr;
+    if (lam) {
+        // far-field node values: the chunks' partial node sums, plus the
+        // super-tile's (summed over chunks) translated to this tile's nodes
+        const int p = threadIdx.x;
+        const int g = tile / kSuperTiles;
+        if (a.Tg && p < kFarNodes) {
+            float F2 = 0.f;
+            for (int c = 0; c < a.C; ++c) F2 += a.fnode2[((static_cast<size_t>(c) * a.S + s) * a.Tg + g) * kFarNodes + p];
+            sF2[p] = F2;
+        }
+        __syncthreads();
+        if (p < kFarNodes) {
+            float F = 0.f;
+            for (int c = 0; c < a.C; ++c) F += a.fnode[((static_cast<size_t>(c) * a.S + s) * a.T + tile) * kFarNodes + p];
+            if (a.Tg) {
+                const float *M = a.Mf + static_cast<size_t>(tile) * kFarNodes * kFarNodes + p;
+#pragma unroll 8
+                for (int P = 0; P < kFarNodes; ++P) F = fmaf(M[P * kFarNodes], sF2[P], F);
+            }
+            sFn[p] = F;
+        }
+        __syncthreads();
+    }
     if (i < a.N) {
         float f = a.bg[i];
         for (int c = 0; c < a.C; ++c) f += a.fpart[(static_cast<size_t>(c) * a.S + s) * a.Npad + i];
         if (lam) {   // far field: interpolated from the tile's nodes
-            const float *fn = a.fnode + static_cast<size_t>(blockIdx.x) * kFarNodes;
             float ff = 0.f;
 #pragma unroll 8
-            for (int p = 0; p < kFarNodes; ++p) ff = fmaf(lam[p * kTile], fn[p], ff);
+            for (int p = 0; p < kFarNodes; ++p) ff = fmaf(lam[p * kTile], sFn[p], ff);
             f += ff;
         }
         const float yv = a.y[i];
@@ -1589,6 +1485,12 @@ __device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], int lane) 
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Gradient sums with the far field on: per (sample, tile, phase chunk) and
+// phase, the direct sums at the tile's points (near band, mixed range,
+// Gaussian reach) plus, at lane p, the far sums at node p weighted by W_p
+// (and, for a super-tile's first tile, the super-far sums at super node p
+// weighted by W2_p, which k_grad attributes to the phase like any tile's),
+// reduced once and written to gpart.
 template <bool kWide, bool kSec>
 __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
     extern __shared__ float4 s_raw[];
@@ -1609,6 +1511,25 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
         const float *gs = a.g + static_cast<size_t>(s) * a.Npad + i0 + lane;
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
+        // far field: this lane's node, its weight W_p = sum_i g_i lam_p(x_i), and
+        // for a super-tile's first tile the super node and W2_P = sum_t sum_p Mb[t][p][P] W_t,p
+        const bool lvl2 = a.Tg && tile % kSuperTiles == 0;
+        const int g = tile / kSuperTiles;
+        const float xn = a.node_x[tile * kFarNodes + lane];
+        const float cn = kSec ? a.node_c[tile * kFarNodes + lane] : 1.f;
+        const float wn = a.wfar[(static_cast<size_t>(s) * a.T + tile) * kFarNodes + lane];
+        float xn2 = 0.f, cn2 = 1.f, wn2 = 0.f;
+        if (lvl2) {
+            xn2 = a.node_x2[g * kFarNodes + lane];
+            if (kSec) cn2 = a.node_c2[g * kFarNodes + lane];
+            const int t1 = min(tile + kSuperTiles, a.T);
+            for (int t = tile; t < t1; ++t) {
+                const float *M = a.Mb + static_cast<size_t>(t) * kFarNodes * kFarNodes + lane;
+                const float *wt = a.wfar + (static_cast<size_t>(s) * a.T + t) * kFarNodes;
+#pragma unroll 8
+                for (int p = 0; p < kFarNodes; ++p) wn2 = fmaf(M[p * kFarNodes], wt[p], wn2);
+            }
+        }
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
         for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
             const PhaseConst cp = cs[k];
@@ -1650,6 +1571,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
                 v[1] += sum2(S1s);
                 A[side] = sum2(As);
                 B[side] = sum2(sub2(S1s, C2s));
+            }
+            {   // far peaks at the nodes (lane-local, folded into the same sums)
+                const FarRanges fr = far_ranges(a, r, s, k, tile);
+                far_node_grad<PeakTable<kWide>, PhaseConst, kSec>(tab, cp, xn, cn, wn, wn * cn, fr.l1[0], fr.l1[1],
+                                                                  fr.l1[2], fr.l1[3], v[1], A, B);
+                if (lvl2)
+                    far_node_grad<PeakTable<kWide>, PhaseConst, kSec>(tab, cp, xn2, cn2, wn2, wn2 * cn2, fr.l2[0],
+                                                                      fr.l2[1], fr.l2[2], fr.l2[3], v[1], A, B);
             }
             // side 0: all d > 0 (|t| = t); side 1: all d < 0 (|t| = -t)
             v[3] = A[0] + A[1];
@@ -2183,21 +2112,7 @@ void configure_grids(Problem &P, int sm_count) {
     set_smem_attr(k_bwd_direct<true, false>, smax);
     set_smem_attr(k_bwd_direct<false, true>, smax);
     set_smem_attr(k_bwd_direct<true, true>, smax);
-    set_smem_attr(k_far_fwd<false, false>, smax);
-    set_smem_attr(k_far_fwd<true, false>, smax);
-    set_smem_attr(k_far_fwd<false, true>, smax);
-    set_smem_attr(k_far_fwd<true, true>, smax);
-    set_smem_attr(k_far_bwd<false, false>, smax);
-    set_smem_attr(k_far_bwd<true, false>, smax);
-    set_smem_attr(k_far_bwd<false, true>, smax);
-    set_smem_attr(k_far_bwd<true, true>, smax);
-    int bf = 1, bb = 1, bfar = 1;
-    if (P.wide)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfar, k_far_bwd<true, false>, kThreads, P.smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfar, k_far_bwd<false, false>, kThreads, P.smem);
-    if (bfar < 1) bfar = 1;
-    P.grid_far = bfar * sm_count;
+    int bf = 1, bb = 1;
     int bd = 1;
     if (P.wide)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_bwd_direct<true, false>, kThreads, P.smem);
@@ -2242,6 +2157,10 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     a.fnode = far ? W.fnode : nullptr;
     a.wfar = far ? W.wfar : nullptr;
     a.node_x = P.node_x; a.node_c = P.node_c; a.lam = P.lam; a.far_order = P.far_order;
+    a.Tg = far && W.sranges ? P.Tg : 0;
+    a.sranges = a.Tg ? W.sranges : nullptr;
+    a.fnode2 = a.Tg ? W.fnode2 : nullptr;
+    a.node_x2 = P.node_x2; a.node_c2 = P.node_c2; a.sgap = P.sgap; a.Mf = P.Mf; a.Mb = P.Mb;
     return a;
 }
 
@@ -2252,8 +2171,9 @@ static int grid_for(int grid_max, int items) {
 
 void choose_chunks(const Problem &P, const int *offsets, int S, Workspace &W, int max_chunks) {
     const long long base = static_cast<long long>(S) * P.T;
-    const long long resident = static_cast<long long>(P.grid_fwd) * kWarps;
-    int C = static_cast<int>((kItemsPerWarp * resident + base - 1) / base);
+    const long long resident = static_cast<long long>(P.far ? P.grid_fwd_direct : P.grid_fwd) * kWarps;
+    const int per_warp = kItemsPerWarp;
+    int C = static_cast<int>((per_warp * resident + base - 1) / base);
     C = C < 1 ? 1 : C;
     C = C > kMaxChunks ? kMaxChunks : C;
     C = C > max_chunks ? max_chunks : C;
@@ -2335,16 +2255,6 @@ void launch_forward(const Problem &P, Workspace &W, float *f_out, bool naive, cu
         k_forward<false, false><<<grid, kThreads, P.smem_fwd, st>>>(a);
     }
     if (marks) cudaEventRecord(marks[1], st);
-    if (a.fnode) {   // far field at the nodes (k_lik interpolates it)
-        const int gf = grid_for(P.grid_far, W.S * P.T);
-        if (P.sec) {
-            if (P.wide) k_far_fwd<true, true><<<gf, kThreads, P.smem, st>>>(a);
-            else k_far_fwd<false, true><<<gf, kThreads, P.smem, st>>>(a);
-        } else {
-            if (P.wide) k_far_fwd<true, false><<<gf, kThreads, P.smem, st>>>(a);
-            else k_far_fwd<false, false><<<gf, kThreads, P.smem, st>>>(a);
-        }
-    }
     if (marks) cudaEventRecord(marks[2], st);
     k_lik<<<W.S * P.T, kTile, 0, st>>>(a);
 }
@@ -2387,16 +2297,6 @@ void launch_backward(const Problem &P, Workspace &W, cudaStream_t st, cudaEvent_
             k_bwd_near<false><<<grid, kThreads, P.smem, st>>>(a);
     }
     if (marks) cudaEventRecord(marks[1], st);
-    if (a.wfar) {   // far-field sums, added after the direct kernels (fixed order)
-        const int gf = grid_for(P.grid_far, W.S * P.T);
-        if (P.sec) {
-            if (P.wide) k_far_bwd<true, true><<<gf, kThreads, P.smem, st>>>(a);
-            else k_far_bwd<false, true><<<gf, kThreads, P.smem, st>>>(a);
-        } else {
-            if (P.wide) k_far_bwd<true, false><<<gf, kThreads, P.smem, st>>>(a);
-            else k_far_bwd<false, false><<<gf, kThreads, P.smem, st>>>(a);
-        }
-    }
 }
 
 void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,

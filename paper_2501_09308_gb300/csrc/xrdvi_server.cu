@@ -109,11 +109,12 @@ extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, i
                        a256(static_cast<size_t>(K) * 4)
                  : a256(s * 8);
         // far field: range ends, node sums (and node weights of g in a fit)
-        b += a256(sk * T * 4) + a256(s * T * kFarNodes * 4) * (fit ? 2 : 1);
+        b += a256(sk * T * 4) * 2 + a256(kMaxChunks * s * T * kFarNodes * 4) * 2 + a256(s * T * kFarNodes * 4);
         return b;
     };
     size_t b = a256(M_total * 4) * 2 + a256((K + 1) * 4) + a256(N * 4) * 3 + a256(K * 8);
     b += a256(T * kFarNodes * kTile * 4) + a256(T * kFarNodes * 4) * 2;   // far-field tables
+    b += a256(T * kFarNodes * kFarNodes * 4) * 2 + a256(T * kFarNodes * 4) * 2 + a256(T * 4);   // second level
     b += ws(S, true);
     b += a256(K * 20) * 2 + a256(K * 40) * 3 + a256(8) * 2 + a256(kTraceCap * 8) + a256(4) * 2;
     if (S_post > 0) {
