@@ -129,6 +129,21 @@ def sum_over_ranks(world, value):
     return float(t.item())
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu record of the
+    K=50 step, or None when the kernel source changed since it was taken."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "dram_traffic_K50_N4500_S256.json")
+    src = os.path.join(ROOT, "paper_2501_09308_gb300", "csrc", "xrdvi_kernels.cu")
+    try:
+        d = json.load(open(rec))
+        if d.get("kernels_source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+            return None
+        return d["dram_bytes_per_launch"].get(kernel)
+    except Exception:
+        return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -502,7 +517,7 @@ def main():
             "peak": fp32_peak,
             "unit": "Top/s (FP32 lane ops)",
             "frac": per_kernel[dom]["frac"],
-            "traffic": None,
+            "traffic": recorded_traffic(kernel_names[dom]),
             "peak_source": f"FP32 pipe: {sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({peak_src} sm_max_mhz); "
                            "algorithmic FP32 ops per executed evaluation of each kind x the step's counts",
             "mufu_frac": per_kernel[dom]["mufu_frac"],
