@@ -97,3 +97,32 @@ def test_far_field_fit_steps_match_the_oracle():
     np.testing.assert_allclose(trace, ref["trace"], rtol=F_TOL)
     np.testing.assert_allclose(loc1, ref["loc"], rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(raw1, ref["raw"], rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("K,M,N,S,seed,flags,okw", [
+    (3, 6, 300, 4, 11, 0, {}),
+    (8, 20, 2600, 8, 12, 0, {}),
+    (1, 1, 1, 1, 13, 0, {}),
+    (6, 30, 3000, 4, 14, xrdvi.FLAG_SEC_WIDTH, {"width": "sec"}),
+    (5, 12, 1500, 4, 15, xrdvi.FLAG_NAIVE_SUM, {}),
+])
+def test_dense_path_parity(K, M, N, S, seed, flags, okw):
+    """XRDVI_FLAG_DENSE (every peak at every point: k_forward, k_bwd_uniform,
+    k_bwd_near) against the oracle."""
+    inst = synth.small_problem(K=K, M=M, N=N, S=S, seed=seed, x_lo=40.0 if flags & xrdvi.FLAG_SEC_WIDTH else 10.0,
+                               x_step=max(0.02, 40.0 / N))
+    _against_oracle(inst, S, seed, xrdvi.FLAG_DENSE | flags, **okw)
+
+
+def test_dense_path_fit_steps_match_the_oracle():
+    inst = synth.small_problem(K=4, M=12, N=1200, S=8, seed=16, x_lo=10.0, x_step=0.03)
+    ctx = xrdvi.Context.from_instance(inst, S=8, seed=4246, flags=xrdvi.FLAG_DENSE)
+    loc0, raw0 = ctx.params()
+    trace = ctx.fit(3)
+    loc1, raw1 = ctx.params()
+    ctx.close()
+    ref = oracle.Problem.from_instance(inst).fit(8, 3, 4246, loc=loc0.astype(np.float64),
+                                                 raw=raw0.astype(np.float64))
+    np.testing.assert_allclose(trace, ref["trace"], rtol=F_TOL)
+    np.testing.assert_allclose(loc1, ref["loc"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(raw1, ref["raw"], rtol=1e-5, atol=1e-5)
