@@ -311,10 +311,35 @@ def enumeration_leg(iters=3000):
             "planted": [int(k) for k in inst.planted]}
 
 
+def kernel_rooflines(kern, work, sms, clock_mhz):
+    """Per profile kernel: FP32 and MUFU fractions of the peaks from the
+    step's evaluation counts (OPS) and the kernels' mean times."""
+    fp32_peak = sms * 128 * clock_mhz * 1e6 / 1e12
+    mufu_peak = sms * MUFU_LANES * clock_mhz * 1e6 / 1e12
+    ops_table = dict(OPS)
+    if work["far_nodes"] > 0:   # far field on: node evaluations inside the two direct kernels
+        ops_table = {"direct": dict(OPS["direct"], far_nodes=OPS["far_fwd"]["far_nodes"]),
+                     "bwd_uniform": {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1),
+                                     "far_nodes": OPS["far_bwd"]["far_nodes"]}}
+    out = {}
+    for name, kinds in ops_table.items():
+        if kern[name] <= 1e-4:
+            continue
+        ops = sum(work[kd] * o[0] for kd, o in kinds.items())
+        mufu = sum(work[kd] * o[1] for kd, o in kinds.items())
+        if ops == 0:
+            continue
+        ach = ops / (kern[name] * 1e-3) / 1e12
+        out[name] = {"ms": kern[name], "fp32_tops": ach, "frac": ach / fp32_peak,
+                     "mufu_frac": mufu / (kern[name] * 1e-3) / 1e12 / mufu_peak}
+    return out
+
+
 def variants_leg(peaks, steps=32):
     """Estimator and model variants on the K=50 workload: per-kernel CUDA-event
     times of `steps` SVI steps with the Gaussian likelihood, the
-    importance-weighted objective, the angle-dependent width and the
+    importance-weighted objective, the angle-dependent width, the all-direct
+    evaluation (XRDVI_FLAG_DENSE, with its kernels' rooflines) and the
     shared-shape estimator; for the last also the whole fit
     + posterior (time-to-posterior, CUDA events) and the roofline of its
     backward contraction on the tensor cores."""
@@ -323,6 +348,13 @@ def variants_leg(peaks, steps=32):
     from paper_2501_09308_gb300 import synth, xrdvi
     inst = synth.config(1)
     out = {}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    c = xrdvi.Context.from_instance(inst, S=inst.S, flags=xrdvi.FLAG_DENSE)
+    c.fit(16, trace=False)
+    km, work = c.profile_kernels(steps)
+    c.close()
+    out["dense"] = {"kernel_ms_per_launch": km, "svi_step_ms": sum(km.values()), "work_counts_per_step": work,
+                    "roofline": kernel_rooflines(km, work, sms, float(peaks.get("sm_max_mhz", 2070.0)))}
     for name, flags in (("gauss_lik", xrdvi.FLAG_GAUSS_LIK), ("iw_elbo", xrdvi.FLAG_IW_ELBO),
                         ("sec_width", xrdvi.FLAG_SEC_WIDTH), ("shared_shapes", xrdvi.FLAG_SHARED_SHAPES)):
         c = xrdvi.Context.from_instance(inst, S=inst.S, flags=flags)
@@ -464,21 +496,7 @@ def main():
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * 128 * clock_mhz * 1e6 / 1e12   # FP32 lane operations per second (Top/s)
-    mufu_peak = sms * MUFU_LANES * clock_mhz * 1e6 / 1e12
-    ops_table = dict(OPS)
-    if work["far_nodes"] > 0:   # far field on: node evaluations inside the two direct kernels
-        ops_table = {"direct": dict(OPS["direct"], far_nodes=OPS["far_fwd"]["far_nodes"]),
-                     "bwd_uniform": {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1),
-                                     "far_nodes": OPS["far_bwd"]["far_nodes"]}}
-    per_kernel = {}
-    for name, kinds in ops_table.items():
-        if kern[name] <= 1e-4:
-            continue
-        ops = sum(work[kd] * o[0] for kd, o in kinds.items())
-        mufu = sum(work[kd] * o[1] for kd, o in kinds.items())
-        ach = ops / (kern[name] * 1e-3) / 1e12
-        per_kernel[name] = {"ms": kern[name], "fp32_tops": ach, "frac": ach / fp32_peak,
-                            "mufu_frac": mufu / (kern[name] * 1e-3) / 1e12 / mufu_peak}
+    per_kernel = kernel_rooflines(kern, work, sms, clock_mhz)
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     executed = work["uniform"] + work["mixed"] + work["gauss_reach"] + work["far_nodes"]
     far_on = work["far_nodes"] > 0
