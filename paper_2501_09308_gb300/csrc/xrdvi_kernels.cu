@@ -902,6 +902,7 @@ __device__ __forceinline__ void far_node_grad(const Tab &tab, const PC &cp, floa
         if (m0 >= m1) continue;
         const float sc = side ? cp.sl : cp.sr, cm = side ? cp.nslmu : cp.nsrmu;
         float s1 = 0.f, an = 0.f, c2 = 0.f;
+#pragma unroll 2
         for (int m = m0; m < m1; ++m) {
             float np, I;
             tab.scalar(m, np, I);
