@@ -311,6 +311,21 @@ def enumeration_leg(iters=3000):
             "planted": [int(k) for k in inst.planted]}
 
 
+def kernel_slots(far_on):
+    """The kernels behind the library's per-kernel timing slots on each path
+    (slots without a kernel on a path are left out)."""
+    if far_on:
+        return {"sample": "k_sample", "ranges": "k_ranges", "direct": "k_fwd_direct", "lik": "k_lik",
+                "bwd_uniform": "k_bwd_direct", "grad_adam": "k_grad", "elbo": "k_elbo"}
+    return {"sample": "k_sample", "ranges": "k_ranges", "direct": "k_forward", "lik": "k_lik",
+            "bwd_uniform": "k_bwd_uniform", "bwd_near": "k_bwd_near", "grad_adam": "k_grad", "elbo": "k_elbo"}
+
+
+def named(kern, far_on):
+    """{kernel name: mean ms per launch} of the kernels a step launches."""
+    return {name: kern[slot] for slot, name in kernel_slots(far_on).items()}
+
+
 def kernel_rooflines(kern, work, sms, clock_mhz):
     """Per profile kernel: FP32 and MUFU fractions of the peaks from the
     step's evaluation counts (OPS) and the kernels' mean times."""
@@ -322,15 +337,16 @@ def kernel_rooflines(kern, work, sms, clock_mhz):
                      "bwd_uniform": {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1),
                                      "far_nodes": OPS["far_bwd"]["far_nodes"]}}
     out = {}
+    slots = kernel_slots(work["far_nodes"] > 0)
     for name, kinds in ops_table.items():
-        if kern[name] <= 1e-4:
+        if name not in slots or kern[name] <= 1e-4:
             continue
         ops = sum(work[kd] * o[0] for kd, o in kinds.items())
         mufu = sum(work[kd] * o[1] for kd, o in kinds.items())
         if ops == 0:
             continue
         ach = ops / (kern[name] * 1e-3) / 1e12
-        out[name] = {"ms": kern[name], "fp32_tops": ach, "frac": ach / fp32_peak,
+        out[slots[name]] = {"ms": kern[name], "fp32_tops": ach, "frac": ach / fp32_peak,
                      "mufu_frac": mufu / (kern[name] * 1e-3) / 1e12 / mufu_peak}
     return out
 
@@ -353,7 +369,8 @@ def variants_leg(peaks, steps=32):
     c.fit(16, trace=False)
     km, work = c.profile_kernels(steps)
     c.close()
-    out["dense"] = {"kernel_ms_per_launch": km, "svi_step_ms": sum(km.values()), "work_counts_per_step": work,
+    kd = named(km, False)
+    out["dense"] = {"kernel_ms_per_launch": kd, "svi_step_ms": sum(kd.values()), "work_counts_per_step": work,
                     "roofline": kernel_rooflines(km, work, sms, float(peaks.get("sm_max_mhz", 2070.0)))}
     for name, flags in (("gauss_lik", xrdvi.FLAG_GAUSS_LIK), ("iw_elbo", xrdvi.FLAG_IW_ELBO),
                         ("sec_width", xrdvi.FLAG_SEC_WIDTH), ("shared_shapes", xrdvi.FLAG_SHARED_SHAPES)):
@@ -504,10 +521,8 @@ def main():
     # (dense) or bwd_direct (far field); posterior: sample, ranges, forward, lik, post_sample,
     # post_reduce, post_sort, post_topm
     launches_per_step = (7 if far_on else 8) * iters + 8
-    share = {k: kern[k] / sum(kern.values()) for k in kern}
-    kernel_names = {"direct": "k_fwd_direct" if far_on else "k_forward",
-                    "bwd_uniform": "k_bwd_direct" if far_on else "k_bwd_uniform",
-                    "bwd_near": "k_bwd_near"}
+    kern_named = named(kern, far_on)
+    share = {k: v / sum(kern_named.values()) for k, v in kern_named.items()}
     out = {
         "metric": METRIC,
         "value": value,
@@ -524,18 +539,18 @@ def main():
         "config": workload_config(inst, l2="256 MB buffer written between timed steps (L2 flush)"),
         "time_to_posterior_s": ms_step / 1e3,
         "svi_step_ms": ms_step / iters,
-        "kernel_ms_per_launch": kern,
+        "kernel_ms_per_launch": kern_named,
         "kernel_share": share,
         "executed_evals_per_step": executed,
         "work_counts_per_step": work,
         "roofline": {
             "bound": "alu",
-            "kernel": kernel_names[dom],
+            "kernel": dom,
             "achieved": per_kernel[dom]["fp32_tops"],
             "peak": fp32_peak,
             "unit": "Top/s (FP32 lane ops)",
             "frac": per_kernel[dom]["frac"],
-            "traffic": recorded_traffic(kernel_names[dom]),
+            "traffic": recorded_traffic(dom),
             "peak_source": f"FP32 pipe: {sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({peak_src} sm_max_mhz); "
                            "algorithmic FP32 ops per executed evaluation of each kind x the step's counts",
             "mufu_frac": per_kernel[dom]["mufu_frac"],

@@ -501,6 +501,9 @@ __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
         const PhaseConst c = a.cst[sk];
         if (c.absent != 0.f) {
             a.ranges[idx] = make_ushort4(kAbsentRange, 0, 0, 0);
+            if (a.franges) a.franges[idx] = make_ushort2(0, 0);
+            if (a.sranges && tile % kSuperTiles == 0)
+                a.sranges[(idx / a.T) * a.Tg + tile / kSuperTiles] = make_ushort2(0, 0);
             continue;
         }
         const float xlo = a.x[tile * kTile];
@@ -595,19 +598,25 @@ __device__ __forceinline__ PeakTable<kWide> load_table(const ProfArgs &a, float4
 
 // Peak ranges of one (sample, phase, tile): [mb, fb) far below, [fb, m1)
 // near below, [m1, m2) mixed, [m2, fe) near above, [fe, me) far above, and
-// the Gaussian reach [nb, ne) (inside [fb, fe)).  Without the far field
-// fb = mb and fe = me.
+// the Gaussian reach [nb, ne) (inside [fb, fe)); of the far peaks, [mb, sfb)
+// and [sfe, me) are super-far (beyond the tile's super-tile).  Without the
+// far field fb = sfb = mb and fe = sfe = me; without the second level
+// sfb = mb and sfe = me.
 struct Ranges {
-    int mb, m1, m2, me, nb, ne, fb, fe;
+    int mb, m1, m2, me, nb, ne, fb, fe, sfb, sfe;
 };
 
 __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_off, int s, int k, int tile) {
-    const size_t id = (static_cast<size_t>(s) * a.K + k) * a.T + tile;
+    const size_t sk = static_cast<size_t>(s) * a.K + k;
+    const size_t id = sk * a.T + tile;
+    // every load is issued before any of them is used: one round trip per phase
     const ushort4 r = a.ranges[id];
+    const ushort2 f = a.franges ? a.franges[id] : make_ushort2(0, 0);
+    const ushort2 g = a.sranges ? a.sranges[sk * a.Tg + tile / kSuperTiles] : make_ushort2(0, 0);
     Ranges o;
     o.mb = s_off[k];
     if (r.x == kAbsentRange) {  // phase not in this sample's sub-model: every range empty
-        o.me = o.m1 = o.m2 = o.nb = o.ne = o.fb = o.fe = o.mb;
+        o.me = o.m1 = o.m2 = o.nb = o.ne = o.fb = o.fe = o.sfb = o.sfe = o.mb;
         return o;
     }
     o.me = s_off[k + 1];
@@ -615,14 +624,10 @@ __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_of
     o.m2 = o.mb + r.y;
     o.nb = o.mb + r.z;
     o.ne = o.mb + r.w;
-    if (a.franges) {
-        const ushort2 f = a.franges[id];
-        o.fb = o.mb + f.x;
-        o.fe = o.mb + f.y;
-    } else {
-        o.fb = o.mb;
-        o.fe = o.me;
-    }
+    o.fb = a.franges ? o.mb + f.x : o.mb;
+    o.fe = a.franges ? o.mb + f.y : o.me;
+    o.sfb = a.sranges ? o.mb + g.x : o.mb;
+    o.sfe = a.sranges ? o.mb + g.y : o.me;
     return o;
 }
 
@@ -932,24 +937,18 @@ __device__ __forceinline__ void far_node_grad(const Tab &tab, const PC &cp, floa
 struct FarRanges {
     int l1[4], l2[4];
 };
-__device__ __forceinline__ FarRanges far_ranges(const ProfArgs &a, const Ranges &r, int s, int k, int tile) {
+__device__ __forceinline__ FarRanges far_ranges(const Ranges &r) {
     FarRanges f;
-    int sfb = r.mb, sfe = r.me;
-    if (a.sranges && r.me > r.mb) {
-        const ushort2 sr = a.sranges[(static_cast<size_t>(s) * a.K + k) * a.Tg + tile / kSuperTiles];
-        sfb = r.mb + sr.x;
-        sfe = r.mb + sr.y;
-    }
-    f.l1[0] = sfb; f.l1[1] = r.fb; f.l1[2] = r.fe; f.l1[3] = sfe;
-    f.l2[0] = r.mb; f.l2[1] = sfb; f.l2[2] = sfe; f.l2[3] = r.me;
+    f.l1[0] = r.sfb; f.l1[1] = r.fb; f.l1[2] = r.fe; f.l1[3] = r.sfe;
+    f.l2[0] = r.mb; f.l2[1] = r.sfb; f.l2[2] = r.sfe; f.l2[3] = r.me;
     return f;
 }
 
 // Profile with the far field on: per (sample, tile, phase chunk), each
 // phase's near band [fb, m1), [m2, fe) (a few peaks: t = s (x - p) - s mu per
-// evaluation), its mixed range and its Gaussian reach at the tile's points;
-// the Gaussian of a pair block is skipped when no point of it is within
-// reach.  Phase contributions are summed with packed Kahan compensation (all
+// evaluation), its mixed range and its Gaussian reach at the tile's points
+// (the Gaussian at every point of them: beyond its reach 2^-u is exactly 0,
+// and a branch-free loop beats a warp vote per pair block here).  Phase contributions are summed with packed Kahan compensation (all
 // terms are non-negative).  Lane p also sums the phase's far peaks at node p
 // of the tile (and, for a super-tile's first tile, its super-far peaks at node
 // p of the super-tile), Kahan-compensated over the phases, into the chunk's
@@ -987,7 +986,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
             const PhaseConst cp = cs[k];
             const Ranges r = load_ranges(a, s_off, s, k, tile);
             {   // far peaks at the nodes
-                const FarRanges fr = far_ranges(a, r, s, k, tile);
+                const FarRanges fr = far_ranges(r);
                 const float v = cp.hl * far_node_sum<PeakTable<kWide>, PhaseConst, kSec>(
                                             tab, cp, xn, cn, fr.l1[0], fr.l1[1], fr.l1[2], fr.l1[3]);
                 const float y = v - Fc, t = F + y;   // Kahan (non-negative terms)
@@ -1029,7 +1028,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
                         const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
                         const f2_t u = mul2(t, t);
                         sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
-                        if (any_gauss(u)) sg[q] = fma2(I, ex2neg2(u), sg[q]);
+                        sg[q] = fma2(I, ex2neg2(u), sg[q]);
                     }
                 }
 #pragma unroll 1
@@ -1043,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
                         for (int q = 0; q < kPairs; ++q) {
                             const f2_t t = ps(fma2(s2, add2(x2[q], np), c2), q);
                             const f2_t u = mul2(t, t);
-                            if (any_gauss(u)) sg[q] = fma2(I, ex2neg2(u), sg[q]);
+                            sg[q] = fma2(I, ex2neg2(u), sg[q]);
                         }
                     }
                 }
@@ -1574,7 +1573,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
                 B[side] = sum2(sub2(S1s, C2s));
             }
             {   // far peaks at the nodes (lane-local, folded into the same sums)
-                const FarRanges fr = far_ranges(a, r, s, k, tile);
+                const FarRanges fr = far_ranges(r);
                 far_node_grad<PeakTable<kWide>, PhaseConst, kSec>(tab, cp, xn, cn, wn, wn * cn, fr.l1[0], fr.l1[1],
                                                                   fr.l1[2], fr.l1[3], v[1], A, B);
                 if (lvl2)
