@@ -295,6 +295,7 @@ xrdvi_status alloc_workspace(xrdvi_ctx *c, Workspace &W, int S, bool fit,
         XR_TRY(c->alloc(&W.franges, SK * P.T, list));
         if (P.Tg) XR_TRY(c->alloc(&W.sranges, SK * P.Tg, list));
         if (fit) XR_TRY(c->alloc(&W.wfar, static_cast<size_t>(S) * P.T * kFarNodes, list));
+        if (fit && P.Tg) XR_TRY(c->alloc(&W.wfar2, static_cast<size_t>(S) * P.T * kFarNodes, list));
     }
     choose_chunks(P, c->host_off.data(), S, W);
     W.fpart_cap = static_cast<size_t>(W.C) * S * P.Npad;

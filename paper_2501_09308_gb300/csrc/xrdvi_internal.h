@@ -107,6 +107,7 @@ struct Workspace {
     float *fnode = nullptr;      // [kMaxChunks*S*T*kFarNodes] far-field node sums of each phase chunk
     float *fnode2 = nullptr;     // [kMaxChunks*S*Tg*kFarNodes] the same at the super-tiles' nodes
     float *wfar = nullptr;       // [S*T*kFarNodes] sum_i g_i lam_p(x_i) per tile (fit only)
+    float *wfar2 = nullptr;      // [S*T*kFarNodes] the tile's part of the super-tile's node weights (fit only)
     int *counters = nullptr;     // [kCounters] work counters of the profile kernels
     double *gred = nullptr;      // [K*kGradBlocks*10] gradient partials per sample block (fit only)
     int *tickets = nullptr;      // [K] arrival tickets of the gradient reduction (fit only)

@@ -402,6 +402,7 @@ struct ProfArgs {
     ushort2 *franges;  // [S*K*T] (fb, fe) relative to the phase's first peak
     float *fnode;      // [C*S*T*kFarNodes] far-field profile at the tile nodes per phase chunk
     float *wfar;       // [S*T*kFarNodes] node weights of g (null: not needed)
+    float *wfar2;      // [S*T*kFarNodes] per tile: sum_p Mb[t][p][P] W_t,p (null: no second level)
     const float *node_x, *node_c, *lam;
     const int *far_order;   // [K] phases by decreasing peak count
     // second far-field level (Tg = 0: none)
@@ -1106,6 +1107,17 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
     float dev = 0.f;
     float gv = 0.f;
     const float *lam = a.fnode ? a.lam + static_cast<size_t>(tile) * kFarNodes * kTile + threadIdx.x : nullptr;
+    __shared__ __align__(16) float sMb[kFarNodes * kFarNodes];
+    __shared__ float sW2[kTile / 32][kFarNodes];
+    if (a.wfar2) {
+        // the tile's backward translation matrix (4 KB, 16 bytes a thread), copied
+        // asynchronously so that no warp waits for it before the node weights
+        static_assert(kFarNodes * kFarNodes * 4 == kTile * 16, "one 16-byte copy per thread");
+        const float *M = a.Mb + static_cast<size_t>(tile) * kFarNodes * kFarNodes + threadIdx.x * 4;
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(sMb + threadIdx.x * 4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(M) : "memory");
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     if (lam) {
         // far-field node values: the chunks' partial node sums, plus the
         // super-tile's (summed over chunks) translated to this tile's nodes
@@ -1177,12 +1189,24 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
             }
         }
         shw[w][l] = v[0];
+        if (a.wfar2) asm volatile("cp.async.wait_all;\n" ::: "memory");   // sMb complete before the sync
         __syncthreads();
-        if (threadIdx.x < kFarNodes) {
-            float t = 0.f;
+        // every warp forms W_p at lane p (the same sum in each)
+        float t = 0.f;
 #pragma unroll
-            for (int ww = 0; ww < kTile / 32; ++ww) t += shw[ww][threadIdx.x];
-            a.wfar[static_cast<size_t>(blockIdx.x) * kFarNodes + threadIdx.x] = t;
+        for (int ww = 0; ww < kTile / 32; ++ww) t += shw[ww][l];
+        if (w == 0) a.wfar[static_cast<size_t>(blockIdx.x) * kFarNodes + l] = t;
+        if (a.wfar2) {
+            // this tile's part of the super-tile's node weights, sum_p Mb[t][p][P] W_t,p
+            // at lane P: warp w takes nodes p of [w n, (w + 1) n), the sum of the parts
+            // follows the last sync (k_bwd_direct adds the member tiles' sums in tile order)
+            constexpr int n = kFarNodes / (kTile / 32);
+            static_assert(n * (kTile / 32) == kFarNodes, "nodes split evenly over the warps");
+            float w2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < n; ++j)
+                w2 = fmaf(sMb[(w * n + j) * kFarNodes + l], __shfl_sync(0xffffffffu, t, w * n + j), w2);
+            sW2[w][l] = w2;
         }
     }
     __syncthreads();
@@ -1190,6 +1214,12 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
         float t = threadIdx.x < kTile / 32 ? shf[threadIdx.x] : 0.f;
         t = warp_sumf(t);
         if (threadIdx.x == 0) a.llpart[static_cast<size_t>(s) * a.T + tile] = static_cast<double>(t);
+        if (a.wfar2) {
+            float w2 = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < kTile / 32; ++ww) w2 += sW2[ww][threadIdx.x];
+            a.wfar2[static_cast<size_t>(blockIdx.x) * kFarNodes + threadIdx.x] = w2;
+        }
     }
     if (a.Tb) {   // fitted background: d LL / d beta_j = sum_i g_i B_i(beta) T_j(z_i), per tile
         __shared__ float shb[3][kTile / 32];
@@ -1513,6 +1543,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
         for (int q = 0; q < kPairs; ++q) g2[q] = pk2(gs[(2 * q) * 32], gs[(2 * q + 1) * 32]);
         // far field: this lane's node, its weight W_p = sum_i g_i lam_p(x_i), and
         // for a super-tile's first tile the super node and W2_P = sum_t sum_p Mb[t][p][P] W_t,p
+        // (k_lik leaves each tile's sum over p in wfar2)
         const bool lvl2 = a.Tg && tile % kSuperTiles == 0;
         const int g = tile / kSuperTiles;
         const float xn = a.node_x[tile * kFarNodes + lane];
@@ -1523,12 +1554,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
             xn2 = a.node_x2[g * kFarNodes + lane];
             if (kSec) cn2 = a.node_c2[g * kFarNodes + lane];
             const int t1 = min(tile + kSuperTiles, a.T);
-            for (int t = tile; t < t1; ++t) {
-                const float *M = a.Mb + static_cast<size_t>(t) * kFarNodes * kFarNodes + lane;
-                const float *wt = a.wfar + (static_cast<size_t>(s) * a.T + t) * kFarNodes;
-#pragma unroll 8
-                for (int p = 0; p < kFarNodes; ++p) wn2 = fmaf(M[p * kFarNodes], wt[p], wn2);
-            }
+            for (int t = tile; t < t1; ++t) wn2 += a.wfar2[(static_cast<size_t>(s) * a.T + t) * kFarNodes + lane];
         }
         const PhaseConst *cs = a.cst + static_cast<size_t>(s) * a.K;
         for (int k = a.chunk[c]; k < a.chunk[c + 1]; ++k) {
@@ -2160,6 +2186,7 @@ static ProfArgs prof_args(const Problem &P, Workspace &W, float *f_out) {
     a.Tg = far && W.sranges ? P.Tg : 0;
     a.sranges = a.Tg ? W.sranges : nullptr;
     a.fnode2 = a.Tg ? W.fnode2 : nullptr;
+    a.wfar2 = a.Tg && a.wfar ? W.wfar2 : nullptr;
     a.node_x2 = P.node_x2; a.node_c2 = P.node_c2; a.sgap = P.sgap; a.Mf = P.Mf; a.Mb = P.Mb;
     return a;
 }

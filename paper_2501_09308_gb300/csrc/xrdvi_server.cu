@@ -108,8 +108,8 @@ extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, i
         b += fit ? a256(sk * T * kGradSums * 4) + a256(static_cast<size_t>(K) * kGradBlocks * kGredVals * 8) +
                        a256(static_cast<size_t>(K) * 4)
                  : a256(s * 8);
-        // far field: range ends, node sums (and node weights of g in a fit)
-        b += a256(sk * T * 4) * 2 + a256(kMaxChunks * s * T * kFarNodes * 4) * 2 + a256(s * T * kFarNodes * 4);
+        // far field: range ends, node sums (and node weights of g in a fit, both levels)
+        b += a256(sk * T * 4) * 2 + a256(kMaxChunks * s * T * kFarNodes * 4) * 2 + a256(s * T * kFarNodes * 4) * 2;
         return b;
     };
     size_t b = a256(M_total * 4) * 2 + a256((K + 1) * 4) + a256(N * 4) * 3 + a256(K * 8);
