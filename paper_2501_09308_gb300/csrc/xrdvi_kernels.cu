@@ -342,10 +342,12 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
         if (a.lq) a.lq[s] = totq;
     }
     if (s_loc == 0 && a.ent) {
+        // Gaussian entropy sum_j (ln sigma_j + (1 + ln 2 pi)/2): the terms in FP32
+        // (FP64 transcendentals are slow on this part), their sum in FP64
         double H = 0.0;
         for (int i = threadIdx.x; i < 5 * a.K; i += blockDim.x)
             if ((!a.mask || ((mk >> (i / 5)) & 1u)) && !((i % 5 == 3 && a.fix_r) || (i % 5 == 4 && a.fix_a)))
-                H += log(softplusd(static_cast<double>(raw[i]))) + 0.5 * (1.0 + kLog2Pi);
+                H += static_cast<double>(logf(softplusf(raw[i]))) + 0.5 * (1.0 + kLog2Pi);
         H = block_sum(H, sh);
         if (threadIdx.x == 0) a.ent[b] = H;
     }
@@ -1861,7 +1863,11 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         if (!is_raw) {
             grad = a.iw ? red[j] : red[j] / a.S_sub;
         } else {
-            grad = ((a.iw ? red[5 + j] : red[5 + j] / a.S_sub) + 1.0 / softplusd(rw)) * sigmoidd(rw);
+            // d/d raw of sigma = softplus(raw): sigmoid(raw); entropy gradient 1 / sigma
+            // (both in FP32: FP64 transcendentals are slow on this part)
+            const float rwf = static_cast<float>(rw);
+            grad = ((a.iw ? red[5 + j] : red[5 + j] / a.S_sub) + static_cast<double>(1.f / softplusf(rwf))) *
+                   static_cast<double>(sigmoidf(rwf));
         }
         const bool fixed = (j == 3 && a.fix_r) || (j == 4 && a.fix_a);   // not part of q: no gradient
         if (fixed) grad = 0.0;
@@ -1869,15 +1875,17 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         if (a.adam && !fixed) {
             const int t = *a.d_iter + 1;
             const int idx = bk * 10 + threadIdx.x;
-            const double gm = -grad;  // minimise -ELBO
-            const double mm = a.ac.b1 * static_cast<double>(a.m[idx]) + (1.0 - a.ac.b1) * gm;
-            const double vv = a.ac.b2 * static_cast<double>(a.v[idx]) + (1.0 - a.ac.b2) * gm * gm;
-            a.m[idx] = static_cast<float>(mm);
-            a.v[idx] = static_cast<float>(vv);
-            // bias corrections in FP32 (a few ulps; FP64 pow is slow on this part)
-            const double c1 = 1.0 - static_cast<double>(powf(a.ac.b1, static_cast<float>(t)));
-            const double c2 = 1.0 - static_cast<double>(powf(a.ac.b2, static_cast<float>(t)));
-            const double step = a.ac.lr * (mm / c1) / (sqrt(vv / c2) + a.ac.eps);
+            // the Adam rule in FP32 (its state is FP32; FP64 division and square
+            // root are slow on this part)
+            const float gm = -static_cast<float>(grad);  // minimise -ELBO
+            const float b1 = a.ac.b1, b2 = a.ac.b2;
+            const float mm = fmaf(b1, a.m[idx], (1.f - b1) * gm);
+            const float vv = fmaf(b2, a.v[idx], (1.f - b2) * gm * gm);
+            a.m[idx] = mm;
+            a.v[idx] = vv;
+            const float c1 = 1.f - powf(b1, static_cast<float>(t));
+            const float c2 = 1.f - powf(b2, static_cast<float>(t));
+            const double step = a.ac.lr * __fdiv_rn(mm, c1) / (sqrtf(__fdiv_rn(vv, c2)) + a.ac.eps);
             if (!is_raw) {
                 a.loc_out[bk * 5 + j] = static_cast<float>(a.loc_in[bk * 5 + j] - step);
             } else {
