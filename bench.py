@@ -517,10 +517,10 @@ def main():
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     executed = work["uniform"] + work["mixed"] + work["gauss_reach"] + work["far_nodes"]
     far_on = work["far_nodes"] > 0
-    # per SVI step: sample, ranges, forward, lik, grad, elbo and either bwd_uniform + bwd_near
-    # (dense) or bwd_direct (far field); posterior: sample, ranges, forward, lik, post_sample,
-    # post_reduce, post_sort, post_topm
-    launches_per_step = (7 if far_on else 8) * iters + 8
+    # per SVI step: sample, ranges, forward, lik, grad (whose extra block forms the ELBO) and
+    # either bwd_uniform + bwd_near (dense) or bwd_direct (far field); posterior: sample,
+    # ranges, forward, lik, post_sample, post_reduce, post_sort, post_topm
+    launches_per_step = (6 if far_on else 7) * iters + 8
     kern_named = named(kern, far_on)
     share = {k: v / sum(kern_named.values()) for k, v in kern_named.items()}
     out = {
