@@ -54,9 +54,12 @@ REF_STEP_ITERS = 1          # reference-arm step: one oracle SVI step (S = 256)
 #   mixed range, forward: x - p - mu (2), s t, t^2, 1 + t^2, two accumulations
 #                                               -> 7 FP32 + 2 MUFU (rcp, ex2)
 #   mixed range, backward: t (3), t^2, 1 + t^2, g I, q L, q L^2, q L^2 t, q L^2 t^2
-#       and their five sums (Lorentzian part)   -> 14 FP32 + 1 MUFU
-#   Gaussian reach beyond the mixed range: t (2), t^2, accumulate (forward: 4 FP32,
-#       backward: g I G, three sums: 9 FP32), 1 MUFU (ex2)
+#       and their five sums (Lorentzian part)   -> 14 FP32 + 1 MUFU; its Gaussian part,
+#       on the 64-point blocks within the peak's reach: q G, q G t and five sums
+#                                               -> 7 FP32 + 1 MUFU (ex2)
+#   Gaussian reach beyond the mixed range: t (2), t^2, accumulate (forward, every
+#       point: 4 FP32; backward, the blocks within reach: g I G, three sums: 9 FP32),
+#       1 MUFU (ex2)
 #   far field, per (peak, node): x_p - p, t, 1 + t^2, accumulate -> 4 FP32 + 1 MUFU
 #       forward; backward t (2), 1 + t^2, I L, I L^2 and three sums -> 8 FP32 + 1 MUFU
 #   likelihood: the far-field interpolation and node weights, 32 FMAs each per point
@@ -65,7 +68,7 @@ OPS = {
     "direct": {"uniform": (4, 0.5), "mixed": (7, 2), "gauss_reach": (4, 1)},
     "far_fwd": {"far_nodes": (4, 1)},
     "bwd_uniform": {"uniform": (7, 1)},
-    "bwd_near": {"mixed": (14, 1), "gauss_reach": (9, 1)},
+    "bwd_near": {"mixed": (14, 1), "mixed_gauss_bwd": (7, 1), "gauss_reach_bwd": (9, 1)},
     "far_bwd": {"far_nodes": (8, 1)},
 }
 MUFU_LANES = 32
@@ -334,7 +337,8 @@ def kernel_rooflines(kern, work, sms, clock_mhz):
     ops_table = dict(OPS)
     if work["far_nodes"] > 0:   # far field on: node evaluations inside the two direct kernels
         ops_table = {"direct": dict(OPS["direct"], far_nodes=OPS["far_fwd"]["far_nodes"]),
-                     "bwd_uniform": {"uniform": (7, 1), "mixed": (14, 1), "gauss_reach": (9, 1),
+                     "bwd_uniform": {"uniform": (7, 1), "mixed": (14, 1), "mixed_gauss_bwd": (7, 1),
+                                     "gauss_reach_bwd": (9, 1),
                                      "far_nodes": OPS["far_bwd"]["far_nodes"]}}
     out = {}
     slots = kernel_slots(work["far_nodes"] > 0)

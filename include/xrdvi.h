@@ -276,12 +276,16 @@ xrdvi_status xrdvi_profile_steps(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms
  *   (XRDVI_FLAG_DENSE; else ~0), 7 reserved (~0), 8 gradient reduction +
  *   Adam, 9 ELBO
  * (a kernel the configuration does not launch reads ~0; the shared-shape
- * variant's contractions count as 2 and 5).  work (NULL or [4], HOST)
- * receives the last step's evaluation counts, (peak, point) pairs over all
- * samples: 0 direct on side-uniform ranges, 1 on mixed ranges, 2 Gaussian
- * terms beyond the mixed range, 3 far-field (peak, node) pairs (zeros for the
+ * variant's contractions count as 2 and 5).  work (NULL or
+ * [XRDVI_PROFILE_WORK], HOST) receives the last step's evaluation counts,
+ * (peak, point) pairs over all samples: 0 direct on side-uniform ranges, 1 on
+ * mixed ranges, 2 Gaussian terms beyond the mixed range, 3 far-field (peak,
+ * node) pairs; and the Gaussian terms the backward evaluates, which skips a
+ * block of 64 points (a warp's pair of point rows) that lies wholly beyond a
+ * peak's Gaussian reach: 4 on mixed ranges, 5 beyond them (zeros for the
  * shared-shape variant).  Blocks until done.  For measurement only. */
 #define XRDVI_PROFILE_KERNELS 10
+#define XRDVI_PROFILE_WORK 6
 xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *ctx, int32_t steps, float *kernel_ms, int64_t *work);
 
 /* Allocation-free variant of xrdvi_elbo_grad, for callers that may not

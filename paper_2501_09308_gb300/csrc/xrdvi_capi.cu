@@ -1037,7 +1037,7 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms
     c->host_step += steps;
     for (int k = 0; k < nk; ++k) kernel_ms[k] = static_cast<float>(acc[k] / steps);
     if (work) {   // evaluation counts of the last step, from its peak ranges
-        for (int j = 0; j < 4; ++j) work[j] = 0;
+        for (int j = 0; j < XRDVI_PROFILE_WORK; ++j) work[j] = 0;
         if (!W.shared) {
             const size_t nr = static_cast<size_t>(W.S) * P.K * P.T;
             std::vector<ushort4> rg(nr);
@@ -1047,13 +1047,36 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms
             XR_CUDA(cudaMemcpyAsync(rg.data(), W.ranges, nr * sizeof(ushort4), cudaMemcpyDeviceToHost, st));
             if (P.far) XR_CUDA(cudaMemcpyAsync(fr.data(), W.franges, nr * sizeof(ushort2), cudaMemcpyDeviceToHost, st));
             if (ng) XR_CUDA(cudaMemcpyAsync(sr.data(), W.sranges, ng * sizeof(ushort2), cudaMemcpyDeviceToHost, st));
+            // the backward's Gaussian votes: per-(sample, phase) shift and reach,
+            // peak positions and the grid
+            std::vector<PhaseConst> cs(static_cast<size_t>(W.S) * P.K);
+            std::vector<float> xs(P.N), ps(P.Mtot);
+            XR_CUDA(cudaMemcpyAsync(cs.data(), W.cst, cs.size() * sizeof(PhaseConst), cudaMemcpyDeviceToHost, st));
+            XR_CUDA(cudaMemcpyAsync(xs.data(), P.x, xs.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+            XR_CUDA(cudaMemcpyAsync(ps.data(), P.pos, ps.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
             XR_CUDA(cudaStreamSynchronize(st));
+            constexpr int kBlk = 64;   // points of a warp's pair block
             for (size_t id = 0; id < nr; ++id) {
                 const ushort4 r = rg[id];
                 if (r.x == 0xffffu) continue;   // phase absent from this sample's sub-model
                 const int k = static_cast<int>((id / P.T) % P.K);
                 const int64_t me = c->host_off[k + 1] - c->host_off[k];
                 const int64_t m1 = r.x, m2 = r.y, nb = r.z, ne = r.w;
+                {   // pair blocks within a peak's Gaussian reach (p + mu - rl, p + mu + rr)
+                    const PhaseConst &pc = cs[id / P.T];
+                    const int i0 = static_cast<int>(id % P.T) * kTile;
+                    const int mb = c->host_off[k];
+                    for (int64_t m = std::min(nb, m1); m < std::max(ne, m2); ++m) {
+                        const double cen = static_cast<double>(ps[mb + m]) + pc.mu;
+                        int64_t blocks = 0;
+                        for (int q = 0; q < kTile / kBlk; ++q) {
+                            const double xa = xs[std::min(i0 + q * kBlk, P.N - 1)];
+                            const double xb = xs[std::min(i0 + q * kBlk + kBlk - 1, P.N - 1)];
+                            blocks += (xb > cen - pc.rl && xa < cen + pc.rr) ? 1 : 0;
+                        }
+                        work[(m >= m1 && m < m2) ? 4 : 5] += blocks * kBlk;
+                    }
+                }
                 const int64_t fb = P.far ? fr[id].x : 0, fe = P.far ? fr[id].y : me;
                 work[0] += ((m1 - fb) + (fe - m2)) * kTile;
                 work[1] += (m2 - m1) * kTile;

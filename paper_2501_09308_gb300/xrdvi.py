@@ -520,7 +520,7 @@ def xrdvi_get_gates(h):
 
 PROFILE_KERNELS = ("sample", "ranges", "direct", "far_fwd", "lik", "bwd_uniform", "bwd_near", "far_bwd",
                    "grad_adam", "elbo")
-WORK_COUNTS = ("uniform", "mixed", "gauss_reach", "far_nodes")
+WORK_COUNTS = ("uniform", "mixed", "gauss_reach", "far_nodes", "mixed_gauss_bwd", "gauss_reach_bwd")
 
 
 def xrdvi_profile_kernels(h, steps):
