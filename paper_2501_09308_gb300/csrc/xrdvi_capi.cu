@@ -985,15 +985,18 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms
     if (steps < 1) return fail(XRDVI_EINVAL, "steps must be >= 1");
     if (c->host_step + steps > INT32_MAX) return fail(XRDVI_EINVAL, "step counter would overflow");
     constexpr int nk = XRDVI_PROFILE_KERNELS;
-    cudaEvent_t ev[nk + 1];
-    for (auto &e : ev) XR_CUDA(cudaEventCreate(&e));
+    // one set of events per step, read after the last step: the steps run back
+    // to back (no host round trip before a step's first kernel)
+    std::vector<cudaEvent_t> evs(static_cast<size_t>(steps) * (nk + 1));
+    for (auto &e : evs) XR_CUDA(cudaEventCreate(&e));
     double acc[nk] = {};
     cudaStream_t st = c->stream;
     const Problem &P = c->P;
     Workspace &W = c->W;
     const bool naive = (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0;
     xrdvi_status rc = XRDVI_OK;
-    for (int i = 0; i < steps && rc == XRDVI_OK; ++i) {
+    for (int i = 0; i < steps; ++i) {
+        cudaEvent_t *ev = evs.data() + static_cast<size_t>(i) * (nk + 1);
         cudaEventRecord(ev[0], st);
         launch_sample(P, W, c->loc, c->raw, nullptr, c->cfg.seed, 0u, c->step, 0u, c->iter, c->ent, st);
         cudaEventRecord(ev[1], st);
@@ -1022,17 +1025,20 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *c, int32_t steps, float *kernel_ms
         launch_grad(P, W, c->loc, c->raw, nullptr, nullptr, nullptr, false, adam_const(c->cfg), nullptr, nullptr,
                     c->iter, c->step, c->ent, c->elbo, c->trace, st);
         cudaEventRecord(ev[10], st);
-        if (cudaEventSynchronize(ev[nk]) != cudaSuccess) {
-            rc = fail(XRDVI_ECUDA, std::string("profile_kernels: ") + cudaGetErrorString(cudaGetLastError()));
-            break;
-        }
-        for (int k = 0; k < nk; ++k) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-            acc[k] += ms;
+    }
+    if (cudaEventSynchronize(evs.back()) != cudaSuccess) {
+        rc = fail(XRDVI_ECUDA, std::string("profile_kernels: ") + cudaGetErrorString(cudaGetLastError()));
+    } else {
+        for (int i = 0; i < steps; ++i) {
+            const cudaEvent_t *ev = evs.data() + static_cast<size_t>(i) * (nk + 1);
+            for (int k = 0; k < nk; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+                acc[k] += ms;
+            }
         }
     }
-    for (auto &e : ev) cudaEventDestroy(e);
+    for (auto &e : evs) cudaEventDestroy(e);
     if (rc != XRDVI_OK) return rc;
     c->host_step += steps;
     for (int k = 0; k < nk; ++k) kernel_ms[k] = static_cast<float>(acc[k] / steps);
