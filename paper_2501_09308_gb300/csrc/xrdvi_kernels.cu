@@ -951,8 +951,9 @@ __device__ __forceinline__ FarRanges far_ranges(const Ranges &r) {
 // phase's near band [fb, m1), [m2, fe) (a few peaks: t = s (x - p) - s mu per
 // evaluation), its mixed range and its Gaussian reach at the tile's points
 // (the Gaussian at every point of them: beyond its reach 2^-u is exactly 0,
-// and a branch-free loop beats a warp vote per pair block here).  Phase contributions are summed with packed Kahan compensation (all
-// terms are non-negative).  Lane p also sums the phase's far peaks at node p
+// and a branch-free loop beats a warp vote per pair block here).  Phase
+// contributions are summed with packed Kahan compensation (all terms are
+// non-negative).  Lane p also sums the phase's far peaks at node p
 // of the tile (and, for a super-tile's first tile, its super-far peaks at node
 // p of the super-tile), Kahan-compensated over the phases, into the chunk's
 // node partials fnode (fnode2), which k_lik combines and interpolates.
