@@ -543,9 +543,11 @@ __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
 }
 
 // Shared-memory peak table.  Entries hold -p (so that x + (-p) is one packed
-// add) and I.  The wide layout stores each value twice, (-p, -p, I, I), so a
-// single 16-byte load yields both packed pairs; it is used when the table is
-// small enough not to limit occupancy.
+// add) and I.  The wide layout's entry m also holds peak m + 1's values,
+// (-p_m, -p_m+1, I_m, I_m+1), so that a single 16-byte load yields the packed
+// pairs of two consecutive peaks (the far-field loops run two peaks per
+// packed instruction); it is used when the table is small enough not to
+// limit occupancy.
 template <bool kWide>
 struct PeakTable;
 template <>
@@ -555,6 +557,12 @@ struct PeakTable<false> {
         const float2 v = p[m];
         np = bc2(v.x);
         I = bc2(v.y);
+    }
+    // peaks m and m + 1 as packed pairs
+    __device__ __forceinline__ void pair(int m, f2_t &np, f2_t &I) const {
+        const float2 v0 = p[m], v1 = p[m + 1];
+        np = pk2(v0.x, v1.x);
+        I = pk2(v0.y, v1.y);
     }
     __device__ __forceinline__ void scalar(int m, float &np, float &I) const {
         const float2 v = p[m];
@@ -566,6 +574,11 @@ template <>
 struct PeakTable<true> {
     const float4 *p;
     __device__ __forceinline__ void get(int m, f2_t &np, f2_t &I) const {
+        const float4 v = p[m];
+        np = bc2(v.x);
+        I = bc2(v.z);
+    }
+    __device__ __forceinline__ void pair(int m, f2_t &np, f2_t &I) const {
         const float4 v = p[m];
         np = pk2(v.x, v.y);
         I = pk2(v.z, v.w);
@@ -583,8 +596,8 @@ __device__ __forceinline__ PeakTable<kWide> load_table(const ProfArgs &a, float4
     if constexpr (kWide) {
         float4 *q = s_raw;
         for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) {
-            const float np = -a.pos[i], I = a.inten[i];
-            q[i] = make_float4(np, np, I, I);
+            const int j = i + 1 < a.Mtot ? i + 1 : i;
+            q[i] = make_float4(-a.pos[i], -a.pos[j], a.inten[i], a.inten[j]);
         }
         t.p = q;
         s_off = reinterpret_cast<int *>(q + a.Mtot);
@@ -881,12 +894,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_forward(ProfArgs a) {
 template <class Tab, class PC, bool kSec>
 __device__ __forceinline__ float far_node_sum(const Tab &tab, const PC &cp, float x, float cx, int lo0, int hi0,
                                               int lo1, int hi1) {
-    float acc = 0.f;
+    const f2_t x2 = bc2(x), one2 = bc2(1.f);
+    f2_t acc2 = 0ull;   // two peaks per packed instruction
+    float acc = 0.f;    // the odd peak of a range
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         const int m0 = side ? lo1 : lo0, m1 = side ? hi1 : hi0;
         const float sc = side ? cp.sl : cp.sr, cm = side ? cp.nslmu : cp.nsrmu;
-        for (int m = m0; m < m1; ++m) {
+        const f2_t sc2 = bc2(sc), cm2 = bc2(cm);
+        int m = m0;
+        for (; m + 1 < m1; m += 2) {
+            f2_t np2, I2;
+            tab.pair(m, np2, I2);
+            f2_t t2 = fma2(sc2, add2(x2, np2), cm2);
+            if (kSec) t2 = mul2(t2, bc2(cx));
+            acc2 = fma2(I2, rcp2(fma2(t2, t2, one2)), acc2);
+        }
+        if (m < m1) {
             float np, I;
             tab.scalar(m, np, I);
             float t = fmaf(sc, x + np, cm);
@@ -894,7 +918,7 @@ __device__ __forceinline__ float far_node_sum(const Tab &tab, const PC &cp, floa
             acc = fmaf(I, rcp_approx(fmaf(t, t, 1.f)), acc);
         }
     }
-    return acc;
+    return acc + sum2(acc2);
 }
 
 // One phase's far gradient sums at this lane's node (weight w, w cos(x/2) for
@@ -904,14 +928,29 @@ template <class Tab, class PC, bool kSec>
 __device__ __forceinline__ void far_node_grad(const Tab &tab, const PC &cp, float x, float cx, float w, float wa,
                                               int lo0, int hi0, int lo1, int hi1, float &S1, float (&A)[2],
                                               float (&B)[2]) {
+    const f2_t x2 = bc2(x), one2 = bc2(1.f);
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         const int m0 = side ? lo1 : lo0, m1 = side ? hi1 : hi0;
         if (m0 >= m1) continue;
         const float sc = side ? cp.sl : cp.sr, cm = side ? cp.nslmu : cp.nsrmu;
-        float s1 = 0.f, an = 0.f, c2 = 0.f;
-#pragma unroll 2
-        for (int m = m0; m < m1; ++m) {
+        const f2_t sc2 = bc2(sc), cm2 = bc2(cm);
+        f2_t s1p = 0ull, anp = 0ull, c2p = 0ull;   // two peaks per packed instruction
+        int m = m0;
+        for (; m + 1 < m1; m += 2) {
+            f2_t np2, I2;
+            tab.pair(m, np2, I2);
+            f2_t t2 = fma2(sc2, add2(x2, np2), cm2);
+            if (kSec) t2 = mul2(t2, bc2(cx));
+            const f2_t L2 = rcp2(fma2(t2, t2, one2));
+            const f2_t q1 = mul2(I2, L2);
+            s1p = add2(s1p, q1);
+            const f2_t q2 = mul2(q1, L2);
+            anp = fma2(q2, t2, anp);
+            c2p = add2(c2p, q2);
+        }
+        float s1 = sum2(s1p), an = sum2(anp), c2 = sum2(c2p);
+        if (m < m1) {   // the odd peak
             float np, I;
             tab.scalar(m, np, I);
             float t = fmaf(sc, x + np, cm);
