@@ -123,3 +123,27 @@ def test_angle_dependent_width_needs_angles_below_174_degrees():
         xrdvi.xrdvi_create(a["offsets"], a["pos"], a["inten"], a["x"], a["y"], a["bg"],
                            xrdvi.xrdvi_config_default(flags=xrdvi.FLAG_SEC_WIDTH))
     assert e.value.status == 1
+
+
+def header_macros():
+    out = {}
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            for name, val in re.findall(r"^#define\s+(XRDVI_\w+)\s+\(?([0-9u <]+)\)?", open(os.path.join(inc, fn)).read(),
+                                        flags=re.M):
+                v = val.replace("u", "").strip()
+                out[name] = eval(v, {"__builtins__": {}}) if "<<" in v else int(v)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Flags and the profiler's array sizes are the header's values: a
+    mismatch would pass wrong options or under-sized buffers across the ABI."""
+    m = header_macros()
+    flags = {k[len("XRDVI_"):]: v for k, v in m.items() if k.startswith("XRDVI_FLAG_")}
+    assert len(flags) >= 13
+    for name, v in flags.items():
+        assert getattr(xrdvi, name) == v, name
+    assert m["XRDVI_PROFILE_KERNELS"] == len(xrdvi.PROFILE_KERNELS)
+    assert m["XRDVI_PROFILE_WORK"] == len(xrdvi.WORK_COUNTS)
