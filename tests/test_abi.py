@@ -126,14 +126,16 @@ def test_angle_dependent_width_needs_angles_below_174_degrees():
 
 
 def header_macros():
+    """Integer macros of include/*.h (literals, shifts and products only)."""
     out = {}
     inc = os.path.join(ROOT, "include")
     for fn in os.listdir(inc):
         if fn.endswith(".h"):
-            for name, val in re.findall(r"^#define\s+(XRDVI_\w+)\s+\(?([0-9u <]+)\)?", open(os.path.join(inc, fn)).read(),
-                                        flags=re.M):
-                v = val.replace("u", "").strip()
-                out[name] = eval(v, {"__builtins__": {}}) if "<<" in v else int(v)
+            text = open(os.path.join(inc, fn)).read()
+            for name, body in re.findall(r"^#define\s+(XRDVI_\w+)\s+([^/\n]*)", text, flags=re.M):
+                expr = re.sub(r"(\d+)[uUlL]+", r"\1", body.strip())
+                if expr and re.fullmatch(r"[0-9()<* ]+", expr):
+                    out[name] = eval(expr, {"__builtins__": {}})
     return out
 
 
@@ -147,3 +149,4 @@ def test_binding_constants_match_the_header():
         assert getattr(xrdvi, name) == v, name
     assert m["XRDVI_PROFILE_KERNELS"] == len(xrdvi.PROFILE_KERNELS)
     assert m["XRDVI_PROFILE_WORK"] == len(xrdvi.WORK_COUNTS)
+    assert m["XRDVI_STATIC_SCRATCH_BYTES"] == 32 << 20
