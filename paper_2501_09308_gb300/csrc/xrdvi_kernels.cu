@@ -66,20 +66,10 @@ __device__ __forceinline__ float softplusf(float x) {
     return x > 0.f ? x + log1pf(expf(-x)) : log1pf(expf(x));
 }
 
-__device__ __forceinline__ double softplusd(double x) {
-    return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x));
-}
-
 __device__ __forceinline__ float sigmoidf(float x) {
     if (x >= 0.f) return 1.f / (1.f + expf(-x));
     const float e = expf(x);
     return e / (1.f + e);
-}
-
-__device__ __forceinline__ double sigmoidd(double x) {
-    if (x >= 0.0) return 1.0 / (1.0 + exp(-x));
-    const double e = exp(x);
-    return e / (1.0 + e);
 }
 
 // Area of the unit-height split pseudo-Voigt of FWHM w (left) and alpha w
