@@ -296,27 +296,43 @@ xrdvi_status xrdvi_profile_kernels(xrdvi_ctx *ctx, int32_t steps, float *kernel_
  * has no counterpart; this is an interface convenience.
  *
  * Inputs (DEVICE pointers, caller-owned): the peak table in CSR form
- * (d_offsets [K+1], d_pos / d_inten [M_total], any peak order), the pattern
- * (d_x, d_y, d_bg [N], validated as by xrdvi_create), d_loc / d_raw [K*5],
- * d_eps [S*K*5] standard normals; cfg (HOST) gives S, the priors, alpha_min
- * and flags (XRDVI_FLAG_IW_ELBO: EINVAL).  data_const = sum_i [y ln y - y -
- * ln y!] (with XRDVI_FLAG_GAUSS_LIK: -sum_i ln(2 pi max(y_i, 1)) / 2) and
- * lambda_ = 1 / max(Y - B) are the values xrdvi_create derives from the
- * pattern (xrdvi_get_info reports both).  Outputs (DEVICE): d_elbo [1] (double),
+ * (d_offsets [K+1], d_pos / d_inten [M_total], peaks in any order within a
+ * phase: the call sorts each phase by position into its scratch, a stable
+ * sort like xrdvi_create's), the pattern (d_x, d_y, d_bg [N]), d_loc / d_raw
+ * [K*5], d_eps [S*K*5] standard normals; cfg (HOST) gives S, the priors,
+ * alpha_min and flags.  Accepted flags: XRDVI_FLAG_BF16_INT (intensities
+ * rounded to bfloat16 on the device, as xrdvi_create rounds them on the host),
+ * XRDVI_FLAG_NAIVE_SUM, XRDVI_FLAG_GAUSS_LIK, XRDVI_FLAG_DENSE (the profile
+ * is always evaluated with every peak at every point here); IW_ELBO,
+ * SHARED_SHAPES, SEC_WIDTH, FIT_BACKGROUND, FIX_R, FIX_ALPHA, AREA_NORM, GATES
+ * and DEVICE_PTRS give EINVAL.  data_const = sum_i [y ln y - y - ln y!] (with
+ * XRDVI_FLAG_GAUSS_LIK: -sum_i ln(2 pi max(y_i, 1)) / 2) and lambda_ =
+ * 1 / max(Y - B) are the values xrdvi_create derives from the pattern
+ * (xrdvi_get_info reports both).  Outputs (DEVICE): d_elbo [1] (double),
  * d_grad [K*10] (float), written asynchronously on cuda_stream (a
  * cudaStream_t; NULL is the legacy default stream).
+ *
+ * Validation: sizes, pointers, flags and the scratch size are checked on the
+ * host (EINVAL before any work).  The device arrays are checked on the device,
+ * before any kernel indexes with them, against the rules of xrdvi_create
+ * (offsets[0] = 0, offsets[K] = M_total, every phase non-empty; positions in
+ * (0, 180); intensities in [0, 1]; x strictly increasing in (0, 180); y
+ * non-negative integers; bg finite and >= 0).  Since the call does not wait
+ * for the GPU, a violation cannot change the returned status: it makes
+ * *d_elbo and every d_grad entry NaN instead (lambda_ and data_const are the
+ * caller's and are not re-derived).
  *
  * Scratch: one file-scope device array of XRDVI_STATIC_SCRATCH_BYTES
  * (32 MiB), which every GPU that loads the library holds until the process
  * exits.  A problem needing more (48*S*K*T + 2056*S*T + 104*S*K + 16*S +
- * 1284*K bytes with T = ceil(N/256), plus 256-byte alignment of each of its 14
- * arrays) is rejected with EINVAL before any work.
- * The first call on a device looks up the array's device address (a one-time
- * set-up per device); make that first call before any stream capture.  All
- * calls share the one array and it keeps the last call's contents (every
- * element is rewritten before use, nothing needs clearing): calls that
- * overlap on the GPU — on different streams, or from different threads —
- * race, so serialise them. */
+ * 1416*K + 8*M_total + 32 bytes with T = ceil(N/256), plus up to 255 bytes of
+ * alignment for each of its 18 arrays) is rejected with EINVAL before any
+ * work.  The first call on a device looks up the array's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (every element is rewritten before use, nothing needs clearing):
+ * calls that overlap on the GPU — on different streams, or from different
+ * threads — race, so serialise them. */
 #define XRDVI_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 xrdvi_status xrdvi_elbo_grad_static(int32_t K, int32_t M_total, const int32_t *d_offsets,
                                     const float *d_pos, const float *d_inten, int32_t N,
@@ -456,6 +472,16 @@ xrdvi_status xrdvi_get_background(xrdvi_ctx *ctx, float *beta, float *bg_curve, 
  * ETIMEOUT if a pipeline wait gave up.  No counterpart in the paper. */
 xrdvi_status xrdvi_gemm_nt_tf32x3(int32_t M, int32_t N, int32_t K, const float *d_A, int32_t lda,
                                   const float *d_B, int32_t ldb, float *d_C, int32_t ldc, void *cuda_stream);
+
+/* The Monte-Carlo noise generator, exported for known-answer tests: Philox4x32
+ * with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11), run on the GPU by the
+ * same device function that draws every sample's normals (Box-Muller of the
+ * top 24 bits of each word; the reparameterised draw of Sec. 3.2).  Block i
+ * takes counter ctr[4i..4i+3] and key key[2i..2i+1] and writes out[4i..4i+3]
+ * (HOST arrays, caller-owned).  0 <= n <= 2^20 (EINVAL otherwise).  Allocates
+ * and frees a small device buffer on a private stream; blocks until done.
+ * No counterpart in the paper, which does not name its generator. */
+xrdvi_status xrdvi_philox4x32_10(int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *xrdvi_last_error(void);

@@ -1220,6 +1220,30 @@ xrdvi_status xrdvi_get_background(xrdvi_ctx *c, float *beta, float *bg_curve, fl
     return XRDVI_OK;
 }
 
+xrdvi_status xrdvi_philox4x32_10(int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+    if (n < 0 || n > (1 << 20)) return fail(XRDVI_EINVAL, "n must be in [0, 2^20]");
+    if (n == 0) return XRDVI_OK;
+    if (!ctr || !key || !out) return fail(XRDVI_EINVAL, "null argument");
+    cudaStream_t s = nullptr;
+    XR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    uint32_t *d = nullptr;
+    const size_t nw = static_cast<size_t>(n) * 10;   // counters 4n, keys 2n, output 4n
+    cudaError_t e = cudaMallocAsync(&d, nw * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, ctr, 16 * static_cast<size_t>(n), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 4 * n, key, 8 * static_cast<size_t>(n), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        launch_philox_words(n, d, d + 4 * n, d + 6 * n, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 6 * n, 16 * static_cast<size_t>(n), cudaMemcpyDeviceToHost, s);
+    if (d) cudaFreeAsync(d, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("philox4x32_10: ") + cudaGetErrorString(e));
+    return XRDVI_OK;
+}
+
 xrdvi_status xrdvi_get_info(xrdvi_ctx *c, xrdvi_info *info) {
     if (!c || !info) return fail(XRDVI_EINVAL, "null argument");
     info->K = c->P.K;

@@ -256,6 +256,9 @@ xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, co
 // order (one block).
 void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st);
 
+// Philox4x32-10 blocks of n (counter [4], key [2]) pairs, device arrays.
+void launch_philox_words(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
+
 // Fitted-background variant: B(beta) for the step (before the likelihood),
 // and after the gradient sums the beta gradient (weights 1/S or the
 // importance weights) with Adam on beta (adam) or written to grad_out [3].

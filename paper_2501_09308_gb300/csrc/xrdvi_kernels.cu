@@ -2436,6 +2436,23 @@ void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m,
 
 
 namespace {
+// Raw Philox4x32-10 blocks through the same device function the sampling
+// kernel draws its noise with (exported for known-answer tests).
+__global__ void k_philox_words(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[4 * i + j] = c[j];
+}
+}  // namespace
+
+void launch_philox_words(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st) {
+    if (n > 0) k_philox_words<<<(n + 127) / 128, 128, 0, st>>>(n, ctr, key, out);
+}
+
+namespace {
 // Normalised log-probabilities of enumerated combinations: logp = elbo -
 // logsumexp(elbo), FP64, strided per-thread partials combined by a fixed
 // tree (one block, deterministic).

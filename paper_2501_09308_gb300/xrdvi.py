@@ -16,7 +16,8 @@ import numpy as np
 
 from . import build as _build
 
-STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EBUSY"}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EBUSY",
+          7: "ECANCELED"}
 FLAG_BF16_INT = 1 << 0
 FLAG_NAIVE_SUM = 1 << 1
 FLAG_GAUSS_LIK = 1 << 2   # Gaussian likelihood, variance max(y, 1)
@@ -127,6 +128,7 @@ SIGNATURES = {
     "xrdvi_gemm_nt_tf32x3": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp]),
     "xrdvi_get_background": (ctypes.c_int, [_vp, P(_f), P(_f), P(_f)]),
     "xrdvi_get_gates": (ctypes.c_int, [_vp, P(_f), P(_f)]),
+    "xrdvi_philox4x32_10": (ctypes.c_int, [_i32, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -319,6 +321,19 @@ def xrdvi_profile_steps(h, steps):
     ms = np.zeros(5, dtype=np.float32)
     _check(lib().xrdvi_profile_steps(h, int(steps), _ptr(ms, _f)))
     return dict(zip(KERNELS, ms.astype(float)))
+
+
+def xrdvi_philox4x32_10(ctr, key):
+    """Philox4x32-10 blocks computed on the GPU: ctr [n, 4], key [n, 2] (uint32)
+    -> [n, 4] uint32."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    if len(c) != len(k):
+        raise ValueError("one key per counter")
+    out = np.zeros_like(c)
+    u32 = ctypes.c_uint32
+    _check(lib().xrdvi_philox4x32_10(len(c), _ptr(c, u32), _ptr(k, u32), _ptr(out, u32)))
+    return out
 
 
 def xrdvi_version() -> str:

@@ -106,6 +106,41 @@ def test_peaks_outside_grid_and_zero_counts():
     assert_parity(g, o)
 
 
+def _shuffled_within_phases(inst, seed):
+    rng = np.random.default_rng(seed)
+    pos, inten = inst.pos.copy(), inst.inten.copy()
+    for k in range(inst.K):
+        a, b = inst.offsets[k], inst.offsets[k + 1]
+        perm = rng.permutation(b - a) + a
+        pos[a:b], inten[a:b] = inst.pos[perm], inst.inten[perm]
+    # equal positions inside a phase exercise the stable order of the sort
+    pos[inst.offsets[0] + 1] = pos[inst.offsets[0]]
+    assert np.any(np.diff(pos) < 0)
+    return synth.Instance(**{**inst.__dict__, "pos": pos, "inten": inten})
+
+
+@pytest.mark.parametrize("device_arrays", [False, True])
+def test_unsorted_peak_tables_match_the_oracle(device_arrays):
+    """The candidate list of a phase is an unordered set of (p_m, I_m) pairs
+    (App. A.1): xrdvi_create sorts each phase itself, from host arrays and from
+    device arrays (XRDVI_FLAG_DEVICE_PTRS), and the result matches the oracle
+    (whose direct sums do not depend on the order) element by element."""
+    import torch
+    inst = _shuffled_within_phases(synth.small_problem(K=6, M=15, N=1100, S=6, seed=21), 21)
+    if device_arrays:
+        d = [torch.tensor(a, device="cuda") for a in (inst.offsets, inst.pos, inst.inten, inst.x, inst.y, inst.bg)]
+        ctx = xrdvi.Context.from_device(inst.K, inst.N, *[t.data_ptr() for t in d], S=6)
+    else:
+        ctx = xrdvi.Context.from_instance(inst, S=6)
+    loc, raw = perturbed_params(ctx, 21)
+    eps = synth.normals(1021, 6, inst.K)
+    g = ctx.elbo_grad(eps, want_f=True)
+    ctx.close()
+    o = oracle.Problem.from_instance(inst).elbo_grad(loc.astype(np.float64), raw.astype(np.float64),
+                                                    eps.astype(np.float64), want_f=True)
+    assert_parity(g, o)
+
+
 def test_alpha_below_clamp():
     inst = synth.small_problem(K=2, M=5, N=300, S=4, seed=12)
     ctx = xrdvi.Context.from_instance(inst, S=4)
@@ -140,6 +175,28 @@ def test_philox_noise_matches_oracle_stream():
     for b in range(10):
         ref = np.max(np.abs(g_inj["grad"][:, b]))
         assert np.max(np.abs(g_rng["grad"][:, b] - g_inj["grad"][:, b])) <= 1e-4 * ref
+
+
+def test_gpu_philox_matches_published_known_answers():
+    """The device generator that draws the fit's noise reproduces the
+    published Philox4x32-10 known-answer vectors (Salmon et al., SC'11;
+    tests/golden/philox4x32_10_kat.json), bit for bit, and agrees with the
+    oracle's generator on a spread of counters and keys."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.json")
+    vecs = json.load(open(path))["vectors"]
+    h = lambda ws: [int(w, 16) for w in ws]
+    ctr = np.array([h(v["counter"]) for v in vecs], dtype=np.uint32)
+    key = np.array([h(v["key"]) for v in vecs], dtype=np.uint32)
+    out = xrdvi.xrdvi_philox4x32_10(ctr, key)
+    np.testing.assert_array_equal(out, np.array([h(v["output"]) for v in vecs], dtype=np.uint32))
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, size=(300, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(300, 2), dtype=np.uint64).astype(np.uint32)
+    out = xrdvi.xrdvi_philox4x32_10(ctr, key)
+    ref = np.array([oracle.philox(c.tolist(), k.tolist()) for c, k in zip(ctr, key)], dtype=np.uint32)
+    np.testing.assert_array_equal(out, ref)
 
 
 def test_adam_steps_match_oracle():

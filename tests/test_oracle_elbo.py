@@ -1,6 +1,8 @@
 """Pins of the oracle's Monte-Carlo ELBO, gradient, optimiser and noise stream
 (no GPU)."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -136,6 +138,36 @@ def test_adam_step_matches_torch():
         tp.grad = torch.tensor(-g)
         opt.step()
         np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def _philox_kat():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.json")
+    with open(path) as fh:
+        vecs = json.load(fh)["vectors"]
+    h = lambda ws: [int(w, 16) for w in ws]
+    return [(h(v["counter"]), h(v["key"]), h(v["output"])) for v in vecs]
+
+
+def test_philox_matches_published_known_answers():
+    """The oracle's Philox4x32-10 reproduces the generator authors' published
+    known-answer vectors (Salmon et al., SC'11): a wrong round count, multiplier,
+    Weyl constant or word order fails here."""
+    for ctr, key, out in _philox_kat():
+        assert list(oracle.philox(ctr, key)) == out, (ctr, key)
+
+
+def test_first_normals_of_seed_zero_follow_from_the_zero_vector():
+    """Seed 0, sample 0, phase 0, step 0, fit stream: the first Philox block is
+    the all-zero known-answer vector, so the first two normals are the
+    Box-Muller pair of its first two words (top 24 bits, centred)."""
+    ctr, key, out = _philox_kat()[0]
+    assert ctr == [0, 0, 0, 0] and key == [0, 0]
+    u1 = ((out[0] >> 8) + 0.5) / 2.0 ** 24
+    u2 = ((out[1] >> 8) + 0.5) / 2.0 ** 24
+    z = oracle.normals(0, 0, 0, 1, 1).ravel()
+    r = math.sqrt(-2.0 * math.log(u1))
+    assert z[0] == pytest.approx(r * math.cos(2 * math.pi * u2), rel=1e-14)
+    assert z[1] == pytest.approx(r * math.sin(2 * math.pi * u2), rel=1e-14)
 
 
 def test_philox_noise_is_standard_normal_and_counter_keyed():
