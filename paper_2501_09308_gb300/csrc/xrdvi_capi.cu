@@ -434,6 +434,54 @@ xrdvi_status batch_tail_sums(xrdvi_ctx *c, double *host) {
 }
 }  // namespace xrdvi
 
+namespace xrdvi {
+// Access to a context's device state for the continuous-batching server.
+void ctx_fit_step(xrdvi_ctx *c, FitStep *out) {
+    out->P = &c->P;
+    out->W = &c->W;
+    out->loc = c->loc;
+    out->raw = c->raw;
+    out->m = c->m;
+    out->v = c->v;
+    out->iter = c->iter;
+    out->step = c->step;
+    out->ent = c->ent;
+    out->elbo = c->elbo;
+    out->trace = c->trace;
+    out->seed = c->cfg.seed;
+    out->ac = adam_const(c->cfg);
+}
+
+bool ctx_multi_eligible(const xrdvi_ctx *c) {
+    return multi_fit_eligible(c->P, c->W, (c->cfg.flags & XRDVI_FLAG_NAIVE_SUM) != 0,
+                              (c->cfg.flags & XRDVI_FLAG_IW_ELBO) != 0);
+}
+
+void ctx_enqueue_steps(xrdvi_ctx *c, int n, cudaStream_t st) {
+    for (int i = 0; i < n; ++i) enqueue_step(c, st);
+}
+
+void ctx_advance(xrdvi_ctx *c, int n) { c->host_step += n; }
+
+cudaStream_t ctx_stream(const xrdvi_ctx *c) { return c->stream; }
+
+// The ELBO estimates of the last n steps (host copy; synchronises the
+// context's stream) and the last one's finiteness.
+xrdvi_status ctx_read_trace(xrdvi_ctx *c, int n, double *host) {
+    if (n <= 0) return XRDVI_OK;
+    const int64_t s0 = c->host_step - n;
+    for (int done = 0; done < n;) {
+        const int64_t a = (s0 + done) & (kTraceCap - 1);
+        const int64_t len = std::min<int64_t>(n - done, kTraceCap - a);
+        XR_CUDA(cudaMemcpyAsync(host + done, c->trace + a, len * 8, cudaMemcpyDeviceToHost, c->stream));
+        done += static_cast<int>(len);
+    }
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(host[n - 1])) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
+    return XRDVI_OK;
+}
+}  // namespace xrdvi
+
 extern "C" {
 
 const char *xrdvi_last_error(void) { return g_err.c_str(); }

@@ -42,6 +42,14 @@ constexpr int kCounters = 4;
 // Sample blocks per phase in the gradient reduction.
 constexpr int kGradBlocks = 16;
 
+// Fits one multi-fit launch can hold (continuous batching), and the block
+// ranges of the fits in one such launch: fit f owns blocks [start[f], start[f+1]).
+constexpr int kMaxBatch = 64;
+struct FitMap {
+    int n = 0;
+    int start[kMaxBatch + 1] = {0};
+};
+
 // The Gaussian component 2^-u of a peak is evaluated only for warps with a
 // point inside the peak's reach u < kGaussU; beyond it 2^-u < 2^-128, which
 // flushes to zero in single precision anyway.
@@ -248,6 +256,39 @@ xrdvi_status create_batch_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt
 xrdvi_status batch_set_tail(xrdvi_ctx *c, int tail_start);
 // Copies the nsub tail sums (FP64) to host memory.
 xrdvi_status batch_tail_sums(xrdvi_ctx *c, double *host);
+
+// Continuous batching: one SVI step of several fits in the same launches
+// (six kernels for the whole batch).  FitStep names a fit's device state;
+// only fits that run the plain far-field step qualify (multi_fit_eligible):
+// no shared shapes, angle-dependent width, fitted background, naive sums,
+// importance weights or sub-model batches.
+struct FitStep {
+    const Problem *P = nullptr;
+    Workspace *W = nullptr;
+    float *loc = nullptr, *raw = nullptr, *m = nullptr, *v = nullptr;
+    int *iter = nullptr, *step = nullptr;
+    double *ent = nullptr, *elbo = nullptr, *trace = nullptr;
+    uint64_t seed = 0;
+    AdamConst ac{};
+};
+struct MultiStepPlan;
+MultiStepPlan *multi_plan_create(int cap);   // device argument storage for cap <= kMaxBatch fits
+void multi_plan_destroy(MultiStepPlan *p);
+bool multi_fit_eligible(const Problem &P, const Workspace &W, bool naive, bool iw);
+// Builds the batch's kernel arguments and block maps and uploads them on st
+// (stream-ordered after the steps already queued there).
+bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, cudaStream_t st);
+// Enqueues one SVI step (sample, ranges, profile, likelihood, backward,
+// gradient + Adam + ELBO) of every fit of the plan.
+void multi_plan_launch_step(const MultiStepPlan *p, cudaStream_t st);
+
+// Context access for the continuous-batching server (xrdvi_capi.cu).
+void ctx_fit_step(xrdvi_ctx *c, FitStep *out);
+bool ctx_multi_eligible(const xrdvi_ctx *c);
+void ctx_enqueue_steps(xrdvi_ctx *c, int n, cudaStream_t st);   // n fit steps, kernel by kernel
+void ctx_advance(xrdvi_ctx *c, int n);                          // host step counter += n
+cudaStream_t ctx_stream(const xrdvi_ctx *c);
+xrdvi_status ctx_read_trace(xrdvi_ctx *c, int n, double *host);  // last n ELBO estimates
 
 // Host validation of a problem and config (the checks of xrdvi_create).
 xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg);

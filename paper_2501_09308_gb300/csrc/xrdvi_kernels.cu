@@ -17,6 +17,8 @@
 #include <math_constants.h>
 
 #include <cstdint>
+#include <cstring>
+#include <vector>
 
 #include "xrdvi_internal.h"
 
@@ -160,9 +162,22 @@ struct SampleArgs {
     float pr_lambda, pr_mu_isd, pr_alpha_mean, pr_alpha_isd, pr_wsm1, pr_wrate;
 };
 
-__global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
+// Block indices of a kernel body: the launch's own (re-read from the special
+// register wherever used, which keeps register pressure as in a plain kernel)
+// or a fixed value (a block of a multi-fit launch, relative to its fit).
+struct GridBlock {
+    __device__ __forceinline__ int x() const { return static_cast<int>(blockIdx.x); }
+    __device__ __forceinline__ int y() const { return static_cast<int>(blockIdx.y); }
+};
+struct FixedBlock {
+    int bx, by;
+    __device__ __forceinline__ int x() const { return bx; }
+    __device__ __forceinline__ int y() const { return by; }
+};
+
+// Draw s of one sample set (one block of 128 threads per draw).
+__device__ __forceinline__ void sample_body(const SampleArgs &a, int s) {
     __shared__ double sh[4];
-    const int s = blockIdx.x;
     const uint32_t step = a.d_step ? static_cast<uint32_t>(*a.d_step) : a.step;
     if (s == 0 && threadIdx.x == 0) {
         if (a.d_iter) *a.d_iter = static_cast<int>(step);
@@ -343,6 +358,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(128) k_sample(SampleArgs a) { sample_body(a, blockIdx.x); }
+
 // ---------------------------------------------------------------------------
 // Profile kernels
 // ---------------------------------------------------------------------------
@@ -485,9 +502,9 @@ __device__ __forceinline__ int first_beyond(const float *pos, int lo, int hi, fl
 
 // Peak index ranges of every (sample, phase, tile):
 //   [mb, m1) all d > 0,  [m1, m2) mixed,  [m2, me) all d < 0,  [nb, ne) Gaussian reach.
-__global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
+__device__ __forceinline__ void ranges_body(const ProfArgs &a, int vb, int vgrid) {
     const int total = a.S * a.K * a.T;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    for (int idx = vb * blockDim.x + threadIdx.x; idx < total; idx += vgrid * blockDim.x) {
         const int tile = idx % a.T;
         const int sk = idx / a.T;
         const int k = sk % a.K;
@@ -531,6 +548,8 @@ __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) {
         }
     }
 }
+
+__global__ void __launch_bounds__(256) k_ranges(ProfArgs a) { ranges_body(a, blockIdx.x, gridDim.x); }
 
 // Shared-memory peak table.  Entries hold -p (so that x + (-p) is one packed
 // add) and I.  The wide layout's entry m also holds peak m + 1's values,
@@ -987,10 +1006,7 @@ __device__ __forceinline__ FarRanges far_ranges(const Ranges &r) {
 // p of the super-tile), Kahan-compensated over the phases, into the chunk's
 // node partials fnode (fnode2), which k_lik combines and interpolates.
 template <bool kNaive, bool kWide, bool kSec>
-__global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
-    extern __shared__ float4 s_raw[];
-    int *s_off;
-    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+__device__ __forceinline__ void fwd_direct_items(const ProfArgs &a, const PeakTable<kWide> &tab, const int *s_off) {
     const int lane = threadIdx.x & 31;
     const f2_t one2 = bc2(1.f);
     const int items = a.S * a.T * a.C;
@@ -1107,6 +1123,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
     }
 }
 
+template <bool kNaive, bool kWide, bool kSec>
+__global__ void __launch_bounds__(kThreads, 3) k_fwd_direct(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    fwd_direct_items<kNaive, kWide, kSec>(a, tab, s_off);
+}
+
 // Poisson log-likelihood term minus its data constant, D(y, f) =
 // y ln(f / y) - (f - y) (= -f for y = 0).  Near f = y it is evaluated by the
 // series of Loader (2000, "Fast and accurate computation of binomial
@@ -1131,10 +1155,12 @@ __device__ __forceinline__ float deviance_term(float y, float f) {
 // and the per-tile deviance sum (all terms <= 0: an FP32 tree sum without
 // cancellation, stored in FP64).  One block per (sample, tile);
 // kTile == blockDim.x.
-__global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
+template <class Blk>
+__device__ __forceinline__ void lik_body(const ProfArgs &a, Blk blk) {
     __shared__ float shf[kTile / 32];
     __shared__ float sFn[kFarNodes], sF2[kFarNodes];
-    const int s = blockIdx.x / a.T, tile = blockIdx.x - s * a.T;
+    // unsigned division (the indices are non-negative; cheaper than the signed form)
+    const int s = static_cast<int>(static_cast<unsigned>(blk.x()) / static_cast<unsigned>(a.T)), tile = blk.x() - s * a.T;
     const int i = tile * kTile + threadIdx.x;
     float dev = 0.f;
     float gv = 0.f;
@@ -1227,7 +1253,7 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
         float t = 0.f;
 #pragma unroll
         for (int ww = 0; ww < kTile / 32; ++ww) t += shw[ww][l];
-        if (w == 0) a.wfar[static_cast<size_t>(blockIdx.x) * kFarNodes + l] = t;
+        if (w == 0) a.wfar[static_cast<size_t>(blk.x()) * kFarNodes + l] = t;
         if (a.wfar2) {
             // this tile's part of the super-tile's node weights, sum_p Mb[t][p][P] W_t,p
             // at lane P: warp w takes nodes p of [w n, (w + 1) n), the sum of the parts
@@ -1250,7 +1276,7 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
             float w2 = 0.f;
 #pragma unroll
             for (int ww = 0; ww < kTile / 32; ++ww) w2 += sW2[ww][threadIdx.x];
-            a.wfar2[static_cast<size_t>(blockIdx.x) * kFarNodes + threadIdx.x] = w2;
+            a.wfar2[static_cast<size_t>(blk.x()) * kFarNodes + threadIdx.x] = w2;
         }
     }
     if (a.Tb) {   // fitted background: d LL / d beta_j = sum_i g_i B_i(beta) T_j(z_i), per tile
@@ -1277,6 +1303,8 @@ __global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) {
         }
     }
 }
+
+__global__ void __launch_bounds__(kTile) k_lik(ProfArgs a) { lik_body(a, GridBlock()); }
 
 // --- backward -----------------------------------------------------------------
 // Gradient sums per (sample, phase, tile), with q = (y/f - 1) I:
@@ -1555,10 +1583,7 @@ __device__ __forceinline__ void warp_reduce_scatter16(V (&v)[16], int lane) {
 // weighted by W2_p, which k_grad attributes to the phase like any tile's),
 // reduced once and written to gpart.
 template <bool kWide, bool kSec>
-__global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
-    extern __shared__ float4 s_raw[];
-    int *s_off;
-    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+__device__ __forceinline__ void bwd_direct_items(const ProfArgs &a, const PeakTable<kWide> &tab, const int *s_off) {
     const int lane = threadIdx.x & 31;
     const f2_t one2 = bc2(1.f);
     const int items = a.S * a.T * a.C;
@@ -1660,6 +1685,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
     }
 }
 
+template <bool kWide, bool kSec>
+__global__ void __launch_bounds__(kThreads, 3) k_bwd_direct(ProfArgs a) {
+    extern __shared__ float4 s_raw[];
+    int *s_off;
+    const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+    bwd_direct_items<kWide, kSec>(a, tab, s_off);
+}
+
 // ---------------------------------------------------------------------------
 // Gradient reduction + Adam + ELBO
 // ---------------------------------------------------------------------------
@@ -1750,11 +1783,12 @@ __global__ void __launch_bounds__(256) k_elbo(GradArgs a) { elbo_block(a, blockI
 // are combined by a fixed shuffle tree.  The last block of the phase to
 // arrive adds the block totals in a fixed order (deterministic) and applies
 // Adam.
-__global__ void __launch_bounds__(256) k_grad(GradArgs a) {
+template <class Blk>
+__device__ __forceinline__ void grad_body(const GradArgs &a, Blk blk) {
     __shared__ float qs[32][kGradSums + 1];
     __shared__ double red[kGredVals];
     __shared__ int is_last;
-    const int bk = blockIdx.x, b = blockIdx.y;   // (sub-model, phase), sample block
+    const int bk = blk.x(), b = blk.y();   // (sub-model, phase), sample block
     if (a.elbo_blocks && bk >= a.B * a.K) {   // extra blocks: the ELBO of sub-model bk - B K, beside the gradient
         if (b == 0) elbo_block(a, bk - a.B * a.K);
         return;
@@ -1930,6 +1964,92 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
                 a.raw_out[bk * 5 + j] = static_cast<float>(rw - step);
             }
         }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_grad(GradArgs a) { grad_body(a, GridBlock()); }
+
+// ---------------------------------------------------------------------------
+// Multi-fit step kernels (continuous batching of fits of different K and N):
+// one launch runs one SVI-step kernel for every fit of a batch.  Fit f owns
+// the blocks [start[f], start[f+1]) of the per-fit grid (sampling, ranges,
+// likelihood, gradient); its arguments are staged in shared memory and the
+// per-fit body runs on block indices relative to the fit.  The two profile
+// kernels are persistent over all fits: a block starts on the fit its index
+// falls in and then helps the others, re-staging the peak table for each fit
+// it visits; each fit's items come from that fit's own work counter.  Every
+// fit's work items and reductions are those of its standalone kernels, so a
+// fit's result does not depend on the batch it runs in.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int fit_of_block(const FitMap &m, int b) {
+    int lo = 0, hi = m.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (m.start[mid] <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Copies one fit's arguments into shared memory (ends with a barrier).
+template <class T>
+__device__ __forceinline__ void stage_args(T &dst, const T &src) {
+    static_assert(sizeof(T) % 4 == 0, "argument blocks are whole words");
+    const int *q = reinterpret_cast<const int *>(&src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(T) / 4); i += blockDim.x) d[i] = q[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_sample_multi(const SampleArgs *fa, FitMap m) {
+    __shared__ SampleArgs a;
+    const int f = fit_of_block(m, blockIdx.x);
+    stage_args(a, fa[f]);
+    sample_body(a, static_cast<int>(blockIdx.x) - m.start[f]);
+}
+
+__global__ void __launch_bounds__(256) k_ranges_multi(const ProfArgs *fa, FitMap m) {
+    __shared__ ProfArgs a;
+    const int f = fit_of_block(m, blockIdx.x);
+    stage_args(a, fa[f]);
+    ranges_body(a, static_cast<int>(blockIdx.x) - m.start[f], m.start[f + 1] - m.start[f]);
+}
+
+__global__ void __launch_bounds__(kTile) k_lik_multi(const ProfArgs *fa, FitMap m) {
+    __shared__ ProfArgs a;
+    const int f = fit_of_block(m, blockIdx.x);
+    stage_args(a, fa[f]);
+    lik_body(a, FixedBlock{static_cast<int>(blockIdx.x) - m.start[f], 0});
+}
+
+__global__ void __launch_bounds__(256) k_grad_multi(const GradArgs *fa, FitMap m) {
+    __shared__ GradArgs a;
+    const int f = fit_of_block(m, blockIdx.x);
+    stage_args(a, fa[f]);
+    const int lb = static_cast<int>(blockIdx.x) - m.start[f];
+    const int X = a.B * a.K + a.elbo_blocks;   // blocks per sample block (phases, then ELBO blocks)
+    grad_body(a, FixedBlock{lb % X, lb / X});
+}
+
+// Persistent profile kernels over all fits (forward: kFwd, else backward).
+template <bool kFwd, bool kWide>
+__global__ void __launch_bounds__(kThreads, 3) k_direct_multi(const ProfArgs *fa, FitMap m) {
+    extern __shared__ float4 s_raw[];
+    __shared__ ProfArgs a;
+    __shared__ int s_done;
+    const int f0 = fit_of_block(m, blockIdx.x);
+    for (int v = 0; v < m.n; ++v) {
+        const int f = f0 + v < m.n ? f0 + v : f0 + v - m.n;
+        __syncthreads();   // every warp is done with the previous fit's table and arguments
+        stage_args(a, fa[f]);
+        if (threadIdx.x == 0) s_done = atomicAdd(a.counter, 0) >= a.S * a.T * a.C;   // nothing left: skip the table
+        __syncthreads();
+        if (s_done) continue;
+        int *s_off;
+        const PeakTable<kWide> tab = load_table<kWide>(a, s_raw, s_off);
+        if constexpr (kFwd)
+            fwd_direct_items<false, kWide, false>(a, tab, s_off);
+        else
+            bwd_direct_items<kWide, false>(a, tab, s_off);
     }
 }
 
@@ -2268,9 +2388,9 @@ void choose_chunks(const Problem &P, const int *offsets, int S, Workspace &W, in
     W.C = C;
 }
 
-void launch_sample(const Problem &P, Workspace &W, const float *loc, const float *raw,
-                   const float *eps_in, uint64_t seed, uint32_t tag, const int *d_step,
-                   uint32_t step, int *d_iter, double *ent, cudaStream_t st) {
+static SampleArgs sample_args(const Problem &P, Workspace &W, const float *loc, const float *raw,
+                              const float *eps_in, uint64_t seed, uint32_t tag, const int *d_step, uint32_t step,
+                              int *d_iter, double *ent) {
     SampleArgs a;
     a.S = W.S; a.K = P.K; a.loc = loc; a.raw = raw; a.eps_in = eps_in;
     a.key0 = static_cast<uint32_t>(seed & 0xffffffffu);
@@ -2292,7 +2412,13 @@ void launch_sample(const Problem &P, Workspace &W, const float *loc, const float
     a.pr_alpha_isd = static_cast<float>(1.0 / P.prior.alpha_sd);
     a.pr_wsm1 = static_cast<float>(P.prior.w_shape - 1.0);
     a.pr_wrate = static_cast<float>(P.prior.w_rate);
-    k_sample<<<W.S, 128, 0, st>>>(a);
+    return a;
+}
+
+void launch_sample(const Problem &P, Workspace &W, const float *loc, const float *raw,
+                   const float *eps_in, uint64_t seed, uint32_t tag, const int *d_step,
+                   uint32_t step, int *d_iter, double *ent, cudaStream_t st) {
+    k_sample<<<W.S, 128, 0, st>>>(sample_args(P, W, loc, raw, eps_in, seed, tag, d_step, step, d_iter, ent));
 }
 
 void launch_lik(const Problem &P, Workspace &W, float *f_out, int C, cudaStream_t st) {
@@ -2372,10 +2498,10 @@ void launch_backward(const Problem &P, Workspace &W, cudaStream_t st, cudaEvent_
     if (marks) cudaEventRecord(marks[1], st);
 }
 
-void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,
-                 float *loc_out, float *raw_out, float *grad_out, bool adam, AdamConst ac,
-                 float *m, float *v, const int *d_iter, int *d_step, const double *ent,
-                 double *elbo_out, double *trace, cudaStream_t st) {
+static GradArgs grad_args(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,
+                          float *loc_out, float *raw_out, float *grad_out, bool adam, AdamConst ac, float *m,
+                          float *v, const int *d_iter, int *d_step, const double *ent, double *elbo_out,
+                          double *trace) {
     GradArgs a;
     a.S = W.S; a.K = P.K; a.T = P.T; a.pr = P.prior; a.csum = P.csum;
     a.gpart = W.gpart; a.theta = W.theta; a.eps = W.eps;
@@ -2400,6 +2526,16 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
     a.gate_a = P.gate_a; a.m_gate = P.m_gate; a.v_gate = P.v_gate; a.grad_gate = grad_out ? P.grad_gate : nullptr;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
     a.NB = a.NB < kGradBlocks ? a.NB : kGradBlocks;
+    a.elbo_blocks = 0;
+    return a;
+}
+
+void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const float *raw_in,
+                 float *loc_out, float *raw_out, float *grad_out, bool adam, AdamConst ac,
+                 float *m, float *v, const int *d_iter, int *d_step, const double *ent,
+                 double *elbo_out, double *trace, cudaStream_t st) {
+    GradArgs a = grad_args(P, W, loc_in, raw_in, loc_out, raw_out, grad_out, adam, ac, m, v, d_iter, d_step, ent,
+                           elbo_out, trace);
     const bool want_grad = grad_out || adam, want_elbo = elbo_out || trace || W.tail_sum;
     a.elbo_blocks = 0;
     if (W.iw) {
@@ -2414,6 +2550,171 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
         if (want_grad) k_grad<<<dim3(W.B * P.K, a.NB), 256, 0, st>>>(a);
         if (want_elbo) k_elbo<<<W.B, 256, 0, st>>>(a);
     }
+}
+
+// --- multi-fit step (continuous batching) ---------------------------------------
+struct MultiStepPlan {
+    int cap = 0, n = 0;
+    unsigned char *d_args = nullptr;          // [cap] SampleArgs, ProfArgs (fwd), ProfArgs (bwd), GradArgs
+    unsigned char *h_args[2] = {nullptr, nullptr};   // pinned host images of d_args, used in turn
+    cudaEvent_t h_done[2] = {nullptr, nullptr};      // the upload from each image has been read
+    int h_next = 0;
+    size_t bytes = 0;
+    FitMap m_sample, m_ranges, m_fwd, m_lik, m_bwd, m_grad;
+    size_t smem = 0;
+    bool wide = true;
+    size_t o_prof_f = 0, o_prof_b = 0, o_grad = 0;
+};
+
+void multi_plan_destroy(MultiStepPlan *p) {
+    if (!p) return;
+    if (p->d_args) cudaFree(p->d_args);
+    for (int i = 0; i < 2; ++i) {
+        if (p->h_done[i]) cudaEventSynchronize(p->h_done[i]);
+        if (p->h_args[i]) cudaFreeHost(p->h_args[i]);
+        if (p->h_done[i]) cudaEventDestroy(p->h_done[i]);
+    }
+    delete p;
+}
+
+MultiStepPlan *multi_plan_create(int cap) {
+    if (cap < 1 || cap > kMaxBatch) return nullptr;
+    MultiStepPlan *p = new MultiStepPlan();
+    p->cap = cap;
+    const size_t a16 = 16;
+    auto up = [&](size_t v) { return (v + a16 - 1) / a16 * a16; };
+    p->o_prof_f = up(sizeof(SampleArgs) * cap);
+    p->o_prof_b = p->o_prof_f + up(sizeof(ProfArgs) * cap);
+    p->o_grad = p->o_prof_b + up(sizeof(ProfArgs) * cap);
+    p->bytes = p->o_grad + up(sizeof(GradArgs) * cap);
+    bool ok = cudaMalloc(&p->d_args, p->bytes) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = cudaMallocHost(&p->h_args[i], p->bytes) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->h_done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        multi_plan_destroy(p);
+        return nullptr;
+    }
+    // the shared-memory attribute of the persistent kernels (largest table any fit may have)
+    const int smax = static_cast<int>(static_cast<size_t>(kMaxPeaks) * sizeof(float2) +
+                                      static_cast<size_t>(kMaxK + 1) * sizeof(int));
+    set_smem_attr(k_direct_multi<true, true>, smax);
+    set_smem_attr(k_direct_multi<true, false>, smax);
+    set_smem_attr(k_direct_multi<false, true>, smax);
+    set_smem_attr(k_direct_multi<false, false>, smax);
+    return p;
+}
+
+bool multi_fit_eligible(const Problem &P, const Workspace &W, bool naive, bool iw) {
+    return P.far && W.franges && W.wfar && !W.shared && !P.sec && !P.bgfit && !naive && !iw && W.B == 1 &&
+           !W.mask;
+}
+
+// Splits `grid` persistent blocks over the fits in proportion to their work
+// items (at least one block each).
+static void persistent_map(FitMap &m, const std::vector<long long> &items, int grid) {
+    const int n = static_cast<int>(items.size());
+    long long tot = 0;
+    for (long long v : items) tot += v;
+    if (grid < n) grid = n;
+    m.n = n;
+    m.start[0] = 0;
+    long long acc = 0;
+    for (int f = 0; f < n; ++f) {
+        acc += items[f];
+        int e = static_cast<int>((acc * grid + tot - 1) / tot);
+        e = e < m.start[f] + 1 ? m.start[f] + 1 : e;
+        e = e > grid - (n - 1 - f) ? grid - (n - 1 - f) : e;
+        m.start[f + 1] = e;
+    }
+    m.start[n] = grid;
+}
+
+bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, cudaStream_t st) {
+    if (!p || n < 1 || n > p->cap) return false;
+    // the host image used two uploads ago must have been read before it is rewritten
+    unsigned char *h = p->h_args[p->h_next];
+    if (cudaEventSynchronize(p->h_done[p->h_next]) != cudaSuccess) return false;
+    p->n = n;
+    p->wide = true;
+    for (int f = 0; f < n; ++f) p->wide = p->wide && fits[f].P->wide;
+    size_t smem = 0;
+    std::vector<long long> items(n);
+    int bs = 0, br = 0, bl = 0, bg = 0;
+    p->m_sample.n = p->m_ranges.n = p->m_lik.n = p->m_grad.n = n;
+    for (int f = 0; f < n; ++f) {
+        const FitStep &F = fits[f];
+        const Problem &P = *F.P;
+        Workspace &W = *F.W;
+        SampleArgs sa = sample_args(P, W, F.loc, F.raw, nullptr, F.seed, 0u, F.step, 0u, F.iter, F.ent);
+        ProfArgs pf = prof_args(P, W, nullptr);
+        ProfArgs pb = pf;
+        pb.counter = W.counters + 2;
+        GradArgs ga = grad_args(P, W, F.loc, F.raw, F.loc, F.raw, nullptr, true, F.ac, F.m, F.v, F.iter, F.step,
+                                F.ent, F.elbo, F.trace);
+        ga.elbo_blocks = W.B;   // the ELBO in extra blocks of the gradient kernel, as in a fit step
+        std::memcpy(h + sizeof(SampleArgs) * f, &sa, sizeof(sa));
+        std::memcpy(h + p->o_prof_f + sizeof(ProfArgs) * f, &pf, sizeof(pf));
+        std::memcpy(h + p->o_prof_b + sizeof(ProfArgs) * f, &pb, sizeof(pb));
+        std::memcpy(h + p->o_grad + sizeof(GradArgs) * f, &ga, sizeof(ga));
+        const size_t tb = static_cast<size_t>(P.Mtot) * (p->wide ? sizeof(float4) : sizeof(float2)) +
+                          static_cast<size_t>(P.K + 1) * sizeof(int);
+        smem = tb > smem ? tb : smem;
+        items[f] = static_cast<long long>(W.S) * P.T * W.C;
+        p->m_sample.start[f] = bs;
+        bs += W.S;
+        p->m_ranges.start[f] = br;
+        const int nr = W.S * P.K * P.T;
+        br += (nr + 255) / 256 < 4096 ? (nr + 255) / 256 : 4096;
+        p->m_lik.start[f] = bl;
+        bl += W.S * P.T;
+        p->m_grad.start[f] = bg;
+        bg += (W.B * P.K + ga.elbo_blocks) * ga.NB;
+    }
+    p->m_sample.start[n] = bs;
+    p->m_ranges.start[n] = br;
+    p->m_lik.start[n] = bl;
+    p->m_grad.start[n] = bg;
+    p->smem = smem;
+    int occ_f = 1, occ_b = 1;
+    if (p->wide) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_direct_multi<true, true>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_direct_multi<false, true>, kThreads, smem);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_direct_multi<true, false>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_direct_multi<false, false>, kThreads, smem);
+    }
+    occ_f = occ_f < 1 ? 1 : occ_f;
+    occ_b = occ_b < 1 ? 1 : occ_b;
+    long long tot = 0;
+    for (long long v : items) tot += v;
+    const auto cap_grid = [&](int occ) {
+        const long long need = (tot + kWarps - 1) / kWarps;
+        const long long g = static_cast<long long>(occ) * sm_count;
+        return static_cast<int>(need < g ? need : g);
+    };
+    persistent_map(p->m_fwd, items, cap_grid(occ_f));
+    persistent_map(p->m_bwd, items, cap_grid(occ_b));
+    // stream-ordered: the kernels of steps queued before read the previous image
+    if (cudaMemcpyAsync(p->d_args, h, p->bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return false;
+    if (cudaEventRecord(p->h_done[p->h_next], st) != cudaSuccess) return false;
+    p->h_next ^= 1;
+    return true;
+}
+
+void multi_plan_launch_step(const MultiStepPlan *p, cudaStream_t st) {
+    const SampleArgs *sa = reinterpret_cast<const SampleArgs *>(p->d_args);
+    const ProfArgs *pf = reinterpret_cast<const ProfArgs *>(p->d_args + p->o_prof_f);
+    const ProfArgs *pb = reinterpret_cast<const ProfArgs *>(p->d_args + p->o_prof_b);
+    const GradArgs *ga = reinterpret_cast<const GradArgs *>(p->d_args + p->o_grad);
+    k_sample_multi<<<p->m_sample.start[p->n], 128, 0, st>>>(sa, p->m_sample);
+    k_ranges_multi<<<p->m_ranges.start[p->n], 256, 0, st>>>(pf, p->m_ranges);
+    if (p->wide) k_direct_multi<true, true><<<p->m_fwd.start[p->n], kThreads, p->smem, st>>>(pf, p->m_fwd);
+    else k_direct_multi<true, false><<<p->m_fwd.start[p->n], kThreads, p->smem, st>>>(pf, p->m_fwd);
+    k_lik_multi<<<p->m_lik.start[p->n], kTile, 0, st>>>(pf, p->m_lik);
+    if (p->wide) k_direct_multi<false, true><<<p->m_bwd.start[p->n], kThreads, p->smem, st>>>(pb, p->m_bwd);
+    else k_direct_multi<false, false><<<p->m_bwd.start[p->n], kThreads, p->smem, st>>>(pb, p->m_bwd);
+    k_grad_multi<<<p->m_grad.start[p->n], 256, 0, st>>>(ga, p->m_grad);
 }
 
 void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m, cudaStream_t st) {

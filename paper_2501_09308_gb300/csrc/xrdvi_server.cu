@@ -1,17 +1,23 @@
 // Continuous-batching fit server (xrdvi_server_*): host runtime around the
 // fit kernels.
 //
-// Requests (a problem + fit options) enter a FIFO queue.  max_slots worker
-// threads, each with its own CUDA stream, take the head request whenever it
-// fits into the device-memory budget next to the fits already running
-// (admission by HBM footprint), so requests that arrive while others run are
-// admitted as slots and memory free up, and the fits of different slots
-// overlap on the GPU.  A fit's whole state (tables, variational parameters,
-// Adam moments, sample workspaces) stays on the device from creation to its
-// posterior; all of it comes from one stream-ordered memory pool, so starting
-// and finishing fits never synchronises the device.  Each fit runs the same
-// deterministic kernels as a standalone context, so its result does not
-// depend on what else is running.
+// Requests (a problem + fit options) enter a FIFO queue.  An admission thread
+// takes the head request whenever its device footprint fits into the budget
+// next to the resident fits (admission by HBM footprint) and a slot is free,
+// and creates its context (validation, tables, upload) from one
+// stream-ordered memory pool.  An engine thread advances every resident fit
+// together: each SVI step of the whole batch is six kernel launches
+// (xrdvi::multi_plan_launch_step) whose work lists span all resident fits,
+// whatever their K, N and peak counts; fits that run a variant outside the
+// batched step (shared shapes, angle-dependent width, fitted background,
+// naive sums, importance weights) take their own kernels between those
+// launches.  Fits join and leave the batch between slices of a few steps, so
+// requests that arrive while others run start within a slice.  A reaper
+// thread draws the posterior of each finished fit, copies its results and
+// frees it.  All device work runs on one stream in submission order; a fit's
+// whole state stays on the device from creation to posterior; each fit's work
+// items and reductions are those of its standalone kernels, so its result is
+// the same alone and in the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,9 +58,17 @@ struct Request {
     double final_elbo = 0, log_evidence = 0, ess = 0, coverage_log = 0, elbo_tail_mean = 0;
 };
 
+// A resident fit: its request, its context and the steps enqueued so far.
+struct Fit {
+    std::shared_ptr<Request> r;
+    xrdvi_ctx *c = nullptr;
+    int steps = 0;
+    bool batched = false;
+};
+
 size_t a256(size_t n) { return (n + 511) & ~static_cast<size_t>(511); }  // pool granularity allowance
 
-constexpr int kSliceSteps = 128;   // SVI steps a served fit queues at a time
+constexpr int kSliceSteps = 8;   // SVI steps between changes of the batch
 
 #define XR_TRY_STATUS(expr)                  \
     do {                                     \
@@ -65,26 +79,201 @@ constexpr int kSliceSteps = 128;   // SVI steps a served fit queues at a time
 }  // namespace
 
 struct xrdvi_server {
-    int device = 0;
+    int device = 0, sm_count = 0;
     size_t budget = 0;
     int slots = 0;
     cudaMemPool_t pool = nullptr;
+    cudaStream_t stream = nullptr;          // every fit's device work, in submission order
+    xrdvi::MultiStepPlan *plan = nullptr;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<std::shared_ptr<Request>> queue;
+    std::condition_variable cv_work, cv_done, cv_engine, cv_reap;
+    std::deque<std::shared_ptr<Request>> queue;    // waiting for admission
+    std::vector<Fit *> ready;                      // created, waiting to join the batch
+    std::deque<Fit *> finished;                    // all steps enqueued, waiting for the posterior
     std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
     size_t in_use = 0, peak = 0;
-    int64_t running = 0, completed = 0;
+    int64_t resident = 0, completed = 0;
     uint64_t next_id = 1;
-    bool stopping = false;
-    std::vector<std::thread> workers;
-    std::vector<cudaStream_t> streams;
+    bool stopping = false, admit_done = false, engine_done = false;
+    std::thread admit_thread, engine_thread, reap_thread;
     Clock::time_point t0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
-    void worker(int slot);
-    void run(Request &r, cudaStream_t st);
+    void admit_loop();
+    void engine_loop();
+    void reap_loop();
+    void finish(Request &r);   // under mu: release the request's budget and slot, mark it done
 };
+
+void xrdvi_server::finish(Request &r) {
+    in_use -= r.footprint;
+    --resident;
+    ++completed;
+    r.t_done = now();
+    r.done = true;
+}
+
+void xrdvi_server::admit_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] {
+                return stopping || (!queue.empty() && queue.front()->footprint <= budget - in_use && resident < slots);
+            });
+            if (stopping) {
+                admit_done = true;
+                cv_engine.notify_all();
+                return;
+            }
+            r = queue.front();
+            queue.pop_front();
+            in_use += r->footprint;
+            peak = std::max(peak, in_use);
+            ++resident;
+            r->t_admit = now();
+        }
+        xrdvi_peaks pk{static_cast<int32_t>(r->off.size() - 1), r->off.data(), r->pos.data(), r->inten.data()};
+        xrdvi_pattern pt{static_cast<int32_t>(r->x.size()), r->x.data(), r->y.data(), r->bg.data()};
+        xrdvi_ctx *c = nullptr;
+        const xrdvi_status s = xrdvi::create_context(&pk, &pt, &r->cfg, pool, stream, &c);
+        std::lock_guard<std::mutex> lk(mu);
+        if (s != XRDVI_OK) {
+            r->status = s;
+            r->error = xrdvi_last_error();
+            finish(*r);
+            cv_done.notify_all();
+            cv_work.notify_all();
+            continue;
+        }
+        Fit *f = new Fit();
+        f->r = r;
+        f->c = c;
+        f->batched = xrdvi::ctx_multi_eligible(c);
+        ready.push_back(f);
+        cv_engine.notify_all();
+    }
+}
+
+void xrdvi_server::engine_loop() {
+    cudaSetDevice(device);
+    std::vector<Fit *> members;
+    bool dirty = true;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    bool ev_live[2] = {false, false};
+    int slot = 0;
+    std::vector<xrdvi::FitStep> fs;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (members.empty())
+                cv_engine.wait(lk, [&] { return !ready.empty() || (stopping && admit_done); });
+            if (!ready.empty()) {
+                for (Fit *f : ready) members.push_back(f);
+                ready.clear();
+                dirty = true;
+            }
+            if (members.empty() && stopping && admit_done) break;
+        }
+        // fits with nothing to run go straight to the reaper
+        for (size_t i = 0; i < members.size();) {
+            if (members[i]->steps >= members[i]->r->opts.iters) {
+                std::lock_guard<std::mutex> lk(mu);
+                finished.push_back(members[i]);
+                cv_reap.notify_all();
+                if (members[i]->batched) dirty = true;
+                members.erase(members.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+        if (members.empty()) continue;
+        if (dirty) {
+            fs.clear();
+            for (Fit *f : members)
+                if (f->batched) {
+                    xrdvi::FitStep st;
+                    xrdvi::ctx_fit_step(f->c, &st);
+                    fs.push_back(st);
+                }
+            if (!fs.empty()) xrdvi::multi_plan_set(plan, fs.data(), static_cast<int>(fs.size()), sm_count, stream);
+            dirty = false;
+        }
+        int n = kSliceSteps;
+        for (Fit *f : members) n = std::min(n, f->r->opts.iters - f->steps);
+        for (int i = 0; i < n; ++i) {
+            if (!fs.empty()) xrdvi::multi_plan_launch_step(plan, stream);
+            for (Fit *f : members)
+                if (!f->batched) xrdvi::ctx_enqueue_steps(f->c, 1, stream);
+        }
+        for (Fit *f : members) {
+            f->steps += n;
+            xrdvi::ctx_advance(f->c, n);
+        }
+        cudaEventRecord(ev[slot], stream);
+        ev_live[slot] = true;
+        // at most two slices in flight: new arrivals join within about a slice
+        if (ev_live[slot ^ 1]) cudaEventSynchronize(ev[slot ^ 1]);
+        slot ^= 1;
+    }
+    for (int i = 0; i < 2; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    std::lock_guard<std::mutex> lk(mu);
+    engine_done = true;
+    cv_reap.notify_all();
+}
+
+void xrdvi_server::reap_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        Fit *f = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_reap.wait(lk, [&] { return !finished.empty() || engine_done; });
+            if (finished.empty()) return;
+            f = finished.front();
+            finished.pop_front();
+        }
+        Request &r = *f->r;
+        xrdvi_ctx *c = f->c;
+        const int K = static_cast<int>(r.off.size()) - 1, W = (K + 63) / 64;
+        xrdvi_status s = XRDVI_OK;
+        if (r.opts.iters > 0) {
+            std::vector<double> trace(r.opts.iters);
+            s = xrdvi::ctx_read_trace(c, r.opts.iters, trace.data());
+            r.final_elbo = trace[r.opts.iters - 1];
+            const int tail = std::max(1, r.opts.iters / 4);
+            double acc = 0.0;
+            for (int i = r.opts.iters - tail; i < r.opts.iters; ++i) acc += trace[i];
+            r.elbo_tail_mean = acc / tail;
+        }
+        if (s == XRDVI_OK && r.opts.S_post > 0) {
+            r.pi.resize(K);
+            r.combos.resize(static_cast<size_t>(r.opts.top_m) * W);
+            r.combo_logp.resize(r.opts.top_m);
+            s = xrdvi_posterior(c, r.opts.S_post, r.opts.post_seed, r.opts.top_m, r.pi.data(), r.combos.data(),
+                                r.combo_logp.data(), &r.log_evidence, &r.ess, &r.coverage_log);
+        }
+        if (s == XRDVI_OK) {
+            r.loc.resize(K * 5);
+            r.raw.resize(K * 5);
+            s = xrdvi_get_params(c, r.loc.data(), r.raw.data());
+        }
+        if (s != XRDVI_OK) r.error = xrdvi_last_error();
+        r.status = s;
+        xrdvi_destroy(c);   // stream-ordered frees
+        delete f;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            finish(r);
+        }
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+}
 
 extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, int32_t S, int32_t S_post,
                                         int32_t top_m) {
@@ -127,85 +316,17 @@ extern "C" size_t xrdvi_footprint_bytes(int32_t K, int32_t N, int32_t M_total, i
     return b;
 }
 
-void xrdvi_server::run(Request &r, cudaStream_t st) {
-    xrdvi_peaks pk{static_cast<int32_t>(r.off.size() - 1), r.off.data(), r.pos.data(), r.inten.data()};
-    xrdvi_pattern pt{static_cast<int32_t>(r.x.size()), r.x.data(), r.y.data(), r.bg.data()};
-    xrdvi_ctx *c = nullptr;
-    xrdvi_status s = xrdvi::create_context(&pk, &pt, &r.cfg, pool, st, &c);
-    std::vector<double> trace(std::max(r.opts.iters, 1));
-    // Advance in slices with a wait between them: a fit never has more than
-    // kSliceSteps steps queued on its stream, so the kernels of fits admitted
-    // later interleave with it instead of queueing behind all of its steps.
-    for (int done = 0; s == XRDVI_OK && done < r.opts.iters; done += kSliceSteps)
-        s = xrdvi_fit(c, std::min(kSliceSteps, r.opts.iters - done), trace.data() + done);
-    const int K = pk.K, W = (K + 63) / 64;
-    if (s == XRDVI_OK) {
-        r.final_elbo = r.opts.iters > 0 ? trace[r.opts.iters - 1] : 0.0;
-        if (r.opts.iters > 0) {
-            const int tail = std::max(1, r.opts.iters / 4);
-            double acc = 0.0;
-            for (int i = r.opts.iters - tail; i < r.opts.iters; ++i) acc += trace[i];
-            r.elbo_tail_mean = acc / tail;
-        }
-        if (r.opts.S_post > 0) {
-            r.pi.resize(K);
-            r.combos.resize(static_cast<size_t>(r.opts.top_m) * W);
-            r.combo_logp.resize(r.opts.top_m);
-            s = xrdvi_posterior(c, r.opts.S_post, r.opts.post_seed, r.opts.top_m, r.pi.data(), r.combos.data(),
-                                r.combo_logp.data(), &r.log_evidence, &r.ess, &r.coverage_log);
-        }
-    }
-    if (s == XRDVI_OK) {
-        r.loc.resize(K * 5);
-        r.raw.resize(K * 5);
-        s = xrdvi_get_params(c, r.loc.data(), r.raw.data());
-    }
-    if (s != XRDVI_OK) r.error = xrdvi_last_error();
-    r.status = s;
-    xrdvi_destroy(c);  // stream-ordered frees on the slot stream
-}
-
-void xrdvi_server::worker(int slot) {
-    cudaSetDevice(device);
-    cudaStream_t st = streams[slot];
-    for (;;) {
-        std::shared_ptr<Request> r;
-        {
-            std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] {
-                return stopping || (!queue.empty() && queue.front()->footprint <= budget - in_use);
-            });
-            if (stopping) return;
-            r = queue.front();
-            queue.pop_front();
-            in_use += r->footprint;
-            peak = std::max(peak, in_use);
-            ++running;
-            r->t_admit = now();
-        }
-        run(*r, st);
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            in_use -= r->footprint;
-            --running;
-            ++completed;
-            r->t_done = now();
-            r->done = true;
-        }
-        cv_done.notify_all();
-        cv_work.notify_all();
-    }
-}
-
 extern "C" {
 
 xrdvi_status xrdvi_server_create(size_t hbm_budget, int32_t max_slots, xrdvi_server **out) {
     if (!out) return xrdvi::report_error(XRDVI_EINVAL, "null output pointer");
     *out = nullptr;
-    if (max_slots < 1 || max_slots > 64) return xrdvi::report_error(XRDVI_EINVAL, "max_slots must be in [1, 64]");
+    if (max_slots < 1 || max_slots > xrdvi::kMaxBatch)
+        return xrdvi::report_error(XRDVI_EINVAL, "max_slots must be in [1, 64]");
     if (hbm_budget == 0) return xrdvi::report_error(XRDVI_EINVAL, "hbm_budget must be positive");
     auto srv = std::make_unique<xrdvi_server>();
     cudaError_t e = cudaGetDevice(&srv->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&srv->sm_count, cudaDevAttrMultiProcessorCount, srv->device);
     if (e != cudaSuccess) return xrdvi::report_error(XRDVI_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof(props));
@@ -216,20 +337,23 @@ xrdvi_status xrdvi_server_create(size_t hbm_budget, int32_t max_slots, xrdvi_ser
     if (e != cudaSuccess) return xrdvi::report_error(XRDVI_ECUDA, std::string("cudaMemPoolCreate: ") + cudaGetErrorString(e));
     uint64_t keep = UINT64_MAX;  // keep released memory reserved for the next fits
     cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        srv->plan = xrdvi::multi_plan_create(max_slots);
+        if (!srv->plan) e = cudaErrorMemoryAllocation;
+    }
+    if (e != cudaSuccess) {
+        if (srv->stream) cudaStreamDestroy(srv->stream);
+        cudaMemPoolDestroy(srv->pool);
+        return xrdvi::report_error(XRDVI_ECUDA, std::string("server set-up: ") + cudaGetErrorString(e));
+    }
     srv->budget = hbm_budget;
     srv->slots = max_slots;
-    srv->streams.resize(max_slots);
-    for (auto &st : srv->streams) {
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            for (auto &s2 : srv->streams)
-                if (s2) cudaStreamDestroy(s2);
-            cudaMemPoolDestroy(srv->pool);
-            return xrdvi::report_error(XRDVI_ECUDA, "cudaStreamCreate failed");
-        }
-    }
     srv->t0 = Clock::now();
-    for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back([s = srv.get(), i] { s->worker(i); });
+    xrdvi_server *p = srv.get();
+    srv->admit_thread = std::thread([p] { p->admit_loop(); });
+    srv->engine_thread = std::thread([p] { p->engine_loop(); });
+    srv->reap_thread = std::thread([p] { p->reap_loop(); });
     *out = srv.release();
     return XRDVI_OK;
 }
@@ -326,7 +450,7 @@ xrdvi_status xrdvi_server_get_stats(xrdvi_server *srv, xrdvi_server_stats *st) {
     if (!srv || !st) return xrdvi::report_error(XRDVI_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(srv->mu);
     st->queued = static_cast<int64_t>(srv->queue.size());
-    st->running = srv->running;
+    st->running = srv->resident;
     st->completed = srv->completed;
     st->bytes_in_use = srv->in_use;
     st->peak_bytes = srv->peak;
@@ -349,12 +473,14 @@ void xrdvi_server_destroy(xrdvi_server *srv) {
         srv->queue.clear();
     }
     srv->cv_work.notify_all();
+    srv->cv_engine.notify_all();
     srv->cv_done.notify_all();
-    for (auto &t : srv->workers) t.join();  // running fits finish first
-    for (auto &s : srv->streams) {
-        cudaStreamSynchronize(s);
-        cudaStreamDestroy(s);
-    }
+    srv->admit_thread.join();    // a context being created joins the batch first
+    srv->engine_thread.join();   // running fits finish their steps
+    srv->reap_thread.join();     // and their posteriors
+    cudaStreamSynchronize(srv->stream);
+    xrdvi::multi_plan_destroy(srv->plan);
+    cudaStreamDestroy(srv->stream);
     cudaMemPoolDestroy(srv->pool);
     delete srv;
 }

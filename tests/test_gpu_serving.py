@@ -1,5 +1,7 @@
-"""Continuous-batching fit server: results equal to standalone fits, admission
-by device-memory footprint, continuous admission while fits run, cancellation."""
+"""Continuous-batching fit server: results equal to standalone fits (fits of
+different K and N share every step's kernel launches, and a variant fit runs
+its own kernels between them), admission by device-memory footprint,
+continuous admission while fits run, device-side overlap, cancellation."""
 import time
 
 import numpy as np
@@ -46,6 +48,60 @@ def test_served_results_equal_standalone_results():
         assert r["final_elbo"] == e
         np.testing.assert_array_equal(r["pi"], post["pi"])
         np.testing.assert_array_equal(r["combo_logp"], post["combo_logp"])
+
+
+def test_batched_and_variant_fits_in_one_mix_equal_their_standalone_fits():
+    """Five fits of different K, N and peak counts, one of them with the
+    angle-dependent width (outside the batched step: its own kernels), one
+    with the Gaussian likelihood and fixed r (inside it): each result equals
+    the standalone fit bit for bit."""
+    probs = _problems() + [synth.small_problem(K=5, M=9, N=1100, S=8, seed=77, x_step=0.04),
+                           synth.small_problem(K=4, M=7, N=700, S=8, seed=78)]
+    extra = [{}, {}, {}, {"flags": xrdvi.FLAG_SEC_WIDTH},
+             {"flags": xrdvi.FLAG_GAUSS_LIK | xrdvi.FLAG_FIX_R, "fix_r_value": 0.4}]
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=5)
+    ids = [srv.submit(p, iters=ITERS, S_post=128, post_seed=6, top_m=4, seed=200 + i, **extra[i])
+           for i, p in enumerate(probs)]
+    served = [srv.wait(i) for i in ids]
+    srv.close()
+    for i, (p, r) in enumerate(zip(probs, served)):
+        assert r["status"] == 0, r
+        c = xrdvi.Context.from_instance(p, S=p.S, seed=200 + i, **extra[i])
+        tr = c.fit(ITERS)
+        post = c.posterior(128, 6, top_m=4)
+        loc, raw = c.params()
+        c.close()
+        np.testing.assert_array_equal(r["loc"], loc)
+        np.testing.assert_array_equal(r["raw"], raw)
+        assert r["final_elbo"] == tr[-1]
+        np.testing.assert_array_equal(r["pi"], post["pi"])
+
+
+def test_batched_fits_overlap_on_the_device():
+    """Eight small fits served together finish in much less time than the
+    same fits run one after another: their steps share kernel launches
+    instead of taking turns on the GPU."""
+    probs = [synth.small_problem(K=4 + i % 5, M=8, N=600 + 150 * i, S=16, seed=90 + i) for i in range(8)]
+    iters = 300
+    for p in probs[:2]:   # warm-up (module loading, pool growth)
+        c = xrdvi.Context.from_instance(p, S=p.S)
+        c.fit(20)
+        c.close()
+    t0 = time.perf_counter()
+    for p in probs:
+        c = xrdvi.Context.from_instance(p, S=p.S)
+        c.fit(iters)
+        c.close()
+    t_seq = time.perf_counter() - t0
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=8)
+    t0 = time.perf_counter()
+    ids = [srv.submit(p, iters=iters, S_post=0) for p in probs]
+    res = [srv.wait(i) for i in ids]
+    t_mix = time.perf_counter() - t0
+    srv.close()
+    assert all(r["status"] == 0 for r in res)
+    print(f"\n8 fits x {iters} steps: one after another {t_seq:.3f} s, served together {t_mix:.3f} s")
+    assert t_mix < 0.6 * t_seq, (t_mix, t_seq)
 
 
 def test_admission_by_footprint_serialises_when_only_one_fits():
