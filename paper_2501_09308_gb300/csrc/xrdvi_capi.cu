@@ -316,6 +316,17 @@ xrdvi_status check_launch(const char *what) {
     return XRDVI_OK;
 }
 
+// Reads and clears the flag the gradient reduction sets on a NaN or infinite
+// gradient entry (in any step since the last check); synchronises the stream.
+xrdvi_status check_gradients(xrdvi_ctx *c) {
+    int bad = 0;
+    XR_CUDA(cudaMemcpyAsync(&bad, c->P.nonfinite, 4, cudaMemcpyDeviceToHost, c->stream));
+    XR_CUDA(cudaMemsetAsync(c->P.nonfinite, 0, 4, c->stream));
+    XR_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) return fail(XRDVI_ENONFINITE, "a gradient entry is not finite");
+    return XRDVI_OK;
+}
+
 AdamConst adam_const(const xrdvi_config &cfg) {
     return AdamConst{cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps};
 }
@@ -463,6 +474,24 @@ void ctx_enqueue_steps(xrdvi_ctx *c, int n, cudaStream_t st) {
 
 void ctx_advance(xrdvi_ctx *c, int n) { c->host_step += n; }
 
+// Captures `steps` SVI steps of a batch (the plan's multi-fit launches, then
+// each solo context's own kernels) on the private stream `cap` as one graph.
+xrdvi_status capture_batch_steps(const MultiStepPlan *plan, xrdvi_ctx *const *solo, int nsolo, int steps,
+                                 cudaStream_t cap, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    XR_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < steps; ++i) {
+        if (plan) multi_plan_launch_step(plan, cap);
+        for (int j = 0; j < nsolo; ++j) enqueue_step(solo[j], cap);
+    }
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    return XRDVI_OK;
+}
+
 cudaStream_t ctx_stream(const xrdvi_ctx *c) { return c->stream; }
 
 // The ELBO estimates of the last n steps (host copy; synchronises the
@@ -477,8 +506,9 @@ xrdvi_status ctx_read_trace(xrdvi_ctx *c, int n, double *host) {
         done += static_cast<int>(len);
     }
     XR_CUDA(cudaStreamSynchronize(c->stream));
+    const xrdvi_status gs = check_gradients(c);
     if (!std::isfinite(host[n - 1])) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
-    return XRDVI_OK;
+    return gs;
 }
 }  // namespace xrdvi
 
@@ -548,6 +578,7 @@ xrdvi_status xrdvi::create_context(const xrdvi_peaks *pk, const xrdvi_pattern *p
 xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_pattern *pt, const xrdvi_config *cfg,
                                          int nsub, const uint32_t *masks, cudaMemPool_t pool, cudaStream_t stream,
                                          xrdvi_ctx **out) {
+    NvtxRange nvtx("xrdvi_create");
     g_err.clear();
     if (!out) return fail(XRDVI_EINVAL, "null output pointer");
     *out = nullptr;
@@ -677,6 +708,7 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     XR_C(c->alloc(&P.y, N));
     XR_C(c->alloc(&P.bg, N));
     XR_C(c->alloc(&P.isum, K));
+    XR_C(c->alloc(&P.nonfinite, 1));
     if (sec) XR_C(c->alloc(&P.csec, N));
     if (P.gates) {   // gate logits start at 0 (z = sigmoid(L / tau))
         XR_C(c->alloc(&P.gate_a, K));
@@ -802,6 +834,7 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         up(c->loc, loc.data(), KB * 20) ||
         up(c->raw, raw.data(), KB * 20) || cudaMemsetAsync(c->m, 0, KB * 40, s) ||
         cudaMemsetAsync(c->v, 0, KB * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
+        cudaMemsetAsync(P.nonfinite, 0, 4, s) ||
         cudaMemsetAsync(c->trace, 0, kTraceCap * 8, s) ||
         (d_mask && (up(d_mask, masks, static_cast<size_t>(nsub) * 4) ||
                     cudaMemsetAsync(c->W.tail_sum, 0, static_cast<size_t>(nsub) * 8, s))) ||
@@ -839,6 +872,7 @@ xrdvi_status xrdvi_set_stream(xrdvi_ctx *c, void *stream) {
 }
 
 xrdvi_status xrdvi_fit(xrdvi_ctx *c, int32_t iters, double *trace) {
+    NvtxRange nvtx("xrdvi_fit");
     if (!c) return fail(XRDVI_EINVAL, "null context");
     if (iters < 0) return fail(XRDVI_EINVAL, "iters must be >= 0");
     if (iters == 0) return XRDVI_OK;
@@ -872,12 +906,86 @@ xrdvi_status xrdvi_fit(xrdvi_ctx *c, int32_t iters, double *trace) {
     XR_CUDA(cudaStreamSynchronize(c->stream));
     c->host_step += iters;
     if (gerr) return fail(XRDVI_ETIMEOUT, "tensor-core pipeline wait gave up");
+    const xrdvi_status gs = check_gradients(c);   // read and cleared in every case
     if (!std::isfinite(last)) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
-    return XRDVI_OK;
+    return gs;
+}
+
+xrdvi_status xrdvi_fit_batch(xrdvi_ctx *const *ctxs, int32_t n, int32_t iters, double *last_elbo) {
+    NvtxRange nvtx("xrdvi_fit_batch");
+    if (!ctxs || n < 1 || n > kMaxBatch) return fail(XRDVI_EINVAL, "n must be in [1, 64] with a context array");
+    if (iters < 0) return fail(XRDVI_EINVAL, "iters must be >= 0");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(XRDVI_EINVAL, "null context");
+        if (ctxs[i]->device != ctxs[0]->device) return fail(XRDVI_EINVAL, "contexts on different devices");
+        if (ctxs[i]->host_step + iters > INT32_MAX) return fail(XRDVI_EINVAL, "step counter would overflow");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(XRDVI_EINVAL, "a context appears twice");
+    }
+    for (int i = 0; i < n; ++i) XR_CUDA(cudaStreamSynchronize(ctxs[i]->stream));
+    cudaStream_t st = ctxs[0]->stream;
+    std::vector<FitStep> fs;
+    std::vector<xrdvi_ctx *> solo;
+    for (int i = 0; i < n; ++i) {
+        if (ctx_multi_eligible(ctxs[i])) {
+            FitStep f;
+            ctx_fit_step(ctxs[i], &f);
+            fs.push_back(f);
+        } else {
+            solo.push_back(ctxs[i]);
+        }
+    }
+    MultiStepPlan *plan = nullptr;
+    if (!fs.empty()) {
+        int sms = 0;
+        XR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device));
+        plan = multi_plan_create(static_cast<int>(fs.size()));
+        if (!plan || !multi_plan_set(plan, fs.data(), static_cast<int>(fs.size()), sms, st)) {
+            multi_plan_destroy(plan);
+            return fail(XRDVI_ECUDA, "fit_batch: batch set-up failed");
+        }
+    }
+    // kUnroll steps per captured graph (captured on a private stream), the rest one by one
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gmany = nullptr, gone = nullptr;
+    xrdvi_status cs = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess
+                          ? XRDVI_OK
+                          : fail(XRDVI_ECUDA, "fit_batch: cudaStreamCreate failed");
+    if (cs == XRDVI_OK && iters >= kUnroll)
+        cs = capture_batch_steps(plan, solo.data(), static_cast<int>(solo.size()), kUnroll, cap, &gmany);
+    if (cs == XRDVI_OK && iters % kUnroll)
+        cs = capture_batch_steps(plan, solo.data(), static_cast<int>(solo.size()), 1, cap, &gone);
+    if (cs == XRDVI_OK) {
+        int left = iters;
+        for (; left >= kUnroll && cs == XRDVI_OK; left -= kUnroll)
+            if (cudaGraphLaunch(gmany, st) != cudaSuccess) cs = fail(XRDVI_ECUDA, "fit_batch: graph launch failed");
+        for (; left > 0 && cs == XRDVI_OK; --left)
+            if (cudaGraphLaunch(gone, st) != cudaSuccess) cs = fail(XRDVI_ECUDA, "fit_batch: graph launch failed");
+    }
+    multi_plan_destroy(plan);
+    const xrdvi_status ls = cs != XRDVI_OK ? cs : check_launch("fit_batch");
+    std::vector<double> last(n, 0.0);
+    for (int i = 0; i < n; ++i) XR_CUDA(cudaMemcpyAsync(&last[i], ctxs[i]->elbo, 8, cudaMemcpyDeviceToHost, st));
+    XR_CUDA(cudaStreamSynchronize(st));
+    if (gmany) cudaGraphExecDestroy(gmany);
+    if (gone) cudaGraphExecDestroy(gone);
+    if (cap) cudaStreamDestroy(cap);
+    if (ls != XRDVI_OK) return ls;
+    xrdvi_status out = XRDVI_OK;
+    for (int i = 0; i < n; ++i) {
+        ctxs[i]->host_step += iters;
+        if (last_elbo) last_elbo[i] = last[i];
+        const xrdvi_status gs = iters > 0 ? check_gradients(ctxs[i]) : XRDVI_OK;
+        if (out == XRDVI_OK && iters > 0 && !std::isfinite(last[i]))
+            out = fail(XRDVI_ENONFINITE, "ELBO is not finite (context " + std::to_string(i) + ")");
+        if (out == XRDVI_OK && gs != XRDVI_OK) out = gs;
+    }
+    return out;
 }
 
 xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float *grad, float *f_out,
                              double *ll_out, double *lpj_out) {
+    NvtxRange nvtx("xrdvi_elbo_grad");
     if (!c) return fail(XRDVI_EINVAL, "null context");
     const Problem &P = c->P;
     const int S = c->W.S;
@@ -906,8 +1014,9 @@ xrdvi_status xrdvi_elbo_grad(xrdvi_ctx *c, const float *eps, double *elbo, float
     if (lpj_out) XR_CUDA(cudaMemcpyAsync(lpj_out, c->W.lpj, S * 8, cudaMemcpyDeviceToHost, st));
     XR_CUDA(cudaStreamSynchronize(st));
     if (elbo) *elbo = e;
+    const xrdvi_status gs = check_gradients(c);
     if (!std::isfinite(e)) return fail(XRDVI_ENONFINITE, "ELBO is not finite");
-    return XRDVI_OK;
+    return gs;
 }
 
 xrdvi_status xrdvi_forward_dev(xrdvi_ctx *c, const float *d_loc, const float *d_raw, const float *d_eps,
@@ -934,6 +1043,7 @@ xrdvi_status xrdvi_backward_dev(xrdvi_ctx *c, const float *d_loc, const float *d
 xrdvi_status xrdvi_posterior(xrdvi_ctx *c, int32_t S_post, uint64_t seed, int32_t top_m, double *pi,
                              uint64_t *combos, double *combo_logp, double *log_evidence, double *ess,
                              double *coverage_log) {
+    NvtxRange nvtx("xrdvi_posterior");
     if (!c) return fail(XRDVI_EINVAL, "null context");
     if (S_post < 1 || S_post > kMaxS) return fail(XRDVI_EINVAL, "S_post must be in [1, 65536]");
     if (top_m < 1 || top_m > 4096) return fail(XRDVI_EINVAL, "top_m must be in [1, 4096]");

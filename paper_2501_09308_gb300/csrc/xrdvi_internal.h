@@ -8,9 +8,20 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/xrdvi.h"
 
 namespace xrdvi {
+
+// NVTX range over a host scope (a profiler timeline shows create, fit,
+// posterior and the server's admission, slices and posteriors).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Profile kernels: 8 warps per block; each warp owns one (sample, 2-theta
 // tile) work item of 32 * kPts consecutive points, lane l holding points
@@ -193,6 +204,7 @@ struct Problem {
     float *Tb = nullptr;         // [3*N] Chebyshev terms T_j(z_i)
     float *Bb = nullptr;         // [N] B(beta) of the current step
     int grid_fwd = 0, grid_bwd = 0, grid_bwd_direct = 0, grid_fwd_direct = 0;
+    int *nonfinite = nullptr;    // [1] set by the gradient reduction on a NaN / infinite gradient (may be null)
 };
 
 // --- kernel launchers (xrdvi_kernels.cu) ------------------------------------
@@ -275,8 +287,8 @@ struct MultiStepPlan;
 MultiStepPlan *multi_plan_create(int cap);   // device argument storage for cap <= kMaxBatch fits
 void multi_plan_destroy(MultiStepPlan *p);
 bool multi_fit_eligible(const Problem &P, const Workspace &W, bool naive, bool iw);
-// Builds the batch's kernel arguments and block maps and uploads them on st
-// (stream-ordered after the steps already queued there).
+// Builds the batch's kernel arguments and block maps (host only: the
+// arguments are passed by value with every launch; st is unused).
 bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, cudaStream_t st);
 // Enqueues one SVI step (sample, ranges, profile, likelihood, backward,
 // gradient + Adam + ELBO) of every fit of the plan.
@@ -287,6 +299,10 @@ void ctx_fit_step(xrdvi_ctx *c, FitStep *out);
 bool ctx_multi_eligible(const xrdvi_ctx *c);
 void ctx_enqueue_steps(xrdvi_ctx *c, int n, cudaStream_t st);   // n fit steps, kernel by kernel
 void ctx_advance(xrdvi_ctx *c, int n);                          // host step counter += n
+// `steps` SVI steps of a batch (multi-fit launches of the plan, if any, then
+// the solo contexts' own kernels) captured on stream cap as one graph.
+xrdvi_status capture_batch_steps(const MultiStepPlan *plan, xrdvi_ctx *const *solo, int nsolo, int steps,
+                                 cudaStream_t cap, cudaGraphExec_t *out);
 cudaStream_t ctx_stream(const xrdvi_ctx *c);
 xrdvi_status ctx_read_trace(xrdvi_ctx *c, int n, double *host);  // last n ELBO estimates
 

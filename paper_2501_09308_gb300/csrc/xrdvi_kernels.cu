@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -1729,6 +1730,7 @@ struct GradArgs {
     float gate_tau, gate_a0;
     float *gate_a, *m_gate, *v_gate;   // [K] gate logits and their Adam moments
     float *grad_gate;   // [K] gate gradient out (may be null)
+    int *nonfinite;     // set to 1 when a gradient entry is NaN or infinite (may be null)
 };
 
 // ELBO = mean_s [LL_s + log prior + log Jacobian] + entropy, in FP64 with a
@@ -1944,6 +1946,7 @@ __device__ __forceinline__ void grad_body(const GradArgs &a, Blk blk) {
         const bool fixed = (j == 3 && a.fix_r) || (j == 4 && a.fix_a);   // not part of q: no gradient
         if (fixed) grad = 0.0;
         if (a.grad_out) a.grad_out[bk * 10 + threadIdx.x] = static_cast<float>(grad);
+        if (a.nonfinite && !isfinite(grad)) atomicOr(a.nonfinite, 1);
         if (a.adam && !fixed) {
             const int t = *a.d_iter + 1;
             const int idx = bk * 10 + threadIdx.x;
@@ -1973,8 +1976,8 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) { grad_body(a, GridBlo
 // Multi-fit step kernels (continuous batching of fits of different K and N):
 // one launch runs one SVI-step kernel for every fit of a batch.  Fit f owns
 // the blocks [start[f], start[f+1]) of the per-fit grid (sampling, ranges,
-// likelihood, gradient); its arguments are staged in shared memory and the
-// per-fit body runs on block indices relative to the fit.  The two profile
+// likelihood, gradient); every fit's arguments travel in the launch's
+// parameters, and the per-fit body runs on block indices relative to the fit.  The two profile
 // kernels are persistent over all fits: a block starts on the fit its index
 // falls in and then helps the others, re-staging the peak table for each fit
 // it visits; each fit's items come from that fit's own work counter.  Every
@@ -1990,41 +1993,36 @@ __device__ __forceinline__ int fit_of_block(const FitMap &m, int b) {
     return lo;
 }
 
-// Copies one fit's arguments into shared memory (ends with a barrier).
+// The arguments of every fit of a batch, passed by value: they live in the
+// kernel's parameter space like a plain kernel's, which the compiler reloads
+// instead of holding in registers (a copy in shared memory made the backward
+// spill).  Under the 32 KB parameter limit for kMaxBatch fits.
 template <class T>
-__device__ __forceinline__ void stage_args(T &dst, const T &src) {
-    static_assert(sizeof(T) % 4 == 0, "argument blocks are whole words");
-    const int *q = reinterpret_cast<const int *>(&src);
-    int *d = reinterpret_cast<int *>(&dst);
-    for (int i = threadIdx.x; i < static_cast<int>(sizeof(T) / 4); i += blockDim.x) d[i] = q[i];
-    __syncthreads();
+struct MultiArgs {
+    T fit[kMaxBatch];
+};
+static_assert(sizeof(MultiArgs<ProfArgs>) + sizeof(FitMap) < 32000, "kernel parameter space");
+static_assert(sizeof(MultiArgs<SampleArgs>) + sizeof(FitMap) < 32000, "kernel parameter space");
+static_assert(sizeof(MultiArgs<GradArgs>) + sizeof(FitMap) < 32000, "kernel parameter space");
+
+__global__ void __launch_bounds__(128) k_sample_multi(const __grid_constant__ MultiArgs<SampleArgs> ma, FitMap m) {
+    const int f = fit_of_block(m, blockIdx.x);
+    sample_body(ma.fit[f], static_cast<int>(blockIdx.x) - m.start[f]);
 }
 
-__global__ void __launch_bounds__(128) k_sample_multi(const SampleArgs *fa, FitMap m) {
-    __shared__ SampleArgs a;
+__global__ void __launch_bounds__(256) k_ranges_multi(const __grid_constant__ MultiArgs<ProfArgs> ma, FitMap m) {
     const int f = fit_of_block(m, blockIdx.x);
-    stage_args(a, fa[f]);
-    sample_body(a, static_cast<int>(blockIdx.x) - m.start[f]);
+    ranges_body(ma.fit[f], static_cast<int>(blockIdx.x) - m.start[f], m.start[f + 1] - m.start[f]);
 }
 
-__global__ void __launch_bounds__(256) k_ranges_multi(const ProfArgs *fa, FitMap m) {
-    __shared__ ProfArgs a;
+__global__ void __launch_bounds__(kTile) k_lik_multi(const __grid_constant__ MultiArgs<ProfArgs> ma, FitMap m) {
     const int f = fit_of_block(m, blockIdx.x);
-    stage_args(a, fa[f]);
-    ranges_body(a, static_cast<int>(blockIdx.x) - m.start[f], m.start[f + 1] - m.start[f]);
+    lik_body(ma.fit[f], FixedBlock{static_cast<int>(blockIdx.x) - m.start[f], 0});
 }
 
-__global__ void __launch_bounds__(kTile) k_lik_multi(const ProfArgs *fa, FitMap m) {
-    __shared__ ProfArgs a;
+__global__ void __launch_bounds__(256) k_grad_multi(const __grid_constant__ MultiArgs<GradArgs> ma, FitMap m) {
     const int f = fit_of_block(m, blockIdx.x);
-    stage_args(a, fa[f]);
-    lik_body(a, FixedBlock{static_cast<int>(blockIdx.x) - m.start[f], 0});
-}
-
-__global__ void __launch_bounds__(256) k_grad_multi(const GradArgs *fa, FitMap m) {
-    __shared__ GradArgs a;
-    const int f = fit_of_block(m, blockIdx.x);
-    stage_args(a, fa[f]);
+    const GradArgs &a = ma.fit[f];
     const int lb = static_cast<int>(blockIdx.x) - m.start[f];
     const int X = a.B * a.K + a.elbo_blocks;   // blocks per sample block (phases, then ELBO blocks)
     grad_body(a, FixedBlock{lb % X, lb / X});
@@ -2032,15 +2030,15 @@ __global__ void __launch_bounds__(256) k_grad_multi(const GradArgs *fa, FitMap m
 
 // Persistent profile kernels over all fits (forward: kFwd, else backward).
 template <bool kFwd, bool kWide>
-__global__ void __launch_bounds__(kThreads, 3) k_direct_multi(const ProfArgs *fa, FitMap m) {
+__global__ void __launch_bounds__(kThreads, 3) k_direct_multi(const __grid_constant__ MultiArgs<ProfArgs> ma,
+                                                              FitMap m) {
     extern __shared__ float4 s_raw[];
-    __shared__ ProfArgs a;
     __shared__ int s_done;
     const int f0 = fit_of_block(m, blockIdx.x);
     for (int v = 0; v < m.n; ++v) {
         const int f = f0 + v < m.n ? f0 + v : f0 + v - m.n;
-        __syncthreads();   // every warp is done with the previous fit's table and arguments
-        stage_args(a, fa[f]);
+        const ProfArgs &a = ma.fit[f];
+        __syncthreads();   // every warp is done with the previous fit's table
         if (threadIdx.x == 0) s_done = atomicAdd(a.counter, 0) >= a.S * a.T * a.C;   // nothing left: skip the table
         __syncthreads();
         if (s_done) continue;
@@ -2522,6 +2520,7 @@ static GradArgs grad_args(const Problem &P, Workspace &W, const float *loc_in, c
     a.pr_alpha_isd2 = static_cast<float>(1.0 / (P.prior.alpha_sd * P.prior.alpha_sd));
     a.fix_r = P.fix_r ? 1 : 0; a.fix_a = P.fix_alpha ? 1 : 0;
     a.area_norm = P.area_norm ? 1 : 0;
+    a.nonfinite = P.nonfinite;
     a.gzy = P.gates ? W.gzy : nullptr; a.gate_tau = P.gate_tau; a.gate_a0 = P.gate_a0;
     a.gate_a = P.gate_a; a.m_gate = P.m_gate; a.v_gate = P.v_gate; a.grad_gate = grad_out ? P.grad_gate : nullptr;
     a.NB = (a.S_sub + 31) / 32;   // 32 samples (4 per warp) per block
@@ -2553,48 +2552,33 @@ void launch_grad(const Problem &P, Workspace &W, const float *loc_in, const floa
 }
 
 // --- multi-fit step (continuous batching) ---------------------------------------
-struct MultiStepPlan {
-    int cap = 0, n = 0;
-    unsigned char *d_args = nullptr;          // [cap] SampleArgs, ProfArgs (fwd), ProfArgs (bwd), GradArgs
-    unsigned char *h_args[2] = {nullptr, nullptr};   // pinned host images of d_args, used in turn
-    cudaEvent_t h_done[2] = {nullptr, nullptr};      // the upload from each image has been read
-    int h_next = 0;
-    size_t bytes = 0;
-    FitMap m_sample, m_ranges, m_fwd, m_lik, m_bwd, m_grad;
-    size_t smem = 0;
+// Fits whose peak tables take the same layout and allow the same number of
+// resident profile blocks per SM share one persistent launch; a fit with a
+// larger table (fewer blocks per SM) does not lower the others' occupancy.
+struct MultiClass {
     bool wide = true;
-    size_t o_prof_f = 0, o_prof_b = 0, o_grad = 0;
+    int n = 0;
+    size_t smem = 0;
+    int grid1_fwd = 0, grid1_bwd = 0;   // a class of one fit runs the fit's own kernels on these grids
+    MultiArgs<ProfArgs> pf, pb;   // forward (work counter 0) and backward (counter 2) arguments
+    FitMap m_fwd, m_bwd;
 };
 
-void multi_plan_destroy(MultiStepPlan *p) {
-    if (!p) return;
-    if (p->d_args) cudaFree(p->d_args);
-    for (int i = 0; i < 2; ++i) {
-        if (p->h_done[i]) cudaEventSynchronize(p->h_done[i]);
-        if (p->h_args[i]) cudaFreeHost(p->h_args[i]);
-        if (p->h_done[i]) cudaEventDestroy(p->h_done[i]);
-    }
-    delete p;
-}
+struct MultiStepPlan {
+    int cap = 0, n = 0;
+    MultiArgs<SampleArgs> sa;
+    MultiArgs<ProfArgs> pf;       // every fit: ranges and likelihood
+    MultiArgs<GradArgs> ga;
+    FitMap m_sample, m_ranges, m_lik, m_grad;
+    std::vector<MultiClass> classes;
+};
+
+void multi_plan_destroy(MultiStepPlan *p) { delete p; }
 
 MultiStepPlan *multi_plan_create(int cap) {
     if (cap < 1 || cap > kMaxBatch) return nullptr;
     MultiStepPlan *p = new MultiStepPlan();
     p->cap = cap;
-    const size_t a16 = 16;
-    auto up = [&](size_t v) { return (v + a16 - 1) / a16 * a16; };
-    p->o_prof_f = up(sizeof(SampleArgs) * cap);
-    p->o_prof_b = p->o_prof_f + up(sizeof(ProfArgs) * cap);
-    p->o_grad = p->o_prof_b + up(sizeof(ProfArgs) * cap);
-    p->bytes = p->o_grad + up(sizeof(GradArgs) * cap);
-    bool ok = cudaMalloc(&p->d_args, p->bytes) == cudaSuccess;
-    for (int i = 0; i < 2 && ok; ++i)
-        ok = cudaMallocHost(&p->h_args[i], p->bytes) == cudaSuccess &&
-             cudaEventCreateWithFlags(&p->h_done[i], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-        multi_plan_destroy(p);
-        return nullptr;
-    }
     // the shared-memory attribute of the persistent kernels (largest table any fit may have)
     const int smax = static_cast<int>(static_cast<size_t>(kMaxPeaks) * sizeof(float2) +
                                       static_cast<size_t>(kMaxK + 1) * sizeof(int));
@@ -2611,7 +2595,7 @@ bool multi_fit_eligible(const Problem &P, const Workspace &W, bool naive, bool i
 }
 
 // Splits `grid` persistent blocks over the fits in proportion to their work
-// items (at least one block each).
+// (at least one block each); blocks that finish their fit help the others.
 static void persistent_map(FitMap &m, const std::vector<long long> &items, int grid) {
     const int n = static_cast<int>(items.size());
     long long tot = 0;
@@ -2630,37 +2614,39 @@ static void persistent_map(FitMap &m, const std::vector<long long> &items, int g
     m.start[n] = grid;
 }
 
+static int direct_occupancy(bool fwd, bool wide, size_t smem) {
+    int occ = 1;
+    if (fwd) {
+        if (wide) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direct_multi<true, true>, kThreads, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direct_multi<true, false>, kThreads, smem);
+    } else {
+        if (wide) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direct_multi<false, true>, kThreads, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direct_multi<false, false>, kThreads, smem);
+    }
+    return occ < 1 ? 1 : occ;
+}
+
 bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, cudaStream_t st) {
+    (void)st;
     if (!p || n < 1 || n > p->cap) return false;
-    // the host image used two uploads ago must have been read before it is rewritten
-    unsigned char *h = p->h_args[p->h_next];
-    if (cudaEventSynchronize(p->h_done[p->h_next]) != cudaSuccess) return false;
     p->n = n;
-    p->wide = true;
-    for (int f = 0; f < n; ++f) p->wide = p->wide && fits[f].P->wide;
-    size_t smem = 0;
-    std::vector<long long> items(n);
+    p->classes.clear();
     int bs = 0, br = 0, bl = 0, bg = 0;
     p->m_sample.n = p->m_ranges.n = p->m_lik.n = p->m_grad.n = n;
+    std::vector<long long> work(n), items(n);
+    std::vector<int> cls(n);
     for (int f = 0; f < n; ++f) {
         const FitStep &F = fits[f];
         const Problem &P = *F.P;
         Workspace &W = *F.W;
         SampleArgs sa = sample_args(P, W, F.loc, F.raw, nullptr, F.seed, 0u, F.step, 0u, F.iter, F.ent);
         ProfArgs pf = prof_args(P, W, nullptr);
-        ProfArgs pb = pf;
-        pb.counter = W.counters + 2;
         GradArgs ga = grad_args(P, W, F.loc, F.raw, F.loc, F.raw, nullptr, true, F.ac, F.m, F.v, F.iter, F.step,
                                 F.ent, F.elbo, F.trace);
         ga.elbo_blocks = W.B;   // the ELBO in extra blocks of the gradient kernel, as in a fit step
-        std::memcpy(h + sizeof(SampleArgs) * f, &sa, sizeof(sa));
-        std::memcpy(h + p->o_prof_f + sizeof(ProfArgs) * f, &pf, sizeof(pf));
-        std::memcpy(h + p->o_prof_b + sizeof(ProfArgs) * f, &pb, sizeof(pb));
-        std::memcpy(h + p->o_grad + sizeof(GradArgs) * f, &ga, sizeof(ga));
-        const size_t tb = static_cast<size_t>(P.Mtot) * (p->wide ? sizeof(float4) : sizeof(float2)) +
-                          static_cast<size_t>(P.K + 1) * sizeof(int);
-        smem = tb > smem ? tb : smem;
-        items[f] = static_cast<long long>(W.S) * P.T * W.C;
+        p->sa.fit[f] = sa;
+        p->pf.fit[f] = pf;
+        p->ga.fit[f] = ga;
         p->m_sample.start[f] = bs;
         bs += W.S;
         p->m_ranges.start[f] = br;
@@ -2670,51 +2656,82 @@ bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, 
         bl += W.S * P.T;
         p->m_grad.start[f] = bg;
         bg += (W.B * P.K + ga.elbo_blocks) * ga.NB;
+        // the fit's own table layout and residency, as in its standalone kernels
+        const size_t tb = P.smem;
+        const int occ = std::min(direct_occupancy(true, P.wide, tb), direct_occupancy(false, P.wide, tb));
+        int c = 0;
+        for (; c < static_cast<int>(p->classes.size()); ++c)
+            if (p->classes[c].wide == P.wide &&
+                std::min(direct_occupancy(true, P.wide, p->classes[c].smem),
+                         direct_occupancy(false, P.wide, p->classes[c].smem)) == occ)
+                break;
+        if (c == static_cast<int>(p->classes.size())) {
+            p->classes.emplace_back();
+            p->classes[c].wide = P.wide;
+        }
+        MultiClass &C = p->classes[c];
+        C.smem = std::max(C.smem, tb);
+        C.grid1_fwd = grid_for(P.grid_fwd_direct, W.S * P.T * W.C);
+        C.grid1_bwd = grid_for(P.grid_bwd_direct, W.S * P.T * W.C);
+        ProfArgs pb = pf;
+        pb.counter = W.counters + 2;
+        C.pf.fit[C.n] = pf;
+        C.pb.fit[C.n] = pb;
+        cls[f] = c;
+        work[f] = static_cast<long long>(W.S) * P.T * P.Mtot;   // (sample, tile, peak) triples
+        items[f] = static_cast<long long>(W.S) * P.T * W.C;
+        ++C.n;
     }
     p->m_sample.start[n] = bs;
     p->m_ranges.start[n] = br;
     p->m_lik.start[n] = bl;
     p->m_grad.start[n] = bg;
-    p->smem = smem;
-    int occ_f = 1, occ_b = 1;
-    if (p->wide) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_direct_multi<true, true>, kThreads, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_direct_multi<false, true>, kThreads, smem);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_direct_multi<true, false>, kThreads, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_direct_multi<false, false>, kThreads, smem);
+    for (int c = 0; c < static_cast<int>(p->classes.size()); ++c) {
+        MultiClass &C = p->classes[c];
+        std::vector<long long> w;
+        long long nitems = 0;
+        for (int f = 0; f < n; ++f)
+            if (cls[f] == c) {
+                w.push_back(work[f]);
+                nitems += items[f];
+            }
+        const auto grid = [&](int occ) {
+            const long long need = (nitems + kWarps - 1) / kWarps;
+            const long long g = static_cast<long long>(occ) * sm_count;
+            return static_cast<int>(need < g ? need : g);
+        };
+        persistent_map(C.m_fwd, w, grid(direct_occupancy(true, C.wide, C.smem)));
+        persistent_map(C.m_bwd, w, grid(direct_occupancy(false, C.wide, C.smem)));
     }
-    occ_f = occ_f < 1 ? 1 : occ_f;
-    occ_b = occ_b < 1 ? 1 : occ_b;
-    long long tot = 0;
-    for (long long v : items) tot += v;
-    const auto cap_grid = [&](int occ) {
-        const long long need = (tot + kWarps - 1) / kWarps;
-        const long long g = static_cast<long long>(occ) * sm_count;
-        return static_cast<int>(need < g ? need : g);
-    };
-    persistent_map(p->m_fwd, items, cap_grid(occ_f));
-    persistent_map(p->m_bwd, items, cap_grid(occ_b));
-    // stream-ordered: the kernels of steps queued before read the previous image
-    if (cudaMemcpyAsync(p->d_args, h, p->bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return false;
-    if (cudaEventRecord(p->h_done[p->h_next], st) != cudaSuccess) return false;
-    p->h_next ^= 1;
     return true;
 }
 
 void multi_plan_launch_step(const MultiStepPlan *p, cudaStream_t st) {
-    const SampleArgs *sa = reinterpret_cast<const SampleArgs *>(p->d_args);
-    const ProfArgs *pf = reinterpret_cast<const ProfArgs *>(p->d_args + p->o_prof_f);
-    const ProfArgs *pb = reinterpret_cast<const ProfArgs *>(p->d_args + p->o_prof_b);
-    const GradArgs *ga = reinterpret_cast<const GradArgs *>(p->d_args + p->o_grad);
-    k_sample_multi<<<p->m_sample.start[p->n], 128, 0, st>>>(sa, p->m_sample);
-    k_ranges_multi<<<p->m_ranges.start[p->n], 256, 0, st>>>(pf, p->m_ranges);
-    if (p->wide) k_direct_multi<true, true><<<p->m_fwd.start[p->n], kThreads, p->smem, st>>>(pf, p->m_fwd);
-    else k_direct_multi<true, false><<<p->m_fwd.start[p->n], kThreads, p->smem, st>>>(pf, p->m_fwd);
-    k_lik_multi<<<p->m_lik.start[p->n], kTile, 0, st>>>(pf, p->m_lik);
-    if (p->wide) k_direct_multi<false, true><<<p->m_bwd.start[p->n], kThreads, p->smem, st>>>(pb, p->m_bwd);
-    else k_direct_multi<false, false><<<p->m_bwd.start[p->n], kThreads, p->smem, st>>>(pb, p->m_bwd);
-    k_grad_multi<<<p->m_grad.start[p->n], 256, 0, st>>>(ga, p->m_grad);
+    // the arguments travel with each launch (kernel parameters)
+    k_sample_multi<<<p->m_sample.start[p->n], 128, 0, st>>>(p->sa, p->m_sample);
+    k_ranges_multi<<<p->m_ranges.start[p->n], 256, 0, st>>>(p->pf, p->m_ranges);
+    for (const MultiClass &C : p->classes) {
+        if (C.n == 1) {   // alone in its class: the fit's own kernel (arguments in the constant bank)
+            if (C.wide) k_fwd_direct<false, true, false><<<C.grid1_fwd, kThreads, C.smem, st>>>(C.pf.fit[0]);
+            else k_fwd_direct<false, false, false><<<C.grid1_fwd, kThreads, C.smem, st>>>(C.pf.fit[0]);
+        } else if (C.wide) {
+            k_direct_multi<true, true><<<C.m_fwd.start[C.n], kThreads, C.smem, st>>>(C.pf, C.m_fwd);
+        } else {
+            k_direct_multi<true, false><<<C.m_fwd.start[C.n], kThreads, C.smem, st>>>(C.pf, C.m_fwd);
+        }
+    }
+    k_lik_multi<<<p->m_lik.start[p->n], kTile, 0, st>>>(p->pf, p->m_lik);
+    for (const MultiClass &C : p->classes) {
+        if (C.n == 1) {
+            if (C.wide) k_bwd_direct<true, false><<<C.grid1_bwd, kThreads, C.smem, st>>>(C.pb.fit[0]);
+            else k_bwd_direct<false, false><<<C.grid1_bwd, kThreads, C.smem, st>>>(C.pb.fit[0]);
+        } else if (C.wide) {
+            k_direct_multi<false, true><<<C.m_bwd.start[C.n], kThreads, C.smem, st>>>(C.pb, C.m_bwd);
+        } else {
+            k_direct_multi<false, false><<<C.m_bwd.start[C.n], kThreads, C.smem, st>>>(C.pb, C.m_bwd);
+        }
+    }
+    k_grad_multi<<<p->m_grad.start[p->n], 256, 0, st>>>(p->ga, p->m_grad);
 }
 
 void launch_posterior(const Problem &P, Workspace &W, PostBuffers &B, int top_m, cudaStream_t st) {

@@ -137,7 +137,11 @@ void xrdvi_server::admit_loop() {
         xrdvi_peaks pk{static_cast<int32_t>(r->off.size() - 1), r->off.data(), r->pos.data(), r->inten.data()};
         xrdvi_pattern pt{static_cast<int32_t>(r->x.size()), r->x.data(), r->y.data(), r->bg.data()};
         xrdvi_ctx *c = nullptr;
-        const xrdvi_status s = xrdvi::create_context(&pk, &pt, &r->cfg, pool, stream, &c);
+        xrdvi_status s;
+        {
+            xrdvi::NvtxRange nvtx("server admit");
+            s = xrdvi::create_context(&pk, &pt, &r->cfg, pool, stream, &c);
+        }
         std::lock_guard<std::mutex> lk(mu);
         if (s != XRDVI_OK) {
             r->status = s;
@@ -166,6 +170,17 @@ void xrdvi_server::engine_loop() {
     bool ev_live[2] = {false, false};
     int slot = 0;
     std::vector<xrdvi::FitStep> fs;
+    std::vector<xrdvi_ctx *> solo;
+    // the batch's steps are replayed from graphs captured (on a private
+    // stream) whenever the batch changes: one of a whole slice, one of a step
+    cudaStream_t cap = nullptr;
+    cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    cudaGraphExec_t g_slice = nullptr, g_one = nullptr;
+    auto drop_graphs = [&] {
+        if (g_slice) cudaGraphExecDestroy(g_slice);
+        if (g_one) cudaGraphExecDestroy(g_one);
+        g_slice = g_one = nullptr;
+    };
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(mu);
@@ -184,7 +199,7 @@ void xrdvi_server::engine_loop() {
                 std::lock_guard<std::mutex> lk(mu);
                 finished.push_back(members[i]);
                 cv_reap.notify_all();
-                if (members[i]->batched) dirty = true;
+                dirty = true;   // the captured steps must no longer include it
                 members.erase(members.begin() + i);
             } else {
                 ++i;
@@ -193,21 +208,38 @@ void xrdvi_server::engine_loop() {
         if (members.empty()) continue;
         if (dirty) {
             fs.clear();
-            for (Fit *f : members)
+            solo.clear();
+            for (Fit *f : members) {
                 if (f->batched) {
                     xrdvi::FitStep st;
                     xrdvi::ctx_fit_step(f->c, &st);
                     fs.push_back(st);
+                } else {
+                    solo.push_back(f->c);
                 }
+            }
             if (!fs.empty()) xrdvi::multi_plan_set(plan, fs.data(), static_cast<int>(fs.size()), sm_count, stream);
+            drop_graphs();
+            const xrdvi::MultiStepPlan *pl = fs.empty() ? nullptr : plan;
+            if (xrdvi::capture_batch_steps(pl, solo.data(), static_cast<int>(solo.size()), kSliceSteps, cap,
+                                           &g_slice) != XRDVI_OK ||
+                xrdvi::capture_batch_steps(pl, solo.data(), static_cast<int>(solo.size()), 1, cap, &g_one) !=
+                    XRDVI_OK)
+                drop_graphs();   // launched kernel by kernel instead
             dirty = false;
         }
+        xrdvi::NvtxRange nvtx("server slice");
         int n = kSliceSteps;
         for (Fit *f : members) n = std::min(n, f->r->opts.iters - f->steps);
-        for (int i = 0; i < n; ++i) {
-            if (!fs.empty()) xrdvi::multi_plan_launch_step(plan, stream);
-            for (Fit *f : members)
-                if (!f->batched) xrdvi::ctx_enqueue_steps(f->c, 1, stream);
+        if (n == kSliceSteps && g_slice) {
+            cudaGraphLaunch(g_slice, stream);
+        } else if (g_one) {
+            for (int i = 0; i < n; ++i) cudaGraphLaunch(g_one, stream);
+        } else {
+            for (int i = 0; i < n; ++i) {
+                if (!fs.empty()) xrdvi::multi_plan_launch_step(plan, stream);
+                for (xrdvi_ctx *c : solo) xrdvi::ctx_enqueue_steps(c, 1, stream);
+            }
         }
         for (Fit *f : members) {
             f->steps += n;
@@ -219,6 +251,9 @@ void xrdvi_server::engine_loop() {
         if (ev_live[slot ^ 1]) cudaEventSynchronize(ev[slot ^ 1]);
         slot ^= 1;
     }
+    cudaStreamSynchronize(stream);
+    drop_graphs();
+    if (cap) cudaStreamDestroy(cap);
     for (int i = 0; i < 2; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
     std::lock_guard<std::mutex> lk(mu);
@@ -237,6 +272,7 @@ void xrdvi_server::reap_loop() {
             f = finished.front();
             finished.pop_front();
         }
+        xrdvi::NvtxRange nvtx("server posterior");
         Request &r = *f->r;
         xrdvi_ctx *c = f->c;
         const int K = static_cast<int>(r.off.size()) - 1, W = (K + 63) / 64;

@@ -103,6 +103,7 @@ SIGNATURES = {
     "xrdvi_destroy": (None, [_vp]),
     "xrdvi_set_stream": (ctypes.c_int, [_vp, _vp]),
     "xrdvi_fit": (ctypes.c_int, [_vp, _i32, P(_d)]),
+    "xrdvi_fit_batch": (ctypes.c_int, [P(_vp), _i32, _i32, P(_d)]),
     "xrdvi_elbo_grad": (ctypes.c_int, [_vp, P(_f), P(_d), P(_f), P(_f), P(_d), P(_d)]),
     "xrdvi_posterior": (ctypes.c_int, [_vp, _i32, _u64, _i32, P(_d), P(_u64), P(_d), P(_d), P(_d), P(_d)]),
     "xrdvi_get_params": (ctypes.c_int, [_vp, P(_f), P(_f)]),
@@ -218,6 +219,15 @@ def xrdvi_fit(h, iters, trace=True):
     tr = np.zeros(max(iters, 1), dtype=np.float64) if trace else None
     _check(lib().xrdvi_fit(h, int(iters), _ptr(tr, _d) if trace else None))
     return tr[:iters] if trace else None
+
+
+def xrdvi_fit_batch(handles, iters):
+    """Advances several contexts together (shared kernel launches per step);
+    returns each fit's last ELBO estimate."""
+    arr = (_vp * len(handles))(*[h.value if isinstance(h, _vp) else h for h in handles])
+    last = np.zeros(len(handles))
+    _check(lib().xrdvi_fit_batch(arr, len(handles), int(iters), _ptr(last, _d)))
+    return last
 
 
 def xrdvi_get_info(h) -> Info:

@@ -141,6 +141,31 @@ def test_unsorted_peak_tables_match_the_oracle(device_arrays):
     assert_parity(g, o)
 
 
+def test_non_finite_fit_is_reported_and_cleared():
+    """A state whose intensity overflows FP32 (h = e^200) makes the profile,
+    the ELBO and the gradient non-finite: the fit returns ENONFINITE (the
+    gradient reduction flags a NaN or infinite entry on the device, the host
+    checks it with the last ELBO).  The flag is cleared when read, so the fit
+    resumes normally from a checkpoint taken before."""
+    inst = synth.small_problem(K=3, M=6, N=300, S=4, seed=17)
+    ctx = xrdvi.Context.from_instance(inst, S=4)
+    loc0, raw0 = ctx.params()
+    good = ctx.state()
+    loc = loc0.copy()
+    loc[:, 0] = 200.0
+    ctx.set_params(loc, raw0)
+    with pytest.raises(xrdvi.XrdviError) as e:
+        ctx.fit(3)
+    assert e.value.status == 5
+    with pytest.raises(xrdvi.XrdviError) as e:
+        ctx.elbo_grad(synth.normals(3, 4, inst.K))
+    assert e.value.status == 5
+    ctx.set_state(good)   # parameters and Adam moments from before the overflow
+    tr = ctx.fit(3)
+    ctx.close()
+    assert np.all(np.isfinite(tr))
+
+
 def test_alpha_below_clamp():
     inst = synth.small_problem(K=2, M=5, N=300, S=4, seed=12)
     ctx = xrdvi.Context.from_instance(inst, S=4)

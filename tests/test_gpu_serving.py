@@ -77,6 +77,35 @@ def test_batched_and_variant_fits_in_one_mix_equal_their_standalone_fits():
         np.testing.assert_array_equal(r["pi"], post["pi"])
 
 
+def test_fit_batch_equals_standalone_fits():
+    """xrdvi_fit_batch: five contexts of different K and N (one a variant that
+    takes its own kernels) advanced together end exactly where xrdvi_fit
+    leaves each of them, also when the steps are split over several calls;
+    a context listed twice is rejected."""
+    probs = _problems() + [synth.small_problem(K=5, M=9, N=1100, S=8, seed=77, x_step=0.04),
+                           synth.small_problem(K=4, M=7, N=700, S=8, seed=78)]
+    extra = [{}, {}, {}, {"flags": xrdvi.FLAG_SEC_WIDTH}, {"flags": xrdvi.FLAG_AREA_NORM}]
+    ref = []
+    for i, p in enumerate(probs):
+        c = xrdvi.Context.from_instance(p, S=p.S, seed=300 + i, **extra[i])
+        tr = c.fit(ITERS)
+        ref.append((c.params(), tr[-1]))
+        c.close()
+    cs = [xrdvi.Context.from_instance(p, S=p.S, seed=300 + i, **extra[i]) for i, p in enumerate(probs)]
+    last = xrdvi.xrdvi_fit_batch([c.h for c in cs], 37)
+    last = xrdvi.xrdvi_fit_batch([c.h for c in cs], ITERS - 37)
+    for c, (params, e), le in zip(cs, ref, last):
+        np.testing.assert_array_equal(c.params()[0], params[0])
+        np.testing.assert_array_equal(c.params()[1], params[1])
+        assert le == e
+        assert c.info.step == ITERS
+    with pytest.raises(xrdvi.XrdviError) as err:
+        xrdvi.xrdvi_fit_batch([cs[0].h, cs[0].h], 1)
+    assert err.value.status == 1
+    for c in cs:
+        c.close()
+
+
 def test_batched_fits_overlap_on_the_device():
     """Eight small fits served together finish in much less time than the
     same fits run one after another: their steps share kernel launches
