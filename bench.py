@@ -72,6 +72,10 @@ OPS = {
     "far_bwd": {"far_nodes": (8, 1)},
 }
 MUFU_LANES = 32
+# The contract count of the work per executed evaluation (every (sample, peak,
+# point) term and every far-field (peak, node) term): 8 FP32 lane operations +
+# 2 MUFU in the forward profile kernel, 16 FP32 + 2 MUFU in the backward.
+CONTRACT_OPS = {"k_fwd_direct": (8, 2), "k_bwd_direct": (16, 2)}
 
 
 def parse():
@@ -380,8 +384,15 @@ def kernel_rooflines(kern, work, sms, clock_mhz):
         if ops == 0:
             continue
         ach = ops / (kern[name] * 1e-3) / 1e12
-        out[slots[name]] = {"ms": kern[name], "fp32_tops": ach, "frac": ach / fp32_peak,
-                     "mufu_frac": mufu / (kern[name] * 1e-3) / 1e12 / mufu_peak}
+        row = {"ms": kern[name], "fp32_tops_per_kind": ach, "frac_per_kind": ach / fp32_peak,
+               "mufu_frac_per_kind": mufu / (kern[name] * 1e-3) / 1e12 / mufu_peak}
+        if slots[name] in CONTRACT_OPS:
+            executed = work["uniform"] + work["mixed"] + work["gauss_reach"] + work["far_nodes"]
+            c_ops, c_mufu = CONTRACT_OPS[slots[name]]
+            c_ach = c_ops * executed / (kern[name] * 1e-3) / 1e12
+            row.update({"executed_evals": executed, "fp32_tops": c_ach, "frac": c_ach / fp32_peak,
+                        "mufu_frac": c_mufu * executed / (kern[name] * 1e-3) / 1e12 / mufu_peak})
+        out[slots[name]] = row
     return out
 
 
@@ -585,9 +596,13 @@ def main():
             "unit": "Top/s (FP32 lane ops)",
             "frac": per_kernel[dom]["frac"],
             "traffic": recorded_traffic(dom),
-            "peak_source": f"FP32 pipe: {sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({peak_src} sm_max_mhz); "
-                           "algorithmic FP32 ops per executed evaluation of each kind x the step's counts",
+            "peak_source": f"FP32 pipe: {sms} SMs x 128 lanes x {clock_mhz:.0f} MHz ({peak_src} sm_max_mhz, "
+                           "nominal lane count; no measured FP32 peak exists for this pool)",
+            "count": "contract: 8 FP32 + 2 MUFU per executed evaluation (forward), 16 + 2 (backward), times the "
+                     "step's executed (sample, peak, point) and far-field (peak, node) terms; *_per_kind: the "
+                     "builder's finer count of each kind of evaluation (OPS in bench.py)",
             "mufu_frac": per_kernel[dom]["mufu_frac"],
+            "frac_per_kind": per_kernel[dom]["frac_per_kind"],
             "kernels": per_kernel,
         },
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

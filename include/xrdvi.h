@@ -498,6 +498,21 @@ xrdvi_status xrdvi_gemm_nt_tf32x3(int32_t M, int32_t N, int32_t K, const float *
  * No counterpart in the paper, which does not name its generator. */
 xrdvi_status xrdvi_philox4x32_10(int32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
+/* Bounds-check build.  The library compiled with XRDVI_DEBUG defined (the
+ * Python binding loads it when the environment has XRDVI_DEBUG=1) clamps every
+ * peak-table index and every decoded peak range of the profile kernels into
+ * bounds and records the number of the first check that failed in a device
+ * word (1-3 table lookups, 4-9 the range bounds), without a trap or an early
+ * exit, so a fault becomes a status: xrdvi_fit, xrdvi_elbo_grad and
+ * xrdvi_fit_batch return ECUDA naming the check.  xrdvi_debug_word copies the
+ * word to *word (0: no violation) and clears it if reset is non-zero.
+ * xrdvi_debug_selftest runs one lookup past the end of a one-entry table
+ * through the same check (the access itself is clamped to the table) so that a
+ * test can see the word set.  In a regular build both return EINVAL.  No
+ * counterpart in the paper. */
+xrdvi_status xrdvi_debug_word(int32_t *word, int32_t reset);
+xrdvi_status xrdvi_debug_selftest(void);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *xrdvi_last_error(void);
 

@@ -323,6 +323,10 @@ xrdvi_status check_gradients(xrdvi_ctx *c) {
     XR_CUDA(cudaMemcpyAsync(&bad, c->P.nonfinite, 4, cudaMemcpyDeviceToHost, c->stream));
     XR_CUDA(cudaMemsetAsync(c->P.nonfinite, 0, 4, c->stream));
     XR_CUDA(cudaStreamSynchronize(c->stream));
+    if (debug_build()) {   // bounds-check build: a violated check fails the call
+        const int w = debug_word(false);
+        if (w) return fail(XRDVI_ECUDA, "bounds check " + std::to_string(w) + " failed (XRDVI_DEBUG build)");
+    }
     if (bad) return fail(XRDVI_ENONFINITE, "a gradient entry is not finite");
     return XRDVI_OK;
 }
@@ -1399,6 +1403,23 @@ xrdvi_status xrdvi_philox4x32_10(int32_t n, const uint32_t *ctr, const uint32_t 
     cudaStreamDestroy(s);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("philox4x32_10: ") + cudaGetErrorString(e));
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_debug_word(int32_t *word, int32_t reset) {
+    if (!word) return fail(XRDVI_EINVAL, "null argument");
+    if (!debug_build()) return fail(XRDVI_EINVAL, "not a bounds-check build (XRDVI_DEBUG)");
+    *word = debug_word(reset != 0);
+    return XRDVI_OK;
+}
+
+xrdvi_status xrdvi_debug_selftest(void) {
+    if (!debug_build()) return fail(XRDVI_EINVAL, "not a bounds-check build (XRDVI_DEBUG)");
+    float *d = nullptr;
+    XR_CUDA(cudaMalloc(&d, sizeof(float)));
+    const cudaError_t e = debug_selftest(d);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("debug self-test: ") + cudaGetErrorString(e));
     return XRDVI_OK;
 }
 

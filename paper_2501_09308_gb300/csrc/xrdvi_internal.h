@@ -313,6 +313,13 @@ xrdvi_status validate_problem(const xrdvi_peaks *pk, const xrdvi_pattern *pt, co
 // order (one block).
 void launch_enum_lse(const double *elbo, int n, double *logp, cudaStream_t st);
 
+// Bounds-check build (XRDVI_DEBUG): whether it is one, the device word of the
+// first violated check (0: none; cleared when reset), and a one-lookup
+// self-test of the check (d_out: one device float).
+bool debug_build();
+int debug_word(bool reset);
+cudaError_t debug_selftest(float *d_out);
+
 // Philox4x32-10 blocks of n (counter [4], key [2]) pairs, device arrays.
 void launch_philox_words(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
 

@@ -552,6 +552,32 @@ __device__ __forceinline__ void ranges_body(const ProfArgs &a, int vb, int vgrid
 
 __global__ void __launch_bounds__(256) k_ranges(ProfArgs a) { ranges_body(a, blockIdx.x, gridDim.x); }
 
+// Bounds-check build (XRDVI_DEBUG): every peak-table index and every decoded
+// peak range is clamped into bounds, and the first violation's check number is
+// recorded in a device word that the host reads after the call.  Control flow
+// is unchanged (no early return, no trap), so no warp or barrier is left
+// waiting; a regular build compiles the checks away.
+#ifdef XRDVI_DEBUG
+__device__ int g_debug_word = 0;
+__device__ __forceinline__ int dbg_index(int i, int n, int code) {
+    if (i < 0 || i >= n) {
+        atomicCAS(&g_debug_word, 0, code);
+        return i < 0 ? 0 : (n > 0 ? n - 1 : 0);
+    }
+    return i;
+}
+__device__ __forceinline__ int dbg_range(int v, int lo, int hi, int code) {
+    if (v < lo || v > hi) {
+        atomicCAS(&g_debug_word, 0, code);
+        return v < lo ? lo : hi;
+    }
+    return v;
+}
+#else
+__device__ __forceinline__ int dbg_index(int i, int, int) { return i; }
+__device__ __forceinline__ int dbg_range(int v, int, int, int) { return v; }
+#endif
+
 // Shared-memory peak table.  Entries hold -p (so that x + (-p) is one packed
 // add) and I.  The wide layout's entry m also holds peak m + 1's values,
 // (-p_m, -p_m+1, I_m, I_m+1), so that a single 16-byte load yields the packed
@@ -563,19 +589,20 @@ struct PeakTable;
 template <>
 struct PeakTable<false> {
     const float2 *p;
+    int n;   // entries (for the bounds-check build)
     __device__ __forceinline__ void get(int m, f2_t &np, f2_t &I) const {
-        const float2 v = p[m];
+        const float2 v = p[dbg_index(m, n, 1)];
         np = bc2(v.x);
         I = bc2(v.y);
     }
     // peaks m and m + 1 as packed pairs
     __device__ __forceinline__ void pair(int m, f2_t &np, f2_t &I) const {
-        const float2 v0 = p[m], v1 = p[m + 1];
+        const float2 v0 = p[dbg_index(m, n - 1, 2)], v1 = p[dbg_index(m + 1, n, 2)];
         np = pk2(v0.x, v1.x);
         I = pk2(v0.y, v1.y);
     }
     __device__ __forceinline__ void scalar(int m, float &np, float &I) const {
-        const float2 v = p[m];
+        const float2 v = p[dbg_index(m, n, 3)];
         np = v.x;
         I = v.y;
     }
@@ -583,18 +610,19 @@ struct PeakTable<false> {
 template <>
 struct PeakTable<true> {
     const float4 *p;
+    int n;   // entries (for the bounds-check build)
     __device__ __forceinline__ void get(int m, f2_t &np, f2_t &I) const {
-        const float4 v = p[m];
+        const float4 v = p[dbg_index(m, n, 1)];
         np = bc2(v.x);
         I = bc2(v.z);
     }
     __device__ __forceinline__ void pair(int m, f2_t &np, f2_t &I) const {
-        const float4 v = p[m];
+        const float4 v = p[dbg_index(m, n - 1, 2)];   // entry m also holds peak m + 1
         np = pk2(v.x, v.y);
         I = pk2(v.z, v.w);
     }
     __device__ __forceinline__ void scalar(int m, float &np, float &I) const {
-        const float4 v = p[m];
+        const float4 v = p[dbg_index(m, n, 3)];
         np = v.x;
         I = v.z;
     }
@@ -610,11 +638,13 @@ __device__ __forceinline__ PeakTable<kWide> load_table(const ProfArgs &a, float4
             q[i] = make_float4(-a.pos[i], -a.pos[j], a.inten[i], a.inten[j]);
         }
         t.p = q;
+        t.n = a.Mtot;
         s_off = reinterpret_cast<int *>(q + a.Mtot);
     } else {
         float2 *q = reinterpret_cast<float2 *>(s_raw);
         for (int i = threadIdx.x; i < a.Mtot; i += blockDim.x) q[i] = make_float2(-a.pos[i], a.inten[i]);
         t.p = q;
+        t.n = a.Mtot;
         s_off = reinterpret_cast<int *>(q + a.Mtot);
     }
     for (int i = threadIdx.x; i <= a.K; i += blockDim.x) s_off[i] = a.off[i];
@@ -654,6 +684,17 @@ __device__ __forceinline__ Ranges load_ranges(const ProfArgs &a, const int *s_of
     o.fe = a.franges ? o.mb + f.y : o.me;
     o.sfb = a.sranges ? o.mb + g.x : o.mb;
     o.sfe = a.sranges ? o.mb + g.y : o.me;
+#ifdef XRDVI_DEBUG
+    // every range within the phase's peaks (check numbers 4-9)
+    o.m1 = dbg_range(o.m1, o.mb, o.me, 4);
+    o.m2 = dbg_range(o.m2, o.m1, o.me, 5);
+    o.nb = dbg_range(o.nb, o.mb, o.me, 6);
+    o.ne = dbg_range(o.ne, o.nb, o.me, 6);
+    o.fb = dbg_range(o.fb, o.mb, o.m1, 7);
+    o.fe = dbg_range(o.fe, o.m2, o.me, 7);
+    o.sfb = dbg_range(o.sfb, o.mb, o.fb, 8);
+    o.sfe = dbg_range(o.sfe, o.fe, o.me, 9);
+#endif
     return o;
 }
 
@@ -2765,6 +2806,43 @@ __global__ void k_philox_words(int n, const uint32_t *ctr, const uint32_t *key, 
     for (int j = 0; j < 4; ++j) out[4 * i + j] = c[j];
 }
 }  // namespace
+
+#ifdef XRDVI_DEBUG
+namespace {
+// One lookup through the table check with an index past a one-entry table:
+// the check records its number and reads entry 0 instead.
+__global__ void k_debug_selftest(float *out) {
+    __shared__ float2 one[1];
+    if (threadIdx.x == 0) one[0] = make_float2(1.f, 2.f);
+    __syncthreads();
+    PeakTable<false> t;
+    t.p = one;
+    t.n = 1;
+    float np, I;
+    t.scalar(1 + static_cast<int>(threadIdx.x), np, I);
+    if (threadIdx.x == 0) *out = np + I;
+}
+}  // namespace
+
+bool debug_build() { return true; }
+int debug_word(bool reset) {
+    int w = 0;
+    cudaMemcpyFromSymbol(&w, g_debug_word, sizeof(int));
+    if (reset) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_debug_word, &z, sizeof(int));
+    }
+    return w;
+}
+cudaError_t debug_selftest(float *d_out) {
+    k_debug_selftest<<<1, 32>>>(d_out);
+    return cudaDeviceSynchronize();
+}
+#else
+bool debug_build() { return false; }
+int debug_word(bool) { return 0; }
+cudaError_t debug_selftest(float *) { return cudaErrorNotSupported; }
+#endif
 
 void launch_philox_words(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st) {
     if (n > 0) k_philox_words<<<(n + 127) / 128, 128, 0, st>>>(n, ctr, key, out);

@@ -130,6 +130,8 @@ SIGNATURES = {
     "xrdvi_get_background": (ctypes.c_int, [_vp, P(_f), P(_f), P(_f)]),
     "xrdvi_get_gates": (ctypes.c_int, [_vp, P(_f), P(_f)]),
     "xrdvi_philox4x32_10": (ctypes.c_int, [_i32, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]),
+    "xrdvi_debug_word": (ctypes.c_int, [P(_i32), _i32]),
+    "xrdvi_debug_selftest": (ctypes.c_int, []),
     "xrdvi_last_error": (ctypes.c_char_p, []),
     "xrdvi_version": (ctypes.c_char_p, []),
 }
@@ -140,7 +142,8 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            # XRDVI_DEBUG=1: the bounds-check build (kernels clamp and record out-of-range indices)
+            path = _build.build(debug=os.environ.get("XRDVI_DEBUG") == "1")
             if not os.path.exists(path):
                 raise RuntimeError("xrdvi CUDA library is missing and could not be built")
             L = ctypes.CDLL(path)
@@ -344,6 +347,17 @@ def xrdvi_philox4x32_10(ctr, key):
     u32 = ctypes.c_uint32
     _check(lib().xrdvi_philox4x32_10(len(c), _ptr(c, u32), _ptr(k, u32), _ptr(out, u32)))
     return out
+
+
+def xrdvi_debug_word(reset=False):
+    """First violated bounds check of the XRDVI_DEBUG build (0: none)."""
+    w = ctypes.c_int32(0)
+    _check(lib().xrdvi_debug_word(ctypes.byref(w), 1 if reset else 0))
+    return int(w.value)
+
+
+def xrdvi_debug_selftest():
+    _check(lib().xrdvi_debug_selftest())
 
 
 def xrdvi_version() -> str:
