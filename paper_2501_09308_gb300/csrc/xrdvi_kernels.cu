@@ -1220,24 +1220,47 @@ __device__ __forceinline__ void lik_body(const ProfArgs &a, Blk blk) {
     }
     if (lam) {
         // far-field node values: the chunks' partial node sums, plus the
-        // super-tile's (summed over chunks) translated to this tile's nodes
-        const int p = threadIdx.x;
+        // super-tile's (summed over chunks) translated to this tile's nodes.
+        // The translation is split over the eight warps (warp w takes super
+        // nodes [4w, 4w + 4)), whose matrix entries are loaded while warp 0
+        // sums the super-level chunks and warp 1 the tile's, so the node values
+        // cost about one round trip instead of a warp's 32-term chain.
+        constexpr int kPer = kFarNodes / (kTile / 32);
+        static_assert(kPer * (kTile / 32) == kFarNodes, "super nodes split evenly over the warps");
+        __shared__ float sFc[kFarNodes], sPart[kTile / 32][kFarNodes];
+        const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
         const int g = tile / kSuperTiles;
-        if (a.Tg && p < kFarNodes) {
+        float mf[kPer];
+        if (a.Tg) {
+            const float *M = a.Mf + (static_cast<size_t>(tile) * kFarNodes + w * kPer) * kFarNodes + l;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) mf[j] = M[j * kFarNodes];
+        }
+        if (w == 0 && a.Tg) {
             float F2 = 0.f;
-            for (int c = 0; c < a.C; ++c) F2 += a.fnode2[((static_cast<size_t>(c) * a.S + s) * a.Tg + g) * kFarNodes + p];
-            sF2[p] = F2;
+            for (int c = 0; c < a.C; ++c) F2 += a.fnode2[((static_cast<size_t>(c) * a.S + s) * a.Tg + g) * kFarNodes + l];
+            sF2[l] = F2;
+        }
+        if (w == 1) {
+            float F = 0.f;
+            for (int c = 0; c < a.C; ++c) F += a.fnode[((static_cast<size_t>(c) * a.S + s) * a.T + tile) * kFarNodes + l];
+            sFc[l] = F;
         }
         __syncthreads();
-        if (p < kFarNodes) {
-            float F = 0.f;
-            for (int c = 0; c < a.C; ++c) F += a.fnode[((static_cast<size_t>(c) * a.S + s) * a.T + tile) * kFarNodes + p];
+        if (a.Tg) {
+            float part = 0.f;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) part = fmaf(mf[j], sF2[w * kPer + j], part);
+            sPart[w][l] = part;
+            __syncthreads();
+        }
+        if (w == 0) {
+            float F = sFc[l];
             if (a.Tg) {
-                const float *M = a.Mf + static_cast<size_t>(tile) * kFarNodes * kFarNodes + p;
-#pragma unroll 8
-                for (int P = 0; P < kFarNodes; ++P) F = fmaf(M[P * kFarNodes], sF2[P], F);
+#pragma unroll
+                for (int ww = 0; ww < kTile / 32; ++ww) F += sPart[ww][l];
             }
-            sFn[p] = F;
+            sFn[l] = F;
         }
         __syncthreads();
     }
@@ -1847,9 +1870,9 @@ __device__ __forceinline__ void grad_body(const GradArgs &a, Blk blk) {
         for (int i = warp; i < nc; i += kWarps) {
             const size_t sk = static_cast<size_t>(c0 + i) * a.K + k;
             const float2 *gp = reinterpret_cast<const float2 *>(a.gpart + sk * a.Tg * kGradSums);
-            float qf[kGradSums];
+            float qf[16];   // the ten sums, padded for one reduce-scatter (16 shuffles for all ten)
 #pragma unroll
-            for (int j = 0; j < kGradSums; ++j) qf[j] = 0.f;
+            for (int j = 0; j < 16; ++j) qf[j] = 0.f;
             for (int t = lane; t < a.Tg; t += 32) {
 #pragma unroll
                 for (int j = 0; j < kGradSums / 2; ++j) {
@@ -1858,14 +1881,8 @@ __device__ __forceinline__ void grad_body(const GradArgs &a, Blk blk) {
                     qf[2 * j + 1] += v.y;
                 }
             }
-#pragma unroll
-            for (int j = 0; j < kGradSums; ++j) qf[j] = warp_sumf(qf[j]);
-            if (lane < kGradSums) {
-                float v = qf[0];
-#pragma unroll
-                for (int j = 1; j < kGradSums; ++j) v = lane == j ? qf[j] : v;
-                qs[i][lane] = v;
-            }
+            warp_reduce_scatter16(qf, lane);   // lane 2j holds the warp's total of sum j
+            if ((lane & 1) == 0 && (lane >> 1) < kGradSums) qs[i][lane >> 1] = qf[0];
         }
         __syncthreads();
         if (warp == 0 && lane < nc) {
