@@ -89,6 +89,10 @@ def parse():
     ap.add_argument("--no-enumeration", action="store_true", help="skip the K=8 exact-enumeration and estimator-variant legs")
     ap.add_argument("--variants-only", action="store_true",
                     help="run only the estimator/model-variant leg and print its JSON (profiling aid)")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="NFITS",
+                    help="run only the batched-fits leg on this many serving-workload requests and print its JSON "
+                         "(profiling aid)")
+    ap.add_argument("--batch-iters", type=int, default=100, help="SVI steps of the batched-fits leg")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
     return ap.parse_args()
@@ -322,6 +326,36 @@ def serving_leg(n_requests, plain_ms):
     return out
 
 
+def batch_leg(n_fits, iters):
+    """xrdvi_fit_batch against the same fits run one after another: n_fits
+    serving-workload requests (contexts created up front, graphs warmed), each
+    set advanced by `iters` SVI steps; wall-clock times and whether every fit
+    ends bit-identical."""
+    import numpy as np
+    import torch
+    from paper_2501_09308_gb300 import synth, xrdvi
+    reqs = [synth.config(4, instance=i) for i in range(1, n_fits + 1)]
+    A = [xrdvi.Context.from_instance(r, S=r.S) for r in reqs]
+    B = [xrdvi.Context.from_instance(r, S=r.S) for r in reqs]
+    for c in A:
+        c.fit(16, trace=False)
+    xrdvi.xrdvi_fit_batch([c.h for c in B], 16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in A:
+        c.fit(iters, trace=False)
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    xrdvi.xrdvi_fit_batch([c.h for c in B], iters)
+    t_bat = time.perf_counter() - t0
+    same = all(np.array_equal(a.params()[0], b.params()[0]) and np.array_equal(a.params()[1], b.params()[1])
+               for a, b in zip(A, B))
+    for c in A + B:
+        c.close()
+    return {"fits": n_fits, "svi_steps": iters, "K": [int(r.K) for r in reqs], "N": [int(r.N) for r in reqs],
+            "one_after_another_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "bit_identical": same}
+
+
 def enumeration_leg(iters=3000):
     """Exact posterior over all 2^8 - 1 phase combinations of the tiny
     workload (K = 8 candidates, 20 peaks each, N = 2000, S = 16): every
@@ -464,6 +498,9 @@ def main():
     args = parse()
     if args.variants_only:
         print(json.dumps({"variants": variants_leg(measured_peaks()[0])}), flush=True)
+        return
+    if args.batch_only > 0:
+        print(json.dumps({"batch": batch_leg(args.batch_only, args.batch_iters)}), flush=True)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

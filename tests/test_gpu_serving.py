@@ -165,6 +165,23 @@ def test_requests_arriving_during_a_fit_are_admitted_before_it_ends():
     assert rb["t_admit"] < ra["t_done"] and rb["t_done"] < ra["t_done"]
 
 
+def test_invalid_request_completes_with_its_error_and_the_others_run():
+    """A problem that fails validation (a negative count) is rejected when its
+    context is created: its result carries EINVAL, and a valid request served
+    beside it completes normally."""
+    good = _problems()[0]
+    y = good.y.copy()
+    y[5] = -1.0
+    bad = synth.Instance(**{**good.__dict__, "y": y})
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=2)
+    rb = srv.submit(bad, iters=20, S_post=0)
+    rg = srv.submit(good, iters=20, S_post=0)
+    out_b, out_g = srv.wait(rb), srv.wait(rg)
+    srv.close()
+    assert out_b["status"] == 1
+    assert out_g["status"] == 0 and np.isfinite(out_g["final_elbo"])
+
+
 def test_request_over_budget_is_rejected():
     p = _problems()[2]
     srv = serving.Server(hbm_budget=1 << 20, max_slots=1)
