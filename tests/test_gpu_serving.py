@@ -82,8 +82,8 @@ def test_fit_batch_equals_standalone_fits():
     takes its own kernels) advanced together end exactly where xrdvi_fit
     leaves each of them, also when the steps are split over several calls;
     a context listed twice is rejected."""
-    probs = _problems() + [synth.small_problem(K=5, M=9, N=1100, S=8, seed=77, x_step=0.04),
-                           synth.small_problem(K=4, M=7, N=700, S=8, seed=78)]
+    probs = _problems() + [synth.small_problem(K=5, M=9, N=1100, S=32, seed=77, x_step=0.04),
+                           synth.small_problem(K=4, M=7, N=700, S=3, seed=78)]
     extra = [{}, {}, {}, {"flags": xrdvi.FLAG_SEC_WIDTH}, {"flags": xrdvi.FLAG_AREA_NORM}]
     ref = []
     for i, p in enumerate(probs):
@@ -180,6 +180,20 @@ def test_invalid_request_completes_with_its_error_and_the_others_run():
     srv.close()
     assert out_b["status"] == 1
     assert out_g["status"] == 0 and np.isfinite(out_g["final_elbo"])
+
+
+def test_zero_step_request_returns_the_posterior_of_the_initial_q():
+    """iters = 0: the server skips the fit and draws the posterior of the
+    standard initial q, as a standalone context does."""
+    p = _problems()[1]
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=2)
+    r = srv.wait(srv.submit(p, iters=0, S_post=128, post_seed=3, top_m=2, seed=5))
+    srv.close()
+    c = xrdvi.Context.from_instance(p, S=p.S, seed=5)
+    post = c.posterior(128, 3, top_m=2)
+    c.close()
+    assert r["status"] == 0
+    np.testing.assert_array_equal(r["pi"], post["pi"])
 
 
 def test_request_over_budget_is_rejected():
