@@ -150,3 +150,32 @@ def test_binding_constants_match_the_header():
     assert m["XRDVI_PROFILE_KERNELS"] == len(xrdvi.PROFILE_KERNELS)
     assert m["XRDVI_PROFILE_WORK"] == len(xrdvi.WORK_COUNTS)
     assert m["XRDVI_STATIC_SCRATCH_BYTES"] == 32 << 20
+
+
+def _static_formula(S, K, T, M):
+    """Scratch bytes of xrdvi_elbo_grad_static as include/xrdvi.h states them
+    (before the alignment of its 18 arrays)."""
+    return 48 * S * K * T + 2056 * S * T + 104 * S * K + 16 * S + 1416 * K + 8 * M + 32
+
+
+def test_static_entry_rejects_every_size_the_header_formula_puts_above_the_limit():
+    """The allocation-free entry checks its scratch size on the host before it
+    touches a device pointer: every problem whose stated need exceeds the
+    32 MiB array is refused with EINVAL (so the formula never overstates what
+    the code needs).  The pointers passed are never dereferenced."""
+    limit = 32 << 20
+    m = header_macros()
+    assert m["XRDVI_STATIC_SCRATCH_BYTES"] == limit
+    K, N, M = 5, 700, 60
+    T = (N + 255) // 256
+    S = 1
+    while _static_formula(S, K, T, M) <= limit:
+        S += 1
+    dummy = 1 << 20   # a non-null address the call must not use
+    for s_try in (S, S + 1, S + 7):
+        assert _static_formula(s_try, K, T, M) > limit
+        cfg = xrdvi.xrdvi_config_default(S=s_try)
+        with pytest.raises(xrdvi.XrdviError) as e:
+            xrdvi.xrdvi_elbo_grad_static(K, M, dummy, dummy, dummy, N, dummy, dummy, dummy, 0.0, 1e-3, cfg,
+                                         dummy, dummy, dummy, dummy, dummy, 0)
+        assert e.value.status == 1 and "scratch" in str(e.value), (s_try, e.value)
