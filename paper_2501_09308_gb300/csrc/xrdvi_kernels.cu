@@ -2618,6 +2618,8 @@ struct MultiClass {
     int n = 0;
     size_t smem = 0;
     int grid1_fwd = 0, grid1_bwd = 0;   // a class of one fit runs the fit's own kernels on these grids
+    int grid1_lik = 0;                  // ... and, if it fills the GPU by itself, its own likelihood kernel
+    bool own = false;                   // a fit that fills the GPU by itself: never shared
     MultiArgs<ProfArgs> pf, pb;   // forward (work counter 0) and backward (counter 2) arguments
     FitMap m_fwd, m_bwd;
 };
@@ -2625,7 +2627,8 @@ struct MultiClass {
 struct MultiStepPlan {
     int cap = 0, n = 0;
     MultiArgs<SampleArgs> sa;
-    MultiArgs<ProfArgs> pf;       // every fit: ranges and likelihood
+    MultiArgs<ProfArgs> pf;       // every fit: ranges
+    MultiArgs<ProfArgs> pl;       // the fits that share profile launches: likelihood
     MultiArgs<GradArgs> ga;
     FitMap m_sample, m_ranges, m_lik, m_grad;
     std::vector<MultiClass> classes;
@@ -2690,7 +2693,8 @@ bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, 
     p->n = n;
     p->classes.clear();
     int bs = 0, br = 0, bl = 0, bg = 0;
-    p->m_sample.n = p->m_ranges.n = p->m_lik.n = p->m_grad.n = n;
+    p->m_sample.n = p->m_ranges.n = p->m_grad.n = n;
+    p->m_lik.n = 0;
     std::vector<long long> work(n), items(n);
     std::vector<int> cls(n);
     for (int f = 0; f < n; ++f) {
@@ -2710,24 +2714,35 @@ bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, 
         p->m_ranges.start[f] = br;
         const int nr = W.S * P.K * P.T;
         br += (nr + 255) / 256 < 4096 ? (nr + 255) / 256 : 4096;
-        p->m_lik.start[f] = bl;
-        bl += W.S * P.T;
         p->m_grad.start[f] = bg;
         bg += (W.B * P.K + ga.elbo_blocks) * ga.NB;
         // the fit's own table layout and residency, as in its standalone kernels
         const size_t tb = P.smem;
         const int occ = std::min(direct_occupancy(true, P.wide, tb), direct_occupancy(false, P.wide, tb));
-        int c = 0;
-        for (; c < static_cast<int>(p->classes.size()); ++c)
-            if (p->classes[c].wide == P.wide &&
+        // a fit with at least four work items per resident warp fills the GPU
+        // by itself: it keeps its own persistent kernels (per-fit arguments in
+        // the constant bank), and only the smaller fits share multi-fit launches
+        const long long fit_items = static_cast<long long>(W.S) * P.T * W.C;
+        const bool own = fit_items >= 4LL * occ * sm_count * kWarps;
+        int c = own ? static_cast<int>(p->classes.size()) : 0;
+        for (; c < static_cast<int>(p->classes.size()); ++c) {
+            if (!p->classes[c].own && p->classes[c].wide == P.wide &&
                 std::min(direct_occupancy(true, P.wide, p->classes[c].smem),
                          direct_occupancy(false, P.wide, p->classes[c].smem)) == occ)
                 break;
+        }
         if (c == static_cast<int>(p->classes.size())) {
             p->classes.emplace_back();
             p->classes[c].wide = P.wide;
+            p->classes[c].own = own;
         }
         MultiClass &C = p->classes[c];
+        if (!own) {   // likelihood in the shared launch
+            p->pl.fit[p->m_lik.n] = pf;
+            p->m_lik.start[p->m_lik.n++] = bl;
+            bl += W.S * P.T;
+        }
+        C.grid1_lik = W.S * P.T;
         C.smem = std::max(C.smem, tb);
         C.grid1_fwd = grid_for(P.grid_fwd_direct, W.S * P.T * W.C);
         C.grid1_bwd = grid_for(P.grid_bwd_direct, W.S * P.T * W.C);
@@ -2742,7 +2757,7 @@ bool multi_plan_set(MultiStepPlan *p, const FitStep *fits, int n, int sm_count, 
     }
     p->m_sample.start[n] = bs;
     p->m_ranges.start[n] = br;
-    p->m_lik.start[n] = bl;
+    p->m_lik.start[p->m_lik.n] = bl;
     p->m_grad.start[n] = bg;
     for (int c = 0; c < static_cast<int>(p->classes.size()); ++c) {
         MultiClass &C = p->classes[c];
@@ -2768,7 +2783,19 @@ void multi_plan_launch_step(const MultiStepPlan *p, cudaStream_t st) {
     // the arguments travel with each launch (kernel parameters)
     k_sample_multi<<<p->m_sample.start[p->n], 128, 0, st>>>(p->sa, p->m_sample);
     k_ranges_multi<<<p->m_ranges.start[p->n], 256, 0, st>>>(p->pf, p->m_ranges);
+    // fits that fill the GPU by themselves: their own profile, likelihood and
+    // backward kernels back to back (their intermediates stay in L2)
     for (const MultiClass &C : p->classes) {
+        if (!C.own) continue;
+        const ProfArgs &a = C.pf.fit[0];
+        if (C.wide) k_fwd_direct<false, true, false><<<C.grid1_fwd, kThreads, C.smem, st>>>(a);
+        else k_fwd_direct<false, false, false><<<C.grid1_fwd, kThreads, C.smem, st>>>(a);
+        k_lik<<<C.grid1_lik, kTile, 0, st>>>(a);
+        if (C.wide) k_bwd_direct<true, false><<<C.grid1_bwd, kThreads, C.smem, st>>>(C.pb.fit[0]);
+        else k_bwd_direct<false, false><<<C.grid1_bwd, kThreads, C.smem, st>>>(C.pb.fit[0]);
+    }
+    for (const MultiClass &C : p->classes) {
+        if (C.own) continue;
         if (C.n == 1) {   // alone in its class: the fit's own kernel (arguments in the constant bank)
             if (C.wide) k_fwd_direct<false, true, false><<<C.grid1_fwd, kThreads, C.smem, st>>>(C.pf.fit[0]);
             else k_fwd_direct<false, false, false><<<C.grid1_fwd, kThreads, C.smem, st>>>(C.pf.fit[0]);
@@ -2778,8 +2805,9 @@ void multi_plan_launch_step(const MultiStepPlan *p, cudaStream_t st) {
             k_direct_multi<true, false><<<C.m_fwd.start[C.n], kThreads, C.smem, st>>>(C.pf, C.m_fwd);
         }
     }
-    k_lik_multi<<<p->m_lik.start[p->n], kTile, 0, st>>>(p->pf, p->m_lik);
+    if (p->m_lik.n > 0) k_lik_multi<<<p->m_lik.start[p->m_lik.n], kTile, 0, st>>>(p->pl, p->m_lik);
     for (const MultiClass &C : p->classes) {
+        if (C.own) continue;
         if (C.n == 1) {
             if (C.wide) k_bwd_direct<true, false><<<C.grid1_bwd, kThreads, C.smem, st>>>(C.pb.fit[0]);
             else k_bwd_direct<false, false><<<C.grid1_bwd, kThreads, C.smem, st>>>(C.pb.fit[0]);
