@@ -388,7 +388,8 @@ typedef struct {
     double t_submit, t_admit, t_done;  /* seconds since xrdvi_server_create    */
     double final_elbo, log_evidence, ess, coverage_log;
     double elbo_tail_mean;     /* mean ELBO estimate over the last max(1, iters/4)
-                                  steps (the sub-model score of xrdvi_enumerate) */
+                                  steps, at most 65536 (the sub-model score of
+                                  xrdvi_enumerate) */
     size_t footprint_bytes;
     double *pi;
     uint64_t *combos;

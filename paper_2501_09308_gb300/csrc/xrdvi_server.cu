@@ -278,12 +278,13 @@ void xrdvi_server::reap_loop() {
         const int K = static_cast<int>(r.off.size()) - 1, W = (K + 63) / 64;
         xrdvi_status s = XRDVI_OK;
         if (r.opts.iters > 0) {
-            std::vector<double> trace(r.opts.iters);
-            s = xrdvi::ctx_read_trace(c, r.opts.iters, trace.data());
-            r.final_elbo = trace[r.opts.iters - 1];
-            const int tail = std::max(1, r.opts.iters / 4);
+            // the device keeps the last kTraceCap estimates: the tail mean covers at most those
+            const int tail = std::min(std::max(1, r.opts.iters / 4), xrdvi::kTraceCap);
+            std::vector<double> trace(tail);
+            s = xrdvi::ctx_read_trace(c, tail, trace.data());
+            r.final_elbo = trace[tail - 1];
             double acc = 0.0;
-            for (int i = r.opts.iters - tail; i < r.opts.iters; ++i) acc += trace[i];
+            for (int i = 0; i < tail; ++i) acc += trace[i];
             r.elbo_tail_mean = acc / tail;
         }
         if (s == XRDVI_OK && r.opts.S_post > 0) {
