@@ -93,6 +93,7 @@ def parse():
                     help="run only the batched-fits leg on this many serving-workload requests and print its JSON "
                          "(profiling aid)")
     ap.add_argument("--batch-iters", type=int, default=100, help="SVI steps of the batched-fits leg")
+    ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="resident fits of the serving leg")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
     return ap.parse_args()
@@ -266,16 +267,18 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
-SERVE_SLOTS = 16            # fits the server keeps resident (one batch)
+SERVE_SLOTS = 4             # fits the server keeps resident (one batch); --serve-slots
 SERVE_OVERLAP_FITS = 8      # requests timed alone and served together (device-side overlap)
 
 
-def serving_leg(n_requests, plain_ms):
+def serving_leg(n_requests, plain_ms, slots=SERVE_SLOTS):
     """Continuous batching: the K=50 fit followed by serving-workload requests
     (K ~ U{10..200}, N ~ U{2000..9000}, 5-100 peaks per phase, S=256, 1000
     steps) arriving as a Poisson stream at 200 requests/s, on a server with
-    SERVE_SLOTS resident fits and a 32 GB device-memory budget; every SVI step
-    of the resident fits runs as one set of six multi-fit kernel launches.
+    `slots` resident fits (4 by default: each of these fits fills the GPU by
+    itself, so with the same throughput fewer resident fits finish the early
+    requests sooner) and a 32 GB device-memory budget; every SVI step of the
+    resident fits runs as one batched step.
     Reports time-to-posterior (completion - arrival) percentiles, fits/s, the
     aggregate evaluation rate (dense count) against the single fit's, and the
     K=50 request's served time-to-posterior beside the plain single-fit path's.
@@ -286,7 +289,7 @@ def serving_leg(n_requests, plain_ms):
     from paper_2501_09308_gb300 import serving, synth, xrdvi
     reqs = [synth.config(1)] + [synth.config(4, instance=i) for i in range(1, n_requests)]
     arrivals = synth.arrival_times(n_requests, 200.0, seed=synth.SEED_BASE + 4000)
-    srv = serving.Server(hbm_budget=32 << 30, max_slots=SERVE_SLOTS)
+    srv = serving.Server(hbm_budget=32 << 30, max_slots=slots)
     res = serving.replay_arrivals(srv, reqs, arrivals, S_post=S_POST, post_seed=77, top_m=TOP_M)
     stats = srv.stats()
     srv.close()
@@ -294,7 +297,7 @@ def serving_leg(n_requests, plain_ms):
     out = serving.summarize(res, evals)
     single_rate = reqs[0].evals_per_iter * reqs[0].iters / (plain_ms / 1e3)
     out.update({
-        "slots": SERVE_SLOTS, "hbm_budget_bytes": 32 << 30, "arrival_rate_per_s": 200.0,
+        "slots": slots, "hbm_budget_bytes": 32 << 30, "arrival_rate_per_s": 200.0,
         "peak_bytes_in_use": stats["peak_bytes"],
         "single_fit_evals_per_s": single_rate,
         "aggregate_over_single_fit": out["evals_per_s"] / single_rate,
@@ -578,7 +581,7 @@ def main():
 
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
-        serve = serving_leg(args.serve_requests, ms_step)
+        serve = serving_leg(args.serve_requests, ms_step, args.serve_slots)
     enum = enumeration_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
     variants = variants_leg(measured_peaks()[0]) if rank == 0 and world == 1 and not args.no_enumeration else None
 

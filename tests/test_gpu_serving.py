@@ -78,13 +78,15 @@ def test_batched_and_variant_fits_in_one_mix_equal_their_standalone_fits():
 
 
 def test_fit_batch_equals_standalone_fits():
-    """xrdvi_fit_batch: five contexts of different K and N (one a variant that
-    takes its own kernels) advanced together end exactly where xrdvi_fit
-    leaves each of them, also when the steps are split over several calls;
-    a context listed twice is rejected."""
+    """xrdvi_fit_batch: five contexts of different K, N and S (gates, bf16
+    intensities and area normalisation inside the batched step, the
+    angle-dependent width with its own kernels) advanced together end exactly
+    where xrdvi_fit leaves each of them, also when the steps are split over
+    several calls; a context listed twice is rejected."""
     probs = _problems() + [synth.small_problem(K=5, M=9, N=1100, S=32, seed=77, x_step=0.04),
                            synth.small_problem(K=4, M=7, N=700, S=3, seed=78)]
-    extra = [{}, {}, {}, {"flags": xrdvi.FLAG_SEC_WIDTH}, {"flags": xrdvi.FLAG_AREA_NORM}]
+    extra = [{}, {"flags": xrdvi.FLAG_GATES}, {"flags": xrdvi.FLAG_BF16_INT}, {"flags": xrdvi.FLAG_SEC_WIDTH},
+             {"flags": xrdvi.FLAG_AREA_NORM}]
     ref = []
     for i, p in enumerate(probs):
         c = xrdvi.Context.from_instance(p, S=p.S, seed=300 + i, **extra[i])
