@@ -89,3 +89,31 @@ def test_nothing_of_size_S_K_N_is_kept():
     info = c.info
     c.close()
     assert info.device_bytes < 0.3 * inst.S * inst.K * inst.N * 4
+
+
+@pytest.mark.slow
+def test_autograd_full_size_k50_against_the_oracle():
+    """The differentiation workload at its full size (K=50, N=4500, S=256)
+    through torch.autograd: the loss and the gradients of every variational
+    parameter against the oracle's evaluation (OpenMP, a few seconds)."""
+    import torch
+    from paper_2501_09308_gb300.autograd import PhaseSearch
+    inst = synth.config(1)
+    S = inst.S
+    mod = PhaseSearch(inst, S=S)
+    with torch.no_grad():
+        g = torch.Generator(device="cpu").manual_seed(7)
+        mod.loc.add_((0.02 * torch.randn(mod.loc.shape, generator=g)).cuda())
+        mod.raw.add_((0.05 * torch.randn(mod.raw.shape, generator=g)).cuda())
+    eps_np = synth.normals(77, S, inst.K)
+    loss = mod(torch.tensor(eps_np, device="cuda"))
+    loss.backward()
+    o = oracle.Problem.from_instance(inst).elbo_grad(mod.loc.detach().cpu().numpy().astype(np.float64),
+                                                    mod.raw.detach().cpu().numpy().astype(np.float64),
+                                                    eps_np.astype(np.float64))
+    assert abs(-loss.item() - o["elbo"]) <= 1e-5 * abs(o["elbo"])
+    gl = -mod.loc.grad.cpu().numpy()
+    gr = -mod.raw.grad.cpu().numpy()
+    for j in range(5):
+        for mine, ref in ((gl[:, j], o["grad"][:, j]), (gr[:, j], o["grad"][:, 5 + j])):
+            assert np.max(np.abs(mine - ref)) <= 1e-4 * np.max(np.abs(ref)), j
