@@ -74,9 +74,13 @@ def enumerate_combinations(inst, *, iters=None, hbm_budget=16 << 30, **cfg):
     return masks, elbo, np.exp(logp)
 
 
-def replay_arrivals(server: Server, requests, arrivals_s, **submit_kw):
+def replay_arrivals(server: Server, requests, arrivals_s, jsonl=None, **submit_kw):
     """Submit requests[i] at arrivals_s[i] seconds after the start, then wait
-    for all.  Returns per-request dicts with 'latency' = done - submit."""
+    for all.  Returns per-request dicts with 'latency' = done - submit and
+    'queue_wait' = admit - submit.  jsonl (a path, optional): one JSON record
+    per request (id, K, N, peaks, footprint, submit/admit/done times, latency,
+    queue wait, status, final ELBO), in submission order."""
+    import json
     t0 = time.monotonic()
     ids = []
     for inst, ta in zip(requests, arrivals_s):
@@ -90,6 +94,15 @@ def replay_arrivals(server: Server, requests, arrivals_s, **submit_kw):
         r["latency"] = r["t_done"] - r["t_submit"]
         r["queue_wait"] = r["t_admit"] - r["t_submit"]
         out.append(r)
+    if jsonl:
+        with open(jsonl, "w") as fh:
+            for rid, inst, r in zip(ids, requests, out):
+                fh.write(json.dumps({
+                    "id": int(rid), "K": int(inst.K), "N": int(inst.N), "peaks": int(inst.offsets[-1]),
+                    "footprint_bytes": int(r["footprint_bytes"]), "t_submit": r["t_submit"],
+                    "t_admit": r["t_admit"], "t_done": r["t_done"], "latency_s": r["latency"],
+                    "queue_wait_s": r["queue_wait"], "status": int(r["status"]),
+                    "final_elbo": float(r["final_elbo"])}) + "\n")
     return out
 
 

@@ -198,6 +198,23 @@ def test_zero_step_request_returns_the_posterior_of_the_initial_q():
     np.testing.assert_array_equal(r["pi"], post["pi"])
 
 
+def test_replay_writes_one_jsonl_record_per_request(tmp_path):
+    """The request loop's log: one JSON line per request with its arrival,
+    admission and completion times, footprint and status."""
+    import json
+    probs = _problems()[:2]
+    srv = serving.Server(hbm_budget=8 << 30, max_slots=2)
+    path = tmp_path / "requests.jsonl"
+    res = serving.replay_arrivals(srv, probs, [0.0, 0.01], jsonl=str(path), iters=30, S_post=0)
+    srv.close()
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == 2
+    for rec, p, r in zip(lines, probs, res):
+        assert rec["K"] == p.K and rec["N"] == p.N and rec["status"] == 0
+        assert rec["t_submit"] <= rec["t_admit"] <= rec["t_done"]
+        assert rec["latency_s"] == pytest.approx(r["latency"])
+
+
 def test_request_over_budget_is_rejected():
     p = _problems()[2]
     srv = serving.Server(hbm_budget=1 << 20, max_slots=1)
