@@ -761,12 +761,13 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         XR_C(c->alloc(&P.node_x, nodex.size()));
         XR_C(c->alloc(&P.lam, lamh.size()));
         if (sec) XR_C(c->alloc(&P.node_c, nodec.size()));
-        std::iota(far_order.begin(), far_order.end(), 0);
-        std::stable_sort(far_order.begin(), far_order.end(), [&](int i, int j) {
-            return pk->offsets[i + 1] - pk->offsets[i] > pk->offsets[j + 1] - pk->offsets[j];
-        });
-        XR_C(c->alloc(&P.far_order, static_cast<size_t>(K)));
     }
+    // phases by decreasing peak count (the shared-shape profile kernel starts the heaviest first)
+    std::iota(far_order.begin(), far_order.end(), 0);
+    std::stable_sort(far_order.begin(), far_order.end(), [&](int i, int j) {
+        return pk->offsets[i + 1] - pk->offsets[i] > pk->offsets[j + 1] - pk->offsets[j];
+    });
+    XR_C(c->alloc(&P.far_order, static_cast<size_t>(K)));
     configure_grids(P, sms);
     c->host_off.assign(pk->offsets, pk->offsets + K + 1);
     c->W.B = nsub;
@@ -834,7 +835,8 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
     auto up = [&](void *dst, const void *src, size_t n) { return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s); };
     if (up(P.pos, pos.data(), M * 4) || up(P.inten, inten.data(), M * 4) ||
         up(P.off, pk->offsets, (K + 1) * 4) || up(P.x, pt->x_deg, N * 4) || up(P.y, pt->y_counts, N * 4) ||
-        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) || (sec && up(P.csec, csec.data(), N * 4)) ||
+        up(P.bg, pt->bg, N * 4) || up(P.isum, isum.data(), K * 8) ||
+        up(P.far_order, far_order.data(), static_cast<size_t>(K) * 4) || (sec && up(P.csec, csec.data(), N * 4)) ||
         up(c->loc, loc.data(), KB * 20) ||
         up(c->raw, raw.data(), KB * 20) || cudaMemsetAsync(c->m, 0, KB * 40, s) ||
         cudaMemsetAsync(c->v, 0, KB * 40, s) || cudaMemsetAsync(c->step, 0, 4, s) ||
@@ -845,7 +847,6 @@ xrdvi_status xrdvi::create_batch_context(const xrdvi_peaks *pk, const xrdvi_patt
         (P.gates && (cudaMemsetAsync(P.gate_a, 0, K * 4, s) || cudaMemsetAsync(P.m_gate, 0, K * 4, s) ||
                      cudaMemsetAsync(P.v_gate, 0, K * 4, s) || cudaMemsetAsync(P.grad_gate, 0, K * 4, s))) ||
         (P.far && (up(P.node_x, nodex.data(), nodex.size() * 4) || up(P.lam, lamh.data(), lamh.size() * 4) ||
-                   up(P.far_order, far_order.data(), static_cast<size_t>(K) * 4) ||
                    (P.Tg && (up(P.node_x2, nodex2.data(), nodex2.size() * 4) || up(P.sgap, sgaph.data(), sgaph.size() * 4) ||
                              up(P.Mf, Mfh.data(), Mfh.size() * 4) || up(P.Mb, Mbh.data(), Mbh.size() * 4) ||
                              (sec && up(P.node_c2, nodec2.data(), nodec2.size() * 4)))) ||

@@ -179,7 +179,7 @@ struct Problem {
     float *node_x = nullptr;     // [T*kFarNodes] Chebyshev nodes of each tile's span
     float *node_c = nullptr;     // [T*kFarNodes] cos(x/2) at the nodes (angle-dependent width)
     float *lam = nullptr;        // [T*kFarNodes*kTile] Lagrange weights lam_p(x_i) of the tile's points
-    int *far_order = nullptr;    // [K] phases by decreasing peak count (far-field work balance)
+    int *far_order = nullptr;    // [K] phases by decreasing peak count (work balance)
     int Tg = 0;                  // super-tiles (second far-field level; 0: one level)
     float *node_x2 = nullptr;    // [Tg*kFarNodes] nodes of each super-tile's span
     float *node_c2 = nullptr;    // [Tg*kFarNodes] cos(x/2) there (angle-dependent width)

@@ -290,6 +290,7 @@ struct ShapeArgs {
     const int *off;
     const float *csec;       // [N] cos(x/2) of the angle-dependent width (null: constant width)
     const PhaseConst *cst;   // sample 0's row [K]
+    const int *order;        // [K] phases by decreasing peak count: blockIdx.y -> phase
     const float *theta;      // sample 0's row [K*5]
     float *D, *D_lo;         // [K*10*Npad] TF32 hi / lo parts
     float *Ct, *Ct_lo;       // [Npad*Kpad] TF32 hi / lo parts
@@ -299,7 +300,9 @@ constexpr int kShapeChunk = 512;   // peaks staged in shared memory at a time
 
 __global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
     __shared__ float2 sp[kShapeChunk];   // (p, I) of the phase's peaks
-    const int k = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim.x * gridDim.x == Npad
+    // phase of this block row: the heaviest phases start first (blocks go out in
+    // index order), so the kernel does not end on a phase of many peaks
+    const int k = a.order[blockIdx.y], i = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim.x * gridDim.x == Npad
     const PhaseConst c = a.cst[k];
     const float r = a.theta[k * 5 + 3];
     float acc[kGradSums];
@@ -365,7 +368,7 @@ void launch_shared_forward(const Problem &P, Workspace &W, float *f_out, cudaStr
     ShapeArgs s;
     s.N = P.N; s.Npad = P.Npad; s.K = P.K; s.Kpad = W.Kpad;
     s.x = P.x; s.pos = P.pos; s.inten = P.inten; s.off = P.off;
-    s.cst = W.cst; s.theta = W.theta; s.D = W.D; s.Ct = W.Ct; s.csec = P.csec;
+    s.cst = W.cst; s.theta = W.theta; s.D = W.D; s.Ct = W.Ct; s.csec = P.csec; s.order = P.far_order;
     s.D_lo = W.D + static_cast<size_t>(P.K) * kGradSums * P.Npad;
     s.Ct_lo = W.Ct + static_cast<size_t>(P.Npad) * W.Kpad;
     k_shapes<<<dim3(P.T, P.K), 256, 0, st>>>(s);
