@@ -108,6 +108,30 @@ def test_fit_batch_equals_standalone_fits():
         c.close()
 
 
+def test_fit_batch_with_large_peak_tables_equals_standalone_fits():
+    """Two fits whose peak tables (over 3500 peaks) take the compact layout
+    share the multi-fit profile launches, beside a small fit with the wide
+    layout; a fit with twice as many peaks sits alone in its occupancy group.
+    Each ends bit-identical to its standalone fit."""
+    probs = [synth.small_problem(K=60, M=70, N=900, S=8, seed=95, x_step=0.03),
+             synth.small_problem(K=64, M=70, N=1300, S=8, seed=96, x_step=0.02),
+             synth.small_problem(K=4, M=8, N=700, S=8, seed=97),
+             synth.small_problem(K=150, M=100, N=600, S=4, seed=98, x_step=0.05)]
+    assert int(probs[0].offsets[-1]) > 3500 and int(probs[1].offsets[-1]) > 3500
+    ref = []
+    for i, p in enumerate(probs):
+        c = xrdvi.Context.from_instance(p, S=p.S, seed=400 + i)
+        c.fit(40)
+        ref.append(c.params())
+        c.close()
+    cs = [xrdvi.Context.from_instance(p, S=p.S, seed=400 + i) for i, p in enumerate(probs)]
+    xrdvi.xrdvi_fit_batch([c.h for c in cs], 40)
+    for c, (loc, raw) in zip(cs, ref):
+        np.testing.assert_array_equal(c.params()[0], loc)
+        np.testing.assert_array_equal(c.params()[1], raw)
+        c.close()
+
+
 def test_batched_fits_overlap_on_the_device():
     """Eight small fits served together finish in much less time than the
     same fits run one after another: their steps share kernel launches
