@@ -93,6 +93,8 @@ def parse():
                     help="run only the batched-fits leg on this many serving-workload requests and print its JSON "
                          "(profiling aid)")
     ap.add_argument("--batch-iters", type=int, default=100, help="SVI steps of the batched-fits leg")
+    ap.add_argument("--batch-samples", type=int, default=0,
+                    help="Monte-Carlo samples per fit of the batched-fits leg (0: the requests' own, 256)")
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="resident fits of the serving leg")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
@@ -329,17 +331,19 @@ def serving_leg(n_requests, plain_ms, slots=SERVE_SLOTS):
     return out
 
 
-def batch_leg(n_fits, iters):
+def batch_leg(n_fits, iters, samples=0):
     """xrdvi_fit_batch against the same fits run one after another: n_fits
-    serving-workload requests (contexts created up front, graphs warmed), each
-    set advanced by `iters` SVI steps; wall-clock times and whether every fit
-    ends bit-identical."""
+    serving-workload requests (contexts created up front, graphs warmed; with
+    `samples` > 0 that many Monte-Carlo samples per fit instead of 256, which
+    makes fits too small to fill the GPU alone), each set advanced by `iters`
+    SVI steps; wall-clock times and whether every fit ends bit-identical."""
     import numpy as np
     import torch
     from paper_2501_09308_gb300 import synth, xrdvi
     reqs = [synth.config(4, instance=i) for i in range(1, n_fits + 1)]
-    A = [xrdvi.Context.from_instance(r, S=r.S) for r in reqs]
-    B = [xrdvi.Context.from_instance(r, S=r.S) for r in reqs]
+    S = samples if samples > 0 else None
+    A = [xrdvi.Context.from_instance(r, S=S or r.S) for r in reqs]
+    B = [xrdvi.Context.from_instance(r, S=S or r.S) for r in reqs]
     for c in A:
         c.fit(16, trace=False)
     xrdvi.xrdvi_fit_batch([c.h for c in B], 16)
@@ -355,7 +359,8 @@ def batch_leg(n_fits, iters):
                for a, b in zip(A, B))
     for c in A + B:
         c.close()
-    return {"fits": n_fits, "svi_steps": iters, "K": [int(r.K) for r in reqs], "N": [int(r.N) for r in reqs],
+    return {"fits": n_fits, "svi_steps": iters, "S": S or int(reqs[0].S), "K": [int(r.K) for r in reqs],
+            "N": [int(r.N) for r in reqs],
             "one_after_another_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "bit_identical": same}
 
 
@@ -503,7 +508,7 @@ def main():
         print(json.dumps({"variants": variants_leg(measured_peaks()[0])}), flush=True)
         return
     if args.batch_only > 0:
-        print(json.dumps({"batch": batch_leg(args.batch_only, args.batch_iters)}), flush=True)
+        print(json.dumps({"batch": batch_leg(args.batch_only, args.batch_iters, args.batch_samples)}), flush=True)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
