@@ -200,17 +200,24 @@ xrdvi_status xrdvi_fit(xrdvi_ctx *ctx, int32_t iters, double *elbo_trace);
 
 /* Batched SVI (continuous batching without the server): advances the n
  * contexts ctxs[0..n) (1 <= n <= 64, distinct, one device) by `iters` steps
- * each, the steps of all n fits sharing their kernel launches: one step of
- * the batch is six launches whose work lists span every fit, whatever its K,
- * N and peak counts.  A context whose configuration the batched step does not
- * cover (shared shapes, angle-dependent width, fitted background, naive sums,
- * importance weights) takes its own kernels between those launches.  Every
- * context ends exactly as xrdvi_fit(ctx, iters) would leave it (same kernels
- * per work item, fixed reduction orders).  Runs on ctxs[0]'s stream after
- * waiting for every context's stream; blocks until done.  last_elbo (NULL or
- * host [n]) receives each fit's last ELBO estimate.  ENONFINITE if any fit's
- * last ELBO or gradient is not finite.  No counterpart in the paper, which
- * fits one pattern at a time. */
+ * each, the steps of all n fits sharing their kernel launches: sampling,
+ * window ranges, the likelihood and the gradient are one launch each whose
+ * work lists span every fit, whatever its K, N and peak counts; the profile
+ * passes of fits too small to fill the GPU alone share launches per group of
+ * equal occupancy, while a fit with enough work for the whole GPU runs its
+ * own profile and likelihood kernels back to back.  A context whose
+ * configuration the batched step does not cover (shared shapes,
+ * angle-dependent width, fitted background, naive sums, importance weights)
+ * takes its own kernels between those launches.  Every context ends exactly
+ * as xrdvi_fit(ctx, iters) would leave it (same kernels per work item, fixed
+ * reduction orders).  The step graphs captured for the array are kept with
+ * ctxs[0] and reused by the next call with the same contexts in the same
+ * order (unless one of them was restored by xrdvi_set_state since); they are
+ * freed with ctxs[0].  Do not call it on a context that another thread is
+ * using.  Runs on ctxs[0]'s stream after waiting for every context's stream;
+ * blocks until done.  last_elbo (NULL or host [n]) receives each fit's last
+ * ELBO estimate.  ENONFINITE if any fit's last ELBO or gradient is not
+ * finite.  No counterpart in the paper, which fits one pattern at a time. */
 xrdvi_status xrdvi_fit_batch(xrdvi_ctx *const *ctxs, int32_t n, int32_t iters, double *last_elbo);
 
 /* One ELBO + gradient evaluation at the current q, without an update.

@@ -5,9 +5,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -68,7 +70,32 @@ namespace xrdvi {
 xrdvi_status report_error(xrdvi_status st, const std::string &msg) { return fail(st, msg); }
 }  // namespace xrdvi
 
+namespace {
+std::atomic<uint64_t> g_next_uid{1};
+
+// The captured graphs of the last xrdvi_fit_batch call made with this context
+// first in its array.  `key` holds each member's (uid, graph generation), in
+// array order: a member that is destroyed, or whose captured arguments
+// change, never matches again, so a stale entry is never launched.
+struct BatchGraphs {
+    std::vector<std::pair<uint64_t, uint64_t>> key;
+    xrdvi::MultiStepPlan *plan = nullptr;   // host-side launch plan (null when every fit runs solo)
+    std::vector<xrdvi_ctx *> solo;
+    cudaStream_t cap = nullptr;             // private capture stream
+    cudaGraphExec_t many = nullptr, one = nullptr;
+    ~BatchGraphs() {
+        if (many) cudaGraphExecDestroy(many);
+        if (one) cudaGraphExecDestroy(one);
+        if (cap) cudaStreamDestroy(cap);
+        xrdvi::multi_plan_destroy(plan);
+    }
+};
+}  // namespace
+
 struct xrdvi_ctx {
+    const uint64_t uid = g_next_uid.fetch_add(1);   // never reused within the process
+    uint64_t graph_gen = 0;                         // bumped whenever captured arguments go stale
+    std::unique_ptr<BatchGraphs> batch;             // see BatchGraphs
     int device = 0;
     cudaStream_t own_stream = nullptr;   // private stream (graph capture; default work stream)
     bool owns_stream = true;             // false when the stream was lent by a server slot
@@ -113,6 +140,8 @@ struct xrdvi_ctx {
         if (graph_many) cudaGraphExecDestroy(graph_many);
         if (graph_one) cudaGraphExecDestroy(graph_one);
         graph_many = graph_one = nullptr;
+        ++graph_gen;
+        batch.reset();
     }
 
     void release(void *q) {
@@ -929,53 +958,58 @@ xrdvi_status xrdvi_fit_batch(xrdvi_ctx *const *ctxs, int32_t n, int32_t iters, d
     }
     for (int i = 0; i < n; ++i) XR_CUDA(cudaStreamSynchronize(ctxs[i]->stream));
     cudaStream_t st = ctxs[0]->stream;
-    std::vector<FitStep> fs;
-    std::vector<xrdvi_ctx *> solo;
-    for (int i = 0; i < n; ++i) {
-        if (ctx_multi_eligible(ctxs[i])) {
-            FitStep f;
-            ctx_fit_step(ctxs[i], &f);
-            fs.push_back(f);
-        } else {
-            solo.push_back(ctxs[i]);
+    std::vector<std::pair<uint64_t, uint64_t>> key(n);
+    for (int i = 0; i < n; ++i) key[i] = {ctxs[i]->uid, ctxs[i]->graph_gen};
+    BatchGraphs *bg = ctxs[0]->batch.get();
+    if (!bg || bg->key != key) {   // new member set, or a member's captured arguments changed
+        ctxs[0]->batch.reset();
+        auto fresh = std::make_unique<BatchGraphs>();
+        std::vector<FitStep> fs;
+        for (int i = 0; i < n; ++i) {
+            if (ctx_multi_eligible(ctxs[i])) {
+                FitStep f;
+                ctx_fit_step(ctxs[i], &f);
+                fs.push_back(f);
+            } else {
+                fresh->solo.push_back(ctxs[i]);
+            }
         }
-    }
-    MultiStepPlan *plan = nullptr;
-    if (!fs.empty()) {
-        int sms = 0;
-        XR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device));
-        plan = multi_plan_create(static_cast<int>(fs.size()));
-        if (!plan || !multi_plan_set(plan, fs.data(), static_cast<int>(fs.size()), sms, st)) {
-            multi_plan_destroy(plan);
-            return fail(XRDVI_ECUDA, "fit_batch: batch set-up failed");
+        if (!fs.empty()) {
+            int sms = 0;
+            XR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device));
+            fresh->plan = multi_plan_create(static_cast<int>(fs.size()));
+            if (!fresh->plan || !multi_plan_set(fresh->plan, fs.data(), static_cast<int>(fs.size()), sms, st))
+                return fail(XRDVI_ECUDA, "fit_batch: batch set-up failed");
         }
+        if (cudaStreamCreateWithFlags(&fresh->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(XRDVI_ECUDA, "fit_batch: cudaStreamCreate failed");
+        fresh->key = key;
+        bg = fresh.get();
+        ctxs[0]->batch = std::move(fresh);
     }
-    // kUnroll steps per captured graph (captured on a private stream), the rest one by one
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t gmany = nullptr, gone = nullptr;
-    xrdvi_status cs = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess
-                          ? XRDVI_OK
-                          : fail(XRDVI_ECUDA, "fit_batch: cudaStreamCreate failed");
-    if (cs == XRDVI_OK && iters >= kUnroll)
-        cs = capture_batch_steps(plan, solo.data(), static_cast<int>(solo.size()), kUnroll, cap, &gmany);
-    if (cs == XRDVI_OK && iters % kUnroll)
-        cs = capture_batch_steps(plan, solo.data(), static_cast<int>(solo.size()), 1, cap, &gone);
+    // kUnroll steps per captured graph (captured once per member set on the
+    // private stream, then reused by later calls), the rest one by one
+    xrdvi_status cs = XRDVI_OK;
+    const int nsolo = static_cast<int>(bg->solo.size());
+    if (iters >= kUnroll && !bg->many)
+        cs = capture_batch_steps(bg->plan, bg->solo.data(), nsolo, kUnroll, bg->cap, &bg->many);
+    if (cs == XRDVI_OK && iters % kUnroll && !bg->one)
+        cs = capture_batch_steps(bg->plan, bg->solo.data(), nsolo, 1, bg->cap, &bg->one);
     if (cs == XRDVI_OK) {
         int left = iters;
         for (; left >= kUnroll && cs == XRDVI_OK; left -= kUnroll)
-            if (cudaGraphLaunch(gmany, st) != cudaSuccess) cs = fail(XRDVI_ECUDA, "fit_batch: graph launch failed");
+            if (cudaGraphLaunch(bg->many, st) != cudaSuccess) cs = fail(XRDVI_ECUDA, "fit_batch: graph launch failed");
         for (; left > 0 && cs == XRDVI_OK; --left)
-            if (cudaGraphLaunch(gone, st) != cudaSuccess) cs = fail(XRDVI_ECUDA, "fit_batch: graph launch failed");
+            if (cudaGraphLaunch(bg->one, st) != cudaSuccess) cs = fail(XRDVI_ECUDA, "fit_batch: graph launch failed");
     }
-    multi_plan_destroy(plan);
     const xrdvi_status ls = cs != XRDVI_OK ? cs : check_launch("fit_batch");
     std::vector<double> last(n, 0.0);
     for (int i = 0; i < n; ++i) XR_CUDA(cudaMemcpyAsync(&last[i], ctxs[i]->elbo, 8, cudaMemcpyDeviceToHost, st));
     XR_CUDA(cudaStreamSynchronize(st));
-    if (gmany) cudaGraphExecDestroy(gmany);
-    if (gone) cudaGraphExecDestroy(gone);
-    if (cap) cudaStreamDestroy(cap);
-    if (ls != XRDVI_OK) return ls;
+    if (ls != XRDVI_OK) {
+        ctxs[0]->batch.reset();   // a failed capture or launch is not reused
+        return ls;
+    }
     xrdvi_status out = XRDVI_OK;
     for (int i = 0; i < n; ++i) {
         ctxs[i]->host_step += iters;

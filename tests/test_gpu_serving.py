@@ -108,6 +108,34 @@ def test_fit_batch_equals_standalone_fits():
         c.close()
 
 
+def test_fit_batch_reuses_graphs_only_for_the_same_members():
+    """xrdvi_fit_batch keeps the graphs it captured for a member set: repeated
+    calls on the same set, a member restored from a saved state (new captured
+    arguments), the set in another order and a subset each end exactly where
+    xrdvi_fit leaves the same contexts."""
+    probs = _problems()
+    cs = [xrdvi.Context.from_instance(p, S=p.S, seed=500 + i) for i, p in enumerate(probs)]
+    rs = [xrdvi.Context.from_instance(p, S=p.S, seed=500 + i) for i, p in enumerate(probs)]
+    h = [c.h for c in cs]
+    xrdvi.xrdvi_fit_batch(h, 20)
+    xrdvi.xrdvi_fit_batch(h, 20)
+    saved = cs[1].state()
+    xrdvi.xrdvi_fit_batch(h, 5)
+    cs[1].set_state(saved)
+    xrdvi.xrdvi_fit_batch(h[::-1], 17)
+    xrdvi.xrdvi_fit_batch(h[:2], 16)
+    last = xrdvi.xrdvi_fit_batch(h, 3)
+    for r, n in zip(rs, (81, 76, 65)):
+        tr = r.fit(n)
+    for c, r, le, n in zip(cs, rs, last, (81, 76, 65)):
+        np.testing.assert_array_equal(c.params()[0], r.params()[0])
+        np.testing.assert_array_equal(c.params()[1], r.params()[1])
+        assert c.info.step == n
+    assert last[2] == tr[-1]
+    for c in cs + rs:
+        c.close()
+
+
 def test_fit_batch_with_large_peak_tables_equals_standalone_fits():
     """Two fits whose peak tables (over 3500 peaks) take the compact layout
     share the multi-fit profile launches, beside a small fit with the wide
