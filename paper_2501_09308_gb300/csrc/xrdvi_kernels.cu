@@ -852,7 +852,24 @@ __device__ __forceinline__ void fwd_near(const ProfArgs &a, const Tab &tab, cons
     f2_t x2[kPairs];
     item_points(a, i0, lane, x2);
     const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
-    for (int m = r.m1; m < r.m2; ++m) {
+    // two peaks per pass, their Lorentzians over one reciprocal as in
+    // fwdL_uniform (d = 1 + t^2 stays small on the mixed range)
+    int m = r.m1;
+    for (; m + 1 < r.m2; m += 2) {
+        f2_t np0, I0, np1, I1;
+        tab.get(m, np0, I0);
+        tab.get(m + 1, np1, I1);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const f2_t t0 = ps(t_mixed(x2[q], np0, nmu2, cp.sl, cp.sr), q);
+            const f2_t t1 = ps(t_mixed(x2[q], np1, nmu2, cp.sl, cp.sr), q);
+            const f2_t u0 = mul2(t0, t0), u1 = mul2(t1, t1);
+            const f2_t d0 = add2(u0, one2), d1 = add2(u1, one2);
+            sl[q] = fma2(fma2(I0, d1, mul2(I1, d0)), rcp2(mul2(d0, d1)), sl[q]);
+            sg[q] = fma2(I1, ex2neg2(u1), fma2(I0, ex2neg2(u0), sg[q]));
+        }
+    }
+    if (m < r.m2) {
         f2_t np, I;
         tab.get(m, np, I);
 #pragma unroll
@@ -946,8 +963,7 @@ template <class Tab, class PC, bool kSec>
 __device__ __forceinline__ float far_node_sum(const Tab &tab, const PC &cp, float x, float cx, int lo0, int hi0,
                                               int lo1, int hi1) {
     const f2_t x2 = bc2(x), one2 = bc2(1.f);
-    f2_t acc2 = 0ull;   // two peaks per packed instruction
-    float acc = 0.f;    // the odd peak of a range
+    float acc = 0.f;
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         const int m0 = side ? lo1 : lo0, m1 = side ? hi1 : hi0;
@@ -959,7 +975,12 @@ __device__ __forceinline__ float far_node_sum(const Tab &tab, const PC &cp, floa
             tab.pair(m, np2, I2);
             f2_t t2 = fma2(sc2, add2(x2, np2), cm2);
             if (kSec) t2 = mul2(t2, bc2(cx));
-            acc2 = fma2(I2, rcp2(fma2(t2, t2, one2)), acc2);
+            // I0/d0 + I1/d1 = (I0 d1 + I1 d0) / (d0 d1): one reciprocal per two
+            // peaks (finite while s |x - p| < 1e9, as in fwdL_uniform)
+            float d0, d1, i0, i1;
+            up2(fma2(t2, t2, one2), d0, d1);
+            up2(I2, i0, i1);
+            acc = fmaf(fmaf(i0, d1, i1 * d0), rcp_approx(d0 * d1), acc);
         }
         if (m < m1) {
             float np, I;
@@ -969,7 +990,7 @@ __device__ __forceinline__ float far_node_sum(const Tab &tab, const PC &cp, floa
             acc = fmaf(I, rcp_approx(fmaf(t, t, 1.f)), acc);
         }
     }
-    return acc + sum2(acc2);
+    return acc;
 }
 
 // One phase's far gradient sums at this lane's node (weight w, w cos(x/2) for
