@@ -384,7 +384,7 @@ void launch_shared_backward(const Problem &P, Workspace &W, cudaStream_t st) {
 }
 
 // Tile width: 128 columns where N is wide (fewer re-reads of A), 64 for
-// narrow outputs.
+// narrow outputs (and, in gemm_plan, for short unsplit reductions).
 static int tile_n(int N) { return N > 64 ? 128 : 64; }
 
 size_t gemm_smem_bytes() { return TileCfg<128>::kSmem; }
@@ -445,6 +445,9 @@ bool gemm_plan(GemmPlan &p, int M, int N, int K, const float *Ahi, const float *
     p.tn = tile_n(N);
     p.nkb = (K + kGKB - 1) / kGKB;
     if (splits < 1) splits = 1;
+    // a short unsplit reduction (the forward's K = phases) is latency-bound per
+    // tile: 64-wide tiles give twice the CTAs
+    if (splits == 1 && p.nkb <= 4) p.tn = 64;
     if (splits > p.nkb) splits = p.nkb > 0 ? p.nkb : 1;
     p.kb_per_split = (p.nkb + splits - 1) / splits;
     p.splits = p.nkb > 0 ? (p.nkb + p.kb_per_split - 1) / p.kb_per_split : 1;
