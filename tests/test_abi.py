@@ -179,3 +179,27 @@ def test_static_entry_rejects_every_size_the_header_formula_puts_above_the_limit
             xrdvi.xrdvi_elbo_grad_static(K, M, dummy, dummy, dummy, N, dummy, dummy, dummy, 0.0, 1e-3, cfg,
                                          dummy, dummy, dummy, dummy, dummy, 0)
         assert e.value.status == 1 and "scratch" in str(e.value), (s_try, e.value)
+
+
+def test_one_past_each_size_limit_is_rejected():
+    """K = 1025 phases, 24001 peaks and S = 65537 draws give EINVAL before any
+    device work (the largest accepted sizes run in test_gpu_limits)."""
+    base = synth.small_problem(K=3, M=5, N=300, S=2, seed=63)
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.Context.from_instance(base, S=65537)
+    assert e.value.status == 1
+    big = synth.make_problem(K=1000, m_lo=24, m_hi=24, x_lo=20.0, x_step=0.05, N=300, n_planted=2, S=2,
+                             iters=1, seed=63)
+    assert int(big.offsets[-1]) == 24000
+    over = synth.Instance(**{**big.__dict__, "offsets": np.concatenate([big.offsets[:-1], [24001]]).astype(np.int32),
+                             "pos": np.concatenate([big.pos, big.pos[-1:]]),
+                             "inten": np.concatenate([big.inten, big.inten[-1:]])})
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.Context.from_instance(over, S=2)
+    assert e.value.status == 1 and "24000" in str(e.value)
+    n = 1025
+    many = synth.Instance(**{**base.__dict__, "offsets": np.arange(n + 1, dtype=np.int32),
+                             "pos": np.full(n, 30.0, np.float32), "inten": np.full(n, 0.5, np.float32)})
+    with pytest.raises(xrdvi.XrdviError) as e:
+        xrdvi.Context.from_instance(many, S=2)
+    assert e.value.status == 1 and "1024" in str(e.value)

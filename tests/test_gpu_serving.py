@@ -132,6 +132,18 @@ def test_fit_batch_reuses_graphs_only_for_the_same_members():
         np.testing.assert_array_equal(c.params()[1], r.params()[1])
         assert c.info.step == n
     assert last[2] == tr[-1]
+    # a member closed and a new context in its place (possibly at the same
+    # address): the kept graphs must not be replayed
+    cs[2].close()
+    rs[2].close()
+    cs[2] = xrdvi.Context.from_instance(probs[2], S=probs[2].S, seed=600)
+    rs[2] = xrdvi.Context.from_instance(probs[2], S=probs[2].S, seed=600)
+    xrdvi.xrdvi_fit_batch([c.h for c in cs], 16)
+    for r in rs:
+        r.fit(16)
+    for c, r in zip(cs, rs):
+        np.testing.assert_array_equal(c.params()[0], r.params()[0])
+        np.testing.assert_array_equal(c.params()[1], r.params()[1])
     for c in cs + rs:
         c.close()
 
