@@ -298,6 +298,33 @@ struct ShapeArgs {
 
 constexpr int kShapeChunk = 512;   // peaks staged in shared memory at a time
 
+// The sums over one side's run of peaks [m0, m1) of the staged chunk at scale
+// s (t = s d cos(x/2)): sum I L and sum I G (added to lS, gS in peak order),
+// and the side's sum I L^2 t, I L^2 t^2, I G t, I G t^2.
+__device__ __forceinline__ void shape_side(const float2 *sp, int m0, int m1, float x, float mu, float s, float cx,
+                                           float &lS, float &gS, float &l1, float &l2, float &g1, float &g2) {
+    for (int m = m0; m < m1; ++m) {
+        const float2 pk = sp[m];
+        const float d = (x - pk.x) - mu;
+        const float t = s * d * cx, u = t * t;
+        float L;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(L) : "f"(1.f + u));
+        const float I = pk.y;
+        const float IL = I * L, IL2 = IL * L;
+        lS += IL;
+        l1 = fmaf(IL2, t, l1);
+        l2 = fmaf(IL2, u, l2);
+        if (u < kGaussU) {
+            float G;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(-u));
+            const float IG = I * G;
+            gS += IG;
+            g1 = fmaf(IG, t, g1);
+            g2 = fmaf(IG, u, g2);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
     __shared__ float2 sp[kShapeChunk];   // (p, I) of the phase's peaks
     // phase of this block row: the heaviest phases start first (blocks go out in
@@ -305,9 +332,12 @@ __global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
     const int k = a.order[blockIdx.y], i = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim.x * gridDim.x == Npad
     const PhaseConst c = a.cst[k];
     const float r = a.theta[k * 5 + 3];
-    float acc[kGradSums];
-#pragma unroll
-    for (int j = 0; j < kGradSums; ++j) acc[j] = 0.f;
+    // A phase's peaks are sorted by position, so the peaks with d = x - p - mu
+    // >= 0 (scale s_r, t >= 0) are a leading run and the rest (s_l, t < 0) the
+    // trailing run: no per-peak side choice, and on each side |t| = +-t, so the
+    // four sums in t, |t|, t^2, t|t| of each component come from two per side.
+    float lS = 0.f, gS = 0.f;
+    float l1[2] = {0.f, 0.f}, l2[2] = {0.f, 0.f}, g1[2] = {0.f, 0.f}, g2[2] = {0.f, 0.f};
     const bool live = i < a.N;
     const float x = live ? a.x[i] : 0.f;
     const float cx = (a.csec && live) ? a.csec[i] : 1.f;   // t = s cos(x/2) d; mu sums take cos(x/2) once more
@@ -317,32 +347,29 @@ __global__ void __launch_bounds__(256) k_shapes(ShapeArgs a) {
         for (int j = threadIdx.x; j < mn; j += blockDim.x) sp[j] = make_float2(a.pos[m0 + j], a.inten[m0 + j]);
         __syncthreads();
         if (!live) continue;
-        for (int m = 0; m < mn; ++m) {
-            const float2 pk = sp[m];
-            const float d = (x - pk.x) - c.mu;
-            const float t = (d >= 0.f ? c.sr : c.sl) * d * cx;
-            const float at = fabsf(t), u = t * t;
-            float L;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(L) : "f"(1.f + u));
-            const float I = pk.y;
-            const float IL = I * L, IL2 = IL * L;
-            acc[1] += IL;
-            acc[3] = fmaf(IL2, t, acc[3]);
-            acc[5] = fmaf(IL2, at, acc[5]);
-            acc[7] = fmaf(IL2, u, acc[7]);
-            acc[9] = fmaf(IL2 * t, at, acc[9]);
-            if (u < kGaussU) {
-                float G;
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(-u));
-                const float IG = I * G;
-                acc[0] += IG;
-                acc[2] = fmaf(IG, t, acc[2]);
-                acc[4] = fmaf(IG, at, acc[4]);
-                acc[6] = fmaf(IG, u, acc[6]);
-                acc[8] = fmaf(IG * t, at, acc[8]);
-            }
+        int lo = 0, hi = mn;   // first staged peak with d < 0 (d is non-increasing along the run)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((x - sp[mid].x) - c.mu >= 0.f)
+                lo = mid + 1;
+            else
+                hi = mid;
         }
+        shape_side(sp, 0, lo, x, c.mu, c.sr, cx, lS, gS, l1[0], l2[0], g1[0], g2[0]);
+        shape_side(sp, lo, mn, x, c.mu, c.sl, cx, lS, gS, l1[1], l2[1], g1[1], g2[1]);
     }
+    // the ten sums in the backward's order (t >= 0 on side 0, t < 0 on side 1)
+    float acc[kGradSums];
+    acc[0] = gS;
+    acc[1] = lS;
+    acc[2] = g1[0] + g1[1];
+    acc[3] = l1[0] + l1[1];
+    acc[4] = g1[0] - g1[1];
+    acc[5] = l1[0] - l1[1];
+    acc[6] = g2[0] + g2[1];
+    acc[7] = l2[0] + l2[1];
+    acc[8] = g2[0] - g2[1];
+    acc[9] = l2[0] - l2[1];
     if (a.csec && live) {
         const float cx = a.csec[i];
         acc[2] *= cx; acc[3] *= cx; acc[4] *= cx; acc[5] *= cx;
