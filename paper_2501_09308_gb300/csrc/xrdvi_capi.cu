@@ -400,9 +400,11 @@ xrdvi_status capture(xrdvi_ctx *c, int steps, cudaGraphExec_t *out) {
     for (int i = 0; i < steps; ++i) enqueue_step(c, c->own_stream);
     cudaError_t e = cudaStreamEndCapture(c->own_stream, &g);
     if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    *out = x;   // set only on success
     return XRDVI_OK;
 }
 
@@ -519,9 +521,11 @@ xrdvi_status capture_batch_steps(const MultiStepPlan *plan, xrdvi_ctx *const *so
     }
     cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XRDVI_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    *out = x;   // set only on success: callers destroy what they hold
     return XRDVI_OK;
 }
 
