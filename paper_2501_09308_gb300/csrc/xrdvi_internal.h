@@ -269,8 +269,11 @@ xrdvi_status batch_set_tail(xrdvi_ctx *c, int tail_start);
 // Copies the nsub tail sums (FP64) to host memory.
 xrdvi_status batch_tail_sums(xrdvi_ctx *c, double *host);
 
-// Continuous batching: one SVI step of several fits in the same launches
-// (six kernels for the whole batch).  FitStep names a fit's device state;
+// Continuous batching: one SVI step of several fits in shared launches
+// (sampling, ranges and the gradient one launch each for the whole batch; the
+// profile and likelihood launches per group of small fits of equal occupancy,
+// a fit's own kernels for a fit that fills the GPU alone).  FitStep names a
+// fit's device state;
 // only fits that run the plain far-field step qualify (multi_fit_eligible):
 // no shared shapes, angle-dependent width, fitted background, naive sums,
 // importance weights or sub-model batches.
@@ -284,7 +287,7 @@ struct FitStep {
     AdamConst ac{};
 };
 struct MultiStepPlan;
-MultiStepPlan *multi_plan_create(int cap);   // device argument storage for cap <= kMaxBatch fits
+MultiStepPlan *multi_plan_create(int cap);   // launch plan for up to cap <= kMaxBatch fits (host memory)
 void multi_plan_destroy(MultiStepPlan *p);
 bool multi_fit_eligible(const Problem &P, const Workspace &W, bool naive, bool iw);
 // Builds the batch's kernel arguments and block maps (host only: the

@@ -6,12 +6,14 @@
 // next to the resident fits (admission by HBM footprint) and a slot is free,
 // and creates its context (validation, tables, upload) from one
 // stream-ordered memory pool.  An engine thread advances every resident fit
-// together: each SVI step of the whole batch is six kernel launches
-// (xrdvi::multi_plan_launch_step) whose work lists span all resident fits,
-// whatever their K, N and peak counts; fits that run a variant outside the
-// batched step (shared shapes, angle-dependent width, fitted background,
-// naive sums, importance weights) take their own kernels between those
-// launches.  Fits join and leave the batch between slices of a few steps, so
+// together by one batched step (xrdvi::multi_plan_launch_step): sampling,
+// window ranges and the gradient are single launches whose work lists span
+// all resident fits, whatever their K, N and peak counts; the profile and
+// likelihood launches are shared by the fits too small to fill the GPU alone,
+// while a fit with enough work of its own runs its own kernels inside the
+// step.  Fits that run a variant outside the batched step (shared shapes,
+// angle-dependent width, fitted background, naive sums, importance weights)
+// take their own kernels between those launches.  Fits join and leave the batch between slices of a few steps, so
 // requests that arrive while others run start within a slice.  A reaper
 // thread draws the posterior of each finished fit, copies its results and
 // frees it.  All device work runs on one stream in submission order; a fit's
