@@ -98,6 +98,10 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="resident fits of the serving leg")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving leg (0: skip); the first is the K=50 fit")
+    ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
+                    help="Poisson arrival rate of the serving leg, requests/s (the workload's is 200)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving leg (no overlap sub-leg) and print its JSON")
     return ap.parse_args()
 
 
@@ -271,12 +275,14 @@ def run_reference(args, world, rank):
 
 SERVE_SLOTS = 4             # fits the server keeps resident (one batch); --serve-slots
 SERVE_OVERLAP_FITS = 8      # requests timed alone and served together (device-side overlap)
+SERVE_RATE = 200.0          # Poisson arrival rate of the serving workload, requests/s; --serve-rate
 
 
-def serving_leg(n_requests, plain_ms, slots=SERVE_SLOTS):
+def serving_leg(n_requests, plain_ms, slots=SERVE_SLOTS, rate=None, overlap=True):
     """Continuous batching: the K=50 fit followed by serving-workload requests
     (K ~ U{10..200}, N ~ U{2000..9000}, 5-100 peaks per phase, S=256, 1000
-    steps) arriving as a Poisson stream at 200 requests/s, on a server with
+    steps) arriving as a Poisson stream at `rate` requests/s (the workload's
+    200 by default; a lower rate shows the latency without the queue), on a server with
     `slots` resident fits (4 by default: each of these fits fills the GPU by
     itself, so with the same throughput fewer resident fits finish the early
     requests sooner) and a 32 GB device-memory budget; every SVI step of the
@@ -289,28 +295,32 @@ def serving_leg(n_requests, plain_ms, slots=SERVE_SLOTS):
     together (all submitted at once), wall-clock time of each."""
     import numpy as np
     from paper_2501_09308_gb300 import serving, synth, xrdvi
+    rate = SERVE_RATE if rate is None else float(rate)
     reqs = [synth.config(1)] + [synth.config(4, instance=i) for i in range(1, n_requests)]
-    arrivals = synth.arrival_times(n_requests, 200.0, seed=synth.SEED_BASE + 4000)
+    arrivals = synth.arrival_times(n_requests, rate, seed=synth.SEED_BASE + 4000)
     srv = serving.Server(hbm_budget=32 << 30, max_slots=slots)
     res = serving.replay_arrivals(srv, reqs, arrivals, S_post=S_POST, post_seed=77, top_m=TOP_M)
     stats = srv.stats()
     srv.close()
     evals = [r_.evals_per_iter * r_.iters for r_ in reqs]
     out = serving.summarize(res, evals)
-    single_rate = reqs[0].evals_per_iter * reqs[0].iters / (plain_ms / 1e3)
+    single_rate = reqs[0].evals_per_iter * reqs[0].iters / (plain_ms / 1e3) if plain_ms else None
     out.update({
-        "slots": slots, "hbm_budget_bytes": 32 << 30, "arrival_rate_per_s": 200.0,
+        "slots": slots, "hbm_budget_bytes": 32 << 30, "arrival_rate_per_s": rate,
         "peak_bytes_in_use": stats["peak_bytes"],
         "single_fit_evals_per_s": single_rate,
-        "aggregate_over_single_fit": out["evals_per_s"] / single_rate,
+        "aggregate_over_single_fit": out["evals_per_s"] / single_rate if single_rate else None,
         "k50_served_time_to_posterior_s": res[0]["latency"],
-        "k50_plain_time_to_posterior_s": plain_ms / 1e3,
+        "k50_plain_time_to_posterior_s": plain_ms / 1e3 if plain_ms else None,
         "k50_top_combination": [int(k) for k in np.flatnonzero(res[0]["combos"][0])],
         "requests_K": [int(r_.K) for r_ in reqs], "requests_N": [int(r_.N) for r_ in reqs],
         "latency_s": [float(r["latency"]) for r in res],
         "note": f"the first {n_requests} requests of the 4096-request stream (at ~8e12 evaluations per fit the "
-                "full stream is hours of work for one GPU; latency is queueing-dominated)",
+                "full stream is hours of work for one GPU; latency is queueing-dominated)" if rate >= 10 else
+                f"the first {n_requests} requests of the stream at {rate} requests/s, below the server's throughput",
     })
+    if not overlap:
+        return out
     sub = reqs[1:1 + SERVE_OVERLAP_FITS]
     t0 = time.perf_counter()
     for r_ in sub:
@@ -510,6 +520,10 @@ def main():
     if args.batch_only > 0:
         print(json.dumps({"batch": batch_leg(args.batch_only, args.batch_iters, args.batch_samples)}), flush=True)
         return
+    if args.serve_only:
+        print(json.dumps({"serving": serving_leg(args.serve_requests, None, args.serve_slots, args.serve_rate,
+                                                 overlap=False)}), flush=True)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -586,7 +600,7 @@ def main():
 
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
-        serve = serving_leg(args.serve_requests, ms_step, args.serve_slots)
+        serve = serving_leg(args.serve_requests, ms_step, args.serve_slots, args.serve_rate)
     enum = enumeration_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
     variants = variants_leg(measured_peaks()[0]) if rank == 0 and world == 1 and not args.no_enumeration else None
 
