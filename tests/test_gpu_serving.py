@@ -172,6 +172,29 @@ def test_fit_batch_with_large_peak_tables_equals_standalone_fits():
         c.close()
 
 
+def test_fit_batch_with_fits_that_fill_the_gpu_equals_standalone_fits():
+    """Two full-size fits (the K=50 workload and a K=77 serving request, S=256:
+    enough work items to fill the GPU alone, so each runs its own profile and
+    likelihood kernels inside the batched step) beside a small fit that takes
+    the shared multi-fit launches: each ends bit-identical to its standalone
+    fit, across two calls."""
+    probs = [synth.config(1), synth.config(4, instance=1), synth.small_problem(K=5, M=9, N=900, S=8, seed=81)]
+    ref = []
+    for i, p in enumerate(probs):
+        c = xrdvi.Context.from_instance(p, S=p.S, seed=700 + i)
+        tr = c.fit(24)
+        ref.append((c.params(), tr[-1]))
+        c.close()
+    cs = [xrdvi.Context.from_instance(p, S=p.S, seed=700 + i) for i, p in enumerate(probs)]
+    xrdvi.xrdvi_fit_batch([c.h for c in cs], 16)
+    last = xrdvi.xrdvi_fit_batch([c.h for c in cs], 8)
+    for c, (params, e), le in zip(cs, ref, last):
+        np.testing.assert_array_equal(c.params()[0], params[0])
+        np.testing.assert_array_equal(c.params()[1], params[1])
+        assert le == e
+        c.close()
+
+
 def test_batched_fits_overlap_on_the_device():
     """Eight small fits served together finish in much less time than the
     same fits run one after another: their steps share kernel launches
