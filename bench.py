@@ -105,6 +105,16 @@ def parse():
     return ap.parse_args()
 
 
+def guarded(name, fn):
+    """fn() or, if it raises, {"error": ...} (the message also on stderr)."""
+    try:
+        return fn()
+    except Exception as e:   # noqa: BLE001 - any failure of an extra leg is reported, not raised
+        msg = f"{type(e).__name__}: {e}"[:300]
+        print(f"bench: {name} leg failed: {msg}", file=sys.stderr, flush=True)
+        return {"error": msg}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -598,15 +608,19 @@ def main():
     h2d = (K + 1) * 4 + 2 * M * 4 + 3 * N * 4
     d2h = iters * 8 + 8 + K * 8 + TOP_M * ((K + 63) // 64) * 8 + TOP_M * 8
 
+    # the legs after the timed fits are reported beside the metric; one that fails
+    # reports its error instead of taking the metric's line with it
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
-        serve = serving_leg(args.serve_requests, ms_step, args.serve_slots, args.serve_rate)
-    enum = enumeration_leg() if rank == 0 and world == 1 and not args.no_enumeration else None
-    variants = variants_leg(measured_peaks()[0]) if rank == 0 and world == 1 and not args.no_enumeration else None
+        serve = guarded("serving", lambda: serving_leg(args.serve_requests, ms_step, args.serve_slots,
+                                                       args.serve_rate))
+    enum = guarded("enumeration", enumeration_leg) if rank == 0 and world == 1 and not args.no_enumeration else None
+    variants = (guarded("variants", lambda: variants_leg(measured_peaks()[0]))
+                if rank == 0 and world == 1 and not args.no_enumeration else None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(inst, CPU_SAMPLE_STEPS)
+        cpu = guarded("cpu_baseline", lambda: cpu_baseline(inst, CPU_SAMPLE_STEPS))
 
     if world > 1:
         import torch.distributed as dist
