@@ -706,11 +706,22 @@ __device__ __forceinline__ bool near_work(const Ranges &r) {
 
 // t = s(d) d for a packed pair on the mixed range: the side's scale is
 // selected per point (exact for any asymmetry).
-__device__ __forceinline__ f2_t t_mixed(f2_t x2, f2_t np, f2_t nmu2, float sl, float sr) {
+// The side's scale s_l + m (s_r - s_l) with the mask m = sat(d 2^100): 1 for
+// d >= 2^-100, 0 for d <= 0 (the saturating multiply runs on the FMA pipe;
+// a comparison and a select per point would take the busier ALU pipe).  For
+// 0 < d < 2^-100, where m is fractional, |t| < 1e-27: L = G = 1 and every
+// t-weighted term vanishes in FP32 whichever scale is used.
+__device__ __forceinline__ float mul_sat(float a, float b) {
+    float r;
+    asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t t_mixed(f2_t x2, f2_t np, f2_t nmu2, f2_t sl2, f2_t ds2) {
     const f2_t d2 = add2(add2(x2, np), nmu2);
     float d0, d1;
     up2(d2, d0, d1);
-    return mul2(d2, pk2(d0 >= 0.f ? sr : sl, d1 >= 0.f ? sr : sl));
+    const f2_t m2 = pk2(mul_sat(d0, 0x1p100f), mul_sat(d1, 0x1p100f));
+    return mul2(d2, fma2(m2, ds2, sl2));
 }
 
 __device__ __forceinline__ void item_points(const ProfArgs &a, int i0, int lane, f2_t (&x2)[kPairs]) {
@@ -851,7 +862,7 @@ __device__ __forceinline__ void fwd_near(const ProfArgs &a, const Tab &tab, cons
                                          int i0, int lane, const Sc &ps, f2_t (&sl)[kPairs], f2_t (&sg)[kPairs]) {
     f2_t x2[kPairs];
     item_points(a, i0, lane, x2);
-    const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
+    const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f), sl2 = bc2(cp.sl), ds2 = bc2(cp.sr - cp.sl);
     // two peaks per pass, their Lorentzians over one reciprocal as in
     // fwdL_uniform (d = 1 + t^2 stays small on the mixed range)
     int m = r.m1;
@@ -861,8 +872,8 @@ __device__ __forceinline__ void fwd_near(const ProfArgs &a, const Tab &tab, cons
         tab.get(m + 1, np1, I1);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t0 = ps(t_mixed(x2[q], np0, nmu2, cp.sl, cp.sr), q);
-            const f2_t t1 = ps(t_mixed(x2[q], np1, nmu2, cp.sl, cp.sr), q);
+            const f2_t t0 = ps(t_mixed(x2[q], np0, nmu2, sl2, ds2), q);
+            const f2_t t1 = ps(t_mixed(x2[q], np1, nmu2, sl2, ds2), q);
             const f2_t u0 = mul2(t0, t0), u1 = mul2(t1, t1);
             const f2_t d0 = add2(u0, one2), d1 = add2(u1, one2);
             sl[q] = fma2(fma2(I0, d1, mul2(I1, d0)), rcp2(mul2(d0, d1)), sl[q]);
@@ -874,7 +885,7 @@ __device__ __forceinline__ void fwd_near(const ProfArgs &a, const Tab &tab, cons
         tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
+            const f2_t t = ps(t_mixed(x2[q], np, nmu2, sl2, ds2), q);
             const f2_t u = mul2(t, t);
             sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
             sg[q] = fma2(I, ex2neg2(u), sg[q]);
@@ -1131,13 +1142,13 @@ __device__ __forceinline__ void fwd_direct_items(const ProfArgs &a, const PeakTa
                 }
             }
             if (near_work(r)) {   // warp-uniform
-                const f2_t nmu2 = bc2(-cp.mu);
+                const f2_t nmu2 = bc2(-cp.mu), sl2 = bc2(cp.sl), ds2 = bc2(cp.sr - cp.sl);
                 for (int m = r.m1; m < r.m2; ++m) {
                     f2_t np, I;
                     tab.get(m, np, I);
 #pragma unroll
                     for (int q = 0; q < kPairs; ++q) {
-                        const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
+                        const f2_t t = ps(t_mixed(x2[q], np, nmu2, sl2, ds2), q);
                         const f2_t u = mul2(t, t);
                         sl[q] = fma2(I, rcp2(add2(u, one2)), sl[q]);
                         sg[q] = fma2(I, ex2neg2(u), sg[q]);
@@ -1510,13 +1521,13 @@ template <class Tab, class Sc, class PC>
 __device__ __forceinline__ void bwd_near_sums(const Tab &tab, const Ranges &r, const PC &cp,
                                               const f2_t (&x2)[kPairs], const f2_t (&g2)[kPairs], const Sc &ps,
                                               f2_t (&acc)[kGradSums]) {
-    const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f);
+    const f2_t nmu2 = bc2(-cp.mu), one2 = bc2(1.f), sl2 = bc2(cp.sl), ds2 = bc2(cp.sr - cp.sl);
     for (int m = r.m1; m < r.m2; ++m) {
         f2_t np, I;
         tab.get(m, np, I);
 #pragma unroll
         for (int q = 0; q < kPairs; ++q) {
-            const f2_t t = ps(t_mixed(x2[q], np, nmu2, cp.sl, cp.sr), q);
+            const f2_t t = ps(t_mixed(x2[q], np, nmu2, sl2, ds2), q);
             const f2_t tA = ps(t, q);   // t for the mu sums (times cos(x/2) once more)
             const f2_t u = mul2(t, t);
             const f2_t L = rcp2(add2(u, one2));
